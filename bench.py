@@ -1,0 +1,363 @@
+"""Batched negacyclic NTT throughput on one GB300 (or N, one process each).
+
+Workload (one step): 16 polynomials of N = 2^16 coefficients, L = 32 RNS
+limbs modulo 30-bit primes q = 1 mod 2^17 (u32 words): forward NTT of all 16,
+pointwise product of the 8 pairs, inverse NTT of the 8 products -- 768
+transforms per step.  Fused butterfly path, Shoup reduction, bit-reversed
+evaluation order.  Inputs are seeded synthetic residues (no dataset exists
+for this method); four copies of the batch rotate so every step reads a
+working set (4 x 128 MiB) larger than L2.
+
+Output: one JSON line (rank 0).  `value` is NTTs per second for the whole
+job; `roofline` describes the forward transform (the dominant call);
+`cpu_baseline` times the CPU oracle on a bounded sample; `e2e` is the same
+metric through ntt_polymul_host with pinned host buffers.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import ntt_synth  # noqa: E402
+
+METRIC = "batched NTT throughput (NTTs/s, GB/s vs HBM peak) at N=2^16; ragged vs plain"
+N, L, POLYS, BITS, M = 1 << 16, 32, 16, 30, 17
+PAIRS = POLYS // 2
+WORD = 4
+NTT_PER_STEP = (POLYS + PAIRS) * L
+ROTATE = 4
+WORKLOAD = ("N=2^16, L=32 primes q<2^30 (q=1 mod 2^17), u32, 16 polys: forward NTT x16, "
+            "pointwise x8, inverse NTT x8 per step")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_from_profiles(digest):
+    """Per-launch DRAM bytes of the forward transform from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "fused_forward_n65536_L32_u32.md")
+    try:
+        txt = open(p).read()
+    except OSError:
+        return None
+    m1 = re.search(r"forward_dram_bytes_per_call:\s*([0-9]+)", txt)
+    m2 = re.search(r"source_digest:\s*([0-9a-f]+)", txt)
+    if not m1 or not m2 or m2.group(1) != digest:
+        return None
+    return int(m1.group(1))
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, _, parts in rows:
+            for i, n in enumerate(names):
+                if parts[5 + i].lower() == "active":
+                    reasons.add(n)
+        load = [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ----------------------------------------------------------------- oracle arm
+def oracle_sample(qs, seconds=12.0, max_reps=50):
+    """The CPU oracle (O(N log N) path, OpenMP over transforms) running the
+    step's pipeline on one pair of polynomials x all limbs, repeated for
+    about `seconds`.  Returns (NTTs/s, threads, description)."""
+    import oracle
+    psis = [oracle.psi(q, N) for q in qs]
+    host = ntt_synth.rns_batch(1005, qs, N, 2)
+    done = 0
+    t0 = time.perf_counter()
+    reps = 0
+    while reps < max_reps:
+        A = oracle.ntt_batch(host, qs, psis)
+        P = oracle.pointwise_batch(A[:1], A[1:], qs)
+        oracle.ntt_batch(P, qs, psis, inverse=True)
+        done += 3 * L
+        reps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    desc = ("oracle O(N log N) path: forward of 2 polys, pointwise, inverse of 1 product, "
+            "x %d limbs, %d repetitions (%d NTTs in %.1f s)" % (L, reps, done, dt))
+    return done / dt, oracle.num_threads(), desc
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step is the step's pipeline on
+    one pair of polynomials x all 32 limbs (96 NTTs).  When K such steps
+    would take more than about a minute, only the first ones that fit are
+    timed (reported as timed_steps)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    qs = oracle.find_primes(BITS, M, L)
+    t0 = time.perf_counter()
+    for _ in range(args.warmup):
+        oracle_sample(qs, seconds=0.0, max_reps=1)
+    est = (time.perf_counter() - t0) / max(1, args.warmup)
+    timed = max(1, min(args.steps, int(60.0 / max(est, 1e-3))))
+    t0 = time.perf_counter()
+    v, cores, desc = oracle_sample(qs, seconds=1e9, max_reps=timed)
+    total = time.perf_counter() - t0
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "NTT/s",
+        "n_gpus": args.gpus, "steps": args.steps, "timed_steps": timed, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * total / timed, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64 (128-bit % per product)",
+        "data": "synthetic (seeded SplitMix64 residues)",
+        "config": {"workload": WORKLOAD, "N": N, "L": L, "polys": POLYS, "word": "u32",
+                   "sample": "each step: 1 pair x 32 limbs (96 NTTs)"},
+        "cpu_baseline": {"value": v, "unit": "NTT/s", "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": v, "unit": "NTT/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="nttgb", choices=["nttgb", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    import paper_2405_11353_gb300 as nt
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0 or not os.path.exists(nt.LIB_PATH):
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    nt.lib()
+    from paper_2405_11353_gb300 import build as nb
+    digest = nb._digest()
+
+    qs = nt.ntt_find_primes(BITS, M, L)
+    flags = nt.NTT_ORDER_BITREV | nt.NTT_RED_SHOUP
+    plan = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, flags)
+    host = ntt_synth.rns_batch(1005 + 7919 * rank, qs, N, POLYS, dtype=np.uint32)
+    words = POLYS * L * N
+    half = PAIRS * L * N
+    pinned = torch.from_numpy(host.view(np.int32).reshape(-1).copy()).pin_memory()
+    bufs = []
+    for _ in range(ROTATE):
+        b = torch.empty(words, dtype=torch.int32, device=dev)
+        b.copy_(pinned, non_blocking=False)
+        bufs.append(b)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+
+    def step(b):
+        nt.ntt_forward(plan, b, POLYS, sh)
+        nt.ntt_pointwise_mul(plan, b, b, b[half:], PAIRS, sh)
+        nt.ntt_inverse(plan, b, PAIRS, sh)
+
+    def launches_per_step():
+        nt.ntt_forward(plan, bufs[0], POLYS, sh)
+        n = nt.ntt_plan_last_launches(plan)
+        nt.ntt_pointwise_mul(plan, bufs[0], bufs[0], bufs[0][half:], PAIRS, sh)
+        n += nt.ntt_plan_last_launches(plan)
+        nt.ntt_inverse(plan, bufs[0], PAIRS, sh)
+        n += nt.ntt_plan_last_launches(plan)
+        return n
+
+    lps = launches_per_step()
+    for i in range(args.warmup):
+        step(bufs[i % ROTATE])
+    torch.cuda.synchronize()
+
+    # ---------------- timed region: K steps, events per call for the roofline
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    sampler = ClockSampler(dev.index) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(K):
+        b = bufs[i % ROTATE]
+        e = ev[i]
+        e[0].record(stream)
+        nt.ntt_forward(plan, b, POLYS, sh)
+        e[1].record(stream)
+        nt.ntt_pointwise_mul(plan, b, b, b[half:], PAIRS, sh)
+        e[2].record(stream)
+        nt.ntt_inverse(plan, b, PAIRS, sh)
+        e[3].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    elapsed_ms = t_start.elapsed_time(t_end)
+    fwd_ms = statistics.mean(ev[i][0].elapsed_time(ev[i][1]) for i in range(K))
+    pw_ms = statistics.mean(ev[i][1].elapsed_time(ev[i][2]) for i in range(K))
+    inv_ms = statistics.mean(ev[i][2].elapsed_time(ev[i][3]) for i in range(K))
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / K
+    value = NTT_PER_STEP * world * K / (elapsed_ms / 1000.0)
+
+    # ---------------- end to end through the host-buffer entry point
+    h_in = pinned
+    h_out = torch.empty(half, dtype=torch.int32).pin_memory()
+    work = bufs[0]
+    Ke = max(3, min(K, 200))
+    for _ in range(3):
+        nt.ntt_polymul_host(plan, h_out, h_in, work, PAIRS, sh)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(Ke):
+        nt.ntt_polymul_host(plan, h_out, h_in, work, PAIRS, sh)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = NTT_PER_STEP * world * Ke / (e2e_ms / 1000.0)
+
+    # ---------------- roofline of the forward transform (dominant call)
+    peak, peak_kind = peaks()
+    n_fwd = POLYS * L
+    fwd_bytes = 2 * N * WORD * n_fwd + L * N * 2 * WORD      # data r+w, twiddle pairs once per prime
+    achieved = fwd_bytes / (fwd_ms / 1000.0) / 1e9
+    roofline = {
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "frac": achieved / peak, "traffic": traffic_from_profiles(digest),
+        "kernel": "ntt_forward (column pass + 256-point chunk pass), %d transforms" % n_fwd,
+        "algorithmic_bytes_per_call": fwd_bytes, "avg_ms": fwd_ms,
+        "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
+        else "fallback 6.8 TB/s",
+    }
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, desc = oracle_sample(qs)
+        cpu = {"value": v, "unit": "NTT/s", "cores": cores, "kind": "oracle", "sample": desc}
+
+    nt.ntt_plan_destroy(plan)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "NTT/s", "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic (seeded SplitMix64 residues, uniform in [0,q))",
+            "config": {"workload": WORKLOAD, "N": N, "L": L, "polys": POLYS, "word": "u32",
+                       "variant": "fused", "reduction": "shoup", "order": "bitrev",
+                       "l2": "4 rotating input copies (512 MiB) > 129 MB L2",
+                       "parallelism": "replicas x%d" % world},
+            "per_call_ms": {"forward_16polys": fwd_ms, "pointwise_8pairs": pw_ms,
+                            "inverse_8polys": inv_ms},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "NTT/s",
+                    "h2d_bytes_per_step": POLYS * L * N * WORD,
+                    "d2h_bytes_per_step": PAIRS * L * N * WORD, "steps": Ke},
+            "gpu_launches": lps * K,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,214 @@
+/*
+ * ntt.h -- C ABI of libnttgb, a batched negacyclic number theoretic
+ * transform library for NVIDIA GB300 (sm_103a).
+ *
+ * What is computed.  For a prime q, N = 2^n and psi a primitive 2N-th root of
+ * unity mod q, the forward transform of one limb a[0..N) is
+ *
+ *     X[k] = sum_{n<N} a[n] * psi^((2k+1) n)  mod q,      k = 0..N-1,
+ *
+ * the cyclic transform of Eq. 3 (Sec. II, "Twiddle Factors") with the input
+ * twisted by psi^n so that it evaluates a(x) at the N roots of x^N + 1.  The
+ * inverse maps X back to a: a[n] = N^-1 psi^-n sum_k X[k] psi^(-2nk).  The
+ * pointwise product c[k] = a[k] b[k] mod q turns a negacyclic polynomial
+ * product into O(N) work (Sec. I).  psi defaults to g^((q-1)/(2N)) with g the
+ * smallest generator of Z_q^*.
+ *
+ * Data layout.  A batch is `batch` polynomials of L RNS limbs each, stored
+ * [batch][L][N] contiguously; limb l is reduced modulo q[l].  Words are
+ * uint32_t (q < 2^30) or, with NTT_WORD64, uint64_t (q < 2^60).  Inputs must
+ * lie in [0, q); outputs are fully reduced to [0, q).
+ *
+ * Ownership.  The caller owns every data buffer.  A plan owns its twiddle
+ * tables, its scratch buffer (grown on demand, see ntt_plan_reserve) and a
+ * device status word.  Device pointers must be 16-byte aligned.
+ *
+ * Streams and errors.  Calls that take a stream only enqueue work on it and
+ * return at once; their return value covers argument validation and launch
+ * errors.  Errors found on the device (NTT_CHECK input violations, the
+ * ragged kernel's wait limit) are recorded in the plan's status word and
+ * returned by ntt_get_device_status.  No kernel ever traps.  A plan may be
+ * used from one host thread at a time.
+ */
+#ifndef NTTGB_NTT_H
+#define NTTGB_NTT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ntt_plan_s *ntt_plan_t;
+typedef struct ntt_ragged_s *ntt_ragged_t;
+/* A cudaStream_t passed as an opaque pointer; NULL is the legacy stream. */
+typedef void *ntt_stream_t;
+
+typedef enum {
+    NTT_OK = 0,
+    NTT_ERR_INVALID_ARG = 1,        /* null pointer, L = 0, batch = 0, bad enum */
+    NTT_ERR_N_NOT_POW2 = 2,         /* N is not a power of two */
+    NTT_ERR_N_RANGE = 3,            /* N outside 2^1 .. 2^17 */
+    NTT_ERR_Q_NOT_PRIME = 4,        /* some q[l] is composite */
+    NTT_ERR_Q_NOT_NTT_FRIENDLY = 5, /* some q[l] != 1 (mod 2N) */
+    NTT_ERR_Q_WIDTH = 6,            /* q >= 2^30 (u32) or q >= 2^60 (u64) */
+    NTT_ERR_ALIGNMENT = 7,          /* device pointer not 16-byte aligned */
+    NTT_ERR_CUDA = 8,               /* a CUDA runtime call failed */
+    NTT_ERR_OOM = 9,                /* device allocation failed */
+    NTT_ERR_INPUT_RANGE = 10,       /* NTT_CHECK: an input word was >= q */
+    NTT_ERR_TIMEOUT = 11,           /* a bounded device wait ran out */
+    NTT_ERR_UNSUPPORTED = 12,       /* valid request this build cannot serve */
+    NTT_ERR_PSI = 13                /* caller psi is not a primitive 2N-th root */
+} ntt_status;
+
+/* Dataflow variants of Sec. II.  All produce bit-identical results. */
+typedef enum {
+    NTT_DIT = 0,      /* Algorithm 1: bit reversal, then log2 N in-place stages */
+    NTT_DIF = 1,      /* Algorithm 2: log2 N in-place stages, then bit reversal */
+    NTT_FLAT = 2,     /* Sec. II "Flat-NTT": DIT with the two inner loops fused */
+    NTT_PEASE = 3,    /* Eq. 7 / Algorithm 3: constant geometry + copy back */
+    NTT_PEASE_NC = 4, /* Sec. II/III-B "Pease_nc": constant geometry, buffer swap */
+    NTT_STOCKHAM = 5, /* Sec. II "Stockham": self-sorting ping-pong */
+    NTT_SIXSTEP = 6,  /* Sec. II "Six-step": transposes + small sub-transforms */
+    NTT_FUSED = 7,    /* fast path: stages fused per CTA in registers (Sec. II
+                         twiddle precompute, Sec. III-C reductions) */
+    NTT_TC_FOURSTEP = 8 /* four-step with tensor-core sub-transforms */
+} ntt_variant;
+
+/* plan flags */
+#define NTT_WORD64 0x1u            /* uint64_t words, q < 2^60 */
+#define NTT_ORDER_BITREV 0x2u      /* forward output / inverse input in
+                                      bit-reversed order: position p holds
+                                      X[bitrev_n(p)] */
+#define NTT_RED_SHOUP 0x00u        /* twiddle products: Algorithm 5 (Shoup) */
+#define NTT_RED_BARRETT 0x10u      /* Barrett reduction */
+#define NTT_RED_MONTGOMERY 0x20u   /* Montgomery reduction */
+#define NTT_RED_MASK 0x30u
+#define NTT_CHECK 0x100u           /* record input words >= q on the device */
+
+/*
+ * Create a plan for batches of L-limb polynomials of N coefficients.
+ * q[0..L) are the limb primes (copied).  Validates N (power of two,
+ * 2 <= N <= 2^17), every q (prime, q = 1 mod 2N, below the word limit),
+ * then builds the bit-reversed psi / psi^-1 twiddle tables of Sec. II
+ * ("Twiddle Factors": all twiddles precomputed) with the companions the
+ * selected reduction needs, and copies them to the current CUDA device.
+ * On error *plan is set to NULL and nothing is allocated.
+ */
+ntt_status ntt_plan_create(ntt_plan_t *plan, uint32_t N, const uint64_t *q,
+                           uint32_t L, ntt_variant variant, uint32_t flags);
+
+/* As ntt_plan_create, with the caller's roots psi[0..L) (NULL = default).
+ * Each psi[l] must satisfy psi^N = -1 (mod q[l]); else NTT_ERR_PSI. */
+ntt_status ntt_plan_create_ex(ntt_plan_t *plan, uint32_t N, const uint64_t *q,
+                              uint32_t L, ntt_variant variant, uint32_t flags,
+                              const uint64_t *psi);
+
+/* Release the plan's device memory (after synchronising its last stream). */
+void ntt_plan_destroy(ntt_plan_t plan);
+
+/* Pre-size the plan's scratch buffer for batches up to max_batch
+ * polynomials, so that later calls allocate nothing.  Variants that work in
+ * place (DIT, DIF, Flat, and Fused with NTT_ORDER_BITREV) need none. */
+ntt_status ntt_plan_reserve(ntt_plan_t plan, uint32_t max_batch,
+                            ntt_stream_t stream);
+
+/*
+ * Forward negacyclic NTT of `batch` polynomials in place: d_data holds
+ * [batch][L][N] words on the device; afterwards position k holds X[k]
+ * (natural order) or X[bitrev(k)] (NTT_ORDER_BITREV).  Eq. 3 with the psi
+ * twist; the butterfly dataflow is the plan's variant (Algorithms 1-3,
+ * Sec. II).
+ */
+ntt_status ntt_forward(ntt_plan_t plan, void *d_data, uint32_t batch,
+                       ntt_stream_t stream);
+
+/* Inverse negacyclic NTT in place (input order as ntt_forward's output). */
+ntt_status ntt_inverse(ntt_plan_t plan, void *d_data, uint32_t batch,
+                       ntt_stream_t stream);
+
+/*
+ * c[k] = a[k] * b[k] mod q[l] for [batch][L][N] arrays (Sec. I: the product
+ * step of NTT-based polynomial multiplication).  d_c may alias d_a or d_b.
+ * Uses Barrett reduction (Montgomery under NTT_RED_MONTGOMERY).
+ */
+ntt_status ntt_pointwise_mul(ntt_plan_t plan, void *d_c, const void *d_a,
+                             const void *d_b, uint32_t batch,
+                             ntt_stream_t stream);
+
+/*
+ * End-to-end negacyclic products from host memory, for `pairs` products:
+ * h_in holds [2][pairs][L][N] words (all first factors, then all second
+ * factors), h_out receives [pairs][L][N] words of a_i * b_i mod
+ * (x^N + 1, q).  d_work is a device buffer of at least 2*pairs*L*N words.
+ * Enqueues host-to-device copy, forward NTT of 2*pairs polynomials,
+ * pointwise product, inverse NTT of the products and device-to-host copy on
+ * `stream`; the caller synchronises.  Host buffers should be pinned.
+ */
+ntt_status ntt_polymul_host(ntt_plan_t plan, void *h_out, const void *h_in,
+                            void *d_work, uint32_t pairs, ntt_stream_t stream);
+
+/* Synchronise `stream`, then return and clear the plan's sticky device
+ * status (NTT_OK, NTT_ERR_INPUT_RANGE or NTT_ERR_TIMEOUT). */
+ntt_status ntt_get_device_status(ntt_plan_t plan, ntt_stream_t stream);
+
+/* Copy the plan's roots psi[0..L) to host memory. */
+ntt_status ntt_plan_get_psi(ntt_plan_t plan, uint64_t *psi_out);
+
+/* Number of kernels the last ntt_forward / ntt_inverse / ntt_pointwise_mul
+ * call on this plan launched (for launch accounting). */
+uint32_t ntt_plan_last_launches(ntt_plan_t plan);
+
+/* Human-readable name of a status code (static string). */
+const char *ntt_status_string(ntt_status s);
+
+/* ------------------------------------------------ host-only number theory
+ * These touch no GPU and may be called on a machine without one. */
+
+/* Same checks as ntt_plan_create, without building anything. */
+ntt_status ntt_validate(uint32_t N, const uint64_t *q, uint32_t L,
+                        uint32_t flags);
+
+/* Default root psi = g^((q-1)/(2N)) (g = smallest generator of Z_q^*). */
+ntt_status ntt_default_psi(uint64_t q, uint32_t N, uint64_t *psi_out);
+
+/* The first `count` primes q = 2^bits - k 2^m + 1 (k = 1, 2, ...) with
+ * 2^(bits-1) < q < 2^bits, in descending order; NTT_ERR_INVALID_ARG if
+ * fewer exist or bits is outside 3..62. */
+ntt_status ntt_find_primes(uint32_t bits, uint32_t m, uint32_t count,
+                           uint64_t *out);
+
+/* ------------------------------------------------------- ragged batches
+ * One persistent kernel, captured in a CUDA graph, runs every job of a
+ * heterogeneous set (different N, L, word width, direction). */
+typedef struct {
+    void *d_data;         /* [batch][L][N] words on the device */
+    const uint64_t *q;    /* L host primes (copied at create) */
+    uint32_t N;           /* 2^12 .. 2^17 */
+    uint32_t L;           /* limbs */
+    uint32_t batch;       /* polynomials */
+    uint32_t word64;      /* 0: uint32_t words (q < 2^30), 1: uint64_t */
+    int32_t inverse;      /* 0 forward, 1 inverse */
+    uint32_t reserved;
+} ntt_job;
+
+/* Validate the jobs, build one table per distinct (q, N) and the work list,
+ * choose tiles, and capture the persistent launch into a CUDA graph.
+ * flags: NTT_ORDER_BITREV and NTT_RED_* as for plans. */
+ntt_status ntt_ragged_create(ntt_ragged_t *out, const ntt_job *jobs,
+                             uint32_t n_jobs, uint32_t flags);
+
+/* Replay the captured graph on `stream`. */
+ntt_status ntt_ragged_launch(ntt_ragged_t r, ntt_stream_t stream);
+
+/* Synchronise `stream` and return the ragged kernel's device status. */
+ntt_status ntt_ragged_status(ntt_ragged_t r, ntt_stream_t stream);
+
+void ntt_ragged_destroy(ntt_ragged_t r);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NTTGB_NTT_H */

@@ -66,6 +66,7 @@ def lib():
                 "orc_ntt_inv_fast": (None, [u64, u64, u64, _u64p, _u64p]),
                 "orc_negacyclic_mul": (None, [u64, u64, _u64p, _u64p, _u64p]),
                 "orc_pointwise": (None, [u64, u64, _u64p, _u64p, _u64p]),
+                "orc_negacyclic_mul_at": (u64, [u64, u64, _u64p, _u64p, u64]),
                 "orc_bitrev_permute": (None, [u64, _u64p, _u64p]),
                 "orc_ntt_batch": (None, [ctypes.c_int, ctypes.c_int, u64,
                                          ctypes.c_uint32, ctypes.c_uint32,
@@ -167,6 +168,12 @@ def negacyclic_mul(a, b, q):
     c = np.zeros_like(a)
     lib().orc_negacyclic_mul(q, a.size, _p(a), _p(b), _p(c))
     return c
+
+
+def negacyclic_mul_at(a, b, q, j):
+    a = _u64(a)
+    b = _u64(b)
+    return int(lib().orc_negacyclic_mul_at(q, a.size, _p(a), _p(b), j))
 
 
 def pointwise(a, b, q):

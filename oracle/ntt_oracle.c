@@ -221,6 +221,21 @@ void orc_negacyclic_mul(uint64_t q, uint64_t N, const uint64_t *a,
     }
 }
 
+/* Coefficient j of a * b mod (x^N + 1, q):
+ * sum_{i<=j} a[i] b[j-i] - sum_{i>j} a[i] b[N+j-i]. */
+uint64_t orc_negacyclic_mul_at(uint64_t q, uint64_t N, const uint64_t *a,
+                               const uint64_t *b, uint64_t j)
+{
+    uint64_t acc = 0;
+    for (uint64_t i = 0; i < N; ++i) {
+        if (i <= j)
+            acc = orc_addmod(acc, orc_mulmod(a[i], b[j - i], q), q);
+        else
+            acc = orc_submod(acc, orc_mulmod(a[i], b[N + j - i], q), q);
+    }
+    return acc;
+}
+
 /* c[k] = a[k] b[k] mod q. */
 void orc_pointwise(uint64_t q, uint64_t n, const uint64_t *a,
                    const uint64_t *b, uint64_t *c)

@@ -1,0 +1,429 @@
+// api.cu -- the C ABI of libnttgb: validation, plan building, dispatch.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "host_nt.hpp"
+#include "plan.hpp"
+
+using nttgb::LimbConst;
+namespace H = nttgb::host;
+using u128 = unsigned __int128;
+
+namespace {
+
+constexpr uint32_t kKnownFlags = NTT_WORD64 | NTT_ORDER_BITREV | NTT_RED_MASK | NTT_CHECK;
+constexpr uint32_t kMaxLimbs = 4096;
+
+int red_of(uint32_t flags) {
+    switch (flags & NTT_RED_MASK) {
+    case NTT_RED_BARRETT: return nttgb::RED_BARRETT;
+    case NTT_RED_MONTGOMERY: return nttgb::RED_MONTGOMERY;
+    default: return nttgb::RED_SHOUP;
+    }
+}
+
+bool is_pow2(uint32_t x) { return x && !(x & (x - 1)); }
+
+// Twiddle pair (value, companion) for the plan's reduction.
+struct Enc {
+    uint64_t q;
+    int W;          // 32 or 64
+    int red;
+    uint64_t qinv;  // q^-1 mod 2^W
+    void operator()(uint64_t w, uint64_t &v, uint64_t &c) const {
+        const u128 R = (u128)1 << W;
+        if (red == nttgb::RED_SHOUP) {
+            v = w;
+            c = (uint64_t)(((u128)w << W) / q);
+        } else if (red == nttgb::RED_MONTGOMERY) {
+            uint64_t wm = (uint64_t)(((u128)w % q) * (R % q) % q);
+            v = wm;
+            c = W == 32 ? (uint64_t)((uint32_t)wm * (uint32_t)qinv) : wm * qinv;
+        } else {
+            v = w;
+            c = 0;
+        }
+    }
+};
+
+// Writes a [L][N] table of pairs in the word type into `out` (bytes).
+void put_pair(std::vector<uint8_t> &out, size_t idx, uint64_t v, uint64_t c, bool w64) {
+    if (w64) {
+        uint64_t *p = reinterpret_cast<uint64_t *>(out.data()) + 2 * idx;
+        p[0] = v; p[1] = c;
+    } else {
+        uint32_t *p = reinterpret_cast<uint32_t *>(out.data()) + 2 * idx;
+        p[0] = (uint32_t)v; p[1] = (uint32_t)c;
+    }
+}
+
+ntt_status upload(void **dptr, const std::vector<uint8_t> &h) {
+    if (cudaMalloc(dptr, h.size()) != cudaSuccess) { *dptr = nullptr; cudaGetLastError(); return NTT_ERR_OOM; }
+    if (cudaMemcpy(*dptr, h.data(), h.size(), cudaMemcpyHostToDevice) != cudaSuccess) return NTT_ERR_CUDA;
+    return NTT_OK;
+}
+
+void free_plan_memory(ntt_plan_s *p) {
+    void *ptrs[] = {p->d_limb, p->d_w_fwd, p->d_w_inv, p->d_twist, p->d_untwist, p->d_main_fwd,
+                    p->d_main_inv, p->d_chunk_fwd, p->d_chunk_inv, p->d_scratch, p->d_status};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+ntt_status validate(uint32_t N, const uint64_t *q, uint32_t L, uint32_t flags) {
+    if (!q || L == 0 || L > kMaxLimbs) return NTT_ERR_INVALID_ARG;
+    if (flags & ~kKnownFlags) return NTT_ERR_INVALID_ARG;
+    if ((flags & NTT_RED_MASK) == NTT_RED_MASK) return NTT_ERR_INVALID_ARG;
+    if (!is_pow2(N)) return NTT_ERR_N_NOT_POW2;
+    if (N < 2 || N > (1u << 17)) return NTT_ERR_N_RANGE;
+    const uint64_t limit = (flags & NTT_WORD64) ? (1ull << 60) : (1ull << 30);
+    for (uint32_t l = 0; l < L; ++l) {
+        if (q[l] >= limit || q[l] < 3) return NTT_ERR_Q_WIDTH;
+        if (!H::is_prime(q[l])) return NTT_ERR_Q_NOT_PRIME;
+        if ((q[l] - 1) % (2ull * N) != 0) return NTT_ERR_Q_NOT_NTT_FRIENDLY;
+    }
+    return NTT_OK;
+}
+
+ntt_status build_tables(ntt_plan_s *p) {
+    const uint32_t N = p->N, L = p->L, n = p->logN;
+    const bool w64 = p->word64;
+    const int W = w64 ? 64 : 32;
+    const size_t pair_bytes = w64 ? 16 : 8;
+    const bool variant_tabs = p->variant != NTT_FUSED || p->fused_mode == nttgb::FUSED_STAGES;
+    const bool fused_tabs = p->variant == NTT_FUSED && p->fused_mode != nttgb::FUSED_STAGES;
+    const bool chunk_tabs = fused_tabs && p->fused_mode == nttgb::FUSED_TWO_PASS;
+
+    std::vector<LimbConst> lc(L);
+    std::vector<uint8_t> wf, wi, tw, ut, mf, mi, cf, ci;
+    const size_t tab_bytes = (size_t)L * N * pair_bytes;
+    if (variant_tabs) { wf.resize(tab_bytes); wi.resize(tab_bytes); tw.resize(tab_bytes); ut.resize(tab_bytes); }
+    if (fused_tabs) { mf.resize(tab_bytes); mi.resize(tab_bytes); }
+    if (chunk_tabs) { cf.resize(tab_bytes); ci.resize(tab_bytes); }
+
+    std::vector<uint64_t> pw(N), pwi(N);
+    for (uint32_t l = 0; l < L; ++l) {
+        const uint64_t q = p->q[l], psi = p->psi[l];
+        const uint64_t psi_inv = H::invm(psi, q);
+        const uint64_t ninv = H::invm(N % q, q);
+        const uint64_t qinv64 = H::inv_pow2_64(q);
+        Enc enc{q, W, p->red, w64 ? qinv64 : (uint64_t)(uint32_t)qinv64};
+
+        LimbConst &c = lc[l];
+        std::memset(&c, 0, sizeof(c));
+        c.q = q;
+        c.two_q = 2 * q;
+        c.qinv = enc.qinv;
+        const u128 R = (u128)1 << W;
+        uint64_t rmod = (uint64_t)(R % q);
+        c.r2 = H::mulm(rmod, rmod, q);
+        c.r2c = w64 ? c.r2 * qinv64 : (uint64_t)((uint32_t)c.r2 * (uint32_t)qinv64);
+        c.bits = (uint32_t)H::bit_length(q);
+        if (w64) c.mu = (uint64_t)(((u128)1 << (2 * c.bits + 3)) / q);
+        else c.mu = (uint64_t)((((u128)1) << 64) / q);
+        enc(ninv, c.ninv_w, c.ninv_c);
+        // N^-1 * psi^-bitrev(1) = N^-1 psi^-(N/2)
+        enc(H::mulm(ninv, H::powm(psi_inv, N / 2, q), q), c.ninv_w1_w, c.ninv_w1_c);
+
+        pw[0] = 1; pwi[0] = 1;
+        for (uint32_t i = 1; i < N; ++i) { pw[i] = H::mulm(pw[i - 1], psi, q); pwi[i] = H::mulm(pwi[i - 1], psi_inv, q); }
+        const size_t base = (size_t)l * N;
+        uint64_t v, cc;
+        if (variant_tabs) {
+            // omega^e = psi^(2e): e < N/2 from the psi powers, the rest by omega^(N/2) = -1
+            for (uint32_t e = 0; e < N; ++e) {
+                uint64_t ex = 2ull * e % (2ull * N);
+                uint64_t om = ex < N ? pw[ex] : (q - pw[ex - N]) % q;
+                uint64_t omi = ex < N ? pwi[ex] : (q - pwi[ex - N]) % q;
+                enc(om, v, cc); put_pair(wf, base + e, v, cc, w64);
+                enc(omi, v, cc); put_pair(wi, base + e, v, cc, w64);
+                enc(pw[e], v, cc); put_pair(tw, base + e, v, cc, w64);
+                enc(H::mulm(ninv, pwi[e], q), v, cc); put_pair(ut, base + e, v, cc, w64);
+            }
+        }
+        if (fused_tabs) {
+            for (uint32_t i = 0; i < N; ++i) {
+                uint32_t r = H::bitrev(i, (int)n);
+                enc(pw[r], v, cc); put_pair(mf, base + i, v, cc, w64);
+                enc(pwi[r], v, cc); put_pair(mi, base + i, v, cc, w64);
+            }
+        }
+        if (chunk_tabs) {
+            const uint32_t N1 = 1u << p->s1, N2 = 1u << p->s2;
+            for (uint32_t r = 0; r < N1; ++r) {
+                put_pair(cf, base + (size_t)r * N2, 0, 0, w64);
+                put_pair(ci, base + (size_t)r * N2, 0, 0, w64);
+                for (uint32_t s = 0; s < p->s2; ++s)
+                    for (uint32_t ip = 0; ip < (1u << s); ++ip) {
+                        uint32_t gi = (1u << s) * (N1 + r) + ip;     // global table index
+                        uint32_t e = H::bitrev(gi, (int)n);
+                        size_t at = base + (size_t)r * N2 + (1u << s) + ip;
+                        enc(pw[e], v, cc); put_pair(cf, at, v, cc, w64);
+                        enc(pwi[e], v, cc); put_pair(ci, at, v, cc, w64);
+                    }
+            }
+        }
+    }
+    std::vector<uint8_t> lcb(sizeof(LimbConst) * L);
+    std::memcpy(lcb.data(), lc.data(), lcb.size());
+    ntt_status s;
+    if ((s = upload((void **)&p->d_limb, lcb)) != NTT_OK) return s;
+    if (variant_tabs) {
+        if ((s = upload(&p->d_w_fwd, wf)) != NTT_OK) return s;
+        if ((s = upload(&p->d_w_inv, wi)) != NTT_OK) return s;
+        if ((s = upload(&p->d_twist, tw)) != NTT_OK) return s;
+        if ((s = upload(&p->d_untwist, ut)) != NTT_OK) return s;
+    }
+    if (fused_tabs) {
+        if ((s = upload(&p->d_main_fwd, mf)) != NTT_OK) return s;
+        if ((s = upload(&p->d_main_inv, mi)) != NTT_OK) return s;
+    }
+    if (chunk_tabs) {
+        if ((s = upload(&p->d_chunk_fwd, cf)) != NTT_OK) return s;
+        if ((s = upload(&p->d_chunk_inv, ci)) != NTT_OK) return s;
+    }
+    if (cudaMalloc((void **)&p->d_status, sizeof(uint32_t)) != cudaSuccess) { cudaGetLastError(); return NTT_ERR_OOM; }
+    if (cudaMemset(p->d_status, 0, sizeof(uint32_t)) != cudaSuccess) return NTT_ERR_CUDA;
+    return NTT_OK;
+}
+
+bool needs_scratch(const ntt_plan_s &p) {
+    switch (p.variant) {
+    case NTT_PEASE: case NTT_PEASE_NC: case NTT_STOCKHAM: case NTT_SIXSTEP: return true;
+    default: return false;
+    }
+}
+
+ntt_status run_transform(ntt_plan_t plan, void *d_data, uint32_t batch, ntt_stream_t stream, bool inverse) {
+    if (!plan || !d_data || batch == 0) return NTT_ERR_INVALID_ARG;
+    if (!aligned16(d_data)) return NTT_ERR_ALIGNMENT;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    ntt_plan_s &p = *plan;
+    p.last_launches = 0;
+    if (needs_scratch(p)) {
+        ntt_status s = nttgb::ensure_scratch(p, batch, st);
+        if (s != NTT_OK) return s;
+    }
+    cudaError_t e = cudaSuccess;
+    if (p.check) e = nttgb::launch_check_range(p, d_data, batch, st);
+    if (e == cudaSuccess) {
+        if (p.variant != NTT_FUSED || p.fused_mode == nttgb::FUSED_STAGES) {
+            ntt_variant v = p.variant == NTT_FUSED ? NTT_FLAT : p.variant;
+            e = nttgb::launch_variant(p, v, d_data, batch, inverse, st);
+        } else {
+            // the fused kernels work in bit-reversed order
+            if (inverse && !p.bitrev_order) e = nttgb::launch_bitrev_permute(p, d_data, batch, st);
+            if (e == cudaSuccess) e = nttgb::launch_fused(p, d_data, batch, inverse, st);
+            if (e == cudaSuccess && !inverse && !p.bitrev_order) e = nttgb::launch_bitrev_permute(p, d_data, batch, st);
+        }
+    }
+    if (e != cudaSuccess) { cudaGetLastError(); return NTT_ERR_CUDA; }
+    return NTT_OK;
+}
+
+}  // namespace
+
+namespace nttgb {
+
+ntt_status ensure_scratch(ntt_plan_s &p, uint32_t batch, cudaStream_t st) {
+    size_t need = (size_t)batch * p.L * p.N * p.word_bytes();
+    if (need <= p.scratch_bytes) return NTT_OK;
+    if (cudaStreamSynchronize(st) != cudaSuccess) { cudaGetLastError(); return NTT_ERR_CUDA; }
+    if (p.d_scratch) cudaFree(p.d_scratch);
+    p.d_scratch = nullptr;
+    p.scratch_bytes = 0;
+    if (cudaMalloc(&p.d_scratch, need) != cudaSuccess) { cudaGetLastError(); p.d_scratch = nullptr; return NTT_ERR_OOM; }
+    p.scratch_bytes = need;
+    return NTT_OK;
+}
+
+}  // namespace nttgb
+
+extern "C" {
+
+const char *ntt_status_string(ntt_status s) {
+    switch (s) {
+    case NTT_OK: return "NTT_OK";
+    case NTT_ERR_INVALID_ARG: return "NTT_ERR_INVALID_ARG: invalid argument";
+    case NTT_ERR_N_NOT_POW2: return "NTT_ERR_N_NOT_POW2: N is not a power of two";
+    case NTT_ERR_N_RANGE: return "NTT_ERR_N_RANGE: N outside 2^1..2^17";
+    case NTT_ERR_Q_NOT_PRIME: return "NTT_ERR_Q_NOT_PRIME: modulus is not prime";
+    case NTT_ERR_Q_NOT_NTT_FRIENDLY: return "NTT_ERR_Q_NOT_NTT_FRIENDLY: q != 1 mod 2N";
+    case NTT_ERR_Q_WIDTH: return "NTT_ERR_Q_WIDTH: modulus too wide for the word size";
+    case NTT_ERR_ALIGNMENT: return "NTT_ERR_ALIGNMENT: device pointer not 16-byte aligned";
+    case NTT_ERR_CUDA: return "NTT_ERR_CUDA: CUDA runtime error";
+    case NTT_ERR_OOM: return "NTT_ERR_OOM: device allocation failed";
+    case NTT_ERR_INPUT_RANGE: return "NTT_ERR_INPUT_RANGE: input word >= q";
+    case NTT_ERR_TIMEOUT: return "NTT_ERR_TIMEOUT: bounded device wait expired";
+    case NTT_ERR_UNSUPPORTED: return "NTT_ERR_UNSUPPORTED: not supported by this build";
+    case NTT_ERR_PSI: return "NTT_ERR_PSI: psi is not a primitive 2N-th root of unity";
+    }
+    return "NTT_ERR_UNKNOWN";
+}
+
+ntt_status ntt_validate(uint32_t N, const uint64_t *q, uint32_t L, uint32_t flags) {
+    return validate(N, q, L, flags);
+}
+
+ntt_status ntt_default_psi(uint64_t q, uint32_t N, uint64_t *psi_out) {
+    if (!psi_out || !is_pow2(N) || q < 3 || q >= (1ull << 62)) return NTT_ERR_INVALID_ARG;
+    if (!H::is_prime(q)) return NTT_ERR_Q_NOT_PRIME;
+    if ((q - 1) % (2ull * N) != 0) return NTT_ERR_Q_NOT_NTT_FRIENDLY;
+    uint64_t g = H::smallest_generator(q);
+    *psi_out = H::powm(g, (q - 1) / (2ull * N), q);
+    return NTT_OK;
+}
+
+ntt_status ntt_find_primes(uint32_t bits, uint32_t m, uint32_t count, uint64_t *out) {
+    if (!out || bits < 3 || bits > 62 || m >= bits || count == 0) return NTT_ERR_INVALID_ARG;
+    const uint64_t top = 1ull << bits, low = 1ull << (bits - 1), step = 1ull << m;
+    uint32_t found = 0;
+    for (uint64_t k = 1; found < count; ++k) {
+        if (k * step >= top) break;
+        uint64_t q = top - k * step + 1;
+        if (q <= low) break;
+        if (H::is_prime(q)) out[found++] = q;
+    }
+    return found == count ? NTT_OK : NTT_ERR_INVALID_ARG;
+}
+
+ntt_status ntt_plan_create_ex(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t L, ntt_variant variant,
+                              uint32_t flags, const uint64_t *psi) {
+    if (!plan) return NTT_ERR_INVALID_ARG;
+    *plan = nullptr;
+    if ((int)variant < NTT_DIT || (int)variant > NTT_TC_FOURSTEP) return NTT_ERR_INVALID_ARG;
+    ntt_status s = validate(N, q, L, flags);
+    if (s != NTT_OK) return s;
+    if (variant == NTT_TC_FOURSTEP) return NTT_ERR_UNSUPPORTED;
+    ntt_plan_s *p = new (std::nothrow) ntt_plan_s();
+    if (!p) return NTT_ERR_OOM;
+    p->N = N;
+    while ((1u << p->logN) < N) ++p->logN;
+    p->L = L;
+    p->flags = flags;
+    p->variant = variant;
+    p->red = red_of(flags);
+    p->word64 = (flags & NTT_WORD64) != 0;
+    p->bitrev_order = (flags & NTT_ORDER_BITREV) != 0;
+    p->check = (flags & NTT_CHECK) != 0;
+    p->q.assign(q, q + L);
+    p->psi.resize(L);
+    for (uint32_t l = 0; l < L; ++l) {
+        if (psi) {
+            if (psi[l] == 0 || psi[l] >= q[l] || H::powm(psi[l], N, q[l]) != q[l] - 1) { delete p; return NTT_ERR_PSI; }
+            p->psi[l] = psi[l];
+        } else {
+            ntt_default_psi(q[l], N, &p->psi[l]);
+        }
+    }
+    if (variant == NTT_FUSED) {
+        const int single_max = p->word64 ? nttgb::kSingleMaxLog64 : nttgb::kSingleMaxLog32;
+        if (p->logN < 4) p->fused_mode = nttgb::FUSED_STAGES;
+        else if ((int)p->logN <= single_max) p->fused_mode = nttgb::FUSED_SINGLE;
+        else {
+            p->fused_mode = nttgb::FUSED_TWO_PASS;
+            p->s2 = nttgb::kChunkLog;
+            p->s1 = p->logN - p->s2;
+        }
+    }
+    cudaGetDevice(&p->device);
+    s = build_tables(p);
+    if (s != NTT_OK) { free_plan_memory(p); delete p; cudaGetLastError(); return s; }
+    *plan = p;
+    return NTT_OK;
+}
+
+ntt_status ntt_plan_create(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t L, ntt_variant variant,
+                           uint32_t flags) {
+    return ntt_plan_create_ex(plan, N, q, L, variant, flags, nullptr);
+}
+
+void ntt_plan_destroy(ntt_plan_t plan) {
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    free_plan_memory(plan);
+    delete plan;
+}
+
+ntt_status ntt_plan_reserve(ntt_plan_t plan, uint32_t max_batch, ntt_stream_t stream) {
+    if (!plan || max_batch == 0) return NTT_ERR_INVALID_ARG;
+    if (!needs_scratch(*plan)) return NTT_OK;
+    return nttgb::ensure_scratch(*plan, max_batch, reinterpret_cast<cudaStream_t>(stream));
+}
+
+ntt_status ntt_forward(ntt_plan_t plan, void *d_data, uint32_t batch, ntt_stream_t stream) {
+    return run_transform(plan, d_data, batch, stream, false);
+}
+
+ntt_status ntt_inverse(ntt_plan_t plan, void *d_data, uint32_t batch, ntt_stream_t stream) {
+    return run_transform(plan, d_data, batch, stream, true);
+}
+
+ntt_status ntt_pointwise_mul(ntt_plan_t plan, void *d_c, const void *d_a, const void *d_b, uint32_t batch,
+                             ntt_stream_t stream) {
+    if (!plan || !d_c || !d_a || !d_b || batch == 0) return NTT_ERR_INVALID_ARG;
+    if (!aligned16(d_c) || !aligned16(d_a) || !aligned16(d_b)) return NTT_ERR_ALIGNMENT;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    plan->last_launches = 0;
+    cudaError_t e = cudaSuccess;
+    if (plan->check) {
+        e = nttgb::launch_check_range(*plan, d_a, batch, st);
+        if (e == cudaSuccess) e = nttgb::launch_check_range(*plan, d_b, batch, st);
+    }
+    if (e == cudaSuccess) e = nttgb::launch_pointwise(*plan, d_c, d_a, d_b, batch, st);
+    if (e != cudaSuccess) { cudaGetLastError(); return NTT_ERR_CUDA; }
+    return NTT_OK;
+}
+
+ntt_status ntt_polymul_host(ntt_plan_t plan, void *h_out, const void *h_in, void *d_work, uint32_t pairs,
+                            ntt_stream_t stream) {
+    if (!plan || !h_out || !h_in || !d_work || pairs == 0) return NTT_ERR_INVALID_ARG;
+    if (!aligned16(d_work)) return NTT_ERR_ALIGNMENT;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t poly_bytes = (size_t)plan->L * plan->N * plan->word_bytes();
+    const size_t half = (size_t)pairs * poly_bytes;
+    uint8_t *d = reinterpret_cast<uint8_t *>(d_work);
+    if (cudaMemcpyAsync(d, h_in, 2 * half, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        cudaGetLastError();
+        return NTT_ERR_CUDA;
+    }
+    uint32_t launches = 0;
+    ntt_status s = ntt_forward(plan, d, 2 * pairs, stream);
+    launches += plan->last_launches;
+    if (s == NTT_OK) { s = ntt_pointwise_mul(plan, d, d, d + half, pairs, stream); launches += plan->last_launches; }
+    if (s == NTT_OK) { s = ntt_inverse(plan, d, pairs, stream); launches += plan->last_launches; }
+    plan->last_launches = launches;
+    if (s != NTT_OK) return s;
+    if (cudaMemcpyAsync(h_out, d, half, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+        cudaGetLastError();
+        return NTT_ERR_CUDA;
+    }
+    return NTT_OK;
+}
+
+ntt_status ntt_get_device_status(ntt_plan_t plan, ntt_stream_t stream) {
+    if (!plan) return NTT_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(st) != cudaSuccess) { cudaGetLastError(); return NTT_ERR_CUDA; }
+    uint32_t v = 0;
+    if (cudaMemcpy(&v, plan->d_status, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return NTT_ERR_CUDA;
+    if (v) cudaMemset(plan->d_status, 0, sizeof(uint32_t));
+    if (v & 2u) return NTT_ERR_TIMEOUT;
+    if (v & 1u) return NTT_ERR_INPUT_RANGE;
+    return NTT_OK;
+}
+
+ntt_status ntt_plan_get_psi(ntt_plan_t plan, uint64_t *psi_out) {
+    if (!plan || !psi_out) return NTT_ERR_INVALID_ARG;
+    for (uint32_t l = 0; l < plan->L; ++l) psi_out[l] = plan->psi[l];
+    return NTT_OK;
+}
+
+uint32_t ntt_plan_last_launches(ntt_plan_t plan) { return plan ? plan->last_launches : 0; }
+
+}  // extern "C"

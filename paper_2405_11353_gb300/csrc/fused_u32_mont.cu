@@ -1,0 +1,6 @@
+// Instantiates the fused path for uint32_t words with RED_MONTGOMERY.
+#include "fused_launch.cuh"
+
+namespace nttgb {
+template cudaError_t run_fused_t<uint32_t, RED_MONTGOMERY>(ntt_plan_s &, void *, uint32_t, bool, cudaStream_t);
+}

@@ -1,0 +1,6 @@
+// Instantiates the fused path for uint64_t words with RED_SHOUP.
+#include "fused_launch.cuh"
+
+namespace nttgb {
+template cudaError_t run_fused_t<uint64_t, RED_SHOUP>(ntt_plan_s &, void *, uint32_t, bool, cudaStream_t);
+}

@@ -1,0 +1,71 @@
+// plan.hpp -- internal plan object shared by the API and the launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/ntt.h"
+#include "modarith.cuh"
+
+namespace nttgb {
+
+enum FusedMode : int { FUSED_STAGES = 0, FUSED_SINGLE = 1, FUSED_TWO_PASS = 2 };
+
+// Largest transform done in one pass of the fused kernel (one CTA holds the
+// whole transform in shared memory): 2^14 words of 4 bytes, 2^13 of 8.
+constexpr int kSingleMaxLog32 = 14;
+constexpr int kSingleMaxLog64 = 13;
+constexpr int kLogR = 4;          // 16 words per thread in the fused kernel
+constexpr int kChunkLog = 8;      // pass-B sub-transform size 256
+
+}  // namespace nttgb
+
+struct ntt_plan_s {
+    uint32_t N = 0, logN = 0, L = 0, flags = 0;
+    ntt_variant variant = NTT_FUSED;
+    int red = 0;
+    bool word64 = false, bitrev_order = false, check = false;
+    std::vector<uint64_t> q, psi;
+    int device = 0;
+
+    // device memory (all owned)
+    nttgb::LimbConst *d_limb = nullptr;
+    // variant (per-stage) tables, [L][N] twiddle pairs each
+    void *d_w_fwd = nullptr;     // omega^e
+    void *d_w_inv = nullptr;     // omega^-e
+    void *d_twist = nullptr;     // psi^n
+    void *d_untwist = nullptr;   // N^-1 psi^-n
+    // fused tables, [L][N] twiddle pairs each
+    void *d_main_fwd = nullptr;  // psi^bitrev(i)
+    void *d_main_inv = nullptr;  // psi^-bitrev(i)
+    void *d_chunk_fwd = nullptr; // pass-B per-chunk layout of psi^bitrev
+    void *d_chunk_inv = nullptr;
+    void *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    uint32_t *d_status = nullptr;
+    uint32_t last_launches = 0;
+
+    int fused_mode = nttgb::FUSED_STAGES;
+    uint32_t s1 = 0, s2 = 0;     // two-pass split: N = 2^s1 * 2^s2
+
+    size_t word_bytes() const { return word64 ? 8 : 4; }
+    size_t limb_words() const { return (size_t)N; }
+};
+
+namespace nttgb {
+
+// Launchers (return the CUDA error of the last launch; count launches).
+cudaError_t launch_variant(ntt_plan_s &p, ntt_variant v, void *data, uint32_t batch, bool inverse, cudaStream_t st);
+cudaError_t launch_fused(ntt_plan_s &p, void *data, uint32_t batch, bool inverse, cudaStream_t st);
+cudaError_t launch_pointwise(ntt_plan_s &p, void *c, const void *a, const void *b, uint32_t batch, cudaStream_t st);
+cudaError_t launch_bitrev_permute(ntt_plan_s &p, void *data, uint32_t batch, cudaStream_t st);
+cudaError_t launch_check_range(ntt_plan_s &p, const void *data, uint32_t batch, cudaStream_t st);
+
+ntt_status ensure_scratch(ntt_plan_s &p, uint32_t batch, cudaStream_t st);
+
+// fused path, instantiated in fused_<word>_<reduction>.cu
+template <class W, int RED>
+cudaError_t run_fused_t(ntt_plan_s &p, void *data, uint32_t batch, bool inverse, cudaStream_t st);
+
+}  // namespace nttgb

@@ -1,0 +1,389 @@
+"""Bit-exact parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Every comparison is exact: the transform over Z_q has a unique result for a
+given (q, psi, order), so every variant and reduction must reproduce the
+oracle word for word.  Inputs come from the seeded generators in ntt_synth;
+expected values only from oracle/.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import ntt_synth  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def nt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2405_11353_gb300 as nt
+    torch.cuda.init()
+    return nt
+
+
+ALL_VARIANTS = ["dit", "dif", "flat", "pease", "pease_nc", "stockham", "sixstep", "fused"]
+
+
+def to_dev(host, w64):
+    a = np.ascontiguousarray(host.astype(np.uint64 if w64 else np.uint32))
+    return torch.from_numpy(a.view(np.int64 if w64 else np.int32).copy()).cuda()
+
+
+def to_host(t, w64, shape):
+    a = t.cpu().numpy().view(np.uint64 if w64 else np.uint32)
+    return a.reshape(shape).astype(np.uint64)
+
+
+class Plan:
+    def __init__(self, nt, N, qs, variant="fused", red="shoup", w64=False, bitrev=False, check=False):
+        self.nt = nt
+        flags = nt.REDUCTIONS[red]
+        if w64:
+            flags |= nt.NTT_WORD64
+        if bitrev:
+            flags |= nt.NTT_ORDER_BITREV
+        if check:
+            flags |= nt.NTT_CHECK
+        self.h = nt.ntt_plan_create(N, qs, nt.VARIANTS[variant], flags)
+        self.N, self.L, self.w64, self.bitrev = N, len(qs), w64, bitrev
+
+    def fwd(self, t, batch):
+        self.nt.ntt_forward(self.h, t, batch)
+
+    def inv(self, t, batch):
+        self.nt.ntt_inverse(self.h, t, batch)
+
+    def close(self):
+        self.nt.ntt_plan_destroy(self.h)
+
+
+def reorder(X, bitrev, orc):
+    """Oracle output (natural order) in the plan's output order."""
+    if not bitrev:
+        return X
+    B, L, N = X.shape
+    return np.stack([np.stack([orc.bitrev_permute(X[b, l]) for l in range(L)]) for b in range(B)])
+
+
+def primes_for(orc, N, w64, L):
+    bits = 60 if w64 else 30
+    m = max(18, N.bit_length())
+    return orc.find_primes(bits, m, L)
+
+
+def roundtrip_check(nt, orc, N, qs, batch, variant, red="shoup", w64=False, bitrev=False, seed=1,
+                    naive=False):
+    psis = [orc.psi(q, N) for q in qs]
+    host = ntt_synth.rns_batch(seed, qs, N, batch)
+    want = orc.ntt_batch(host, qs, psis, fast=not naive)
+    p = Plan(nt, N, qs, variant, red, w64, bitrev)
+    try:
+        assert nt.ntt_plan_get_psi(p.h, len(qs)) == psis
+        d = to_dev(host, w64)
+        p.fwd(d, batch)
+        got = to_host(d, w64, host.shape)
+        assert np.array_equal(got, reorder(want, bitrev, orc)), (variant, red, N, w64, bitrev)
+        p.inv(d, batch)
+        back = to_host(d, w64, host.shape)
+        assert np.array_equal(back, host), ("inverse", variant, red, N, w64, bitrev)
+        assert nt.ntt_get_device_status(p.h) == nt.NTT_OK
+    finally:
+        p.close()
+
+
+# ------------------------------------------------------------------ variants
+@pytest.mark.parametrize("variant", ALL_VARIANTS)
+@pytest.mark.parametrize("bitrev", [False, True])
+def test_variants_all_sizes_u32(nt, orc, variant, bitrev):
+    for n in range(1, 13):
+        N = 1 << n
+        qs = [12289] if N <= 2048 else []
+        qs += primes_for(orc, N, False, 2)
+        roundtrip_check(nt, orc, N, qs, 3, variant, bitrev=bitrev, seed=n, naive=N <= 256)
+
+
+@pytest.mark.parametrize("variant", ALL_VARIANTS)
+def test_variants_large_u32(nt, orc, variant):
+    for n in (13, 14, 15, 16, 17):
+        N = 1 << n
+        qs = primes_for(orc, N, False, 2)
+        roundtrip_check(nt, orc, N, qs, 2, variant, seed=100 + n)
+
+
+@pytest.mark.parametrize("variant", ["dit", "pease_nc", "stockham", "sixstep", "fused"])
+def test_variants_u64(nt, orc, variant):
+    for n in (1, 2, 5, 10, 12, 13, 14, 15, 16, 17):
+        N = 1 << n
+        qs = primes_for(orc, N, True, 2)
+        roundtrip_check(nt, orc, N, qs, 2, variant, w64=True, seed=200 + n)
+
+
+@pytest.mark.parametrize("red", ["shoup", "barrett", "montgomery"])
+@pytest.mark.parametrize("w64", [False, True])
+@pytest.mark.parametrize("variant", ["fused", "flat"])
+def test_reductions(nt, orc, red, w64, variant):
+    for n in (4, 10, 13, 14, 16, 17):
+        N = 1 << n
+        qs = primes_for(orc, N, w64, 3)
+        roundtrip_check(nt, orc, N, qs, 2, variant, red=red, w64=w64, seed=300 + n,
+                        bitrev=(n % 2 == 0))
+
+
+# ------------------------------------------------------------ workloads
+def polymul_pipeline(nt, orc, N, qs, pairs, variant, red="shoup", w64=False, bitrev=False, seed=1):
+    """forward (2*pairs polys) -> pointwise -> inverse; returns GPU and oracle."""
+    psis = [orc.psi(q, N) for q in qs]
+    host = ntt_synth.rns_batch(seed, qs, N, 2 * pairs)
+    p = Plan(nt, N, qs, variant, red, w64, bitrev)
+    try:
+        d = to_dev(host, w64)
+        p.fwd(d, 2 * pairs)
+        fwd = to_host(d, w64, host.shape)
+        half = pairs * len(qs) * N
+        nt.ntt_pointwise_mul(p.h, d, d, d[half:], pairs)
+        prod = to_host(d[:half], w64, (pairs, len(qs), N))
+        p.inv(d, pairs)
+        out = to_host(d[:half], w64, (pairs, len(qs), N))
+        assert nt.ntt_get_device_status(p.h) == nt.NTT_OK
+    finally:
+        p.close()
+    A = orc.ntt_batch(host, qs, psis)
+    assert np.array_equal(fwd, reorder(A, bitrev, orc))
+    P = orc.pointwise_batch(A[:pairs], A[pairs:], qs)
+    assert np.array_equal(prod, reorder(P, bitrev, orc))
+    want = orc.ntt_batch(P, qs, psis, inverse=True)
+    assert np.array_equal(out, want)
+    return host, out
+
+
+@pytest.mark.parametrize("variant", ALL_VARIANTS)
+def test_workload_n1024_q12289_64polys(nt, orc, variant):
+    """N = 1024, q = 12289, 64 polys: forward, 32 pointwise products,
+    inverse; every output against the O(N^2) oracle and a few products
+    against the schoolbook negacyclic product."""
+    N, qs = 1024, [12289]
+    psis = [orc.psi(12289, N)]
+    host = ntt_synth.rns_batch(1001, qs, N, 64)
+    want = orc.ntt_batch(host, qs, psis, fast=False)
+    p = Plan(nt, N, qs, variant)
+    try:
+        d = to_dev(host, False)
+        p.fwd(d, 64)
+        assert np.array_equal(to_host(d, False, host.shape), want)
+        half = 32 * N
+        nt.ntt_pointwise_mul(p.h, d, d, d[half:], 32)
+        p.inv(d, 32)
+        out = to_host(d[:half], False, (32, 1, N))
+    finally:
+        p.close()
+    P = orc.pointwise_batch(want[:32], want[32:], qs)
+    assert np.array_equal(out, orc.ntt_batch(P, qs, psis, inverse=True, fast=False))
+    for i in (0, 17, 31):
+        assert np.array_equal(out[i, 0], orc.negacyclic_mul(host[i, 0], host[32 + i, 0], 12289))
+
+
+@pytest.mark.parametrize("bitrev", [True, False])
+def test_workload_n2p14_L8_128polys(nt, orc, bitrev):
+    qs = orc.find_primes(30, 15, 8)
+    polymul_pipeline(nt, orc, 1 << 14, qs, 64, "fused", bitrev=bitrev, seed=1002)
+
+
+@pytest.mark.parametrize("red", ["montgomery", "shoup"])
+def test_workload_n2p16_L24_u64(nt, orc, red):
+    """N = 2^16, 24 60-bit primes, 8 polys: forward + inverse, full
+    comparison with the O(N log N) oracle and 64 sampled O(N^2) values."""
+    N = 1 << 16
+    qs = orc.find_primes(60, 17, 24)
+    psis = [orc.psi(q, N) for q in qs]
+    host = ntt_synth.rns_batch(1003, qs, N, 8)
+    p = Plan(nt, N, qs, "fused", red, w64=True, bitrev=True)
+    try:
+        d = to_dev(host, True)
+        p.fwd(d, 8)
+        got = to_host(d, True, host.shape)
+        p.inv(d, 8)
+        back = to_host(d, True, host.shape)
+    finally:
+        p.close()
+    want = orc.ntt_batch(host, qs, psis)
+    assert np.array_equal(got, reorder(want, True, orc))
+    assert np.array_equal(back, host)
+    t, k = ntt_synth.sample_indices(1003, 8 * 24, N, 64)
+    vals = orc.ntt_batch_at(host, qs, psis, t, k)
+    nat = want.reshape(8 * 24, N)
+    assert np.array_equal(nat[t.astype(int), k.astype(int)], vals)
+
+
+def test_workload_n2p16_L32_u32(nt, orc):
+    """N = 2^16, 32 30-bit primes, 16 polys, butterfly form, as bench.py
+    runs it: forward, 8 x 32 pointwise products, inverse."""
+    qs = orc.find_primes(30, 17, 32)
+    host, out = polymul_pipeline(nt, orc, 1 << 16, qs, 8, "fused", bitrev=True, seed=1005)
+    # sampled coefficients of products against the schoolbook definition
+    for i, l, j in [(0, 0, 0), (3, 5, 12345), (7, 31, (1 << 16) - 1), (5, 17, 40000)]:
+        assert int(out[i, l, j]) == orc.negacyclic_mul_at(host[i, l], host[8 + i, l], qs[l], j)
+
+
+# ------------------------------------------------------------- edge cases
+def test_ragged_tail_tiles(nt, orc):
+    # single-pass tiles hold 4 transforms at N = 1024: 5 limbs x 1 poly
+    qs = primes_for(orc, 1024, False, 5)
+    roundtrip_check(nt, orc, 1024, qs, 1, "fused", seed=7)
+    roundtrip_check(nt, orc, 256, qs[:3], 1, "fused", seed=8)
+
+
+def test_batch_one_and_max_size(nt, orc):
+    for w64 in (False, True):
+        qs = primes_for(orc, 1 << 17, w64, 1)
+        roundtrip_check(nt, orc, 1 << 17, qs, 1, "fused", w64=w64, seed=9)
+
+
+def test_check_flag_reports_out_of_range(nt, orc):
+    N, qs = 1024, [12289]
+    host = ntt_synth.rns_batch(5, qs, N, 2)
+    p = Plan(nt, N, qs, "fused", check=True)
+    try:
+        d = to_dev(host, False)
+        p.fwd(d, 2)
+        assert nt.ntt_get_device_status(p.h) == nt.NTT_OK
+        bad = host.copy()
+        bad[1, 0, 77] = 12289
+        d = to_dev(bad, False)
+        p.fwd(d, 2)
+        assert nt.ntt_get_device_status(p.h) == nt.NTT_ERR_INPUT_RANGE
+        # the status is sticky until read, then cleared
+        assert nt.ntt_get_device_status(p.h) == nt.NTT_OK
+    finally:
+        p.close()
+
+
+def test_argument_errors(nt, orc):
+    p = Plan(nt, 1024, [12289], "fused")
+    try:
+        d = torch.zeros(4 * 1024 + 4, dtype=torch.int32, device="cuda")
+        with pytest.raises(nt.NttError) as e:
+            nt.ntt_forward(p.h, d.data_ptr() + 4, 1)
+        assert e.value.status == nt.NTT_ERR_ALIGNMENT
+        with pytest.raises(nt.NttError) as e:
+            nt.ntt_forward(p.h, d, 0)
+        assert e.value.status == nt.NTT_ERR_INVALID_ARG
+        with pytest.raises(nt.NttError) as e:
+            nt.ntt_pointwise_mul(p.h, d, d.data_ptr() + 8, d, 1)
+        assert e.value.status == nt.NTT_ERR_ALIGNMENT
+    finally:
+        p.close()
+
+
+def test_pointwise_aliasing_and_reductions(nt, orc):
+    N = 1 << 12
+    for w64 in (False, True):
+        qs = primes_for(orc, N, w64, 3)
+        a = ntt_synth.rns_batch(11, qs, N, 2)
+        b = ntt_synth.rns_batch(12, qs, N, 2)
+        want = orc.pointwise_batch(a, b, qs)
+        for red in ("shoup", "barrett", "montgomery"):
+            p = Plan(nt, N, qs, "fused", red, w64)
+            try:
+                da, db = to_dev(a, w64), to_dev(b, w64)
+                nt.ntt_pointwise_mul(p.h, db, da, db, 2)     # c aliases b
+                assert np.array_equal(to_host(db, w64, a.shape), want), (red, w64)
+            finally:
+                p.close()
+
+
+def test_pointwise_edge_values(nt, orc):
+    """Products of q-1, q-2, 1, 0 and (q-1)/2 with each other, every reduction."""
+    N = 1024
+    for w64 in (False, True):
+        qs = primes_for(orc, N, w64, 2)
+        edge = lambda q: [0, 1, 2, q - 1, q - 2, (q - 1) // 2, (q + 1) // 2, q // 3]
+        a = np.zeros((1, 2, N), np.uint64)
+        b = np.zeros((1, 2, N), np.uint64)
+        for l, q in enumerate(qs):
+            e = edge(q)
+            pairs = [(x, y) for x in e for y in e]
+            for i, (x, y) in enumerate(pairs):
+                a[0, l, i], b[0, l, i] = x, y
+        want = orc.pointwise_batch(a, b, qs)
+        for red in ("shoup", "barrett", "montgomery"):
+            p = Plan(nt, N, qs, "fused", red, w64)
+            try:
+                da, db = to_dev(a, w64), to_dev(b, w64)
+                nt.ntt_pointwise_mul(p.h, da, da, db, 1)
+                assert np.array_equal(to_host(da, w64, a.shape), want), (red, w64)
+            finally:
+                p.close()
+
+
+def test_extreme_inputs_all_q_minus_1(nt, orc):
+    """Inputs at q-1 everywhere drive the lazy butterflies to their bounds."""
+    for w64 in (False, True):
+        N = 1 << 16
+        qs = primes_for(orc, N, w64, 2)
+        host = np.zeros((2, 2, N), np.uint64)
+        for l, q in enumerate(qs):
+            host[:, l, :] = q - 1
+        psis = [orc.psi(q, N) for q in qs]
+        want = orc.ntt_batch(host, qs, psis)
+        for red in ("shoup", "barrett", "montgomery"):
+            p = Plan(nt, N, qs, "fused", red, w64)
+            try:
+                d = to_dev(host, w64)
+                p.fwd(d, 2)
+                assert np.array_equal(to_host(d, w64, host.shape), want), (red, w64)
+                p.inv(d, 2)
+                assert np.array_equal(to_host(d, w64, host.shape), host), (red, w64)
+            finally:
+                p.close()
+
+
+def test_polymul_host_entry(nt, orc):
+    """The host-buffer entry point: copies, transforms and products in one call."""
+    N, pairs = 2048, 3
+    qs = primes_for(orc, N, False, 2)
+    host = ntt_synth.rns_batch(21, qs, N, 2 * pairs).astype(np.uint32)
+    p = Plan(nt, N, qs, "fused", bitrev=True)
+    try:
+        h_in = torch.from_numpy(host.view(np.int32).copy()).pin_memory()
+        h_out = torch.zeros(pairs * 2 * N, dtype=torch.int32).pin_memory()
+        work = torch.empty(2 * pairs * 2 * N, dtype=torch.int32, device="cuda")
+        nt.ntt_polymul_host(p.h, h_out, h_in, work, pairs)
+        torch.cuda.synchronize()
+        got = h_out.numpy().view(np.uint32).reshape(pairs, 2, N)
+    finally:
+        p.close()
+    for i in range(pairs):
+        for l in range(2):
+            assert np.array_equal(got[i, l].astype(np.uint64),
+                                  orc.negacyclic_mul(host[i, l], host[pairs + i, l], qs[l]))
+
+
+def test_two_streams(nt, orc):
+    N = 1 << 14
+    qs = primes_for(orc, N, False, 2)
+    psis = [orc.psi(q, N) for q in qs]
+    h1 = ntt_synth.rns_batch(31, qs, N, 4)
+    h2 = ntt_synth.rns_batch(32, qs, N, 4)
+    p1 = Plan(nt, N, qs, "fused")
+    p2 = Plan(nt, N, qs, "stockham")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    try:
+        d1, d2 = to_dev(h1, False), to_dev(h2, False)
+        torch.cuda.synchronize()
+        for _ in range(3):
+            nt.ntt_forward(p1.h, d1, 4, s1)
+            nt.ntt_forward(p2.h, d2, 4, s2)
+            nt.ntt_inverse(p1.h, d1, 4, s1)
+            nt.ntt_inverse(p2.h, d2, 4, s2)
+        nt.ntt_forward(p1.h, d1, 4, s1)
+        nt.ntt_forward(p2.h, d2, 4, s2)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(d1, False, h1.shape), orc.ntt_batch(h1, qs, psis))
+        assert np.array_equal(to_host(d2, False, h2.shape), orc.ntt_batch(h2, qs, psis))
+    finally:
+        p1.close()
+        p2.close()

@@ -161,6 +161,17 @@ def test_delta_closed_forms(orc, q, N):
     assert np.all(orc.ntt_fwd(c, q, psi) == 1234 % q)
 
 
+def test_negacyclic_coefficient_matches_full_product(orc):
+    rng = random.Random(4)
+    for q, N in [(17, 4), (12289, 64), (1152921504606830593, 32)]:
+        a, b = _rand(rng, q, N), _rand(rng, q, N)
+        c = orc.negacyclic_mul(a, b, q)
+        for j in range(N):
+            assert orc.negacyclic_mul_at(a, b, q, j) == int(c[j])
+    g = _read_golden("q17_n4.txt")
+    assert [orc.negacyclic_mul_at(g["a"], g["b"], 17, j) for j in range(4)] == g["c"]
+
+
 def test_negacyclic_wrap(orc):
     q, N = 12289, 16
     a = np.zeros(N, np.uint64)
