@@ -30,7 +30,7 @@ ALL_VARIANTS = ["dit", "dif", "flat", "pease", "pease_nc", "stockham", "sixstep"
 
 def to_dev(host, w64):
     a = np.ascontiguousarray(host.astype(np.uint64 if w64 else np.uint32))
-    return torch.from_numpy(a.view(np.int64 if w64 else np.int32).copy()).cuda()
+    return torch.from_numpy(a.view(np.int64 if w64 else np.int32).reshape(-1).copy()).cuda()
 
 
 def to_host(t, w64, shape):
