@@ -59,7 +59,9 @@ typedef enum {
     NTT_ERR_INPUT_RANGE = 10,       /* NTT_CHECK: an input word was >= q */
     NTT_ERR_TIMEOUT = 11,           /* a bounded device wait ran out */
     NTT_ERR_UNSUPPORTED = 12,       /* valid request this build cannot serve */
-    NTT_ERR_PSI = 13                /* caller psi is not a primitive 2N-th root */
+    NTT_ERR_PSI = 13,               /* caller psi is not a primitive 2N-th root */
+    NTT_ERR_SCRATCH_LIMIT = 14      /* ntt_forward_noalloc: batch needs more
+                                       than its fixed scratch array */
 } ntt_status;
 
 /* Dataflow variants of Sec. II.  All produce bit-identical results. */
@@ -148,6 +150,32 @@ ntt_status ntt_pointwise_mul(ntt_plan_t plan, void *d_c, const void *d_a,
  */
 ntt_status ntt_polymul_host(ntt_plan_t plan, void *h_out, const void *h_in,
                             void *d_work, uint32_t pairs, ntt_stream_t stream);
+
+/*
+ * Forward transform that allocates nothing (the paper has no counterpart;
+ * this is a deployment aid).  For callers that must not allocate device
+ * memory -- a framework that owns all device memory through its own pool, a
+ * latency-bound loop that cannot afford cudaMalloc's implicit device
+ * synchronisation, a plugin under a fixed memory budget -- it runs the
+ * forward transform with the Stockham dataflow (Sec. II) using, as its
+ * ping-pong buffer, a fixed 8 MiB device array that is part of the library
+ * (held by every GPU that loads the library until the process exits).  The
+ * caller passes the data; no cudaMalloc, cudaFree or other allocating call
+ * is made.  Same result and order as ntt_forward on the same plan.
+ *   - Plans with the fused variant and N >= 16 have no per-stage tables:
+ *     NTT_ERR_UNSUPPORTED.
+ *   - batch * L * N * word bytes must not exceed 8 MiB, else
+ *     NTT_ERR_SCRATCH_LIMIT (e.g. at most one 32-limb polynomial of 2^16
+ *     u32 words per call).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before any
+ *     stream capture.
+ *   - All calls share the array and it keeps the last call's contents
+ *     (nothing in it needs to start at zero); calls whose work overlaps on
+ *     the GPU race on it.
+ */
+ntt_status ntt_forward_noalloc(ntt_plan_t plan, void *d_data, uint32_t batch,
+                               ntt_stream_t stream);
 
 /* Synchronise `stream`, then return and clear the plan's sticky device
  * status (NTT_OK, NTT_ERR_INPUT_RANGE or NTT_ERR_TIMEOUT). */

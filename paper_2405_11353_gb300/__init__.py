@@ -24,7 +24,7 @@ STATUS_NAMES = {
     3: "NTT_ERR_N_RANGE", 4: "NTT_ERR_Q_NOT_PRIME", 5: "NTT_ERR_Q_NOT_NTT_FRIENDLY",
     6: "NTT_ERR_Q_WIDTH", 7: "NTT_ERR_ALIGNMENT", 8: "NTT_ERR_CUDA", 9: "NTT_ERR_OOM",
     10: "NTT_ERR_INPUT_RANGE", 11: "NTT_ERR_TIMEOUT", 12: "NTT_ERR_UNSUPPORTED",
-    13: "NTT_ERR_PSI",
+    13: "NTT_ERR_PSI", 14: "NTT_ERR_SCRATCH_LIMIT",
 }
 for _v, _n in STATUS_NAMES.items():
     globals()[_n] = _v
@@ -52,6 +52,7 @@ EXPORTS = [
     "ntt_get_device_status", "ntt_plan_get_psi", "ntt_plan_last_launches",
     "ntt_status_string", "ntt_validate", "ntt_default_psi", "ntt_find_primes",
     "ntt_ragged_create", "ntt_ragged_launch", "ntt_ragged_status", "ntt_ragged_destroy",
+    "ntt_forward_noalloc",
 ]
 
 
@@ -100,6 +101,7 @@ def lib():
             "ntt_ragged_launch": (st, [vp, vp]),
             "ntt_ragged_status": (st, [vp, vp]),
             "ntt_ragged_destroy": (None, [vp]),
+            "ntt_forward_noalloc": (st, [vp, vp, u32, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -218,6 +220,13 @@ def ntt_find_primes(bits, m, count):
     out = (ctypes.c_uint64 * count)()
     _check(lib().ntt_find_primes(bits, m, count, out), "ntt_find_primes")
     return [int(v) for v in out]
+
+
+def ntt_forward_noalloc(plan, data, batch, stream=None):
+    """Forward transform that allocates nothing (fixed 8 MiB scratch array in
+    the library), for callers that must not allocate device memory."""
+    _check(lib().ntt_forward_noalloc(plan, _ptr(data), batch, _stream(stream)),
+           "ntt_forward_noalloc")
 
 
 def ntt_ragged_create(jobs, flags=0):

@@ -262,6 +262,7 @@ const char *ntt_status_string(ntt_status s) {
     case NTT_ERR_TIMEOUT: return "NTT_ERR_TIMEOUT: bounded device wait expired";
     case NTT_ERR_UNSUPPORTED: return "NTT_ERR_UNSUPPORTED: not supported by this build";
     case NTT_ERR_PSI: return "NTT_ERR_PSI: psi is not a primitive 2N-th root of unity";
+    case NTT_ERR_SCRATCH_LIMIT: return "NTT_ERR_SCRATCH_LIMIT: batch exceeds the fixed 8 MiB scratch array";
     }
     return "NTT_ERR_UNKNOWN";
 }
