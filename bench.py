@@ -120,6 +120,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def max_over_ranks(x, dist=None, device=None):
+    """The largest of each rank's x (timings are taken as the slowest rank)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_step_per_rank, world, steps, elapsed_ms):
+    """Whole-job throughput: units every rank processed / the slowest time."""
+    return units_per_step_per_rank * world * steps / (elapsed_ms / 1000.0)
+
+
 # ----------------------------------------------------------------- oracle arm
 def oracle_sample(qs, seconds=12.0, max_reps=50):
     """The CPU oracle (O(N log N) path, OpenMP over transforms) running the
@@ -282,12 +297,9 @@ def main():
     fwd_ms = statistics.mean(ev[i][0].elapsed_time(ev[i][1]) for i in range(K))
     pw_ms = statistics.mean(ev[i][1].elapsed_time(ev[i][2]) for i in range(K))
     inv_ms = statistics.mean(ev[i][2].elapsed_time(ev[i][3]) for i in range(K))
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dist if world > 1 else None, dev)
     ms_per_step = elapsed_ms / K
-    value = NTT_PER_STEP * world * K / (elapsed_ms / 1000.0)
+    value = job_rate(NTT_PER_STEP, world, K, elapsed_ms)
 
     # ---------------- end to end through the host-buffer entry point
     h_in = pinned
@@ -306,12 +318,8 @@ def main():
         nt.ntt_polymul_host(plan, h_out, h_in, work, PAIRS, sh)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = NTT_PER_STEP * world * Ke / (e2e_ms / 1000.0)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist if world > 1 else None, dev)
+    e2e_value = job_rate(NTT_PER_STEP, world, Ke, e2e_ms)
 
     # ---------------- roofline of the forward transform (dominant call)
     peak, peak_kind = peaks()

@@ -21,6 +21,7 @@
 // large NTT into several smaller ones ... fit into a cache") with the
 // inter-step twiddles absorbed by the merged table.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -35,10 +36,12 @@ template <class W> struct FArgs {
     W *data;
     const Tw<W> *tw;          // [L][N] table of this pass
     const LimbConst *lc;
+    uint32_t *status;         // plan status word (bit 1: timeout)
     uint64_t ntrans;          // batch * L
     uint64_t ntiles;
     uint32_t logN, L, logK, s2;   // N2 = 2^s2 (cols / chunks)
     uint32_t final_pass;      // fully reduce output; inverse: fold N^-1
+    CUtensorMap tmap;         // column passes: the data as rows of N2 words
 };
 
 // ---------------------------------------------------- shared-memory layout
@@ -61,148 +64,289 @@ template <class W> __host__ __device__ constexpr uint32_t cols_phys(uint32_t k, 
     return k + K * (u + (u >> 4));
 }
 
-template <class W, int LOGS, int KIND> __host__ constexpr size_t fused_smem_bytes(uint32_t K) {
-    return KIND == TK_COLS ? (size_t)K * ((1u << LOGS) + (1u << LOGS) / 16) * sizeof(W)
-                           : (size_t)K * rows_pitch<W, LOGS>() * sizeof(W);
+template <class W, int LOGS, int KIND> __host__ constexpr size_t fused_smem_bytes();
+
+// Sub-transforms per CTA (compile-time, so every shared-memory address is
+// a per-round base plus an immediate offset): single-pass tiles hold 4096
+// words (or one transform above that), column strips 16 (4-byte) or 8
+// (8-byte) columns and at least 256 threads, chunk tiles 16 chunks.
+template <class W, int LOGS, int KIND> __host__ __device__ constexpr uint32_t tile_k() {
+    return KIND == TK_SINGLE ? (LOGS >= 12 ? 1u : (4096u >> LOGS))
+         : KIND == TK_CHUNKS ? 16u
+         : ((256u >> (LOGS - 4)) > (sizeof(W) == 4 ? 16u : 8u) ? (256u >> (LOGS - 4))
+                                                               : (sizeof(W) == 4 ? 16u : 8u));
 }
 
-// word index u of slot e for a round covering bits [LO, LO+RR) of the
-// sub-transform index, thread tau of the sub-transform
-template <int LOGS, int LO, int RR> __device__ __forceinline__ uint32_t slot_u(uint32_t tau, int e) {
-    if (RR == 4) {
-        return (tau & ((1u << LO) - 1)) | ((uint32_t)e << LO) | ((tau >> LO) << (LO + 4));
+// Round J of a sub-transform covers bits [LO, LO+RR) of the index u.
+// Forward: from the top down with the short round (LOGS mod 4 bits) first;
+// inverse: from the bottom up with the short round last.  Thread tau holds
+// the 16 words u = A(tau) | E(e), e = 0..15, where E places e's bits on the
+// round's bits (and, in a short round, the spare bits of e just above tau's
+// share) and A places tau's bits elsewhere; A and E are disjoint bit fields,
+// so every layout below maps u to A's address plus a constant for E.
+template <int LOGS, bool INV, int J> struct RoundOf {
+    static constexpr int SHORT = LOGS % 4;
+    static constexpr int NR = (LOGS + 3) / 4;
+    static constexpr int RR = INV ? ((LOGS - 4 * J) < 4 ? (LOGS - 4 * J) : 4) : ((SHORT && J == 0) ? SHORT : 4);
+    static constexpr int LO = INV ? 4 * J : ((SHORT && J == 0) ? LOGS - SHORT : LOGS - SHORT - 4 * J - (SHORT ? 0 : 4));
+    __host__ __device__ static constexpr uint32_t E(int e) {
+        return RR == 4 ? ((uint32_t)e << LO)
+                       : (((uint32_t)e >> RR) | (((uint32_t)e & ((1u << RR) - 1)) << LO));
+    }
+    __device__ static __forceinline__ uint32_t A(uint32_t tau) {
+        return RR == 4 ? ((tau & ((1u << LO) - 1)) | ((tau >> LO) << (LO + 4))) : (tau << (4 - RR));
+    }
+};
+
+// shared-memory word offset of u in sub-transform k (linear in u's bits)
+template <class W, int LOGS, int KIND> __host__ __device__ constexpr uint32_t sm_off(uint32_t k, uint32_t u) {
+    return KIND == TK_COLS ? cols_phys<W>(k, u, tile_k<W, LOGS, KIND>()) : k * rows_pitch<W, LOGS>() + pu<W>(u);
+}
+
+// The 2^(RR-1-d) distinct twiddles of stage d (bit LO+d) for this thread,
+// consecutive in the table from index `first`; first is a multiple of the
+// count, so they move as 16-byte vectors.
+template <class W, int CNT> __device__ __forceinline__ void load_tw(Tw<W> (&t)[8], const Tw<W> *__restrict__ p) {
+    if (sizeof(W) == 4) {
+        if (CNT == 1) {
+            uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+            t[0].w = (W)v.x; t[0].c = (W)v.y;
+        } else {
+#pragma unroll
+            for (int i = 0; i < CNT / 2; ++i) {
+                uint4 v = __ldg(reinterpret_cast<const uint4 *>(p) + i);
+                t[2 * i].w = (W)v.x; t[2 * i].c = (W)v.y;
+                t[2 * i + 1].w = (W)v.z; t[2 * i + 1].c = (W)v.w;
+            }
+        }
     } else {
-        // short round, always the top bits: LO = LOGS - RR
-        uint32_t o = (tau << (4 - RR)) | ((uint32_t)e >> RR);
-        return o | (((uint32_t)e & ((1u << RR) - 1)) << LO);
+#pragma unroll
+        for (int i = 0; i < CNT; ++i) {
+            ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(p) + i);
+            t[i].w = (W)v.x; t[i].c = (W)v.y;
+        }
     }
 }
 
-template <class W, int RED, bool INV, int LOGS, int LO, int RR>
+template <class W, int RED, bool INV, int LOGS, int J>
 __device__ __forceinline__ void round_bfly(W (&x)[16], uint32_t tau, const Tw<W> *__restrict__ tw, const Lc<W> &k,
                                            bool last_pass, Tw<W> tn, Tw<W> twn) {
+    using R = RoundOf<LOGS, INV, J>;
+    constexpr int RR = R::RR, LO = R::LO;
     constexpr uint32_t S = 1u << LOGS;
-    if (!INV) {
+    // twiddle index of the butterfly on slots (e, e | 2^d) at stage d:
+    // (S >> (LO+d+1)) + (tau's part) + (e_low >> (d+1))
 #pragma unroll
-        for (int d = RR - 1; d >= 0; --d) {
-            const int b = LO + d;
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                if (e & (1 << d)) continue;
-                uint32_t u = slot_u<LOGS, LO, RR>(tau, e);
-                uint32_t idx = (S >> (b + 1)) + (u >> (b + 1));
-                ct_bfly<RED, W>(x[e], x[e | (1 << d)], ldtw(tw + idx), k);
+    for (int dd = 0; dd < RR; ++dd) {
+        const int d = INV ? dd : RR - 1 - dd;
+        const int b = LO + d;
+        Tw<W> t[8];
+        const bool fold = INV && b == LOGS - 1 && last_pass;
+        if (!fold) {
+            uint32_t first = (S >> (b + 1)) + (RR == 4 ? ((tau >> LO) << (3 - d)) : 0u);
+            const int cnt = 1 << (RR - 1 - d);
+            switch (cnt) {
+            case 1: load_tw<W, 1>(t, tw + first); break;
+            case 2: load_tw<W, 2>(t, tw + first); break;
+            case 4: load_tw<W, 4>(t, tw + first); break;
+            default: load_tw<W, 8>(t, tw + first); break;
             }
         }
-    } else {
 #pragma unroll
-        for (int d = 0; d < RR; ++d) {
-            const int b = LO + d;
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                if (e & (1 << d)) continue;
-                uint32_t u = slot_u<LOGS, LO, RR>(tau, e);
-                if (b == LOGS - 1 && last_pass) {
-                    gs_bfly_last<RED, W>(x[e], x[e | (1 << d)], tn, twn, k);
-                } else {
-                    uint32_t idx = (S >> (b + 1)) + (u >> (b + 1));
-                    gs_bfly<RED, W>(x[e], x[e | (1 << d)], ldtw(tw + idx), k);
-                }
+        for (int e = 0; e < 16; ++e) {
+            if (e & (1 << d)) continue;
+            const int j = (e & ((1 << RR) - 1)) >> (d + 1);
+            if (!INV) {
+                ct_bfly<RED, W>(x[e], x[e | (1 << d)], t[j], k);
+            } else if (fold) {
+                gs_bfly_last<RED, W>(x[e], x[e | (1 << d)], tn, twn, k);
+            } else {
+                gs_bfly<RED, W>(x[e], x[e | (1 << d)], t[j], k);
             }
         }
     }
 }
 
-template <class W, int LOGS, int KIND> __device__ __forceinline__ uint32_t sm_addr(uint32_t k, uint32_t u, uint32_t K) {
-    if (KIND == TK_COLS) return cols_phys<W>(k, u, K);
-    return k * rows_pitch<W, LOGS>() + pu<W>(u);
+template <class W, bool WARP_SYNC> __device__ __forceinline__ void tile_sync() {
+    if (WARP_SYNC) __syncwarp();
+    else __syncthreads();
 }
 
-// One round: load 16 slots from shared memory, apply the stages, store back.
-template <class W, int RED, bool INV, int LOGS, int KIND, int LO, int RR>
-__device__ __forceinline__ void do_round(W *sm, uint32_t k, uint32_t tau, uint32_t K, const Tw<W> *__restrict__ tw,
-                                         const Lc<W> &kk, bool last_pass, Tw<W> tn, Tw<W> twn) {
-    W x[16];
-#pragma unroll
-    for (int e = 0; e < 16; ++e) x[e] = sm[sm_addr<W, LOGS, KIND>(k, slot_u<LOGS, LO, RR>(tau, e), K)];
-    round_bfly<W, RED, INV, LOGS, LO, RR>(x, tau, tw, kk, last_pass, tn, twn);
-#pragma unroll
-    for (int e = 0; e < 16; ++e) sm[sm_addr<W, LOGS, KIND>(k, slot_u<LOGS, LO, RR>(tau, e), K)] = x[e];
-}
+// ------------------------------------------------ TMA / mbarrier helpers
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Rounds of a sub-transform.  Forward: bits from the top down, the short
-// round (LOGS mod 4 bits) first; inverse: from the bottom up, short last.
-template <class W, int RED, bool INV, int LOGS, int KIND, int J>
-__device__ __forceinline__ void all_rounds(W *sm, uint32_t k, uint32_t tau, uint32_t K, const Tw<W> *__restrict__ tw,
-                                           const Lc<W> &kk, bool last_pass, Tw<W> tn, Tw<W> twn) {
-    constexpr int NR = (LOGS + 3) / 4;
-    if constexpr (J < NR) {
-        constexpr int SHORT = LOGS % 4;
-        constexpr int RR = INV ? ((LOGS - 4 * J) < 4 ? (LOGS - 4 * J) : 4) : ((SHORT && J == 0) ? SHORT : 4);
-        constexpr int LO = INV ? 4 * J
-                               : ((SHORT && J == 0) ? LOGS - SHORT : LOGS - SHORT - 4 * J - (SHORT ? 0 : 4));
-        do_round<W, RED, INV, LOGS, KIND, LO, RR>(sm, k, tau, K, tw, kk, last_pass, tn, twn);
-        __syncthreads();
-        all_rounds<W, RED, INV, LOGS, KIND, J + 1>(sm, k, tau, K, tw, kk, last_pass, tn, twn);
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for phase `parity` of the barrier, giving up after about 2^31 SM
+// cycles (about a second): returns false then, and the caller reports
+// NTT_ERR_TIMEOUT instead of hanging the GPU.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > (1ll << 31)) return false;
+    return true;
+}
+// 1-D bulk copy global -> shared, completing on `bar` (16-byte aligned
+// addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+// 2-D tiled tensor copy global -> shared of the box at (x, y).
+__device__ __forceinline__ void tma_2d_g2s(void *dst, const void *tmap, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_addr(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// Rounds J = 1 .. NR-1 of one sub-transform (round 0 is done by the caller
+// on the words read from the staged tile); rounds exchange through the
+// padded shared-memory buffer `xs`.
+template <class W, int RED, bool INV, int LOGS, int KIND, bool WS, int J>
+__device__ __forceinline__ void later_rounds(W (&x)[16], W *xs, uint32_t smb_k, uint32_t tau,
+                                             const Tw<W> *__restrict__ tw, const Lc<W> &kk, bool last_pass,
+                                             Tw<W> tn, Tw<W> twn) {
+    using R = RoundOf<LOGS, INV, J>;
+    if constexpr (J < R::NR) {
+        using RP = RoundOf<LOGS, INV, J - 1>;
+        {
+            const uint32_t base = smb_k + sm_off<W, LOGS, KIND>(0, RP::A(tau));
+            if (J > 1) tile_sync<W, WS>();   // readers of the previous exchange are done
+#pragma unroll
+            for (int e = 0; e < 16; ++e) xs[base + sm_off<W, LOGS, KIND>(0, RP::E(e))] = x[e];
+        }
+        tile_sync<W, WS>();
+        {
+            const uint32_t base = smb_k + sm_off<W, LOGS, KIND>(0, R::A(tau));
+#pragma unroll
+            for (int e = 0; e < 16; ++e) x[e] = xs[base + sm_off<W, LOGS, KIND>(0, R::E(e))];
+        }
+        round_bfly<W, RED, INV, LOGS, J>(x, tau, tw, kk, last_pass, tn, twn);
+        later_rounds<W, RED, INV, LOGS, KIND, WS, J + 1>(x, xs, smb_k, tau, tw, kk, last_pass, tn, twn);
     }
 }
 
+// Pipeline depth: tiles of up to 16 KiB get three buffers, larger ones two.
+template <class W, int LOGS, int KIND> __host__ __device__ constexpr uint32_t tile_words() {
+    return tile_k<W, LOGS, KIND>() << LOGS;
+}
+template <class W, int LOGS, int KIND> __host__ __device__ constexpr uint32_t n_stages() {
+    return tile_words<W, LOGS, KIND>() * sizeof(W) <= 16384 ? 3u : 2u;
+}
+template <class W, int LOGS, int KIND> __host__ __device__ constexpr size_t xchg_bytes() {
+    return KIND == TK_COLS ? (size_t)tile_k<W, LOGS, KIND>() * ((1u << LOGS) + (1u << LOGS) / 16) * sizeof(W)
+                           : (size_t)tile_k<W, LOGS, KIND>() * rows_pitch<W, LOGS>() * sizeof(W);
+}
+
+// Persistent fused pass.  CTA c processes tiles [c T / G, (c+1) T / G) in
+// order; one thread keeps n_stages() tiles in flight with TMA copies into
+// shared memory (1-D bulk copies of contiguous rows tiles, 2-D tensor
+// copies of column strips), completing on one mbarrier per buffer.  Tiles
+// of the two-pass kinds are ordered polynomial-fastest, so consecutive tiles
+// of a CTA reuse the same twiddles from the L1/L2 caches.
 template <class W, int RED, bool INV, int LOGS, int KIND>
 __global__ void __launch_bounds__(sizeof(W) == 4 ? 1024 : 512)
-k_fused(FArgs<W> a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    W *sm = reinterpret_cast<W *>(smem_raw);
+k_fused(const __grid_constant__ FArgs<W> a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     constexpr uint32_t S = 1u << LOGS;
     constexpr uint32_t T = S / 16;
-    constexpr int V = 16 / sizeof(W);
-    using Vec = typename std::conditional<sizeof(W) == 4, uint4, ulonglong2>::type;
-    const uint32_t K = 1u << a.logK;
+    constexpr uint32_t K = tile_k<W, LOGS, KIND>();
+    constexpr uint32_t NS = n_stages<W, LOGS, KIND>();
+    constexpr uint32_t TW_ = tile_words<W, LOGS, KIND>();
+    constexpr bool WS = KIND != TK_COLS && T <= 32;
+    using R0 = RoundOf<LOGS, INV, 0>;
+    using RL = RoundOf<LOGS, INV, R0::NR - 1>;
+    // layout: NS stage buffers (1 KiB aligned), exchange buffer, barriers
+    W *stage = reinterpret_cast<W *>(smem_raw);
+    W *xs = stage + (size_t)NS * TW_;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(xs) +
+                                                 ((xchg_bytes<W, LOGS, KIND>() + 15) & ~size_t(15)));
+    uint32_t &s_abort = *reinterpret_cast<uint32_t *>(bar + NS);
+
     const uint32_t N = 1u << a.logN;
     const uint32_t tid = threadIdx.x;
-    const uint32_t nthr = K * T;
+    uint32_t k, tau;
+    if (KIND == TK_COLS) { k = tid % K; tau = tid / K; }
+    else { tau = tid % T; k = tid / T; }
+    const uint32_t smb_k = sm_off<W, LOGS, KIND>(k, 0);
+    const uint32_t L = a.L;
+    const uint64_t B = a.ntrans / L;
+    const uint32_t per = KIND == TK_SINGLE ? 1u : (KIND == TK_COLS ? (1u << a.s2) : (N >> a.s2)) / K;
+    const uint64_t t_begin = blockIdx.x * a.ntiles / gridDim.x;
+    const uint64_t t_end = (blockIdx.x + 1) * a.ntiles / gridDim.x;
 
-    for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-        // ---------------------------------------------------- tile decode
-        uint64_t t;            // transform of sub 0 (single) / of the tile
-        uint32_t pos0 = 0;     // first column (cols) or chunk (chunks)
+    // tile -> (first transform, column / chunk position)
+    auto decode = [&](uint64_t tile, uint64_t &t, uint32_t &pos0) {
         if (KIND == TK_SINGLE) {
-            t = tile << a.logK;
+            t = tile * K;
+            pos0 = 0;
         } else {
-            const uint32_t per = (KIND == TK_COLS ? (N >> (a.logN - a.s2)) : (N >> a.s2)) >> a.logK;
-            t = tile / per;
-            pos0 = (uint32_t)(tile % per) << a.logK;
+            const uint64_t p = tile % B;
+            const uint64_t r = tile / B;
+            const uint32_t l = (uint32_t)(r / per);
+            pos0 = (uint32_t)(r % per) * K;
+            t = p * L + l;
         }
-        // ---------------------------------------------------- load tile
+    };
+    auto issue = [&](uint64_t tile, uint32_t s) {
+        uint64_t t;
+        uint32_t pos0;
+        decode(tile, t, pos0);
+        W *dst = stage + (size_t)s * TW_;
         if (KIND == TK_COLS) {
-            const W *g = a.data + t * N + pos0;
-            const uint32_t vpr = K / V;   // vectors per row of the strip
-            for (uint32_t i = tid; i < S * vpr; i += nthr) {
-                uint32_t u = i / vpr, kv = (i % vpr) * V;
-                Vec v = *reinterpret_cast<const Vec *>(g + ((size_t)u << a.s2) + kv);
-                *reinterpret_cast<Vec *>(sm + cols_phys<W>(kv, u, K)) = v;
-            }
+            const uint32_t rows = S < 256 ? S : 256u;
+            mbar_expect_tx(&bar[s], TW_ * (uint32_t)sizeof(W));
+            for (uint32_t r0 = 0; r0 < S; r0 += rows)
+                tma_2d_g2s(dst + r0 * K, &a.tmap, (int)pos0, (int)(t * (N >> a.s2) + r0), &bar[s]);
         } else {
-            const uint32_t vps = S / V;
-            for (uint32_t i = tid; i < K * vps; i += nthr) {
-                uint32_t k = i / vps, u = (i % vps) * V;
-                const W *g;
-                if (KIND == TK_SINGLE) {
-                    if (t + k >= a.ntrans) continue;
-                    g = a.data + (t + k) * N;
-                } else {
-                    g = a.data + t * N + ((size_t)(pos0 + k) << a.s2);
-                }
-                Vec v = *reinterpret_cast<const Vec *>(g + u);
-                *reinterpret_cast<Vec *>(sm + sm_addr<W, LOGS, KIND>(k, u, K)) = v;
-            }
+            uint64_t nval = KIND == TK_SINGLE ? (a.ntrans - t < K ? a.ntrans - t : K) : K;
+            const W *src = KIND == TK_SINGLE ? a.data + t * N : a.data + t * N + ((size_t)pos0 << a.s2);
+            uint32_t bytes = (uint32_t)(nval * S * sizeof(W));
+            mbar_expect_tx(&bar[s], bytes);
+            bulk_g2s(dst, src, bytes, &bar[s]);
         }
-        __syncthreads();
-        // ---------------------------------------------------- compute
-        uint32_t k, tau;
-        if (KIND == TK_COLS) { k = tid % K; tau = tid / K; }
-        else { tau = tid % T; k = tid / T; }
-        const uint64_t tk = KIND == TK_SINGLE ? t + k : t;
-        const uint32_t l = (uint32_t)((tk < a.ntrans ? tk : 0) % a.L);
+    };
+
+    if (tid == 0) {
+        s_abort = 0;
+        for (uint32_t s = 0; s < NS; ++s) mbar_init(&bar[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (uint32_t s = 0; s < NS && t_begin + s < t_end; ++s) issue(t_begin + s, s);
+
+    uint32_t i = 0;
+    for (uint64_t tile = t_begin; tile < t_end; ++tile, ++i) {
+        const uint32_t s = i % NS;
+        const uint32_t parity = (i / NS) & 1u;
+        uint64_t t0;
+        uint32_t pos0;
+        decode(tile, t0, pos0);
+        const uint64_t t = KIND == TK_SINGLE ? t0 + k : t0;
+        const bool valid = t < a.ntrans;
+        const uint32_t l = (uint32_t)((valid ? t : 0) % L);
         Lc<W> kk;
         kk.load(a.lc + l);
         const Tw<W> *twb = a.tw + (size_t)l * N + (KIND == TK_CHUNKS ? ((size_t)(pos0 + k) << a.s2) : 0);
@@ -211,50 +355,94 @@ k_fused(FArgs<W> a) {
             tn.w = (W)a.lc[l].ninv_w; tn.c = (W)a.lc[l].ninv_c;
             twn.w = (W)a.lc[l].ninv_w1_w; twn.c = (W)a.lc[l].ninv_w1_c;
         }
-        all_rounds<W, RED, INV, LOGS, KIND, 0>(sm, k, tau, K, twb, kk, INV && a.final_pass, tn, twn);
-        // ---------------------------------------------------- store tile
-        if (KIND == TK_COLS) {
-            W *g = a.data + t * N + pos0;
-            const uint32_t vpr = K / V;
-            for (uint32_t i = tid; i < S * vpr; i += nthr) {
-                uint32_t u = i / vpr, kv = (i % vpr) * V;
-                Vec v = *reinterpret_cast<const Vec *>(sm + cols_phys<W>(kv, u, K));
-                if (a.final_pass) {
-                    // the column pass is last only for the inverse
-                    W *pv = reinterpret_cast<W *>(&v);
+        // ---- round 0 from the staged tile
+        const bool ok = mbar_wait_bounded(&bar[s], parity);
+        W x[16];
+        {
+            const W *sb = stage + (size_t)s * TW_;
+            const uint32_t A0 = R0::A(tau);
+            if (KIND == TK_COLS) {
 #pragma unroll
-                    for (int j = 0; j < V; ++j) pv[j] = csub<W>(pv[j], kk.q);
-                }
-                *reinterpret_cast<Vec *>(g + ((size_t)u << a.s2) + kv) = v;
-            }
-        } else {
-            const uint32_t vps = S / V;
-            for (uint32_t i = tid; i < K * vps; i += nthr) {
-                uint32_t k2 = i / vps, u = (i % vps) * V;
-                W *g;
-                Lc<W> k2c = kk;
-                if (KIND == TK_SINGLE) {
-                    if (t + k2 >= a.ntrans) continue;
-                    g = a.data + (t + k2) * N;
-                    k2c.load(a.lc + (uint32_t)((t + k2) % a.L));
-                } else {
-                    g = a.data + t * N + ((size_t)(pos0 + k2) << a.s2);
-                }
-                Vec v = *reinterpret_cast<const Vec *>(sm + sm_addr<W, LOGS, KIND>(k2, u, K));
-                if (a.final_pass) {
-                    W *pv = reinterpret_cast<W *>(&v);
+                for (int e = 0; e < 16; ++e) x[e] = sb[(A0 | R0::E(e)) * K + k];
+            } else if (R0::RR == 4 && R0::LO == 0) {
+                // sixteen consecutive words: four 16-byte loads
+                const W *q = sb + k * S + A0;
 #pragma unroll
-                    for (int j = 0; j < V; ++j) {
-                        W y = pv[j];
-                        if (!INV) y = csub<W>(y, k2c.two_q);
-                        pv[j] = csub<W>(y, k2c.q);
+                for (int v = 0; v < 16 / (16 / (int)sizeof(W)); ++v) {
+                    if (sizeof(W) == 4) {
+                        uint4 w4 = reinterpret_cast<const uint4 *>(q)[v];
+                        x[4 * v] = (W)w4.x; x[4 * v + 1] = (W)w4.y; x[4 * v + 2] = (W)w4.z; x[4 * v + 3] = (W)w4.w;
+                    } else {
+                        ulonglong2 w2 = reinterpret_cast<const ulonglong2 *>(q)[v];
+                        x[2 * v] = (W)w2.x; x[2 * v + 1] = (W)w2.y;
                     }
                 }
-                *reinterpret_cast<Vec *>(g + u) = v;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) x[e] = sb[k * S + (A0 | R0::E(e))];
             }
         }
-        __syncthreads();
+        // every thread has its words: the buffer can be refilled
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) { s_abort = 1; atomicOr(a.status, 2u); }
+            break;
+        }
+        if (tid == 0 && tile + NS < t_end) {
+            fence_proxy_async();
+            issue(tile + NS, s);
+        }
+        round_bfly<W, RED, INV, LOGS, 0>(x, tau, twb, kk, INV && a.final_pass, tn, twn);
+        later_rounds<W, RED, INV, LOGS, KIND, WS, 1>(x, xs, smb_k, tau, twb, kk, INV && a.final_pass, tn, twn);
+        if (a.final_pass) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                W y = x[e];
+                if (!INV) y = csub<W>(y, kk.two_q);
+                x[e] = csub<W>(y, kk.q);
+            }
+        }
+        // ---- last round straight to global memory
+        if (valid) {
+            const uint32_t AL = RL::A(tau);
+            if (KIND == TK_COLS) {
+                W *g = a.data + t * N + pos0 + k;
+#pragma unroll
+                for (int e = 0; e < 16; ++e) g[(size_t)(AL | RL::E(e)) << a.s2] = x[e];
+            } else {
+                W *g = KIND == TK_SINGLE ? a.data + t * N : a.data + t * N + ((size_t)(pos0 + k) << a.s2);
+                if (RL::RR == 4 && RL::LO == 0) {
+                    W *q = g + AL;
+#pragma unroll
+                    for (int v = 0; v < 16 / (16 / (int)sizeof(W)); ++v) {
+                        if (sizeof(W) == 4)
+                            reinterpret_cast<uint4 *>(q)[v] = make_uint4((uint32_t)x[4 * v], (uint32_t)x[4 * v + 1],
+                                                                         (uint32_t)x[4 * v + 2], (uint32_t)x[4 * v + 3]);
+                        else
+                            reinterpret_cast<ulonglong2 *>(q)[v] = make_ulonglong2((unsigned long long)x[2 * v],
+                                                                                   (unsigned long long)x[2 * v + 1]);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) g[AL | RL::E(e)] = x[e];
+                }
+            }
+        }
     }
+    // on an aborted wait, let the copies already in flight (local tiles
+    // i .. i+NS-1) land before the CTA exits, again with a time limit
+    if (s_abort && tid == 0) {
+        const uint64_t n_local = t_end - t_begin;
+        for (uint64_t j = i; j < i + NS && j < n_local; ++j) {
+            const long long t0 = clock64();
+            while (!mbar_try_wait(&bar[j % NS], (uint32_t)(j / NS) & 1u))
+                if (clock64() - t0 > (1ll << 30)) break;
+        }
+    }
+}
+
+template <class W, int LOGS, int KIND> __host__ constexpr size_t fused_smem_bytes() {
+    return (size_t)n_stages<W, LOGS, KIND>() * tile_words<W, LOGS, KIND>() * sizeof(W) +
+           ((xchg_bytes<W, LOGS, KIND>() + 15) & ~size_t(15)) + 8 * 4 + 16;
 }
 
 }  // namespace nttgb

@@ -2,27 +2,63 @@
 // reduction) pair; each fused_<w>_<red>.cu instantiates it once so the
 // kernels compile in parallel.
 #pragma once
+#include <cstring>
+
 #include "fused.cuh"
 #include "plan.hpp"
 
 namespace nttgb {
 
 template <class W, int RED, bool INV, int LOGS, int KIND>
-cudaError_t launch_pass(FArgs<W> a, uint32_t threads, size_t smem, cudaStream_t st) {
+cudaError_t launch_pass(const FArgs<W> &a, uint32_t threads, size_t smem, cudaStream_t st) {
     auto kern = k_fused<W, RED, INV, LOGS, KIND>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    // persistent grid: as many CTAs as fit on the GPU at once
+    static int resident = 0;
+    if (!resident) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)threads, smem);
+        if (e != cudaSuccess) return e;
+        resident = sms * (per_sm > 0 ? per_sm : 1);
     }
-    unsigned grid = a.ntiles > 0x7fffffffull ? 0x7fffffffu : (unsigned)a.ntiles;
+    unsigned grid = a.ntiles < (uint64_t)resident ? (unsigned)a.ntiles : (unsigned)resident;
+    if (grid == 0) grid = 1;
     kern<<<grid, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
+// Tensor map of the data viewed as (ntrans * N1) rows of N2 words, with a
+// box of K columns by min(N1, 256) rows: one column strip of one transform.
+inline cudaError_t make_cols_tmap(CUtensorMap *m, void *data, bool w64, uint64_t rows, uint32_t N2, uint32_t K,
+                                  uint32_t box_rows) {
+    using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeFn encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return cudaErrorNotSupported;
+        encode = reinterpret_cast<EncodeFn>(fn);
+    }
+    const size_t wb = w64 ? 8 : 4;
+    cuuint64_t dims[2] = {N2, rows};
+    cuuint64_t strides[1] = {(cuuint64_t)N2 * wb};
+    cuuint32_t box[2] = {K, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(m, w64 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, data, dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <class W, int RED, bool INV, int KIND, int LOGS = 4>
-cudaError_t pass_dispatch(int logS, FArgs<W> a, uint32_t threads, size_t smem, cudaStream_t st) {
+cudaError_t pass_dispatch(int logS, const FArgs<W> &a, uint32_t threads, size_t smem, cudaStream_t st) {
     constexpr int MAXS = KIND == TK_SINGLE ? (sizeof(W) == 4 ? kSingleMaxLog32 : kSingleMaxLog64)
                                            : (KIND == TK_COLS ? 9 : kChunkLog);
     constexpr int MINS = KIND == TK_SINGLE ? 4 : (KIND == TK_COLS ? 5 : kChunkLog);
@@ -36,9 +72,19 @@ cudaError_t pass_dispatch(int logS, FArgs<W> a, uint32_t threads, size_t smem, c
     }
 }
 
-template <class W, int KIND> size_t smem_for(int logS, uint32_t K) {
+template <class W, int KIND> uint32_t tile_k_for(int logS) {
     switch (logS) {
-#define NTTGB_CASE(s) case s: return fused_smem_bytes<W, s, KIND>(K);
+#define NTTGB_CASE(s) case s: return tile_k<W, s, KIND>();
+        NTTGB_CASE(4) NTTGB_CASE(5) NTTGB_CASE(6) NTTGB_CASE(7) NTTGB_CASE(8) NTTGB_CASE(9)
+        NTTGB_CASE(10) NTTGB_CASE(11) NTTGB_CASE(12) NTTGB_CASE(13) NTTGB_CASE(14)
+#undef NTTGB_CASE
+    }
+    return 1;
+}
+
+template <class W, int KIND> size_t smem_for(int logS) {
+    switch (logS) {
+#define NTTGB_CASE(s) case s: return fused_smem_bytes<W, s, KIND>();
         NTTGB_CASE(4) NTTGB_CASE(5) NTTGB_CASE(6) NTTGB_CASE(7) NTTGB_CASE(8) NTTGB_CASE(9)
         NTTGB_CASE(10) NTTGB_CASE(11) NTTGB_CASE(12) NTTGB_CASE(13) NTTGB_CASE(14)
 #undef NTTGB_CASE
@@ -54,7 +100,9 @@ template <class W, int RED, bool INV, int KIND>
 cudaError_t run_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, int logS, bool final_pass,
                      cudaStream_t st) {
     FArgs<W> a;
+    std::memset(&a, 0, sizeof(a));
     a.data = data;
+    a.status = p.d_status;
     a.tw = reinterpret_cast<const Tw<W> *>(tw);
     a.lc = p.d_limb;
     a.ntrans = ntrans;
@@ -63,21 +111,18 @@ cudaError_t run_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, in
     a.s2 = p.s2;
     a.final_pass = final_pass ? 1u : 0u;
     const uint32_t T = (1u << logS) / 16;
-    uint32_t K;
-    if (KIND == TK_SINGLE) {
-        K = (1u << logS) >= 4096 ? 1u : 4096u >> logS;
-        a.ntiles = (ntrans + K - 1) / K;
-    } else if (KIND == TK_COLS) {
-        K = 256 / T;
-        uint32_t kmin = sizeof(W) == 4 ? 16 : 8;
-        if (K < kmin) K = kmin;
-        a.ntiles = ntrans * ((1u << p.s2) / K);
-    } else {
-        K = 16;
-        a.ntiles = ntrans * ((1u << (p.logN - p.s2)) / K);
-    }
+    const uint32_t K = tile_k_for<W, KIND>(logS);
+    if (KIND == TK_SINGLE) a.ntiles = (ntrans + K - 1) / K;
+    else if (KIND == TK_COLS) a.ntiles = ntrans * ((1u << p.s2) / K);
+    else a.ntiles = ntrans * ((1u << (p.logN - p.s2)) / K);
     a.logK = ilog2(K);
-    size_t smem = smem_for<W, KIND>(logS, K);
+    if (KIND == TK_COLS) {
+        const uint32_t N1 = 1u << logS;
+        cudaError_t e = make_cols_tmap(&a.tmap, data, sizeof(W) == 8, ntrans * N1, 1u << p.s2, K,
+                                       N1 < 256 ? N1 : 256u);
+        if (e != cudaSuccess) return e;
+    }
+    size_t smem = smem_for<W, KIND>(logS);
     ++p.last_launches;
     return pass_dispatch<W, RED, INV, KIND>(logS, a, K * T, smem, st);
 }
