@@ -104,7 +104,15 @@ ntt_status build_tables(ntt_plan_s *p) {
     const size_t tab_bytes = (size_t)L * N * pair_bytes;
     if (variant_tabs) { wf.resize(tab_bytes); wi.resize(tab_bytes); tw.resize(tab_bytes); ut.resize(tab_bytes); }
     if (fused_tabs) { mf.resize(tab_bytes); mi.resize(tab_bytes); }
-    if (chunk_tabs) { cf.resize(tab_bytes); ci.resize(tab_bytes); }
+    const uint32_t N1 = 1u << p->s1, N2 = 1u << p->s2;
+    const uint32_t CP = w64 ? nttgb::chunk_tab_pitch<uint64_t>() : nttgb::chunk_tab_pitch<uint32_t>();
+    const size_t chunk_limb = (size_t)N1 * CP;       // pairs per limb, chunk tables
+    if (chunk_tabs) { cf.resize(L * chunk_limb * pair_bytes); ci.resize(L * chunk_limb * pair_bytes); }
+    // main-table position of entry i (see level_pos in modarith.cuh)
+    auto main_pos = [&](uint32_t i) -> uint32_t {
+        if (p->fused_mode == nttgb::FUSED_SINGLE) return nttgb::level_pos(i, n);
+        return i < N1 ? nttgb::level_pos(i, p->s1) : i;
+    };
 
     std::vector<uint64_t> pw(N), pwi(N);
     for (uint32_t l = 0; l < L; ++l) {
@@ -149,20 +157,26 @@ ntt_status build_tables(ntt_plan_s *p) {
         if (fused_tabs) {
             for (uint32_t i = 0; i < N; ++i) {
                 uint32_t r = H::bitrev(i, (int)n);
-                enc(pw[r], v, cc); put_pair(mf, base + i, v, cc, w64);
-                enc(pwi[r], v, cc); put_pair(mi, base + i, v, cc, w64);
+                enc(pw[r], v, cc); put_pair(mf, base + main_pos(i), v, cc, w64);
+                enc(pwi[r], v, cc); put_pair(mi, base + main_pos(i), v, cc, w64);
             }
         }
         if (chunk_tabs) {
-            const uint32_t N1 = 1u << p->s1, N2 = 1u << p->s2;
+            // chunk r of the second pass: local entry 2^s + i' is global
+            // entry 2^s (N1 + r) + i' of the bit-reversed psi table
+            const size_t cbase = (size_t)l * chunk_limb;
             for (uint32_t r = 0; r < N1; ++r) {
-                put_pair(cf, base + (size_t)r * N2, 0, 0, w64);
-                put_pair(ci, base + (size_t)r * N2, 0, 0, w64);
+                for (uint32_t j = CP - 1; j >= 1 && j >= N2; --j) {
+                    put_pair(cf, cbase + (size_t)r * CP + j, 0, 0, w64);
+                    put_pair(ci, cbase + (size_t)r * CP + j, 0, 0, w64);
+                }
+                put_pair(cf, cbase + (size_t)r * CP, 0, 0, w64);
+                put_pair(ci, cbase + (size_t)r * CP, 0, 0, w64);
                 for (uint32_t s = 0; s < p->s2; ++s)
                     for (uint32_t ip = 0; ip < (1u << s); ++ip) {
-                        uint32_t gi = (1u << s) * (N1 + r) + ip;     // global table index
+                        uint32_t gi = (1u << s) * (N1 + r) + ip;
                         uint32_t e = H::bitrev(gi, (int)n);
-                        size_t at = base + (size_t)r * N2 + (1u << s) + ip;
+                        size_t at = cbase + (size_t)r * CP + nttgb::level_pos((1u << s) + ip, p->s2);
                         enc(pw[e], v, cc); put_pair(cf, at, v, cc, w64);
                         enc(pwi[e], v, cc); put_pair(ci, at, v, cc, w64);
                     }

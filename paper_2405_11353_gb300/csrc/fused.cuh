@@ -32,6 +32,9 @@ namespace nttgb {
 
 enum TileKind : int { TK_SINGLE = 0, TK_COLS = 1, TK_CHUNKS = 2 };
 
+// Two-pass split: N = N1 * N2 with N2 = 2^kN2Log (chunks of 256 words).
+constexpr uint32_t kN2Log = 8;
+
 template <class W> struct FArgs {
     W *data;
     const Tw<W> *tw;          // [L][N] table of this pass
@@ -64,17 +67,17 @@ template <class W> __host__ __device__ constexpr uint32_t cols_phys(uint32_t k, 
     return k + K * (u + (u >> 4));
 }
 
-template <class W, int LOGS, int KIND> __host__ constexpr size_t fused_smem_bytes();
+template <class W, int LOGS, int KIND, bool INV> __host__ constexpr size_t fused_smem_bytes();
 
 // Sub-transforms per CTA (compile-time, so every shared-memory address is
 // a per-round base plus an immediate offset): single-pass tiles hold 4096
 // words (or one transform above that), column strips 16 (4-byte) or 8
 // (8-byte) columns and at least 256 threads, chunk tiles 16 chunks.
 template <class W, int LOGS, int KIND> __host__ __device__ constexpr uint32_t tile_k() {
+    // column strips: 128-byte rows (32 four-byte or 16 eight-byte columns)
     return KIND == TK_SINGLE ? (LOGS >= 12 ? 1u : (4096u >> LOGS))
          : KIND == TK_CHUNKS ? 16u
-         : ((256u >> (LOGS - 4)) > (sizeof(W) == 4 ? 16u : 8u) ? (256u >> (LOGS - 4))
-                                                               : (sizeof(W) == 4 ? 16u : 8u));
+         : ((256u >> (LOGS - 4)) > (128u / sizeof(W)) ? (256u >> (LOGS - 4)) : (128u / (uint32_t)sizeof(W)));
 }
 
 // Round J of a sub-transform covers bits [LO, LO+RR) of the index u.
@@ -103,53 +106,66 @@ template <class W, int LOGS, int KIND> __host__ __device__ constexpr uint32_t sm
     return KIND == TK_COLS ? cols_phys<W>(k, u, tile_k<W, LOGS, KIND>()) : k * rows_pitch<W, LOGS>() + pu<W>(u);
 }
 
-// The 2^(RR-1-d) distinct twiddles of stage d (bit LO+d) for this thread,
-// consecutive in the table from index `first`; first is a multiple of the
-// count, so they move as 16-byte vectors.
-template <class W, int CNT> __device__ __forceinline__ void load_tw(Tw<W> (&t)[8], const Tw<W> *__restrict__ p) {
-    if (sizeof(W) == 4) {
-        if (CNT == 1) {
-            uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
-            t[0].w = (W)v.x; t[0].c = (W)v.y;
-        } else {
+// Twiddles of one stage for this thread: CNT pairs, pair j at p[j * STRIDE]
+// (level-transposed table, see level_pos); contiguous runs move as 16-byte
+// vectors.  SMEM: the table is staged in shared memory (plain loads), else
+// it is read through the read-only cache.
+template <class W, int CNT, int STRIDE, bool SMEM>
+__device__ __forceinline__ void load_tw(Tw<W> (&t)[8], const Tw<W> *__restrict__ p) {
+    if (STRIDE == 1 && CNT >= 2 && sizeof(W) == 4) {
 #pragma unroll
-            for (int i = 0; i < CNT / 2; ++i) {
-                uint4 v = __ldg(reinterpret_cast<const uint4 *>(p) + i);
-                t[2 * i].w = (W)v.x; t[2 * i].c = (W)v.y;
-                t[2 * i + 1].w = (W)v.z; t[2 * i + 1].c = (W)v.w;
-            }
+        for (int i = 0; i < CNT / 2; ++i) {
+            uint4 v = SMEM ? reinterpret_cast<const uint4 *>(p)[i] : __ldg(reinterpret_cast<const uint4 *>(p) + i);
+            t[2 * i].w = (W)v.x; t[2 * i].c = (W)v.y;
+            t[2 * i + 1].w = (W)v.z; t[2 * i + 1].c = (W)v.w;
         }
     } else {
 #pragma unroll
         for (int i = 0; i < CNT; ++i) {
-            ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(p) + i);
-            t[i].w = (W)v.x; t[i].c = (W)v.y;
+            if (sizeof(W) == 4) {
+                uint2 v = SMEM ? reinterpret_cast<const uint2 *>(p)[i * STRIDE]
+                               : __ldg(reinterpret_cast<const uint2 *>(p) + i * STRIDE);
+                t[i].w = (W)v.x; t[i].c = (W)v.y;
+            } else {
+                ulonglong2 v = SMEM ? reinterpret_cast<const ulonglong2 *>(p)[i * STRIDE]
+                                    : __ldg(reinterpret_cast<const ulonglong2 *>(p) + i * STRIDE);
+                t[i].w = (W)v.x; t[i].c = (W)v.y;
+            }
         }
     }
 }
 
-template <class W, int RED, bool INV, int LOGS, int J>
+template <class W, int RED, bool INV, int LOGS, int J, bool SMEM>
 __device__ __forceinline__ void round_bfly(W (&x)[16], uint32_t tau, const Tw<W> *__restrict__ tw, const Lc<W> &k,
                                            bool last_pass, Tw<W> tn, Tw<W> twn) {
     using R = RoundOf<LOGS, INV, J>;
     constexpr int RR = R::RR, LO = R::LO;
-    constexpr uint32_t S = 1u << LOGS;
-    // twiddle index of the butterfly on slots (e, e | 2^d) at stage d:
-    // (S >> (LO+d+1)) + (tau's part) + (e_low >> (d+1))
 #pragma unroll
     for (int dd = 0; dd < RR; ++dd) {
         const int d = INV ? dd : RR - 1 - dd;
-        const int b = LO + d;
+        const int b = LO + d;                  // index bit of this stage
+        const int lvl = LOGS - 1 - b;          // table level: entries [2^lvl, 2^(lvl+1))
         Tw<W> t[8];
         const bool fold = INV && b == LOGS - 1 && last_pass;
         if (!fold) {
-            uint32_t first = (S >> (b + 1)) + (RR == 4 ? ((tau >> LO) << (3 - d)) : 0u);
-            const int cnt = 1 << (RR - 1 - d);
-            switch (cnt) {
-            case 1: load_tw<W, 1>(t, tw + first); break;
-            case 2: load_tw<W, 2>(t, tw + first); break;
-            case 4: load_tw<W, 4>(t, tw + first); break;
-            default: load_tw<W, 8>(t, tw + first); break;
+            if constexpr (RR == 4) {
+                // full round: pair j of thread tau at 2^lvl + j * ntau + (tau >> LO)
+                constexpr int NTAU_LOG = LOGS - 4 - LO >= 0 ? LOGS - 4 - LO : 0;
+                const Tw<W> *p = tw + (1u << lvl) + (tau >> LO);
+                switch (3 - d) {
+                case 0: load_tw<W, 1, (1 << NTAU_LOG), SMEM>(t, p); break;
+                case 1: load_tw<W, 2, (1 << NTAU_LOG), SMEM>(t, p); break;
+                case 2: load_tw<W, 4, (1 << NTAU_LOG), SMEM>(t, p); break;
+                default: load_tw<W, 8, (1 << NTAU_LOG), SMEM>(t, p); break;
+                }
+            } else {
+                // short round: the stage's entries, shared by every thread
+                const Tw<W> *p = tw + (1u << lvl);
+                switch (RR - 1 - d) {
+                case 0: load_tw<W, 1, 1, SMEM>(t, p); break;
+                case 1: load_tw<W, 2, 1, SMEM>(t, p); break;
+                default: load_tw<W, 4, 1, SMEM>(t, p); break;
+                }
             }
         }
 #pragma unroll
@@ -218,53 +234,126 @@ __device__ __forceinline__ void tma_2d_g2s(void *dst, const void *tmap, int x, i
         : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Pull global data into L2 ahead of its TMA load (no shared memory used).
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void prefetch_tensor_2d(const void *tmap, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(tmap), "r"(x), "r"(y)
+                 : "memory");
+}
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
 // Rounds J = 1 .. NR-1 of one sub-transform (round 0 is done by the caller
 // on the words read from the staged tile); rounds exchange through the
-// padded shared-memory buffer `xs`.
-template <class W, int RED, bool INV, int LOGS, int KIND, bool WS, int J>
+// padded layout sm_off in `xs` (the tile's own stage buffer, whose staged
+// words have all been read by then).
+template <class W, int RED, bool INV, int LOGS, int KIND, bool WS, bool SMEM, int J>
 __device__ __forceinline__ void later_rounds(W (&x)[16], W *xs, uint32_t smb_k, uint32_t tau,
                                              const Tw<W> *__restrict__ tw, const Lc<W> &kk, bool last_pass,
                                              Tw<W> tn, Tw<W> twn) {
     using R = RoundOf<LOGS, INV, J>;
     if constexpr (J < R::NR) {
         using RP = RoundOf<LOGS, INV, J - 1>;
+        // a thread's 16 words are consecutive (round at bit 0) in the rows
+        // layout: move them as 16-byte vectors
+        constexpr bool VST = KIND != TK_COLS && RP::LO == 0 && RP::RR == 4;
+        constexpr bool VLD = KIND != TK_COLS && R::LO == 0 && R::RR == 4;
+        constexpr int V = 16 / sizeof(W);
         {
             const uint32_t base = smb_k + sm_off<W, LOGS, KIND>(0, RP::A(tau));
             if (J > 1) tile_sync<W, WS>();   // readers of the previous exchange are done
+            if constexpr (VST) {
 #pragma unroll
-            for (int e = 0; e < 16; ++e) xs[base + sm_off<W, LOGS, KIND>(0, RP::E(e))] = x[e];
+                for (int v = 0; v < 16 / V; ++v) {
+                    W *q = xs + base + sm_off<W, LOGS, KIND>(0, (uint32_t)(v * V));
+                    if (sizeof(W) == 4)
+                        *reinterpret_cast<uint4 *>(q) = make_uint4((uint32_t)x[4 * v], (uint32_t)x[4 * v + 1],
+                                                                   (uint32_t)x[4 * v + 2], (uint32_t)x[4 * v + 3]);
+                    else
+                        *reinterpret_cast<ulonglong2 *>(q) =
+                            make_ulonglong2((unsigned long long)x[2 * v], (unsigned long long)x[2 * v + 1]);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) xs[base + sm_off<W, LOGS, KIND>(0, RP::E(e))] = x[e];
+            }
         }
         tile_sync<W, WS>();
         {
             const uint32_t base = smb_k + sm_off<W, LOGS, KIND>(0, R::A(tau));
+            if constexpr (VLD) {
 #pragma unroll
-            for (int e = 0; e < 16; ++e) x[e] = xs[base + sm_off<W, LOGS, KIND>(0, R::E(e))];
+                for (int v = 0; v < 16 / V; ++v) {
+                    const W *q = xs + base + sm_off<W, LOGS, KIND>(0, (uint32_t)(v * V));
+                    if (sizeof(W) == 4) {
+                        uint4 w4 = *reinterpret_cast<const uint4 *>(q);
+                        x[4 * v] = (W)w4.x; x[4 * v + 1] = (W)w4.y; x[4 * v + 2] = (W)w4.z; x[4 * v + 3] = (W)w4.w;
+                    } else {
+                        ulonglong2 w2 = *reinterpret_cast<const ulonglong2 *>(q);
+                        x[2 * v] = (W)w2.x; x[2 * v + 1] = (W)w2.y;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) x[e] = xs[base + sm_off<W, LOGS, KIND>(0, R::E(e))];
+            }
         }
-        round_bfly<W, RED, INV, LOGS, J>(x, tau, tw, kk, last_pass, tn, twn);
-        later_rounds<W, RED, INV, LOGS, KIND, WS, J + 1>(x, xs, smb_k, tau, tw, kk, last_pass, tn, twn);
+        round_bfly<W, RED, INV, LOGS, J, SMEM>(x, tau, tw, kk, last_pass, tn, twn);
+        later_rounds<W, RED, INV, LOGS, KIND, WS, SMEM, J + 1>(x, xs, smb_k, tau, tw, kk, last_pass, tn, twn);
     }
 }
 
-// Pipeline depth: tiles of up to 16 KiB get three buffers, larger ones two.
-template <class W, int LOGS, int KIND> __host__ __device__ constexpr uint32_t tile_words() {
-    return tile_k<W, LOGS, KIND>() << LOGS;
+// Staged tile layouts (where TMA puts a tile in shared memory):
+//   cols             [S][K] dense (2-D box of K columns x S rows);
+//   chunks, forward  [K][S + pad]: one bulk copy per chunk, the pad puts the
+//                    two chunks of a warp on different bank halves for the
+//                    first round's word-per-thread reads;
+//   chunks, inverse  [K * S / R][R] rows of 128 bytes (R words) written by a
+//                    2-D copy with the 128-byte swizzle (16-byte unit j of row
+//                    r lands at unit j ^ (r mod 8)), so the first round's
+//                    16-byte reads of 64 consecutive bytes per thread are
+//                    conflict-free;
+//   single           [K][S] dense (one bulk copy of K whole transforms).
+// After the first round has read a tile, the same buffer holds the round
+// exchanges (layout sm_off), so a buffer is sized for the larger of the two.
+template <class W, int LOGS, int KIND, bool INV> __host__ __device__ constexpr bool stage_swizzled() {
+    return KIND == TK_CHUNKS && INV;
 }
-template <class W, int LOGS, int KIND> __host__ __device__ constexpr uint32_t n_stages() {
-    return tile_words<W, LOGS, KIND>() * sizeof(W) <= 16384 ? 3u : 2u;
+template <class W, int LOGS, int KIND, bool INV> __host__ __device__ constexpr uint32_t stage_pitch() {
+    return (KIND == TK_CHUNKS && !INV) ? (1u << LOGS) + (sizeof(W) == 4 ? 16u : 8u) : (1u << LOGS);
 }
-template <class W, int LOGS, int KIND> __host__ __device__ constexpr size_t xchg_bytes() {
-    return KIND == TK_COLS ? (size_t)tile_k<W, LOGS, KIND>() * ((1u << LOGS) + (1u << LOGS) / 16) * sizeof(W)
-                           : (size_t)tile_k<W, LOGS, KIND>() * rows_pitch<W, LOGS>() * sizeof(W);
+template <class W, int LOGS, int KIND> __host__ __device__ constexpr size_t xchg_words() {
+    return KIND == TK_COLS ? (size_t)tile_k<W, LOGS, KIND>() * ((1u << LOGS) + (1u << LOGS) / 16)
+                           : (size_t)tile_k<W, LOGS, KIND>() * rows_pitch<W, LOGS>();
+}
+template <class W, int LOGS, int KIND, bool INV> __host__ __device__ constexpr uint32_t tile_words() {
+    return KIND == TK_COLS ? (tile_k<W, LOGS, KIND>() << LOGS) : tile_k<W, LOGS, KIND>() * stage_pitch<W, LOGS, KIND, INV>();
+}
+template <class W, int LOGS, int KIND, bool INV> __host__ __device__ constexpr uint32_t buf_words() {
+    // multiple of 256 words keeps every buffer 1 KiB aligned
+    return (uint32_t)(((tile_words<W, LOGS, KIND, INV>() > xchg_words<W, LOGS, KIND>() ? tile_words<W, LOGS, KIND, INV>()
+                                                                                        : xchg_words<W, LOGS, KIND>()) +
+                       255) & ~size_t(255));
+}
+// Two buffers per CTA: the next tile lands while the current one computes.
+template <class W, int LOGS, int KIND> __host__ __device__ constexpr uint32_t n_stages() { return 2u; }
+// Twiddles staged in shared memory: the column table (2^LOGS pairs per limb)
+// and, for 4-byte words, the chunk tables of a tile (K chunk tables).
+template <class W, int LOGS, int KIND> __host__ __device__ constexpr bool tw_staged() {
+    return KIND == TK_COLS || (KIND == TK_CHUNKS && sizeof(W) == 4);
+}
+template <class W, int LOGS, int KIND> __host__ __device__ constexpr uint32_t tw_pairs() {
+    return !tw_staged<W, LOGS, KIND>() ? 0u
+           : KIND == TK_COLS ? (1u << LOGS) : tile_k<W, LOGS, KIND>() * chunk_tab_pitch<W>();
 }
 
 // Persistent fused pass.  CTA c processes tiles [c T / G, (c+1) T / G) in
-// order; one thread keeps n_stages() tiles in flight with TMA copies into
+// order; one thread keeps the next tile in flight with TMA copies into
 // shared memory (1-D bulk copies of contiguous rows tiles, 2-D tensor
 // copies of column strips), completing on one mbarrier per buffer.  Tiles
-// of the two-pass kinds are ordered polynomial-fastest, so consecutive tiles
-// of a CTA reuse the same twiddles from the L1/L2 caches.
+// of the two-pass kinds run polynomial-fastest, so a CTA reuses one set of
+// twiddles (staged in shared memory) for many consecutive tiles.
 template <class W, int RED, bool INV, int LOGS, int KIND>
 __global__ void __launch_bounds__(sizeof(W) == 4 ? 1024 : 512)
 k_fused(const __grid_constant__ FArgs<W> a) {
@@ -273,16 +362,23 @@ k_fused(const __grid_constant__ FArgs<W> a) {
     constexpr uint32_t T = S / 16;
     constexpr uint32_t K = tile_k<W, LOGS, KIND>();
     constexpr uint32_t NS = n_stages<W, LOGS, KIND>();
-    constexpr uint32_t TW_ = tile_words<W, LOGS, KIND>();
+    constexpr uint32_t BW = buf_words<W, LOGS, KIND, INV>();
+    constexpr uint32_t SP = stage_pitch<W, LOGS, KIND, INV>();
+    constexpr bool SWZ = stage_swizzled<W, LOGS, KIND, INV>();
+    constexpr bool TWS = tw_staged<W, LOGS, KIND>();
+    constexpr uint32_t TWP = tw_pairs<W, LOGS, KIND>();
+    constexpr uint32_t CP = chunk_tab_pitch<W>();
+    constexpr uint32_t RW = 128 / sizeof(W);     // words per 128-byte row
     constexpr bool WS = KIND != TK_COLS && T <= 32;
     using R0 = RoundOf<LOGS, INV, 0>;
     using RL = RoundOf<LOGS, INV, R0::NR - 1>;
-    // layout: NS stage buffers (1 KiB aligned), exchange buffer, barriers
-    W *stage = reinterpret_cast<W *>(smem_raw);
-    W *xs = stage + (size_t)NS * TW_;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(xs) +
-                                                 ((xchg_bytes<W, LOGS, KIND>() + 15) & ~size_t(15)));
-    uint32_t &s_abort = *reinterpret_cast<uint32_t *>(bar + NS);
+    // layout: NS buffers (1 KiB aligned: the 128-byte swizzle repeats every
+    // 1 KiB), staged twiddles, barriers
+    unsigned char *base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+    W *stage = reinterpret_cast<W *>(base);
+    Tw<W> *tws = reinterpret_cast<Tw<W> *>(stage + (size_t)NS * BW);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tws + TWP);      // NS tile barriers + 1 twiddle barrier
+    uint32_t &s_abort = *reinterpret_cast<uint32_t *>(bar + NS + 1);
 
     const uint32_t N = 1u << a.logN;
     const uint32_t tid = threadIdx.x;
@@ -291,82 +387,156 @@ k_fused(const __grid_constant__ FArgs<W> a) {
     else { tau = tid % T; k = tid / T; }
     const uint32_t smb_k = sm_off<W, LOGS, KIND>(k, 0);
     const uint32_t L = a.L;
-    const uint64_t B = a.ntrans / L;
-    const uint32_t per = KIND == TK_SINGLE ? 1u : (KIND == TK_COLS ? (1u << a.s2) : (N >> a.s2)) / K;
-    const uint64_t t_begin = blockIdx.x * a.ntiles / gridDim.x;
-    const uint64_t t_end = (blockIdx.x + 1) * a.ntiles / gridDim.x;
+    const uint32_t B = (uint32_t)(a.ntrans / L);
+    constexpr uint32_t S2 = kN2Log;   // log2 of the row length N2 (two-pass kinds)
+    const uint32_t N1 = KIND == TK_SINGLE ? 1u : (N >> S2);
+    const uint32_t per = KIND == TK_SINGLE ? 1u : (KIND == TK_COLS ? (1u << S2) : N1) / K;
+    const uint32_t t_begin = (uint32_t)((uint64_t)blockIdx.x * a.ntiles / gridDim.x);
+    const uint32_t t_end = (uint32_t)((uint64_t)(blockIdx.x + 1) * a.ntiles / gridDim.x);
 
-    // tile -> (first transform, column / chunk position)
-    auto decode = [&](uint64_t tile, uint64_t &t, uint32_t &pos0) {
-        if (KIND == TK_SINGLE) {
-            t = tile * K;
-            pos0 = 0;
-        } else {
-            const uint64_t p = tile % B;
-            const uint64_t r = tile / B;
-            const uint32_t l = (uint32_t)(r / per);
-            pos0 = (uint32_t)(r % per) * K;
-            t = p * L + l;
-        }
+    // Tile cursor: single tiles are K consecutive transforms; two-pass tiles
+    // run polynomial-fastest, then position group, then limb.  It is decoded
+    // once and then stepped, so the loop does no division.
+    struct Cur {
+        uint32_t p, g, l;
     };
-    auto issue = [&](uint64_t tile, uint32_t s) {
-        uint64_t t;
-        uint32_t pos0;
-        decode(tile, t, pos0);
-        W *dst = stage + (size_t)s * TW_;
+    auto cur_at = [&](uint32_t tile) {
+        Cur c;
+        if (KIND == TK_SINGLE) { c.p = tile * K; c.g = 0; c.l = 0; }
+        else { c.p = tile % B; const uint32_t r = tile / B; c.g = r % per; c.l = r / per; }
+        return c;
+    };
+    auto cur_next = [&](Cur &c) {
+        if (KIND == TK_SINGLE) { c.p += K; return; }
+        if (++c.p == B) { c.p = 0; if (++c.g == per) { c.g = 0; ++c.l; } }
+    };
+    auto cur_t = [&](const Cur &c) -> uint64_t {
+        return KIND == TK_SINGLE ? (uint64_t)c.p : (uint64_t)c.p * L + c.l;
+    };
+    // twiddle table of limb l (column pass) or of the chunks of group g
+    auto tw_src = [&](uint32_t l, uint32_t g) -> const Tw<W> * {
+        if (KIND == TK_CHUNKS) return a.tw + (size_t)l * N1 * CP + (size_t)g * K * CP;
+        return a.tw + (size_t)l * N;
+    };
+    auto issue = [&](const Cur &c, uint32_t s) {
+        const uint64_t t = cur_t(c);
+        const uint32_t pos0 = c.g * K;
+        W *dst = stage + (size_t)s * BW;
         if (KIND == TK_COLS) {
             const uint32_t rows = S < 256 ? S : 256u;
-            mbar_expect_tx(&bar[s], TW_ * (uint32_t)sizeof(W));
+            mbar_expect_tx(&bar[s], (K << LOGS) * (uint32_t)sizeof(W));
             for (uint32_t r0 = 0; r0 < S; r0 += rows)
-                tma_2d_g2s(dst + r0 * K, &a.tmap, (int)pos0, (int)(t * (N >> a.s2) + r0), &bar[s]);
+                tma_2d_g2s(dst + r0 * K, &a.tmap, (int)pos0, (int)(t * N1 + r0), &bar[s]);
+        } else if (SWZ) {
+            mbar_expect_tx(&bar[s], K * S * (uint32_t)sizeof(W));
+            const uint64_t row0 = (t * N + ((size_t)pos0 << S2)) / RW;
+            tma_2d_g2s(dst, &a.tmap, 0, (int)row0, &bar[s]);
+        } else if (KIND == TK_CHUNKS) {
+            mbar_expect_tx(&bar[s], K * S * (uint32_t)sizeof(W));
+            const W *src = a.data + t * N + ((size_t)pos0 << S2);
+            for (uint32_t c2 = 0; c2 < K; ++c2) bulk_g2s(dst + c2 * SP, src + (size_t)c2 * S, S * sizeof(W), &bar[s]);
         } else {
-            uint64_t nval = KIND == TK_SINGLE ? (a.ntrans - t < K ? a.ntrans - t : K) : K;
-            const W *src = KIND == TK_SINGLE ? a.data + t * N : a.data + t * N + ((size_t)pos0 << a.s2);
-            uint32_t bytes = (uint32_t)(nval * S * sizeof(W));
+            const uint64_t nval = a.ntrans - t < K ? a.ntrans - t : K;
+            const uint32_t bytes = (uint32_t)(nval * S * sizeof(W));
             mbar_expect_tx(&bar[s], bytes);
-            bulk_g2s(dst, src, bytes, &bar[s]);
+            bulk_g2s(dst, a.data + t * N, bytes, &bar[s]);
+        }
+    };
+
+    // L2 prefetch of a tile (one beyond the ones staged in shared memory)
+    auto prefetch = [&](const Cur &c) {
+        const uint64_t t = cur_t(c);
+        const uint32_t pos0 = c.g * K;
+        if (KIND == TK_COLS) {
+            const uint32_t rows = S < 256 ? S : 256u;
+            for (uint32_t r0 = 0; r0 < S; r0 += rows) prefetch_tensor_2d(&a.tmap, (int)pos0, (int)(t * N1 + r0));
+        } else if (KIND == TK_CHUNKS) {
+            prefetch_l2(a.data + t * N + ((size_t)pos0 << S2), K * S * (uint32_t)sizeof(W));
+        } else {
+            const uint64_t nval = a.ntrans - t < K ? a.ntrans - t : K;
+            prefetch_l2(a.data + t * N, (uint32_t)(nval * S * sizeof(W)));
         }
     };
 
     if (tid == 0) {
         s_abort = 0;
-        for (uint32_t s = 0; s < NS; ++s) mbar_init(&bar[s], 1);
+        for (uint32_t s = 0; s <= NS; ++s) mbar_init(&bar[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    if (tid == 0)
-        for (uint32_t s = 0; s < NS && t_begin + s < t_end; ++s) issue(t_begin + s, s);
+    Cur ahead = cur_at(t_begin);   // next tile to issue (thread 0)
+    Cur cur = ahead;               // tile being processed
+    if (tid == 0) {
+        for (uint32_t s = 0; s < NS && t_begin + s < t_end; ++s) { issue(ahead, s); cur_next(ahead); }
+        if (t_begin + NS < t_end) prefetch(ahead);
+    }
+    uint32_t tw_key = 0xffffffffu;  // (limb, group) of the staged twiddles
+    uint32_t tw_phase = 0;
+    bool ok = true;
 
     uint32_t i = 0;
-    for (uint64_t tile = t_begin; tile < t_end; ++tile, ++i) {
+    for (uint32_t tile = t_begin; tile < t_end; ++tile, ++i, cur_next(cur)) {
         const uint32_t s = i % NS;
         const uint32_t parity = (i / NS) & 1u;
-        uint64_t t0;
-        uint32_t pos0;
-        decode(tile, t0, pos0);
-        const uint64_t t = KIND == TK_SINGLE ? t0 + k : t0;
+        const uint32_t pos0 = cur.g * K;
+        const uint64_t t = KIND == TK_SINGLE ? cur_t(cur) + k : cur_t(cur);
         const bool valid = t < a.ntrans;
-        const uint32_t l = (uint32_t)((valid ? t : 0) % L);
+        const uint32_t l = KIND == TK_SINGLE ? (uint32_t)((valid ? t : 0) % L) : cur.l;
         Lc<W> kk;
         kk.load(a.lc + l);
-        const Tw<W> *twb = a.tw + (size_t)l * N + (KIND == TK_CHUNKS ? ((size_t)(pos0 + k) << a.s2) : 0);
         Tw<W> tn{}, twn{};
         if (INV && a.final_pass) {
             tn.w = (W)a.lc[l].ninv_w; tn.c = (W)a.lc[l].ninv_c;
             twn.w = (W)a.lc[l].ninv_w1_w; twn.c = (W)a.lc[l].ninv_w1_c;
         }
+        const Tw<W> *twb;
+        if (TWS) {
+            // restage the twiddles when the tile needs another table (every
+            // thread finished with the old one before the previous refill barrier)
+            const uint32_t key = KIND == TK_CHUNKS ? cur.l * per + cur.g : cur.l;
+            if (key != tw_key) {
+                if (tid == 0) {
+                    fence_proxy_async();
+                    mbar_expect_tx(&bar[NS], TWP * (uint32_t)sizeof(Tw<W>));
+                    bulk_g2s(tws, tw_src(cur.l, cur.g), TWP * (uint32_t)sizeof(Tw<W>), &bar[NS]);
+                }
+                ok = ok && mbar_wait_bounded(&bar[NS], tw_phase & 1u);
+                ++tw_phase;
+                tw_key = key;
+            }
+            twb = tws + (KIND == TK_CHUNKS ? k * CP : 0);
+        } else {
+            twb = KIND == TK_CHUNKS ? tw_src(l, 0) + (size_t)(pos0 + k) * CP : a.tw + (size_t)l * N;
+        }
         // ---- round 0 from the staged tile
-        const bool ok = mbar_wait_bounded(&bar[s], parity);
+        ok = ok && mbar_wait_bounded(&bar[s], parity);
+        W *sb = stage + (size_t)s * BW;
         W x[16];
         {
-            const W *sb = stage + (size_t)s * TW_;
             const uint32_t A0 = R0::A(tau);
             if (KIND == TK_COLS) {
 #pragma unroll
                 for (int e = 0; e < 16; ++e) x[e] = sb[(A0 | R0::E(e)) * K + k];
+            } else if (SWZ && R0::RR == 4 && R0::LO == 0) {
+                // 16 consecutive words of chunk k from swizzled 128-byte rows
+                constexpr int V = 16 / sizeof(W);            // words per 16-byte unit
+#pragma unroll
+                for (int v = 0; v < 16 / V; ++v) {
+                    const uint32_t u = A0 + v * V;            // first word of the unit
+                    const uint32_t row = k * (S / RW) + u / RW;
+                    const uint32_t unit = ((u % RW) / V) ^ (row & 7u);
+                    const W *q = sb + row * RW + unit * V;
+                    if (sizeof(W) == 4) {
+                        uint4 w4 = *reinterpret_cast<const uint4 *>(q);
+                        x[4 * v] = (W)w4.x; x[4 * v + 1] = (W)w4.y; x[4 * v + 2] = (W)w4.z; x[4 * v + 3] = (W)w4.w;
+                    } else {
+                        ulonglong2 w2 = *reinterpret_cast<const ulonglong2 *>(q);
+                        x[2 * v] = (W)w2.x; x[2 * v + 1] = (W)w2.y;
+                    }
+                }
             } else if (R0::RR == 4 && R0::LO == 0) {
                 // sixteen consecutive words: four 16-byte loads
-                const W *q = sb + k * S + A0;
+                const W *q = sb + k * SP + A0;
 #pragma unroll
                 for (int v = 0; v < 16 / (16 / (int)sizeof(W)); ++v) {
                     if (sizeof(W) == 4) {
@@ -379,20 +549,24 @@ k_fused(const __grid_constant__ FArgs<W> a) {
                 }
             } else {
 #pragma unroll
-                for (int e = 0; e < 16; ++e) x[e] = sb[k * S + (A0 | R0::E(e))];
+                for (int e = 0; e < 16; ++e) x[e] = sb[k * SP + (A0 | R0::E(e))];
             }
         }
-        // every thread has its words: the buffer can be refilled
+        // every thread has its words (the buffer now serves the exchanges)
         if (__syncthreads_or(!ok)) {
             if (tid == 0) { s_abort = 1; atomicOr(a.status, 2u); }
             break;
         }
+        round_bfly<W, RED, INV, LOGS, 0, TWS>(x, tau, twb, kk, INV && a.final_pass, tn, twn);
+        later_rounds<W, RED, INV, LOGS, KIND, WS, TWS, 1>(x, sb, smb_k, tau, twb, kk, INV && a.final_pass, tn, twn);
+        // the buffer and the twiddles are free: refill with the tile NS ahead
+        __syncthreads();
         if (tid == 0 && tile + NS < t_end) {
             fence_proxy_async();
-            issue(tile + NS, s);
+            issue(ahead, s);
+            cur_next(ahead);
+            if (tile + NS + 1 < t_end) prefetch(ahead);
         }
-        round_bfly<W, RED, INV, LOGS, 0>(x, tau, twb, kk, INV && a.final_pass, tn, twn);
-        later_rounds<W, RED, INV, LOGS, KIND, WS, 1>(x, xs, smb_k, tau, twb, kk, INV && a.final_pass, tn, twn);
         if (a.final_pass) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
@@ -407,9 +581,9 @@ k_fused(const __grid_constant__ FArgs<W> a) {
             if (KIND == TK_COLS) {
                 W *g = a.data + t * N + pos0 + k;
 #pragma unroll
-                for (int e = 0; e < 16; ++e) g[(size_t)(AL | RL::E(e)) << a.s2] = x[e];
+                for (int e = 0; e < 16; ++e) g[(size_t)(AL | RL::E(e)) << S2] = x[e];
             } else {
-                W *g = KIND == TK_SINGLE ? a.data + t * N : a.data + t * N + ((size_t)(pos0 + k) << a.s2);
+                W *g = KIND == TK_SINGLE ? a.data + t * N : a.data + t * N + ((size_t)(pos0 + k) << S2);
                 if (RL::RR == 4 && RL::LO == 0) {
                     W *q = g + AL;
 #pragma unroll
@@ -429,20 +603,26 @@ k_fused(const __grid_constant__ FArgs<W> a) {
         }
     }
     // on an aborted wait, let the copies already in flight (local tiles
-    // i .. i+NS-1) land before the CTA exits, again with a time limit
+    // i .. i+NS-1 and the twiddle table) land before the CTA exits, again
+    // with a time limit
     if (s_abort && tid == 0) {
-        const uint64_t n_local = t_end - t_begin;
-        for (uint64_t j = i; j < i + NS && j < n_local; ++j) {
+        const uint32_t n_local = t_end - t_begin;
+        for (uint32_t j = i; j < i + NS && j < n_local; ++j) {
             const long long t0 = clock64();
-            while (!mbar_try_wait(&bar[j % NS], (uint32_t)(j / NS) & 1u))
+            while (!mbar_try_wait(&bar[j % NS], (j / NS) & 1u))
+                if (clock64() - t0 > (1ll << 30)) break;
+        }
+        if (TWS && tw_phase > 0) {
+            const long long t0 = clock64();
+            while (!mbar_try_wait(&bar[NS], (tw_phase - 1) & 1u))
                 if (clock64() - t0 > (1ll << 30)) break;
         }
     }
 }
 
-template <class W, int LOGS, int KIND> __host__ constexpr size_t fused_smem_bytes() {
-    return (size_t)n_stages<W, LOGS, KIND>() * tile_words<W, LOGS, KIND>() * sizeof(W) +
-           ((xchg_bytes<W, LOGS, KIND>() + 15) & ~size_t(15)) + 8 * 4 + 16;
+template <class W, int LOGS, int KIND, bool INV> __host__ constexpr size_t fused_smem_bytes() {
+    return (size_t)n_stages<W, LOGS, KIND>() * buf_words<W, LOGS, KIND, INV>() * sizeof(W) +
+           (size_t)tw_pairs<W, LOGS, KIND>() * 2 * sizeof(W) + 8 * 4 + 16 + 1024;
 }
 
 }  // namespace nttgb

@@ -9,6 +9,8 @@
 
 namespace nttgb {
 
+static_assert(kN2Log == (uint32_t)kChunkLog, "two-pass split must match the plan's chunk size");
+
 template <class W, int RED, bool INV, int LOGS, int KIND>
 cudaError_t launch_pass(const FArgs<W> &a, uint32_t threads, size_t smem, cudaStream_t st) {
     auto kern = k_fused<W, RED, INV, LOGS, KIND>;
@@ -57,6 +59,32 @@ inline cudaError_t make_cols_tmap(CUtensorMap *m, void *data, bool w64, uint64_t
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// Tensor map of the data viewed as rows of 128 bytes (RW words), box of
+// box_rows rows, with the 128-byte swizzle.
+inline cudaError_t make_rows_tmap(CUtensorMap *m, void *data, bool w64, uint64_t rows, uint32_t RW,
+                                  uint32_t box_rows) {
+    using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeFn encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return cudaErrorNotSupported;
+        encode = reinterpret_cast<EncodeFn>(fn);
+    }
+    cuuint64_t dims[2] = {RW, rows};
+    cuuint64_t strides[1] = {128};
+    cuuint32_t box[2] = {RW, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(m, w64 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, data, dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <class W, int RED, bool INV, int KIND, int LOGS = 4>
 cudaError_t pass_dispatch(int logS, const FArgs<W> &a, uint32_t threads, size_t smem, cudaStream_t st) {
     constexpr int MAXS = KIND == TK_SINGLE ? (sizeof(W) == 4 ? kSingleMaxLog32 : kSingleMaxLog64)
@@ -82,9 +110,9 @@ template <class W, int KIND> uint32_t tile_k_for(int logS) {
     return 1;
 }
 
-template <class W, int KIND> size_t smem_for(int logS) {
+template <class W, int KIND, bool INV> size_t smem_for(int logS) {
     switch (logS) {
-#define NTTGB_CASE(s) case s: return fused_smem_bytes<W, s, KIND>();
+#define NTTGB_CASE(s) case s: return fused_smem_bytes<W, s, KIND, INV>();
         NTTGB_CASE(4) NTTGB_CASE(5) NTTGB_CASE(6) NTTGB_CASE(7) NTTGB_CASE(8) NTTGB_CASE(9)
         NTTGB_CASE(10) NTTGB_CASE(11) NTTGB_CASE(12) NTTGB_CASE(13) NTTGB_CASE(14)
 #undef NTTGB_CASE
@@ -116,13 +144,21 @@ cudaError_t run_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, in
     else if (KIND == TK_COLS) a.ntiles = ntrans * ((1u << p.s2) / K);
     else a.ntiles = ntrans * ((1u << (p.logN - p.s2)) / K);
     a.logK = ilog2(K);
+    if (a.ntiles >= (1ull << 32) || ntrans >= (1ull << 32)) return cudaErrorInvalidValue;   // 32-bit tile cursor
     if (KIND == TK_COLS) {
         const uint32_t N1 = 1u << logS;
         cudaError_t e = make_cols_tmap(&a.tmap, data, sizeof(W) == 8, ntrans * N1, 1u << p.s2, K,
                                        N1 < 256 ? N1 : 256u);
         if (e != cudaSuccess) return e;
     }
-    size_t smem = smem_for<W, KIND>(logS);
+    if (KIND == TK_CHUNKS && INV) {
+        // inverse chunk tiles: 128-byte rows, swizzled (see fused.cuh)
+        const uint32_t RW = 128 / sizeof(W);
+        cudaError_t e = make_rows_tmap(&a.tmap, data, sizeof(W) == 8, ntrans * p.N / RW, RW,
+                                       K * (1u << logS) / RW);
+        if (e != cudaSuccess) return e;
+    }
+    size_t smem = smem_for<W, KIND, INV>(logS);
     ++p.last_launches;
     return pass_dispatch<W, RED, INV, KIND>(logS, a, K * T, smem, st);
 }
