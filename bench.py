@@ -229,7 +229,7 @@ def main():
         dist.barrier()
     nt.lib()
     from paper_2405_11353_gb300 import build as nb
-    digest = nb._digest()
+    digest = nb.kernel_digest()
 
     qs = nt.ntt_find_primes(BITS, M, L)
     flags = nt.NTT_ORDER_BITREV | nt.NTT_RED_SHOUP

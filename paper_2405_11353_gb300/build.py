@@ -33,11 +33,22 @@ def _headers():
 def _digest(extra=""):
     h = hashlib.sha256()
     for p in _sources() + _headers():
-        h.update(p.encode())
+        h.update(os.path.relpath(p, ROOT).encode())
         with open(p, "rb") as f:
             h.update(f.read())
     h.update(" ".join(ARCH + FLAGS).encode() + extra.encode())
     return h.hexdigest()
+
+
+def kernel_digest():
+    """Digest of the kernel sources and headers (relative paths + contents):
+    identifies the code an ncu capture was taken on."""
+    h = hashlib.sha256()
+    for p in _sources() + _headers():
+        h.update(os.path.relpath(p, ROOT).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def _compile(src):

@@ -61,7 +61,7 @@ template <class W> __host__ __device__ constexpr uint32_t pu(uint32_t u) {
 template <class W, int LOGS> __host__ __device__ constexpr uint32_t rows_pitch() {
     constexpr uint32_t span = pu<W>(1u << LOGS);
     constexpr uint32_t half = sizeof(W) == 4 ? 16 : 8;
-    return ((span + half) / (2 * half)) * (2 * half) + half;
+    return span + ((half + 2 * half - span % (2 * half)) % (2 * half));
 }
 template <class W> __host__ __device__ constexpr uint32_t cols_phys(uint32_t k, uint32_t u, uint32_t K) {
     return k + K * (u + (u >> 4));
