@@ -221,9 +221,15 @@ typedef struct {
     uint32_t reserved;
 } ntt_job;
 
-/* Validate the jobs, build one table per distinct (q, N) and the work list,
- * choose tiles, and capture the persistent launch into a CUDA graph.
- * flags: NTT_ORDER_BITREV and NTT_RED_* as for plans. */
+/* Validate the jobs (2^12 <= N <= 2^17), build twiddle tables once per
+ * (N, word size, prime list) -- a job whose primes are a prefix of another
+ * job's list shares its tables -- cut the passes of every transform into
+ * work items, and capture one cooperative launch of the persistent kernel
+ * into a CUDA graph.  All forward jobs complete before any inverse job
+ * starts, so a set holding a forward and an inverse job on the same buffer
+ * is a round trip.  flags: NTT_ORDER_BITREV (required: the ragged kernel
+ * works in bit-reversed evaluation order) and NTT_RED_*.  The job array
+ * and its q arrays are copied; the data buffers must stay valid. */
 ntt_status ntt_ragged_create(ntt_ragged_t *out, const ntt_job *jobs,
                              uint32_t n_jobs, uint32_t flags);
 

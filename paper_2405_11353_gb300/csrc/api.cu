@@ -75,6 +75,14 @@ void free_plan_memory(ntt_plan_s *p) {
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+}  // namespace
+
+namespace nttgb {
+ntt_status validate_plan_args(uint32_t N, const uint64_t *q, uint32_t L, uint32_t flags);
+}
+
+namespace {
+
 ntt_status validate(uint32_t N, const uint64_t *q, uint32_t L, uint32_t flags) {
     if (!q || L == 0 || L > kMaxLimbs) return NTT_ERR_INVALID_ARG;
     if (flags & ~kKnownFlags) return NTT_ERR_INVALID_ARG;
@@ -244,6 +252,10 @@ ntt_status run_transform(ntt_plan_t plan, void *d_data, uint32_t batch, ntt_stre
 
 namespace nttgb {
 
+ntt_status validate_plan_args(uint32_t N, const uint64_t *q, uint32_t L, uint32_t flags) {
+    return validate(N, q, L, flags);
+}
+
 ntt_status ensure_scratch(ntt_plan_s &p, uint32_t batch, cudaStream_t st) {
     size_t need = (size_t)batch * p.L * p.N * p.word_bytes();
     if (need <= p.scratch_bytes) return NTT_OK;
@@ -307,8 +319,14 @@ ntt_status ntt_find_primes(uint32_t bits, uint32_t m, uint32_t count, uint64_t *
     return found == count ? NTT_OK : NTT_ERR_INVALID_ARG;
 }
 
-ntt_status ntt_plan_create_ex(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t L, ntt_variant variant,
-                              uint32_t flags, const uint64_t *psi) {
+}  // extern "C"
+
+namespace nttgb {
+
+// Plan builder behind ntt_plan_create_ex.  single_max_log >= 0 caps the
+// size done in one fused pass (the ragged kernel uses 12).
+ntt_status create_plan(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t L, ntt_variant variant,
+                       uint32_t flags, const uint64_t *psi, int single_max_log) {
     if (!plan) return NTT_ERR_INVALID_ARG;
     *plan = nullptr;
     if ((int)variant < NTT_DIT || (int)variant > NTT_TC_FOURSTEP) return NTT_ERR_INVALID_ARG;
@@ -337,7 +355,8 @@ ntt_status ntt_plan_create_ex(ntt_plan_t *plan, uint32_t N, const uint64_t *q, u
         }
     }
     if (variant == NTT_FUSED) {
-        const int single_max = p->word64 ? nttgb::kSingleMaxLog64 : nttgb::kSingleMaxLog32;
+        int single_max = p->word64 ? nttgb::kSingleMaxLog64 : nttgb::kSingleMaxLog32;
+        if (single_max_log >= 0 && single_max_log < single_max) single_max = single_max_log;
         if (p->logN < 4) p->fused_mode = nttgb::FUSED_STAGES;
         else if ((int)p->logN <= single_max) p->fused_mode = nttgb::FUSED_SINGLE;
         else {
@@ -351,6 +370,15 @@ ntt_status ntt_plan_create_ex(ntt_plan_t *plan, uint32_t N, const uint64_t *q, u
     if (s != NTT_OK) { free_plan_memory(p); delete p; cudaGetLastError(); return s; }
     *plan = p;
     return NTT_OK;
+}
+
+}  // namespace nttgb
+
+extern "C" {
+
+ntt_status ntt_plan_create_ex(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t L, ntt_variant variant,
+                              uint32_t flags, const uint64_t *psi) {
+    return nttgb::create_plan(plan, N, q, L, variant, flags, psi, -1);
 }
 
 ntt_status ntt_plan_create(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t L, ntt_variant variant,

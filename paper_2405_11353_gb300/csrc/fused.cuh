@@ -67,16 +67,18 @@ template <class W> __host__ __device__ constexpr uint32_t cols_phys(uint32_t k, 
     return k + K * (u + (u >> 4));
 }
 
-template <class W, int LOGS, int KIND, bool INV> __host__ constexpr size_t fused_smem_bytes();
 
 // Sub-transforms per CTA (compile-time, so every shared-memory address is
 // a per-round base plus an immediate offset): single-pass tiles hold 4096
 // words (or one transform above that), column strips 16 (4-byte) or 8
 // (8-byte) columns and at least 256 threads, chunk tiles 16 chunks.
-template <class W, int LOGS, int KIND> __host__ __device__ constexpr uint32_t tile_k() {
-    // column strips: 128-byte rows (32 four-byte or 16 eight-byte columns)
+// P = 0: per-plan passes; column strips have 128-byte rows (32 four-byte or
+// 16 eight-byte columns).  P = 1: the ragged kernel, whose CTAs always have
+// 256 threads (4096-word column tiles).
+template <class W, int LOGS, int KIND, int P = 0> __host__ __device__ constexpr uint32_t tile_k() {
     return KIND == TK_SINGLE ? (LOGS >= 12 ? 1u : (4096u >> LOGS))
          : KIND == TK_CHUNKS ? 16u
+         : P == 1 ? (4096u >> LOGS)
          : ((256u >> (LOGS - 4)) > (128u / sizeof(W)) ? (256u >> (LOGS - 4)) : (128u / (uint32_t)sizeof(W)));
 }
 
@@ -102,8 +104,8 @@ template <int LOGS, bool INV, int J> struct RoundOf {
 };
 
 // shared-memory word offset of u in sub-transform k (linear in u's bits)
-template <class W, int LOGS, int KIND> __host__ __device__ constexpr uint32_t sm_off(uint32_t k, uint32_t u) {
-    return KIND == TK_COLS ? cols_phys<W>(k, u, tile_k<W, LOGS, KIND>()) : k * rows_pitch<W, LOGS>() + pu<W>(u);
+template <class W, int LOGS, int KIND, int P = 0> __host__ __device__ constexpr uint32_t sm_off(uint32_t k, uint32_t u) {
+    return KIND == TK_COLS ? cols_phys<W>(k, u, tile_k<W, LOGS, KIND, P>()) : k * rows_pitch<W, LOGS>() + pu<W>(u);
 }
 
 // Twiddles of one stage for this thread: CNT pairs, pair j at p[j * STRIDE]
@@ -248,7 +250,7 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 // on the words read from the staged tile); rounds exchange through the
 // padded layout sm_off in `xs` (the tile's own stage buffer, whose staged
 // words have all been read by then).
-template <class W, int RED, bool INV, int LOGS, int KIND, bool WS, bool SMEM, int J>
+template <class W, int RED, bool INV, int LOGS, int KIND, bool WS, bool SMEM, int J, int P>
 __device__ __forceinline__ void later_rounds(W (&x)[16], W *xs, uint32_t smb_k, uint32_t tau,
                                              const Tw<W> *__restrict__ tw, const Lc<W> &kk, bool last_pass,
                                              Tw<W> tn, Tw<W> twn) {
@@ -261,12 +263,12 @@ __device__ __forceinline__ void later_rounds(W (&x)[16], W *xs, uint32_t smb_k, 
         constexpr bool VLD = KIND != TK_COLS && R::LO == 0 && R::RR == 4;
         constexpr int V = 16 / sizeof(W);
         {
-            const uint32_t base = smb_k + sm_off<W, LOGS, KIND>(0, RP::A(tau));
+            const uint32_t base = smb_k + sm_off<W, LOGS, KIND, P>(0, RP::A(tau));
             if (J > 1) tile_sync<W, WS>();   // readers of the previous exchange are done
             if constexpr (VST) {
 #pragma unroll
                 for (int v = 0; v < 16 / V; ++v) {
-                    W *q = xs + base + sm_off<W, LOGS, KIND>(0, (uint32_t)(v * V));
+                    W *q = xs + base + sm_off<W, LOGS, KIND, P>(0, (uint32_t)(v * V));
                     if (sizeof(W) == 4)
                         *reinterpret_cast<uint4 *>(q) = make_uint4((uint32_t)x[4 * v], (uint32_t)x[4 * v + 1],
                                                                    (uint32_t)x[4 * v + 2], (uint32_t)x[4 * v + 3]);
@@ -276,16 +278,16 @@ __device__ __forceinline__ void later_rounds(W (&x)[16], W *xs, uint32_t smb_k, 
                 }
             } else {
 #pragma unroll
-                for (int e = 0; e < 16; ++e) xs[base + sm_off<W, LOGS, KIND>(0, RP::E(e))] = x[e];
+                for (int e = 0; e < 16; ++e) xs[base + sm_off<W, LOGS, KIND, P>(0, RP::E(e))] = x[e];
             }
         }
         tile_sync<W, WS>();
         {
-            const uint32_t base = smb_k + sm_off<W, LOGS, KIND>(0, R::A(tau));
+            const uint32_t base = smb_k + sm_off<W, LOGS, KIND, P>(0, R::A(tau));
             if constexpr (VLD) {
 #pragma unroll
                 for (int v = 0; v < 16 / V; ++v) {
-                    const W *q = xs + base + sm_off<W, LOGS, KIND>(0, (uint32_t)(v * V));
+                    const W *q = xs + base + sm_off<W, LOGS, KIND, P>(0, (uint32_t)(v * V));
                     if (sizeof(W) == 4) {
                         uint4 w4 = *reinterpret_cast<const uint4 *>(q);
                         x[4 * v] = (W)w4.x; x[4 * v + 1] = (W)w4.y; x[4 * v + 2] = (W)w4.z; x[4 * v + 3] = (W)w4.w;
@@ -296,11 +298,11 @@ __device__ __forceinline__ void later_rounds(W (&x)[16], W *xs, uint32_t smb_k, 
                 }
             } else {
 #pragma unroll
-                for (int e = 0; e < 16; ++e) x[e] = xs[base + sm_off<W, LOGS, KIND>(0, R::E(e))];
+                for (int e = 0; e < 16; ++e) x[e] = xs[base + sm_off<W, LOGS, KIND, P>(0, R::E(e))];
             }
         }
         round_bfly<W, RED, INV, LOGS, J, SMEM>(x, tau, tw, kk, last_pass, tn, twn);
-        later_rounds<W, RED, INV, LOGS, KIND, WS, SMEM, J + 1>(x, xs, smb_k, tau, tw, kk, last_pass, tn, twn);
+        later_rounds<W, RED, INV, LOGS, KIND, WS, SMEM, J + 1, P>(x, xs, smb_k, tau, tw, kk, last_pass, tn, twn);
     }
 }
 
@@ -323,17 +325,19 @@ template <class W, int LOGS, int KIND, bool INV> __host__ __device__ constexpr b
 template <class W, int LOGS, int KIND, bool INV> __host__ __device__ constexpr uint32_t stage_pitch() {
     return (KIND == TK_CHUNKS && !INV) ? (1u << LOGS) + (sizeof(W) == 4 ? 16u : 8u) : (1u << LOGS);
 }
-template <class W, int LOGS, int KIND> __host__ __device__ constexpr size_t xchg_words() {
-    return KIND == TK_COLS ? (size_t)tile_k<W, LOGS, KIND>() * ((1u << LOGS) + (1u << LOGS) / 16)
-                           : (size_t)tile_k<W, LOGS, KIND>() * rows_pitch<W, LOGS>();
+template <class W, int LOGS, int KIND, int P = 0> __host__ __device__ constexpr size_t xchg_words() {
+    return KIND == TK_COLS ? (size_t)tile_k<W, LOGS, KIND, P>() * ((1u << LOGS) + (1u << LOGS) / 16)
+                           : (size_t)tile_k<W, LOGS, KIND, P>() * rows_pitch<W, LOGS>();
 }
-template <class W, int LOGS, int KIND, bool INV> __host__ __device__ constexpr uint32_t tile_words() {
-    return KIND == TK_COLS ? (tile_k<W, LOGS, KIND>() << LOGS) : tile_k<W, LOGS, KIND>() * stage_pitch<W, LOGS, KIND, INV>();
+template <class W, int LOGS, int KIND, bool INV, int P = 0> __host__ __device__ constexpr uint32_t tile_words() {
+    return KIND == TK_COLS ? (tile_k<W, LOGS, KIND, P>() << LOGS)
+                           : tile_k<W, LOGS, KIND, P>() * stage_pitch<W, LOGS, KIND, INV>();
 }
-template <class W, int LOGS, int KIND, bool INV> __host__ __device__ constexpr uint32_t buf_words() {
+template <class W, int LOGS, int KIND, bool INV, int P = 0> __host__ __device__ constexpr uint32_t buf_words() {
     // multiple of 256 words keeps every buffer 1 KiB aligned
-    return (uint32_t)(((tile_words<W, LOGS, KIND, INV>() > xchg_words<W, LOGS, KIND>() ? tile_words<W, LOGS, KIND, INV>()
-                                                                                        : xchg_words<W, LOGS, KIND>()) +
+    return (uint32_t)(((tile_words<W, LOGS, KIND, INV, P>() > xchg_words<W, LOGS, KIND, P>()
+                            ? tile_words<W, LOGS, KIND, INV, P>()
+                            : xchg_words<W, LOGS, KIND, P>()) +
                        255) & ~size_t(255));
 }
 // Two buffers per CTA: the next tile lands while the current one computes.
@@ -343,57 +347,59 @@ template <class W, int LOGS, int KIND> __host__ __device__ constexpr uint32_t n_
 template <class W, int LOGS, int KIND> __host__ __device__ constexpr bool tw_staged() {
     return KIND == TK_COLS || (KIND == TK_CHUNKS && sizeof(W) == 4);
 }
-template <class W, int LOGS, int KIND> __host__ __device__ constexpr uint32_t tw_pairs() {
+template <class W, int LOGS, int KIND, int P = 0> __host__ __device__ constexpr uint32_t tw_pairs() {
     return !tw_staged<W, LOGS, KIND>() ? 0u
-           : KIND == TK_COLS ? (1u << LOGS) : tile_k<W, LOGS, KIND>() * chunk_tab_pitch<W>();
+           : KIND == TK_COLS ? (1u << LOGS) : tile_k<W, LOGS, KIND, P>() * chunk_tab_pitch<W>();
 }
 
-// Persistent fused pass.  CTA c processes tiles [c T / G, (c+1) T / G) in
-// order; one thread keeps the next tile in flight with TMA copies into
-// shared memory (1-D bulk copies of contiguous rows tiles, 2-D tensor
-// copies of column strips), completing on one mbarrier per buffer.  Tiles
+// Pipeline state carried across run_tiles calls of one CTA: how often each
+// stage buffer and the twiddle buffer have completed a phase.
+struct PipeState {
+    uint32_t uses[2];
+    uint32_t tw_phase;
+};
+
+// Process tiles [t_begin, t_end) of one pass.  One thread keeps the next
+// tile in flight with TMA copies into shared memory (1-D bulk copies of
+// contiguous rows tiles, 2-D tensor copies of column strips), completing on
+// one mbarrier per buffer, and prefetches the tile after it into L2.  Tiles
 // of the two-pass kinds run polynomial-fastest, so a CTA reuses one set of
-// twiddles (staged in shared memory) for many consecutive tiles.
-template <class W, int RED, bool INV, int LOGS, int KIND>
-__global__ void __launch_bounds__(sizeof(W) == 4 ? 1024 : 512)
-k_fused(const __grid_constant__ FArgs<W> a) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
+// twiddles (staged in shared memory) for many consecutive tiles.  `bar`
+// holds NS tile barriers and one twiddle barrier, initialised by the caller.
+// Returns false if a wait ran out of time (the abort has been recorded).
+template <class W, int RED, bool INV, int LOGS, int KIND, int P>
+__device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *tmap, uint32_t t_begin,
+                                          uint32_t t_end, unsigned char *base, uint64_t *bar, PipeState &ps) {
     constexpr uint32_t S = 1u << LOGS;
     constexpr uint32_t T = S / 16;
-    constexpr uint32_t K = tile_k<W, LOGS, KIND>();
+    constexpr uint32_t K = tile_k<W, LOGS, KIND, P>();
     constexpr uint32_t NS = n_stages<W, LOGS, KIND>();
-    constexpr uint32_t BW = buf_words<W, LOGS, KIND, INV>();
+    constexpr uint32_t BW = buf_words<W, LOGS, KIND, INV, P>();
     constexpr uint32_t SP = stage_pitch<W, LOGS, KIND, INV>();
     constexpr bool SWZ = stage_swizzled<W, LOGS, KIND, INV>();
     constexpr bool TWS = tw_staged<W, LOGS, KIND>();
-    constexpr uint32_t TWP = tw_pairs<W, LOGS, KIND>();
+    constexpr uint32_t TWP = tw_pairs<W, LOGS, KIND, P>();
     constexpr uint32_t CP = chunk_tab_pitch<W>();
     constexpr uint32_t RW = 128 / sizeof(W);     // words per 128-byte row
     constexpr bool WS = KIND != TK_COLS && T <= 32;
     using R0 = RoundOf<LOGS, INV, 0>;
     using RL = RoundOf<LOGS, INV, R0::NR - 1>;
-    // layout: NS buffers (1 KiB aligned: the 128-byte swizzle repeats every
-    // 1 KiB), staged twiddles, barriers
-    unsigned char *base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     W *stage = reinterpret_cast<W *>(base);
     Tw<W> *tws = reinterpret_cast<Tw<W> *>(stage + (size_t)NS * BW);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(tws + TWP);      // NS tile barriers + 1 twiddle barrier
-    uint32_t &s_abort = *reinterpret_cast<uint32_t *>(bar + NS + 1);
+    if (t_begin >= t_end) return true;
 
     const uint32_t N = 1u << a.logN;
     const uint32_t tid = threadIdx.x;
     uint32_t k, tau;
     if (KIND == TK_COLS) { k = tid % K; tau = tid / K; }
     else { tau = tid % T; k = tid / T; }
-    const uint32_t smb_k = sm_off<W, LOGS, KIND>(k, 0);
+    const bool active = tid < K * T;       // (all threads of the block take part in barriers)
+    const uint32_t smb_k = sm_off<W, LOGS, KIND, P>(k, 0);
     const uint32_t L = a.L;
     const uint32_t B = (uint32_t)(a.ntrans / L);
     constexpr uint32_t S2 = kN2Log;   // log2 of the row length N2 (two-pass kinds)
     const uint32_t N1 = KIND == TK_SINGLE ? 1u : (N >> S2);
     const uint32_t per = KIND == TK_SINGLE ? 1u : (KIND == TK_COLS ? (1u << S2) : N1) / K;
-    const uint32_t t_begin = (uint32_t)((uint64_t)blockIdx.x * a.ntiles / gridDim.x);
-    const uint32_t t_end = (uint32_t)((uint64_t)(blockIdx.x + 1) * a.ntiles / gridDim.x);
-
     // Tile cursor: single tiles are K consecutive transforms; two-pass tiles
     // run polynomial-fastest, then position group, then limb.  It is decoded
     // once and then stepped, so the loop does no division.
@@ -426,11 +432,11 @@ k_fused(const __grid_constant__ FArgs<W> a) {
             const uint32_t rows = S < 256 ? S : 256u;
             mbar_expect_tx(&bar[s], (K << LOGS) * (uint32_t)sizeof(W));
             for (uint32_t r0 = 0; r0 < S; r0 += rows)
-                tma_2d_g2s(dst + r0 * K, &a.tmap, (int)pos0, (int)(t * N1 + r0), &bar[s]);
+                tma_2d_g2s(dst + r0 * K, tmap, (int)pos0, (int)(t * N1 + r0), &bar[s]);
         } else if (SWZ) {
             mbar_expect_tx(&bar[s], K * S * (uint32_t)sizeof(W));
             const uint64_t row0 = (t * N + ((size_t)pos0 << S2)) / RW;
-            tma_2d_g2s(dst, &a.tmap, 0, (int)row0, &bar[s]);
+            tma_2d_g2s(dst, tmap, 0, (int)row0, &bar[s]);
         } else if (KIND == TK_CHUNKS) {
             mbar_expect_tx(&bar[s], K * S * (uint32_t)sizeof(W));
             const W *src = a.data + t * N + ((size_t)pos0 << S2);
@@ -449,7 +455,7 @@ k_fused(const __grid_constant__ FArgs<W> a) {
         const uint32_t pos0 = c.g * K;
         if (KIND == TK_COLS) {
             const uint32_t rows = S < 256 ? S : 256u;
-            for (uint32_t r0 = 0; r0 < S; r0 += rows) prefetch_tensor_2d(&a.tmap, (int)pos0, (int)(t * N1 + r0));
+            for (uint32_t r0 = 0; r0 < S; r0 += rows) prefetch_tensor_2d(tmap, (int)pos0, (int)(t * N1 + r0));
         } else if (KIND == TK_CHUNKS) {
             prefetch_l2(a.data + t * N + ((size_t)pos0 << S2), K * S * (uint32_t)sizeof(W));
         } else {
@@ -458,26 +464,21 @@ k_fused(const __grid_constant__ FArgs<W> a) {
         }
     };
 
-    if (tid == 0) {
-        s_abort = 0;
-        for (uint32_t s = 0; s <= NS; ++s) mbar_init(&bar[s], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
     Cur ahead = cur_at(t_begin);   // next tile to issue (thread 0)
     Cur cur = ahead;               // tile being processed
     if (tid == 0) {
+        fence_proxy_async();   // the buffers may have been read by a previous call
         for (uint32_t s = 0; s < NS && t_begin + s < t_end; ++s) { issue(ahead, s); cur_next(ahead); }
         if (t_begin + NS < t_end) prefetch(ahead);
     }
     uint32_t tw_key = 0xffffffffu;  // (limb, group) of the staged twiddles
-    uint32_t tw_phase = 0;
+    uint32_t &tw_phase = ps.tw_phase;
     bool ok = true;
 
     uint32_t i = 0;
     for (uint32_t tile = t_begin; tile < t_end; ++tile, ++i, cur_next(cur)) {
         const uint32_t s = i % NS;
-        const uint32_t parity = (i / NS) & 1u;
+        const uint32_t parity = (ps.uses[s] + i / NS) & 1u;
         const uint32_t pos0 = cur.g * K;
         const uint64_t t = KIND == TK_SINGLE ? cur_t(cur) + k : cur_t(cur);
         const bool valid = t < a.ntrans;
@@ -554,11 +555,12 @@ k_fused(const __grid_constant__ FArgs<W> a) {
         }
         // every thread has its words (the buffer now serves the exchanges)
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) { s_abort = 1; atomicOr(a.status, 2u); }
+            if (tid == 0) atomicOr(a.status, 2u);
+            ok = false;
             break;
         }
         round_bfly<W, RED, INV, LOGS, 0, TWS>(x, tau, twb, kk, INV && a.final_pass, tn, twn);
-        later_rounds<W, RED, INV, LOGS, KIND, WS, TWS, 1>(x, sb, smb_k, tau, twb, kk, INV && a.final_pass, tn, twn);
+        later_rounds<W, RED, INV, LOGS, KIND, WS, TWS, 1, P>(x, sb, smb_k, tau, twb, kk, INV && a.final_pass, tn, twn);
         // the buffer and the twiddles are free: refill with the tile NS ahead
         __syncthreads();
         if (tid == 0 && tile + NS < t_end) {
@@ -576,7 +578,7 @@ k_fused(const __grid_constant__ FArgs<W> a) {
             }
         }
         // ---- last round straight to global memory
-        if (valid) {
+        if (valid && active) {
             const uint32_t AL = RL::A(tau);
             if (KIND == TK_COLS) {
                 W *g = a.data + t * N + pos0 + k;
@@ -602,27 +604,53 @@ k_fused(const __grid_constant__ FArgs<W> a) {
             }
         }
     }
-    // on an aborted wait, let the copies already in flight (local tiles
-    // i .. i+NS-1 and the twiddle table) land before the CTA exits, again
-    // with a time limit
-    if (s_abort && tid == 0) {
-        const uint32_t n_local = t_end - t_begin;
-        for (uint32_t j = i; j < i + NS && j < n_local; ++j) {
-            const long long t0 = clock64();
-            while (!mbar_try_wait(&bar[j % NS], (j / NS) & 1u))
-                if (clock64() - t0 > (1ll << 30)) break;
+    const uint32_t n_local = t_end - t_begin;
+    if (!ok) {
+        // an aborted wait: let the copies already in flight (local tiles
+        // i .. i+NS-1 and the twiddle table) land before the CTA goes on,
+        // again with a time limit
+        if (tid == 0) {
+            for (uint32_t j = i; j < i + NS && j < n_local; ++j) {
+                const long long t0 = clock64();
+                while (!mbar_try_wait(&bar[j % NS], (ps.uses[j % NS] + j / NS) & 1u))
+                    if (clock64() - t0 > (1ll << 30)) break;
+            }
+            if (TWS && tw_phase > 0) {
+                const long long t0 = clock64();
+                while (!mbar_try_wait(&bar[NS], (tw_phase - 1) & 1u))
+                    if (clock64() - t0 > (1ll << 30)) break;
+            }
         }
-        if (TWS && tw_phase > 0) {
-            const long long t0 = clock64();
-            while (!mbar_try_wait(&bar[NS], (tw_phase - 1) & 1u))
-                if (clock64() - t0 > (1ll << 30)) break;
-        }
+        return false;
     }
+    for (uint32_t s = 0; s < NS; ++s) ps.uses[s] += (n_local + NS - 1 - s) / NS;
+    return true;
 }
 
-template <class W, int LOGS, int KIND, bool INV> __host__ constexpr size_t fused_smem_bytes() {
-    return (size_t)n_stages<W, LOGS, KIND>() * buf_words<W, LOGS, KIND, INV>() * sizeof(W) +
-           (size_t)tw_pairs<W, LOGS, KIND>() * 2 * sizeof(W) + 8 * 4 + 16 + 1024;
+// Per-plan fused pass: CTA c processes tiles [c T / G, (c+1) T / G).
+template <class W, int RED, bool INV, int LOGS, int KIND>
+__global__ void __launch_bounds__(sizeof(W) == 4 ? 1024 : 512)
+k_fused(const __grid_constant__ FArgs<W> a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    constexpr uint32_t NS = n_stages<W, LOGS, KIND>();
+    constexpr uint32_t BW = buf_words<W, LOGS, KIND, INV, 0>();
+    constexpr uint32_t TWP = tw_pairs<W, LOGS, KIND, 0>();
+    unsigned char *base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + (size_t)NS * BW * sizeof(W) + (size_t)TWP * 2 * sizeof(W));
+    if (threadIdx.x == 0) {
+        for (uint32_t s = 0; s <= NS; ++s) mbar_init(&bar[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    PipeState ps{{0, 0}, 0};
+    const uint32_t t_begin = (uint32_t)((uint64_t)blockIdx.x * a.ntiles / gridDim.x);
+    const uint32_t t_end = (uint32_t)((uint64_t)(blockIdx.x + 1) * a.ntiles / gridDim.x);
+    run_tiles<W, RED, INV, LOGS, KIND, 0>(a, &a.tmap, t_begin, t_end, base, bar, ps);
+}
+
+template <class W, int LOGS, int KIND, bool INV, int P = 0> __host__ __device__ constexpr size_t fused_smem_bytes() {
+    return (size_t)n_stages<W, LOGS, KIND>() * buf_words<W, LOGS, KIND, INV, P>() * sizeof(W) +
+           (size_t)tw_pairs<W, LOGS, KIND, P>() * 2 * sizeof(W) + 8 * 4 + 16 + 1024;
 }
 
 }  // namespace nttgb

@@ -64,6 +64,11 @@ cudaError_t launch_check_range(ntt_plan_s &p, const void *data, uint32_t batch, 
 
 ntt_status ensure_scratch(ntt_plan_s &p, uint32_t batch, cudaStream_t st);
 
+// Plan builder (ntt_plan_create_ex with a cap on the single-pass size).
+ntt_status create_plan(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t L, ntt_variant variant,
+                       uint32_t flags, const uint64_t *psi, int single_max_log);
+ntt_status validate_plan_args(uint32_t N, const uint64_t *q, uint32_t L, uint32_t flags);
+
 // fused path, instantiated in fused_<word>_<reduction>.cu
 template <class W, int RED>
 cudaError_t run_fused_t(ntt_plan_s &p, void *data, uint32_t batch, bool inverse, cudaStream_t st);
