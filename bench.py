@@ -194,6 +194,101 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------ side workloads
+def _time_loop(torch, stream, fn, reps, warm=3):
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def ragged_vs_plain(nt, torch, dev, reps=10):
+    """The 512-polynomial ragged workload (N = 2^12..2^17 log-uniform, L =
+    1..32, half 30-bit / half 60-bit primes = 1 mod 2^18): forward + inverse
+    of every job in one graph launch, against the same jobs through the
+    per-plan API (one plan per (N, word size), ntt_*_prefix per job)."""
+    specs = ntt_synth.ragged_jobs(seed=1004, jobs=512)
+    plist = {32: nt.ntt_find_primes(30, 18, 32), 64: nt.ntt_find_primes(60, 18, 32)}
+    bufs, jobs = [], []
+    bytes_total, ntt_total = 0, 0
+    for i, sp in enumerate(specs):
+        qs = plist[sp["word"]][:sp["L"]]
+        N = 1 << sp["logN"]
+        h = ntt_synth.rns_batch(ntt_synth.stream_seed(1004, i, 99), qs, N, 1,
+                                dtype=np.uint32 if sp["word"] == 32 else np.uint64)
+        t = torch.from_numpy(h.view(np.int32 if sp["word"] == 32 else np.int64).reshape(-1).copy()).to(dev)
+        bufs.append(t)
+        jobs.append(dict(data=t, q=qs, N=N, batch=1, word64=sp["word"] == 64, inverse=False))
+        bytes_total += N * sp["L"] * sp["word"] // 8
+        ntt_total += sp["L"]
+    flags = nt.NTT_ORDER_BITREV | nt.NTT_RED_SHOUP
+    r = nt.ntt_ragged_create(jobs + [dict(j, inverse=True) for j in jobs], flags)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    try:
+        ms_r = _time_loop(torch, stream, lambda: nt.ntt_ragged_launch(r, sh), reps)
+        status = nt.ntt_ragged_status(r, sh)
+    finally:
+        nt.ntt_ragged_destroy(r)
+    plans = {}
+    for sp in specs:
+        key = (sp["logN"], sp["word"])
+        if key not in plans:
+            plans[key] = nt.ntt_plan_create(1 << sp["logN"], plist[sp["word"]], nt.NTT_FUSED,
+                                            flags | (nt.NTT_WORD64 if sp["word"] == 64 else 0))
+
+    def plain():
+        for sp, t in zip(specs, bufs):
+            p = plans[(sp["logN"], sp["word"])]
+            nt.ntt_forward_prefix(p, t, 1, sp["L"], sh)
+            nt.ntt_inverse_prefix(p, t, 1, sp["L"], sh)
+    try:
+        ms_p = _time_loop(torch, stream, plain, max(2, reps // 2))
+    finally:
+        for p in plans.values():
+            nt.ntt_plan_destroy(p)
+    n_step = 2 * ntt_total
+    bytes_step = 2 * 2 * bytes_total            # forward + inverse, each reads and writes
+    return {"workload": "512 polys, N=2^12..2^17, L=1..32, half u32/half u64; forward+inverse",
+            "transforms_per_step": n_step, "value": n_step / (ms_r / 1e3), "unit": "NTT/s",
+            "ms_per_step": ms_r, "algorithmic_gbs": bytes_step / (ms_r / 1e3) / 1e9,
+            "plain_value": n_step / (ms_p / 1e3), "plain_ms_per_step": ms_p,
+            "speedup_vs_plain": ms_p / ms_r, "device_status": status,
+            "note": "ragged = one graph-captured cooperative launch; plain = ntt_forward_prefix/"
+                    "ntt_inverse_prefix per job on shared (N, word) plans"}
+
+
+def wide_word(nt, torch, dev, reps=50):
+    """N = 2^16, 24 primes q < 2^60 (= 1 mod 2^17), u64, 8 polys: forward +
+    inverse, Montgomery and Shoup."""
+    qs = nt.ntt_find_primes(60, 17, 24)
+    N, B = 1 << 16, 8
+    host = ntt_synth.rns_batch(1003, qs, N, B, dtype=np.uint64)
+    d = torch.from_numpy(host.view(np.int64).reshape(-1).copy()).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    out = {"workload": "N=2^16, L=24 primes q<2^60, u64, 8 polys: forward + inverse"}
+    for red in ("montgomery", "shoup", "barrett"):
+        p = nt.ntt_plan_create(N, qs, nt.NTT_FUSED,
+                               nt.NTT_WORD64 | nt.NTT_ORDER_BITREV | nt.REDUCTIONS[red])
+        try:
+            def step():
+                nt.ntt_forward(p, d, B, sh)
+                nt.ntt_inverse(p, d, B, sh)
+            ms = _time_loop(torch, stream, step, reps)
+        finally:
+            nt.ntt_plan_destroy(p)
+        out[red] = {"value": 2 * B * 24 / (ms / 1e3), "unit": "NTT/s", "ms_per_step": ms}
+    return out
+
+
 # ------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -202,6 +297,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="nttgb", choices=["nttgb", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the ragged and wide-word side measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -335,6 +432,14 @@ def main():
         else "fallback 6.8 TB/s",
     }
 
+    extras = {}
+    if not args.no_extras:
+        for name, fn in (("ragged", ragged_vs_plain), ("wide_word_u64", wide_word)):
+            try:
+                extras[name] = fn(nt, torch, dev)
+            except Exception as exc:     # a side measurement never hides the main line
+                extras[name] = {"error": repr(exc)[:300]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, desc = oracle_sample(qs)
@@ -361,6 +466,7 @@ def main():
             "gpu_launches": lps * K,
             "clocks": clocks,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -130,6 +130,14 @@ ntt_status ntt_forward(ntt_plan_t plan, void *d_data, uint32_t batch,
 ntt_status ntt_inverse(ntt_plan_t plan, void *d_data, uint32_t batch,
                        ntt_stream_t stream);
 
+/* As ntt_forward / ntt_inverse for polynomials of only the plan's first
+ * `limbs` primes (1 <= limbs <= L): d_data holds [batch][limbs][N] words.
+ * RNS schemes drop limbs as they rescale; one plan serves every level. */
+ntt_status ntt_forward_prefix(ntt_plan_t plan, void *d_data, uint32_t batch,
+                              uint32_t limbs, ntt_stream_t stream);
+ntt_status ntt_inverse_prefix(ntt_plan_t plan, void *d_data, uint32_t batch,
+                              uint32_t limbs, ntt_stream_t stream);
+
 /*
  * c[k] = a[k] * b[k] mod q[l] for [batch][L][N] arrays (Sec. I: the product
  * step of NTT-based polynomial multiplication).  d_c may alias d_a or d_b.

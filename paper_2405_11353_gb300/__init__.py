@@ -52,7 +52,7 @@ EXPORTS = [
     "ntt_get_device_status", "ntt_plan_get_psi", "ntt_plan_last_launches",
     "ntt_status_string", "ntt_validate", "ntt_default_psi", "ntt_find_primes",
     "ntt_ragged_create", "ntt_ragged_launch", "ntt_ragged_status", "ntt_ragged_destroy",
-    "ntt_forward_noalloc",
+    "ntt_forward_noalloc", "ntt_forward_prefix", "ntt_inverse_prefix",
 ]
 
 
@@ -102,6 +102,8 @@ def lib():
             "ntt_ragged_status": (st, [vp, vp]),
             "ntt_ragged_destroy": (None, [vp]),
             "ntt_forward_noalloc": (st, [vp, vp, u32, vp]),
+            "ntt_forward_prefix": (st, [vp, vp, u32, u32, vp]),
+            "ntt_inverse_prefix": (st, [vp, vp, u32, u32, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -174,6 +176,16 @@ def ntt_forward(plan, data, batch, stream=None):
 
 def ntt_inverse(plan, data, batch, stream=None):
     _check(lib().ntt_inverse(plan, _ptr(data), batch, _stream(stream)), "ntt_inverse")
+
+
+def ntt_forward_prefix(plan, data, batch, limbs, stream=None):
+    _check(lib().ntt_forward_prefix(plan, _ptr(data), batch, limbs, _stream(stream)),
+           "ntt_forward_prefix")
+
+
+def ntt_inverse_prefix(plan, data, batch, limbs, stream=None):
+    _check(lib().ntt_inverse_prefix(plan, _ptr(data), batch, limbs, _stream(stream)),
+           "ntt_inverse_prefix")
 
 
 def ntt_pointwise_mul(plan, c, a, b, batch, stream=None):

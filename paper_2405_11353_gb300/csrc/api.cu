@@ -221,10 +221,26 @@ bool needs_scratch(const ntt_plan_s &p) {
     }
 }
 
-ntt_status run_transform(ntt_plan_t plan, void *d_data, uint32_t batch, ntt_stream_t stream, bool inverse) {
+ntt_status run_transform(ntt_plan_t plan, void *d_data, uint32_t batch, ntt_stream_t stream, bool inverse,
+                         uint32_t limbs = 0) {
     if (!plan || !d_data || batch == 0) return NTT_ERR_INVALID_ARG;
     if (!aligned16(d_data)) return NTT_ERR_ALIGNMENT;
+    if (limbs > plan->L) return NTT_ERR_INVALID_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (limbs && limbs != plan->L) {
+        // polynomials of the plan's first `limbs` primes: every table is per
+        // limb, so a view of the plan with a smaller L serves them
+        ntt_plan_s view = *plan;
+        view.L = limbs;
+        view.q.clear();
+        view.psi.clear();
+        ntt_status s = run_transform(&view, d_data, batch, stream, inverse, 0);
+        plan->last_launches = view.last_launches;
+        // the view may have grown (freed and replaced) the scratch buffer
+        plan->d_scratch = view.d_scratch;
+        plan->scratch_bytes = view.scratch_bytes;
+        return s;
+    }
     ntt_plan_s &p = *plan;
     p.last_launches = 0;
     if (needs_scratch(p)) {
@@ -405,6 +421,16 @@ ntt_status ntt_forward(ntt_plan_t plan, void *d_data, uint32_t batch, ntt_stream
 
 ntt_status ntt_inverse(ntt_plan_t plan, void *d_data, uint32_t batch, ntt_stream_t stream) {
     return run_transform(plan, d_data, batch, stream, true);
+}
+
+ntt_status ntt_forward_prefix(ntt_plan_t plan, void *d_data, uint32_t batch, uint32_t limbs, ntt_stream_t stream) {
+    if (limbs == 0) return NTT_ERR_INVALID_ARG;
+    return run_transform(plan, d_data, batch, stream, false, limbs);
+}
+
+ntt_status ntt_inverse_prefix(ntt_plan_t plan, void *d_data, uint32_t batch, uint32_t limbs, ntt_stream_t stream) {
+    if (limbs == 0) return NTT_ERR_INVALID_ARG;
+    return run_transform(plan, d_data, batch, stream, true, limbs);
 }
 
 ntt_status ntt_pointwise_mul(ntt_plan_t plan, void *d_c, const void *d_a, const void *d_b, uint32_t batch,

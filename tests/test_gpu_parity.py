@@ -387,3 +387,25 @@ def test_two_streams(nt, orc):
     finally:
         p1.close()
         p2.close()
+
+
+@pytest.mark.parametrize("variant", ["fused", "stockham"])
+def test_limb_prefix_entry_points(nt, orc, variant):
+    """Polynomials of the plan's first 3 of 5 primes (an RNS level below the top)."""
+    for n, w64 in [(12, False), (16, False), (14, True)]:
+        N = 1 << n
+        qs = primes_for(orc, N, w64, 5)
+        psis = [orc.psi(q, N) for q in qs[:3]]
+        host = ntt_synth.rns_batch(41 + n, qs[:3], N, 2)
+        p = Plan(nt, N, qs, variant, w64=w64, bitrev=True)
+        try:
+            d = to_dev(host, w64)
+            nt.ntt_forward_prefix(p.h, d, 2, 3)
+            got = to_host(d, w64, host.shape)
+            assert np.array_equal(got, reorder(orc.ntt_batch(host, qs[:3], psis), True, orc))
+            nt.ntt_inverse_prefix(p.h, d, 2, 3)
+            assert np.array_equal(to_host(d, w64, host.shape), host)
+            with pytest.raises(nt.NttError):
+                nt.ntt_forward_prefix(p.h, d, 2, 6)
+        finally:
+            p.close()
