@@ -289,6 +289,29 @@ def wide_word(nt, torch, dev, reps=50):
     return out
 
 
+def tc_fourstep(nt, torch, dev, reps=20):
+    """N = 2^16, 32 primes q < 2^30, u32, 16 polys: the forward transform as
+    the tensor-core four-step form (8-bit digit products, mma.sync u8 -> s32)
+    against the butterfly form on the same data."""
+    qs = nt.ntt_find_primes(30, 17, 32)
+    N, B = 1 << 16, 16
+    host = ntt_synth.rns_batch(1005, qs, N, B, dtype=np.uint32)
+    d = torch.from_numpy(host.view(np.int32).reshape(-1).copy()).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    out = {"workload": "N=2^16, L=32 primes q<2^30, u32, 16 polys: forward transform"}
+    macs = 2 * 2 * 256 * 256 * 256 * 16 * B * 32 / 2   # 2 passes x 256^3 per transform x 16 digit pairs
+    for name, variant in (("tensor_core", nt.NTT_TC_FOURSTEP), ("butterfly", nt.NTT_FUSED)):
+        p = nt.ntt_plan_create(N, qs, variant, nt.NTT_ORDER_BITREV)
+        try:
+            ms = _time_loop(torch, stream, lambda: nt.ntt_forward(p, d, B, sh), reps)
+        finally:
+            nt.ntt_plan_destroy(p)
+        out[name] = {"value": B * 32 / (ms / 1e3), "unit": "NTT/s", "ms_per_call": ms}
+    out["tensor_core"]["int8_tops"] = macs * 2 / (out["tensor_core"]["ms_per_call"] / 1e3) / 1e12
+    return out
+
+
 # ------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -434,7 +457,8 @@ def main():
 
     extras = {}
     if not args.no_extras:
-        for name, fn in (("ragged", ragged_vs_plain), ("wide_word_u64", wide_word)):
+        for name, fn in (("ragged", ragged_vs_plain), ("wide_word_u64", wide_word),
+                         ("tc_fourstep", tc_fourstep)):
             try:
                 extras[name] = fn(nt, torch, dev)
             except Exception as exc:     # a side measurement never hides the main line

@@ -68,7 +68,7 @@ ntt_status upload(void **dptr, const std::vector<uint8_t> &h) {
 
 void free_plan_memory(ntt_plan_s *p) {
     void *ptrs[] = {p->d_limb, p->d_w_fwd, p->d_w_inv, p->d_twist, p->d_untwist, p->d_main_fwd,
-                    p->d_main_inv, p->d_chunk_fwd, p->d_chunk_inv, p->d_scratch, p->d_status};
+                    p->d_main_inv, p->d_chunk_fwd, p->d_chunk_inv, p->d_tc, p->d_scratch, p->d_status};
     for (void *q : ptrs)
         if (q) cudaFree(q);
 }
@@ -98,12 +98,65 @@ ntt_status validate(uint32_t N, const uint64_t *q, uint32_t L, uint32_t flags) {
     return NTT_OK;
 }
 
+// Tensor-core four-step tables for N = 2^16 (layout described in tc.cu).
+// With k1 = bitrev8(u), k2 = bitrev8(v):
+//   forward column matrix  [u][n1] = psi^(256 (2 k1 + 1) n1)
+//   forward row matrix     [v][n2] = psi^(512 k2 n2)
+//   inverse row matrix     [n2][v] = psi^(-512 k2 n2) / 256
+//   inverse column matrix  [n1][u] = psi^(-256 (2 k1 + 1) n1) / 256
+//   forward twiddle        [u][n2] = psi^(n2 (2 k1 + 1))
+//   inverse twiddle        [u][n2] = psi^(-n2 (2 k1 + 1))
+// each matrix as four 8-bit digit planes; twiddles as Shoup pairs.
+void build_tc_tables(ntt_plan_s *p, std::vector<uint8_t> &out) {
+    const uint32_t L = p->L, N = p->N;
+    const size_t mat_bytes = (size_t)4 * L * 4 * 65536, tw_bytes = (size_t)2 * L * 65536 * 8;
+    out.assign(mat_bytes + tw_bytes + (size_t)L * 8 * 4, 0);
+    uint8_t *mats = out.data();
+    uint32_t *tws = reinterpret_cast<uint32_t *>(out.data() + mat_bytes);
+    uint32_t *pow8 = reinterpret_cast<uint32_t *>(out.data() + mat_bytes + tw_bytes);
+    std::vector<uint64_t> pw(N), pwi(N);
+    for (uint32_t l = 0; l < L; ++l) {
+        const uint64_t q = p->q[l], psi = p->psi[l], psi_inv = H::invm(psi, q);
+        const uint64_t inv256 = H::invm(256, q);
+        pw[0] = pwi[0] = 1;
+        for (uint32_t i = 1; i < N; ++i) { pw[i] = H::mulm(pw[i - 1], psi, q); pwi[i] = H::mulm(pwi[i - 1], psi_inv, q); }
+        // psi^e and psi^-e for any e >= 0 (psi^N = -1)
+        auto P = [&](uint64_t e, bool inv) -> uint64_t {
+            e %= 2ull * N;
+            const std::vector<uint64_t> &t = inv ? pwi : pw;
+            return e < N ? t[e] : (q - t[e - N]) % q;
+        };
+        auto put_mat = [&](int m, uint32_t row, uint32_t col, uint64_t v) {
+            uint8_t *base = mats + ((size_t)m * L + l) * 4 * 65536 + (size_t)row * 256 + col;
+            for (int d = 0; d < 4; ++d) base[(size_t)d * 65536] = (uint8_t)((v >> (8 * d)) & 255u);
+        };
+        for (uint32_t u = 0; u < 256; ++u) {
+            const uint64_t k1 = H::bitrev(u, 8);
+            for (uint32_t n = 0; n < 256; ++n) {
+                put_mat(0, u, n, P(256ull * (2 * k1 + 1) * n, false));
+                put_mat(1, u, n, P(512ull * k1 * n, false));                       // u plays v, k1 plays k2
+                put_mat(2, n, u, H::mulm(P(512ull * k1 * n, true), inv256, q));     // [n2][v]
+                put_mat(3, n, u, H::mulm(P(256ull * (2 * k1 + 1) * n, true), inv256, q));  // [n1][u]
+                const uint64_t wf = P((uint64_t)n * (2 * k1 + 1), false), wi = P((uint64_t)n * (2 * k1 + 1), true);
+                const size_t at = ((size_t)0 * L + l) * 65536 + (size_t)u * 256 + n;
+                const size_t ai = ((size_t)1 * L + l) * 65536 + (size_t)u * 256 + n;
+                tws[2 * at] = (uint32_t)wf;
+                tws[2 * at + 1] = (uint32_t)(((u128)wf << 32) / q);
+                tws[2 * ai] = (uint32_t)wi;
+                tws[2 * ai + 1] = (uint32_t)(((u128)wi << 32) / q);
+            }
+        }
+        for (int s = 0; s < 8; ++s) pow8[l * 8 + s] = (uint32_t)H::powm(2, 8ull * s, q);
+    }
+}
+
 ntt_status build_tables(ntt_plan_s *p) {
     const uint32_t N = p->N, L = p->L, n = p->logN;
     const bool w64 = p->word64;
     const int W = w64 ? 64 : 32;
     const size_t pair_bytes = w64 ? 16 : 8;
-    const bool variant_tabs = p->variant != NTT_FUSED || p->fused_mode == nttgb::FUSED_STAGES;
+    const bool variant_tabs = (p->variant != NTT_FUSED && p->variant != NTT_TC_FOURSTEP) ||
+                              p->fused_mode == nttgb::FUSED_STAGES;
     const bool fused_tabs = p->variant == NTT_FUSED && p->fused_mode != nttgb::FUSED_STAGES;
     const bool chunk_tabs = fused_tabs && p->fused_mode == nttgb::FUSED_TWO_PASS;
 
@@ -191,9 +244,12 @@ ntt_status build_tables(ntt_plan_s *p) {
             }
         }
     }
+    std::vector<uint8_t> tcb;
+    if (p->variant == NTT_TC_FOURSTEP) build_tc_tables(p, tcb);
     std::vector<uint8_t> lcb(sizeof(LimbConst) * L);
     std::memcpy(lcb.data(), lc.data(), lcb.size());
     ntt_status s;
+    if (!tcb.empty() && (s = upload(&p->d_tc, tcb)) != NTT_OK) return s;
     if ((s = upload((void **)&p->d_limb, lcb)) != NTT_OK) return s;
     if (variant_tabs) {
         if ((s = upload(&p->d_w_fwd, wf)) != NTT_OK) return s;
@@ -250,7 +306,12 @@ ntt_status run_transform(ntt_plan_t plan, void *d_data, uint32_t batch, ntt_stre
     cudaError_t e = cudaSuccess;
     if (p.check) e = nttgb::launch_check_range(p, d_data, batch, st);
     if (e == cudaSuccess) {
-        if (p.variant != NTT_FUSED || p.fused_mode == nttgb::FUSED_STAGES) {
+        if (p.variant == NTT_TC_FOURSTEP) {
+            // works in bit-reversed order, like the fused kernels
+            if (inverse && !p.bitrev_order) e = nttgb::launch_bitrev_permute(p, d_data, batch, st);
+            if (e == cudaSuccess) e = nttgb::launch_tc(p, d_data, batch, inverse, st);
+            if (e == cudaSuccess && !inverse && !p.bitrev_order) e = nttgb::launch_bitrev_permute(p, d_data, batch, st);
+        } else if (p.variant != NTT_FUSED || p.fused_mode == nttgb::FUSED_STAGES) {
             ntt_variant v = p.variant == NTT_FUSED ? NTT_FLAT : p.variant;
             e = nttgb::launch_variant(p, v, d_data, batch, inverse, st);
         } else {
@@ -348,7 +409,10 @@ ntt_status create_plan(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t
     if ((int)variant < NTT_DIT || (int)variant > NTT_TC_FOURSTEP) return NTT_ERR_INVALID_ARG;
     ntt_status s = validate(N, q, L, flags);
     if (s != NTT_OK) return s;
-    if (variant == NTT_TC_FOURSTEP) return NTT_ERR_UNSUPPORTED;
+    // the tensor-core four-step form: N = 2^16, 4-byte words, Shoup twiddles
+    if (variant == NTT_TC_FOURSTEP &&
+        (N != (1u << 16) || (flags & NTT_WORD64) || (flags & NTT_RED_MASK) != NTT_RED_SHOUP))
+        return NTT_ERR_UNSUPPORTED;
     ntt_plan_s *p = new (std::nothrow) ntt_plan_s();
     if (!p) return NTT_ERR_OOM;
     p->N = N;

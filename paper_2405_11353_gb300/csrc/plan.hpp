@@ -41,6 +41,7 @@ struct ntt_plan_s {
     void *d_main_inv = nullptr;  // psi^-bitrev(i)
     void *d_chunk_fwd = nullptr; // pass-B per-chunk layout of psi^bitrev
     void *d_chunk_inv = nullptr;
+    void *d_tc = nullptr;        // tensor-core four-step tables (see tc.cu)
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
     uint32_t *d_status = nullptr;
@@ -61,6 +62,7 @@ cudaError_t launch_fused(ntt_plan_s &p, void *data, uint32_t batch, bool inverse
 cudaError_t launch_pointwise(ntt_plan_s &p, void *c, const void *a, const void *b, uint32_t batch, cudaStream_t st);
 cudaError_t launch_bitrev_permute(ntt_plan_s &p, void *data, uint32_t batch, cudaStream_t st);
 cudaError_t launch_check_range(ntt_plan_s &p, const void *data, uint32_t batch, cudaStream_t st);
+cudaError_t launch_tc(ntt_plan_s &p, void *data, uint32_t batch, bool inverse, cudaStream_t st);
 
 ntt_status ensure_scratch(ntt_plan_s &p, uint32_t batch, cudaStream_t st);
 
