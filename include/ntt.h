@@ -88,6 +88,13 @@ typedef enum {
 #define NTT_RED_MONTGOMERY 0x20u   /* Montgomery reduction */
 #define NTT_RED_MASK 0x30u
 #define NTT_CHECK 0x100u           /* record input words >= q on the device */
+#define NTT_TEST_STALL 0x8000u     /* test hook, fused plans only: in every
+                                      forward call one CTA's first tile waits
+                                      for 16 bytes that never arrive, so its
+                                      bounded wait runs out (about a second)
+                                      and ntt_get_device_status then reports
+                                      NTT_ERR_TIMEOUT; the results of that
+                                      call are not valid */
 
 /*
  * Create a plan for batches of L-limb polynomials of N coefficients.

@@ -14,7 +14,7 @@ using u128 = unsigned __int128;
 
 namespace {
 
-constexpr uint32_t kKnownFlags = NTT_WORD64 | NTT_ORDER_BITREV | NTT_RED_MASK | NTT_CHECK;
+constexpr uint32_t kKnownFlags = NTT_WORD64 | NTT_ORDER_BITREV | NTT_RED_MASK | NTT_CHECK | NTT_TEST_STALL;
 constexpr uint32_t kMaxLimbs = 4096;
 
 int red_of(uint32_t flags) {

@@ -44,6 +44,7 @@ template <class W> struct FArgs {
     uint64_t ntiles;
     uint32_t logN, L, logK, s2;   // N2 = 2^s2 (cols / chunks)
     uint32_t final_pass;      // fully reduce output; inverse: fold N^-1
+    uint32_t stall_tx;        // test hook: extra bytes CTA 0 expects on its first tile
     CUtensorMap tmap;         // column passes: the data as rows of N2 words
 };
 
@@ -199,6 +200,10 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
+}
+// Raise the bytes the current phase waits for, without arriving.
+__device__ __forceinline__ void mbar_add_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
@@ -468,6 +473,8 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     Cur cur = ahead;               // tile being processed
     if (tid == 0) {
         fence_proxy_async();   // the buffers may have been read by a previous call
+        // (test hook: the first barrier waits for bytes no copy delivers)
+        if (a.stall_tx && blockIdx.x == 0) mbar_add_tx(&bar[0], a.stall_tx);
         for (uint32_t s = 0; s < NS && t_begin + s < t_end; ++s) { issue(ahead, s); cur_next(ahead); }
         if (t_begin + NS < t_end) prefetch(ahead);
     }

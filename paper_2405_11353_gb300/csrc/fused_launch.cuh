@@ -143,6 +143,7 @@ cudaError_t run_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, in
     a.L = p.L;
     a.s2 = p.s2;
     a.final_pass = final_pass ? 1u : 0u;
+    a.stall_tx = (p.flags & NTT_TEST_STALL) && !INV && KIND != TK_CHUNKS ? 16u : 0u;
     const uint32_t T = (1u << logS) / 16;
     const uint32_t K = tile_k_for<W, KIND>(logS);
     if (KIND == TK_SINGLE) a.ntiles = (ntrans + K - 1) / K;

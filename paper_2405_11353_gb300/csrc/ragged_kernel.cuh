@@ -73,6 +73,7 @@ __device__ __forceinline__ bool ragged_item(const RaggedArgs &ra, const RItem &i
     a.status = ra.status;
     a.ntrans = J.ntrans;
     a.ntiles = 0;
+    a.stall_tx = 0;
     a.logN = J.logN;
     a.L = J.L;
     a.logK = 0;

@@ -51,7 +51,7 @@ def test_validation_codes(nt):
     assert v(1024, [q60]) == nt.NTT_ERR_Q_WIDTH
     assert v(1024, [q60], nt.NTT_WORD64) == nt.NTT_OK
     assert v(1024, [(1 << 61) - 1], nt.NTT_WORD64) == nt.NTT_ERR_Q_WIDTH
-    assert v(1024, [12289], 0x8000) == nt.NTT_ERR_INVALID_ARG
+    assert v(1024, [12289], 0x40000) == nt.NTT_ERR_INVALID_ARG
     assert v(1024, [12289], nt.NTT_RED_MASK) == nt.NTT_ERR_INVALID_ARG
     assert v(1024, []) == nt.NTT_ERR_INVALID_ARG
 

@@ -409,3 +409,21 @@ def test_limb_prefix_entry_points(nt, orc, variant):
                 nt.ntt_forward_prefix(p.h, d, 2, 6)
         finally:
             p.close()
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(nt, orc):
+    """Failure path on the GPU without a fault: with the test hook, one CTA's
+    first tile waits for bytes that never arrive; its wait gives up after
+    about a second, the call reports NTT_ERR_TIMEOUT, and the next plan on
+    the same context works."""
+    N = 1 << 16
+    qs = primes_for(orc, N, False, 2)
+    host = ntt_synth.rns_batch(61, qs, N, 2)
+    p = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, nt.NTT_ORDER_BITREV | nt.NTT_TEST_STALL)
+    try:
+        d = to_dev(host, False)
+        nt.ntt_forward(p, d, 2)
+        assert nt.ntt_get_device_status(p) == nt.NTT_ERR_TIMEOUT
+    finally:
+        nt.ntt_plan_destroy(p)
+    roundtrip_check(nt, orc, N, qs, 2, "fused", bitrev=True, seed=62)
