@@ -88,6 +88,15 @@ typedef enum {
 #define NTT_RED_MONTGOMERY 0x20u   /* Montgomery reduction */
 #define NTT_RED_MASK 0x30u
 #define NTT_CHECK 0x100u           /* record input words >= q on the device */
+#define NTT_CLUSTER 0x200u         /* NTT_FUSED, N = 2^16, 4-byte words: one
+                                      pass per transform on a cluster of eight
+                                      CTAs (each word through DRAM once, the
+                                      exchange in distributed shared memory)
+                                      instead of the two-pass split; results
+                                      identical, kept for comparison (on
+                                      GB300 it moves half the DRAM bytes but
+                                      takes longer: a cluster barrier per
+                                      transform and single-buffered tiles) */
 #define NTT_TEST_STALL 0x8000u     /* test hook, fused plans only: in every
                                       forward call one CTA's first tile waits
                                       for 16 bytes that never arrive, so its

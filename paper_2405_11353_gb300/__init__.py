@@ -42,6 +42,7 @@ NTT_RED_BARRETT = 0x10
 NTT_RED_MONTGOMERY = 0x20
 NTT_RED_MASK = 0x30
 NTT_CHECK = 0x100
+NTT_CLUSTER = 0x200
 NTT_TEST_STALL = 0x8000
 REDUCTIONS = {"shoup": NTT_RED_SHOUP, "barrett": NTT_RED_BARRETT,
               "montgomery": NTT_RED_MONTGOMERY}

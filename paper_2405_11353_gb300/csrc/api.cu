@@ -14,7 +14,8 @@ using u128 = unsigned __int128;
 
 namespace {
 
-constexpr uint32_t kKnownFlags = NTT_WORD64 | NTT_ORDER_BITREV | NTT_RED_MASK | NTT_CHECK | NTT_TEST_STALL;
+constexpr uint32_t kKnownFlags =
+    NTT_WORD64 | NTT_ORDER_BITREV | NTT_RED_MASK | NTT_CHECK | NTT_CLUSTER | NTT_TEST_STALL;
 constexpr uint32_t kMaxLimbs = 4096;
 
 int red_of(uint32_t flags) {
@@ -67,8 +68,9 @@ ntt_status upload(void **dptr, const std::vector<uint8_t> &h) {
 }
 
 void free_plan_memory(ntt_plan_s *p) {
-    void *ptrs[] = {p->d_limb, p->d_w_fwd, p->d_w_inv, p->d_twist, p->d_untwist, p->d_main_fwd,
-                    p->d_main_inv, p->d_chunk_fwd, p->d_chunk_inv, p->d_tc, p->d_scratch, p->d_status};
+    void *ptrs[] = {p->d_limb,      p->d_w_fwd,     p->d_w_inv,   p->d_twist,    p->d_untwist,
+                    p->d_main_fwd,  p->d_main_inv,  p->d_chunk_fwd, p->d_chunk_inv, p->d_tc,
+                    p->d_clu_fwd,   p->d_clu_inv,   p->d_scratch,  p->d_status};
     for (void *q : ptrs)
         if (q) cudaFree(q);
 }
@@ -157,7 +159,8 @@ ntt_status build_tables(ntt_plan_s *p) {
     const size_t pair_bytes = w64 ? 16 : 8;
     const bool variant_tabs = (p->variant != NTT_FUSED && p->variant != NTT_TC_FOURSTEP) ||
                               p->fused_mode == nttgb::FUSED_STAGES;
-    const bool fused_tabs = p->variant == NTT_FUSED && p->fused_mode != nttgb::FUSED_STAGES;
+    const bool clu_tabs = p->variant == NTT_FUSED && p->fused_mode == nttgb::FUSED_CLUSTER;
+    const bool fused_tabs = p->variant == NTT_FUSED && p->fused_mode != nttgb::FUSED_STAGES && !clu_tabs;
     const bool chunk_tabs = fused_tabs && p->fused_mode == nttgb::FUSED_TWO_PASS;
 
     std::vector<LimbConst> lc(L);
@@ -169,6 +172,8 @@ ntt_status build_tables(ntt_plan_s *p) {
     const uint32_t CP = w64 ? nttgb::chunk_tab_pitch<uint64_t>() : nttgb::chunk_tab_pitch<uint32_t>();
     const size_t chunk_limb = (size_t)N1 * CP;       // pairs per limb, chunk tables
     if (chunk_tabs) { cf.resize(L * chunk_limb * pair_bytes); ci.resize(L * chunk_limb * pair_bytes); }
+    std::vector<uint8_t> kf, ki;   // cluster form tables (below)
+    if (clu_tabs) { kf.resize((size_t)L * 8 * (8192 + 16) * pair_bytes); ki.resize(kf.size()); }
     // main-table position of entry i (see level_pos in modarith.cuh)
     auto main_pos = [&](uint32_t i) -> uint32_t {
         if (p->fused_mode == nttgb::FUSED_SINGLE) return nttgb::level_pos(i, n);
@@ -246,6 +251,48 @@ ntt_status build_tables(ntt_plan_s *p) {
     }
     std::vector<uint8_t> tcb;
     if (p->variant == NTT_TC_FOURSTEP) build_tc_tables(p, tcb);
+    if (clu_tabs) {
+        // cluster form (cluster.cuh), word index g = 8192 k + 1024 r + j; per
+        // (limb, CTA c) a slice of 8192 + 16 pairs: block (c, r) of 1024
+        // points after six stages at 1024 r (local entry 2^s + i' = global
+        // entry 2^(s+6) + (8c + r) 2^s + i', level_pos layout); then round A
+        // (stages 1, 2, 4 across k: entries 1..7) at 8192 + e; then round X
+        // (stages 8, 16, 32 across r in block c: local entry 2^a + b =
+        // global entry 2^(a+3) + c 2^a + b) at 8200 + e.
+        const size_t SL = 8192 + 16;
+        for (uint32_t l = 0; l < L; ++l) {
+            const uint64_t q = p->q[l], psi = p->psi[l], psi_inv = H::invm(psi, q);
+            Enc enc{q, W, p->red, (uint64_t)(uint32_t)H::inv_pow2_64(q)};
+            uint64_t v, cc;
+            std::vector<uint64_t> pw(N), pwi(N);
+            pw[0] = 1; pwi[0] = 1;
+            for (uint32_t i = 1; i < N; ++i) { pw[i] = H::mulm(pw[i - 1], psi, q); pwi[i] = H::mulm(pwi[i - 1], psi_inv, q); }
+            auto put_both = [&](size_t at, uint32_t gidx) {
+                const uint32_t e = H::bitrev(gidx, (int)n);
+                enc(pw[e], v, cc); put_pair(kf, at, v, cc, w64);
+                enc(pwi[e], v, cc); put_pair(ki, at, v, cc, w64);
+            };
+            for (uint32_t c = 0; c < 8; ++c) {
+                const size_t sb = ((size_t)l * 8 + c) * SL;
+                for (uint32_t r = 0; r < 8; ++r) {
+                    const size_t kb = sb + (size_t)r * 1024;
+                    put_pair(kf, kb, 0, 0, w64);
+                    put_pair(ki, kb, 0, 0, w64);
+                    for (uint32_t s = 0; s < 10; ++s)
+                        for (uint32_t ip = 0; ip < (1u << s); ++ip)
+                            put_both(kb + nttgb::level_pos((1u << s) + ip, 10),
+                                     (1u << (s + 6)) + (8 * c + r) * (1u << s) + ip);
+                }
+                for (uint32_t e = 0; e < 16; ++e) { put_pair(kf, sb + 8192 + e, 0, 0, w64); put_pair(ki, sb + 8192 + e, 0, 0, w64); }
+                for (uint32_t a = 0; a < 3; ++a)
+                    for (uint32_t b = 0; b < (1u << a); ++b) {
+                        const uint32_t e = (1u << a) + b;
+                        put_both(sb + 8192 + e, e);
+                        put_both(sb + 8200 + e, (1u << (a + 3)) + c * (1u << a) + b);
+                    }
+            }
+        }
+    }
     std::vector<uint8_t> lcb(sizeof(LimbConst) * L);
     std::memcpy(lcb.data(), lc.data(), lcb.size());
     ntt_status s;
@@ -260,6 +307,10 @@ ntt_status build_tables(ntt_plan_s *p) {
     if (fused_tabs) {
         if ((s = upload(&p->d_main_fwd, mf)) != NTT_OK) return s;
         if ((s = upload(&p->d_main_inv, mi)) != NTT_OK) return s;
+    }
+    if (clu_tabs) {
+        if ((s = upload(&p->d_clu_fwd, kf)) != NTT_OK) return s;
+        if ((s = upload(&p->d_clu_inv, ki)) != NTT_OK) return s;
     }
     if (chunk_tabs) {
         if ((s = upload(&p->d_chunk_fwd, cf)) != NTT_OK) return s;
@@ -439,6 +490,9 @@ ntt_status create_plan(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t
         if (single_max_log >= 0 && single_max_log < single_max) single_max = single_max_log;
         if (p->logN < 4) p->fused_mode = nttgb::FUSED_STAGES;
         else if ((int)p->logN <= single_max) p->fused_mode = nttgb::FUSED_SINGLE;
+        else if ((int)p->logN == nttgb::kClusterLogN && !p->word64 && single_max_log < 0 &&
+                 (flags & NTT_CLUSTER))
+            p->fused_mode = nttgb::FUSED_CLUSTER;
         else {
             p->fused_mode = nttgb::FUSED_TWO_PASS;
             p->s2 = nttgb::kChunkLog;

@@ -10,7 +10,7 @@
 
 namespace nttgb {
 
-enum FusedMode : int { FUSED_STAGES = 0, FUSED_SINGLE = 1, FUSED_TWO_PASS = 2 };
+enum FusedMode : int { FUSED_STAGES = 0, FUSED_SINGLE = 1, FUSED_TWO_PASS = 2, FUSED_CLUSTER = 3 };
 
 // Largest transform done in one pass of the fused kernel (one CTA holds the
 // whole transform in shared memory): 2^14 words of 4 bytes, 2^13 of 8.
@@ -18,6 +18,9 @@ constexpr int kSingleMaxLog32 = 14;
 constexpr int kSingleMaxLog64 = 13;
 constexpr int kLogR = 4;          // 16 words per thread in the fused kernel
 constexpr int kChunkLog = 8;      // pass-B sub-transform size 256
+// One pass on a cluster of eight CTAs (cluster.cuh, flag NTT_CLUSTER):
+// N = 2^16, 4-byte words.
+constexpr int kClusterLogN = 16;
 
 }  // namespace nttgb
 
@@ -42,6 +45,9 @@ struct ntt_plan_s {
     void *d_chunk_fwd = nullptr; // pass-B per-chunk layout of psi^bitrev
     void *d_chunk_inv = nullptr;
     void *d_tc = nullptr;        // tensor-core four-step tables (see tc.cu)
+    // cluster form (cluster.cuh): [L][8][8192 + 16] twiddle pairs each
+    void *d_clu_fwd = nullptr;
+    void *d_clu_inv = nullptr;
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
     uint32_t *d_status = nullptr;
@@ -74,5 +80,8 @@ ntt_status validate_plan_args(uint32_t N, const uint64_t *q, uint32_t L, uint32_
 // fused path, instantiated in fused_<word>_<reduction>.cu
 template <class W, int RED>
 cudaError_t run_fused_t(ntt_plan_s &p, void *data, uint32_t batch, bool inverse, cudaStream_t st);
+// cluster form, instantiated in cluster_<reduction>.cu
+template <int RED>
+cudaError_t run_cluster(ntt_plan_s &p, void *data, uint32_t batch, bool inverse, cudaStream_t st);
 
 }  // namespace nttgb

@@ -425,6 +425,13 @@ cudaError_t launch_variant(ntt_plan_s &p, ntt_variant v, void *data, uint32_t ba
 }
 
 cudaError_t launch_fused(ntt_plan_s &p, void *data, uint32_t batch, bool inverse, cudaStream_t st) {
+    if (p.fused_mode == FUSED_CLUSTER) {
+        switch (p.red) {
+        case RED_SHOUP: return run_cluster<RED_SHOUP>(p, data, batch, inverse, st);
+        case RED_BARRETT: return run_cluster<RED_BARRETT>(p, data, batch, inverse, st);
+        default: return run_cluster<RED_MONTGOMERY>(p, data, batch, inverse, st);
+        }
+    }
     return dispatch(p, [&](auto w, auto r) {
         using W = decltype(w);
         return run_fused_t<W, decltype(r)::value>(p, data, batch, inverse, st);

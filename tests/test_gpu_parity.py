@@ -39,9 +39,10 @@ def to_host(t, w64, shape):
 
 
 class Plan:
-    def __init__(self, nt, N, qs, variant="fused", red="shoup", w64=False, bitrev=False, check=False):
+    def __init__(self, nt, N, qs, variant="fused", red="shoup", w64=False, bitrev=False, check=False,
+                 extra_flags=0):
         self.nt = nt
-        flags = nt.REDUCTIONS[red]
+        flags = nt.REDUCTIONS[red] | extra_flags
         if w64:
             flags |= nt.NTT_WORD64
         if bitrev:
@@ -76,11 +77,11 @@ def primes_for(orc, N, w64, L):
 
 
 def roundtrip_check(nt, orc, N, qs, batch, variant, red="shoup", w64=False, bitrev=False, seed=1,
-                    naive=False):
+                    naive=False, extra_flags=0):
     psis = [orc.psi(q, N) for q in qs]
     host = ntt_synth.rns_batch(seed, qs, N, batch)
     want = orc.ntt_batch(host, qs, psis, fast=not naive)
-    p = Plan(nt, N, qs, variant, red, w64, bitrev)
+    p = Plan(nt, N, qs, variant, red, w64, bitrev, extra_flags=extra_flags)
     try:
         assert nt.ntt_plan_get_psi(p.h, len(qs)) == psis
         d = to_dev(host, w64)
@@ -226,6 +227,50 @@ def test_workload_n2p16_L32_u32(nt, orc):
     # sampled coefficients of products against the schoolbook definition
     for i, l, j in [(0, 0, 0), (3, 5, 12345), (7, 31, (1 << 16) - 1), (5, 17, 40000)]:
         assert int(out[i, l, j]) == orc.negacyclic_mul_at(host[i, l], host[8 + i, l], qs[l], j)
+
+
+# ----------------------------------------- N = 2^16: two-pass and cluster
+@pytest.mark.parametrize("red", ["shoup", "barrett", "montgomery"])
+@pytest.mark.parametrize("cluster", [False, True])
+def test_n2p16_u32_two_pass_and_cluster(nt, orc, red, cluster):
+    """Both fused forms of N = 2^16 with 4-byte words (the two-pass split;
+    one pass on clusters of eight CTAs), both orders, batch sizes that give
+    clusters one transform, none, or uneven ranges, and limb changes inside
+    a cluster's range."""
+    N = 1 << 16
+    extra = nt.NTT_CLUSTER if cluster else 0
+    qs = primes_for(orc, N, False, 10)
+    for i, (batch, L, bitrev) in enumerate([(1, 1, True), (3, 5, False), (10, 10, True), (1, 7, True)]):
+        roundtrip_check(nt, orc, N, qs[:L], batch, "fused", red=red, bitrev=bitrev, seed=1600 + i,
+                        extra_flags=extra)
+
+
+def test_n2p16_u32_cluster_polymul_and_launches(nt, orc):
+    """The cluster form through a forward / pointwise / inverse pipeline of
+    the 32-limb workload shape (fewer polynomials), one launch per call."""
+    N = 1 << 16
+    qs = orc.find_primes(30, 17, 32)
+    pairs = 2
+    psis = [orc.psi(q, N) for q in qs]
+    host = ntt_synth.rns_batch(1606, qs, N, 2 * pairs)
+    p = Plan(nt, N, qs, "fused", bitrev=True, extra_flags=nt.NTT_CLUSTER)
+    try:
+        d = to_dev(host, False)
+        p.fwd(d, 2 * pairs)
+        assert nt.ntt_plan_last_launches(p.h) == 1
+        fwd = to_host(d, False, host.shape)
+        half = pairs * len(qs) * N
+        nt.ntt_pointwise_mul(p.h, d, d, d[half:], pairs)
+        p.inv(d, pairs)
+        assert nt.ntt_plan_last_launches(p.h) == 1
+        out = to_host(d[:half], False, (pairs, len(qs), N))
+        assert nt.ntt_get_device_status(p.h) == nt.NTT_OK
+    finally:
+        p.close()
+    A = orc.ntt_batch(host, qs, psis)
+    assert np.array_equal(fwd, reorder(A, True, orc))
+    P = orc.pointwise_batch(A[:pairs], A[pairs:], qs)
+    assert np.array_equal(out, orc.ntt_batch(P, qs, psis, inverse=True))
 
 
 # ------------------------------------------------------------- edge cases
@@ -392,12 +437,15 @@ def test_two_streams(nt, orc):
 @pytest.mark.parametrize("variant", ["fused", "stockham"])
 def test_limb_prefix_entry_points(nt, orc, variant):
     """Polynomials of the plan's first 3 of 5 primes (an RNS level below the top)."""
-    for n, w64 in [(12, False), (16, False), (14, True)]:
+    cases = [(12, False, 0), (16, False, 0), (14, True, 0)]
+    if variant == "fused":
+        cases.append((16, False, nt.NTT_CLUSTER))
+    for n, w64, extra in cases:
         N = 1 << n
         qs = primes_for(orc, N, w64, 5)
         psis = [orc.psi(q, N) for q in qs[:3]]
         host = ntt_synth.rns_batch(41 + n, qs[:3], N, 2)
-        p = Plan(nt, N, qs, variant, w64=w64, bitrev=True)
+        p = Plan(nt, N, qs, variant, w64=w64, bitrev=True, extra_flags=extra)
         try:
             d = to_dev(host, w64)
             nt.ntt_forward_prefix(p.h, d, 2, 3)
@@ -411,7 +459,8 @@ def test_limb_prefix_entry_points(nt, orc, variant):
             p.close()
 
 
-def test_bounded_wait_reports_timeout_and_context_survives(nt, orc):
+@pytest.mark.parametrize("cluster", [False, True])
+def test_bounded_wait_reports_timeout_and_context_survives(nt, orc, cluster):
     """Failure path on the GPU without a fault: with the test hook, one CTA's
     first tile waits for bytes that never arrive; its wait gives up after
     about a second, the call reports NTT_ERR_TIMEOUT, and the next plan on
@@ -419,7 +468,8 @@ def test_bounded_wait_reports_timeout_and_context_survives(nt, orc):
     N = 1 << 16
     qs = primes_for(orc, N, False, 2)
     host = ntt_synth.rns_batch(61, qs, N, 2)
-    p = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, nt.NTT_ORDER_BITREV | nt.NTT_TEST_STALL)
+    extra = nt.NTT_CLUSTER if cluster else 0
+    p = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, nt.NTT_ORDER_BITREV | nt.NTT_TEST_STALL | extra)
     try:
         d = to_dev(host, False)
         nt.ntt_forward(p, d, 2)
