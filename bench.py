@@ -312,6 +312,29 @@ def tc_fourstep(nt, torch, dev, reps=20):
     return out
 
 
+def cluster_form(nt, torch, dev, reps=50):
+    """N = 2^16, 32 primes q < 2^30, u32, 16 polys: forward and inverse as
+    the two-pass split (default) and as one pass on eight-CTA clusters
+    (NTT_CLUSTER), which reads and writes each word once."""
+    qs = nt.ntt_find_primes(30, 17, 32)
+    N, B = 1 << 16, 16
+    host = ntt_synth.rns_batch(1005, qs, N, B, dtype=np.uint32)
+    d = torch.from_numpy(host.view(np.int32).reshape(-1).copy()).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    out = {"workload": "N=2^16, L=32 primes q<2^30, u32, 16 polys: forward, inverse"}
+    for name, extra in (("two_pass", 0), ("cluster_one_pass", nt.NTT_CLUSTER)):
+        p = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, nt.NTT_ORDER_BITREV | extra)
+        try:
+            ms_f = _time_loop(torch, stream, lambda: nt.ntt_forward(p, d, B, sh), reps)
+            ms_i = _time_loop(torch, stream, lambda: nt.ntt_inverse(p, d, B, sh), reps)
+        finally:
+            nt.ntt_plan_destroy(p)
+        out[name] = {"forward_ms": ms_f, "inverse_ms": ms_i,
+                     "forward_value": B * 32 / (ms_f / 1e3), "unit": "NTT/s"}
+    return out
+
+
 # ------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -458,7 +481,7 @@ def main():
     extras = {}
     if not args.no_extras:
         for name, fn in (("ragged", ragged_vs_plain), ("wide_word_u64", wide_word),
-                         ("tc_fourstep", tc_fourstep)):
+                         ("tc_fourstep", tc_fourstep), ("cluster_form", cluster_form)):
             try:
                 extras[name] = fn(nt, torch, dev)
             except Exception as exc:     # a side measurement never hides the main line

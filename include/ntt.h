@@ -167,10 +167,18 @@ ntt_status ntt_pointwise_mul(ntt_plan_t plan, void *d_c, const void *d_a,
  * End-to-end negacyclic products from host memory, for `pairs` products:
  * h_in holds [2][pairs][L][N] words (all first factors, then all second
  * factors), h_out receives [pairs][L][N] words of a_i * b_i mod
- * (x^N + 1, q).  d_work is a device buffer of at least 2*pairs*L*N words.
- * Enqueues host-to-device copy, forward NTT of 2*pairs polynomials,
- * pointwise product, inverse NTT of the products and device-to-host copy on
- * `stream`; the caller synchronises.  Host buffers should be pinned.
+ * (x^N + 1, q).  d_work is a device buffer of at least 2*pairs*L*N words
+ * (its contents are overwritten).  The products are computed as up to 8
+ * chunks of pairs in a pipeline: each chunk's host-to-device copy, its
+ * forward NTTs, pointwise product and inverse NTT, and its device-to-host
+ * copy, with the copies on two streams the plan owns and the transforms on
+ * `stream`, so copies of one chunk overlap the arithmetic of others.  The
+ * call is ordered after earlier work on `stream`, and later work on `stream`
+ * after all of it; the caller synchronises `stream` before reading h_out.
+ * Host buffers should be pinned (pageable memory serialises the copies).
+ * The first call on a plan creates its streams and events: make it outside
+ * stream capture.  Calls on one plan must not run concurrently from several
+ * host threads.
  */
 ntt_status ntt_polymul_host(ntt_plan_t plan, void *h_out, const void *h_in,
                             void *d_work, uint32_t pairs, ntt_stream_t stream);

@@ -73,6 +73,11 @@ void free_plan_memory(ntt_plan_s *p) {
                     p->d_clu_fwd,   p->d_clu_inv,   p->d_scratch,  p->d_status};
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    if (p->aux_ready) {
+        cudaStreamDestroy(p->aux_h2d);
+        cudaStreamDestroy(p->aux_d2h);
+        for (cudaEvent_t e : p->aux_ev) cudaEventDestroy(e);
+    }
 }
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -572,24 +577,56 @@ ntt_status ntt_polymul_host(ntt_plan_t plan, void *h_out, const void *h_in, void
     if (!plan || !h_out || !h_in || !d_work || pairs == 0) return NTT_ERR_INVALID_ARG;
     if (!aligned16(d_work)) return NTT_ERR_ALIGNMENT;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const size_t poly_bytes = (size_t)plan->L * plan->N * plan->word_bytes();
-    const size_t half = (size_t)pairs * poly_bytes;
+    ntt_plan_s &p = *plan;
+    // Chunks of g pairs run as a three-stage pipeline: host-to-device copies
+    // on one stream, the transforms on the caller's stream, device-to-host
+    // copies on a third, chained by events, so the copies of one chunk
+    // overlap the arithmetic of the others.  Chunk c's inputs land at
+    // d_work + c * 2g polynomials as [a | b].
+    if (!p.aux_ready) {
+        if (cudaStreamCreateWithFlags(&p.aux_h2d, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&p.aux_d2h, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return NTT_ERR_CUDA;
+        }
+        for (cudaEvent_t &e : p.aux_ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); return NTT_ERR_CUDA; }
+        p.aux_ready = true;
+    }
+    const size_t poly = (size_t)p.L * p.N * p.word_bytes();
+    const uint32_t g = (pairs + nttgb::kHostChunks - 1) / nttgb::kHostChunks;
+    const uint32_t chunks = (pairs + g - 1) / g;
+    const uint8_t *hi = reinterpret_cast<const uint8_t *>(h_in);
+    uint8_t *ho = reinterpret_cast<uint8_t *>(h_out);
     uint8_t *d = reinterpret_cast<uint8_t *>(d_work);
-    if (cudaMemcpyAsync(d, h_in, 2 * half, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-        cudaGetLastError();
-        return NTT_ERR_CUDA;
-    }
+    cudaEvent_t *ev = p.aux_ev;   // [0]: start, [1]: end, then per chunk (copied in, computed)
+    bool ok = cudaEventRecord(ev[0], st) == cudaSuccess && cudaStreamWaitEvent(p.aux_h2d, ev[0], 0) == cudaSuccess &&
+              cudaStreamWaitEvent(p.aux_d2h, ev[0], 0) == cudaSuccess;
     uint32_t launches = 0;
-    ntt_status s = ntt_forward(plan, d, 2 * pairs, stream);
-    launches += plan->last_launches;
-    if (s == NTT_OK) { s = ntt_pointwise_mul(plan, d, d, d + half, pairs, stream); launches += plan->last_launches; }
-    if (s == NTT_OK) { s = ntt_inverse(plan, d, pairs, stream); launches += plan->last_launches; }
-    plan->last_launches = launches;
-    if (s != NTT_OK) return s;
-    if (cudaMemcpyAsync(h_out, d, half, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
-        cudaGetLastError();
-        return NTT_ERR_CUDA;
+    ntt_status s = NTT_OK;
+    for (uint32_t c = 0; c < chunks && ok && s == NTT_OK; ++c) {
+        const uint32_t p0 = c * g, gc = pairs - p0 < g ? pairs - p0 : g;
+        uint8_t *dc = d + (size_t)2 * p0 * poly;
+        cudaEvent_t e_in = ev[2 + 2 * c], e_done = ev[3 + 2 * c];
+        ok = cudaMemcpyAsync(dc, hi + (size_t)p0 * poly, gc * poly, cudaMemcpyHostToDevice, p.aux_h2d) == cudaSuccess &&
+             cudaMemcpyAsync(dc + gc * poly, hi + ((size_t)pairs + p0) * poly, gc * poly, cudaMemcpyHostToDevice,
+                             p.aux_h2d) == cudaSuccess &&
+             cudaEventRecord(e_in, p.aux_h2d) == cudaSuccess && cudaStreamWaitEvent(st, e_in, 0) == cudaSuccess;
+        if (!ok) break;
+        s = ntt_forward(plan, dc, 2 * gc, stream);
+        launches += p.last_launches;
+        if (s == NTT_OK) { s = ntt_pointwise_mul(plan, dc, dc, dc + gc * poly, gc, stream); launches += p.last_launches; }
+        if (s == NTT_OK) { s = ntt_inverse(plan, dc, gc, stream); launches += p.last_launches; }
+        if (s != NTT_OK) break;
+        ok = cudaEventRecord(e_done, st) == cudaSuccess && cudaStreamWaitEvent(p.aux_d2h, e_done, 0) == cudaSuccess &&
+             cudaMemcpyAsync(ho + (size_t)p0 * poly, dc, gc * poly, cudaMemcpyDeviceToHost, p.aux_d2h) == cudaSuccess;
     }
+    // the caller's stream resumes after the last copy out (also on an error,
+    // so no work of this call outlives what the caller waits for)
+    const bool joined = cudaEventRecord(ev[1], p.aux_d2h) == cudaSuccess && cudaStreamWaitEvent(st, ev[1], 0) == cudaSuccess;
+    p.last_launches = launches;
+    if (s != NTT_OK) return s;
+    if (!ok || !joined) { cudaGetLastError(); return NTT_ERR_CUDA; }
     return NTT_OK;
 }
 

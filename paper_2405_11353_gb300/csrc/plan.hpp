@@ -21,6 +21,8 @@ constexpr int kChunkLog = 8;      // pass-B sub-transform size 256
 // One pass on a cluster of eight CTAs (cluster.cuh, flag NTT_CLUSTER):
 // N = 2^16, 4-byte words.
 constexpr int kClusterLogN = 16;
+// ntt_polymul_host splits its pairs into at most this many pipelined chunks.
+constexpr uint32_t kHostChunks = 8;
 
 }  // namespace nttgb
 
@@ -52,6 +54,11 @@ struct ntt_plan_s {
     size_t scratch_bytes = 0;
     uint32_t *d_status = nullptr;
     uint32_t last_launches = 0;
+
+    // ntt_polymul_host pipeline: copy streams and events, made on first use
+    bool aux_ready = false;
+    cudaStream_t aux_h2d = nullptr, aux_d2h = nullptr;
+    cudaEvent_t aux_ev[2 + 2 * nttgb::kHostChunks] = {};
 
     int fused_mode = nttgb::FUSED_STAGES;
     uint32_t s1 = 0, s2 = 0;     // two-pass split: N = 2^s1 * 2^s2

@@ -387,24 +387,33 @@ def test_extreme_inputs_all_q_minus_1(nt, orc):
 
 
 def test_polymul_host_entry(nt, orc):
-    """The host-buffer entry point: copies, transforms and products in one call."""
-    N, pairs = 2048, 3
+    """The host-buffer entry point: copies, transforms and products in one
+    call, pipelined in chunks of pairs (1, 3 and 13 pairs: one chunk, chunks
+    of one pair, chunks of two with a short last one); two calls back to back
+    on one non-default stream, read after synchronising only that stream."""
+    N = 2048
     qs = primes_for(orc, N, False, 2)
-    host = ntt_synth.rns_batch(21, qs, N, 2 * pairs).astype(np.uint32)
     p = Plan(nt, N, qs, "fused", bitrev=True)
+    stream = torch.cuda.Stream()
     try:
-        h_in = torch.from_numpy(host.view(np.int32).copy()).pin_memory()
-        h_out = torch.zeros(pairs * 2 * N, dtype=torch.int32).pin_memory()
-        work = torch.empty(2 * pairs * 2 * N, dtype=torch.int32, device="cuda")
-        nt.ntt_polymul_host(p.h, h_out, h_in, work, pairs)
-        torch.cuda.synchronize()
-        got = h_out.numpy().view(np.uint32).reshape(pairs, 2, N)
+        for pairs in (1, 3, 13):
+            work = torch.empty(2 * pairs * 2 * N, dtype=torch.int32, device="cuda")
+            runs = []
+            for seed in (21, 22):
+                host = ntt_synth.rns_batch(seed + 100 * pairs, qs, N, 2 * pairs).astype(np.uint32)
+                h_in = torch.from_numpy(host.view(np.int32).copy()).pin_memory()
+                h_out = torch.zeros(pairs * 2 * N, dtype=torch.int32).pin_memory()
+                nt.ntt_polymul_host(p.h, h_out, h_in, work, pairs, stream.cuda_stream)
+                runs.append((host, h_out))
+            stream.synchronize()
+            for host, h_out in runs:
+                got = h_out.numpy().view(np.uint32).reshape(pairs, 2, N)
+                for i in range(pairs):
+                    for l in range(2):
+                        assert np.array_equal(got[i, l].astype(np.uint64),
+                                              orc.negacyclic_mul(host[i, l], host[pairs + i, l], qs[l]))
     finally:
         p.close()
-    for i in range(pairs):
-        for l in range(2):
-            assert np.array_equal(got[i, l].astype(np.uint64),
-                                  orc.negacyclic_mul(host[i, l], host[pairs + i, l], qs[l]))
 
 
 def test_two_streams(nt, orc):
