@@ -164,6 +164,22 @@ ntt_status ntt_pointwise_mul(ntt_plan_t plan, void *d_c, const void *d_a,
                              ntt_stream_t stream);
 
 /*
+ * c = INTT(a (.) b): the pointwise product followed by the inverse
+ * transform (Sec. I: the last two steps of NTT-based polynomial
+ * multiplication), for [batch][L][N] arrays of forward outputs; c then holds
+ * the coefficients of the negacyclic products.  Same result as
+ * ntt_pointwise_mul(c, a, b) then ntt_inverse(c).  For fused plans of the
+ * two-pass size range (N > 2^14 with 4-byte words, N > 2^13 with 8-byte)
+ * in bit-reversed order without NTT_CHECK, the product is taken inside the
+ * first inverse pass (b is read beside a), saving a write and a read of c;
+ * other plans run the two steps.  d_c may alias d_a or d_b, or be disjoint
+ * from both; partial overlaps are not allowed.
+ */
+ntt_status ntt_pointwise_inverse(ntt_plan_t plan, void *d_c, const void *d_a,
+                                 const void *d_b, uint32_t batch,
+                                 ntt_stream_t stream);
+
+/*
  * End-to-end negacyclic products from host memory, for `pairs` products:
  * h_in holds [2][pairs][L][N] words (all first factors, then all second
  * factors), h_out receives [pairs][L][N] words of a_i * b_i mod

@@ -54,7 +54,7 @@ EXPORTS = [
     "ntt_get_device_status", "ntt_plan_get_psi", "ntt_plan_last_launches",
     "ntt_status_string", "ntt_validate", "ntt_default_psi", "ntt_find_primes",
     "ntt_ragged_create", "ntt_ragged_launch", "ntt_ragged_status", "ntt_ragged_destroy",
-    "ntt_forward_noalloc", "ntt_forward_prefix", "ntt_inverse_prefix",
+    "ntt_forward_noalloc", "ntt_forward_prefix", "ntt_inverse_prefix", "ntt_pointwise_inverse",
 ]
 
 
@@ -91,6 +91,7 @@ def lib():
             "ntt_forward": (st, [vp, vp, u32, vp]),
             "ntt_inverse": (st, [vp, vp, u32, vp]),
             "ntt_pointwise_mul": (st, [vp, vp, vp, vp, u32, vp]),
+            "ntt_pointwise_inverse": (st, [vp, vp, vp, vp, u32, vp]),
             "ntt_polymul_host": (st, [vp, vp, vp, vp, u32, vp]),
             "ntt_get_device_status": (st, [vp, vp]),
             "ntt_plan_get_psi": (st, [vp, u64p]),
@@ -193,6 +194,11 @@ def ntt_inverse_prefix(plan, data, batch, limbs, stream=None):
 def ntt_pointwise_mul(plan, c, a, b, batch, stream=None):
     _check(lib().ntt_pointwise_mul(plan, _ptr(c), _ptr(a), _ptr(b), batch, _stream(stream)),
            "ntt_pointwise_mul")
+
+
+def ntt_pointwise_inverse(plan, c, a, b, batch, stream=None):
+    _check(lib().ntt_pointwise_inverse(plan, _ptr(c), _ptr(a), _ptr(b), batch, _stream(stream)),
+           "ntt_pointwise_inverse")
 
 
 def ntt_polymul_host(plan, h_out, h_in, d_work, pairs, stream=None):

@@ -572,6 +572,30 @@ ntt_status ntt_pointwise_mul(ntt_plan_t plan, void *d_c, const void *d_a, const 
     return NTT_OK;
 }
 
+ntt_status ntt_pointwise_inverse(ntt_plan_t plan, void *d_c, const void *d_a, const void *d_b, uint32_t batch,
+                                 ntt_stream_t stream) {
+    if (!plan || !d_c || !d_a || !d_b || batch == 0) return NTT_ERR_INVALID_ARG;
+    if (!aligned16(d_c) || !aligned16(d_a) || !aligned16(d_b)) return NTT_ERR_ALIGNMENT;
+    ntt_plan_s &p = *plan;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // one fused launch pair where the inverse starts with the chunk pass on
+    // bit-reversed input; otherwise the product, then the inverse
+    if (p.variant == NTT_FUSED && p.fused_mode == nttgb::FUSED_TWO_PASS && p.bitrev_order && !p.check) {
+        p.last_launches = 0;   // (each pass counts itself)
+        if (nttgb::launch_fused_pwinv(p, d_c, d_a, d_b, batch, st) != cudaSuccess) {
+            cudaGetLastError();
+            return NTT_ERR_CUDA;
+        }
+        return NTT_OK;
+    }
+    ntt_status s = ntt_pointwise_mul(plan, d_c, d_a, d_b, batch, stream);
+    if (s != NTT_OK) return s;
+    const uint32_t pw = p.last_launches;
+    s = ntt_inverse(plan, d_c, batch, stream);
+    p.last_launches += pw;
+    return s;
+}
+
 ntt_status ntt_polymul_host(ntt_plan_t plan, void *h_out, const void *h_in, void *d_work, uint32_t pairs,
                             ntt_stream_t stream) {
     if (!plan || !h_out || !h_in || !d_work || pairs == 0) return NTT_ERR_INVALID_ARG;
@@ -615,8 +639,7 @@ ntt_status ntt_polymul_host(ntt_plan_t plan, void *h_out, const void *h_in, void
         if (!ok) break;
         s = ntt_forward(plan, dc, 2 * gc, stream);
         launches += p.last_launches;
-        if (s == NTT_OK) { s = ntt_pointwise_mul(plan, dc, dc, dc + gc * poly, gc, stream); launches += p.last_launches; }
-        if (s == NTT_OK) { s = ntt_inverse(plan, dc, gc, stream); launches += p.last_launches; }
+        if (s == NTT_OK) { s = ntt_pointwise_inverse(plan, dc, dc, dc + gc * poly, gc, stream); launches += p.last_launches; }
         if (s != NTT_OK) break;
         ok = cudaEventRecord(e_done, st) == cudaSuccess && cudaStreamWaitEvent(p.aux_d2h, e_done, 0) == cudaSuccess &&
              cudaMemcpyAsync(ho + (size_t)p0 * poly, dc, gc * poly, cudaMemcpyDeviceToHost, p.aux_d2h) == cudaSuccess;

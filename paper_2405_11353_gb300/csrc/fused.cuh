@@ -36,7 +36,11 @@ enum TileKind : int { TK_SINGLE = 0, TK_COLS = 1, TK_CHUNKS = 2 };
 constexpr uint32_t kN2Log = 8;
 
 template <class W> struct FArgs {
-    W *data;
+    W *data;                  // the tiles are read from here ...
+    W *out;                   // ... and written here (the same buffer but in
+                              // the fused pointwise + inverse first pass)
+    const W *pw_b;            // inverse chunk pass: multiply each word by this
+                              // operand's word first (Eq. 3), or null
     const Tw<W> *tw;          // [L][N] table of this pass
     const LimbConst *lc;
     uint32_t *status;         // plan status word (bit 1: timeout)
@@ -560,6 +564,28 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
                 for (int e = 0; e < 16; ++e) x[e] = sb[k * SP + (A0 | R0::E(e))];
             }
         }
+        if constexpr (KIND == TK_CHUNKS && INV && R0::RR == 4 && R0::LO == 0) {
+            // fused pointwise product: the inverse of a (.) b reads b's 16
+            // words at the same positions
+            if (a.pw_b && valid) {
+                const W *bq = a.pw_b + t * N + ((size_t)(pos0 + k) << S2) + R0::A(tau);
+                constexpr int V = 16 / sizeof(W);
+#pragma unroll
+                for (int v = 0; v < 16 / V; ++v) {
+                    if (sizeof(W) == 4) {
+                        uint4 w4 = __ldg(reinterpret_cast<const uint4 *>(bq) + v);
+                        x[4 * v] = mul_var<RED>(x[4 * v], (W)w4.x, kk);
+                        x[4 * v + 1] = mul_var<RED>(x[4 * v + 1], (W)w4.y, kk);
+                        x[4 * v + 2] = mul_var<RED>(x[4 * v + 2], (W)w4.z, kk);
+                        x[4 * v + 3] = mul_var<RED>(x[4 * v + 3], (W)w4.w, kk);
+                    } else {
+                        ulonglong2 w2 = __ldg(reinterpret_cast<const ulonglong2 *>(bq) + v);
+                        x[2 * v] = mul_var<RED>(x[2 * v], (W)w2.x, kk);
+                        x[2 * v + 1] = mul_var<RED>(x[2 * v + 1], (W)w2.y, kk);
+                    }
+                }
+            }
+        }
         // every thread has its words (the buffer now serves the exchanges)
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicOr(a.status, 2u);
@@ -588,11 +614,11 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
         if (valid && active) {
             const uint32_t AL = RL::A(tau);
             if (KIND == TK_COLS) {
-                W *g = a.data + t * N + pos0 + k;
+                W *g = a.out + t * N + pos0 + k;
 #pragma unroll
                 for (int e = 0; e < 16; ++e) g[(size_t)(AL | RL::E(e)) << S2] = x[e];
             } else {
-                W *g = KIND == TK_SINGLE ? a.data + t * N : a.data + t * N + ((size_t)(pos0 + k) << S2);
+                W *g = KIND == TK_SINGLE ? a.out + t * N : a.out + t * N + ((size_t)(pos0 + k) << S2);
                 if (RL::RR == 4 && RL::LO == 0) {
                     W *q = g + AL;
 #pragma unroll

@@ -129,12 +129,16 @@ template <class W, int KIND, bool INV> size_t smem_for(int logS) {
 // threads each.
 inline uint32_t ilog2(uint32_t x) { uint32_t r = 0; while ((1u << r) < x) ++r; return r; }
 
+// One pass over `data` in place, or (out, pw_b set: the inverse chunk pass
+// of the fused pointwise + inverse) from `data` times pw_b into `out`.
 template <class W, int RED, bool INV, int KIND>
 cudaError_t run_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, int logS, bool final_pass,
-                     cudaStream_t st) {
+                     cudaStream_t st, W *out = nullptr, const W *pw_b = nullptr) {
     FArgs<W> a;
     std::memset(&a, 0, sizeof(a));
     a.data = data;
+    a.out = out ? out : data;
+    a.pw_b = pw_b;
     a.status = p.d_status;
     a.tw = reinterpret_cast<const Tw<W> *>(tw);
     a.lc = p.d_limb;
@@ -186,6 +190,21 @@ cudaError_t run_fused_t(ntt_plan_s &p, void *data_v, uint32_t batch, bool invers
     e = run_pass<W, RED, true, TK_CHUNKS>(p, data, p.d_chunk_inv, ntrans, p.s2, false, st);
     if (e != cudaSuccess) return e;
     return run_pass<W, RED, true, TK_COLS>(p, data, p.d_main_inv, ntrans, p.s1, true, st);
+}
+
+// c = inverse(a (.) b) for two-pass plans: the product is taken in the
+// first inverse pass (its first round reads b beside a), which writes c;
+// the second pass runs on c in place.
+template <class W, int RED>
+cudaError_t run_fused_pwinv_t(ntt_plan_s &p, void *c, const void *a, const void *b, uint32_t batch,
+                              cudaStream_t st) {
+    const uint64_t ntrans = (uint64_t)batch * p.L;
+    W *cw = reinterpret_cast<W *>(c);
+    cudaError_t e = run_pass<W, RED, true, TK_CHUNKS>(p, const_cast<W *>(reinterpret_cast<const W *>(a)),
+                                                      p.d_chunk_inv, ntrans, p.s2, false, st, cw,
+                                                      reinterpret_cast<const W *>(b));
+    if (e != cudaSuccess) return e;
+    return run_pass<W, RED, true, TK_COLS>(p, cw, p.d_main_inv, ntrans, p.s1, true, st);
 }
 
 }  // namespace nttgb

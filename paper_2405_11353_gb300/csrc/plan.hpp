@@ -87,6 +87,11 @@ ntt_status validate_plan_args(uint32_t N, const uint64_t *q, uint32_t L, uint32_
 // fused path, instantiated in fused_<word>_<reduction>.cu
 template <class W, int RED>
 cudaError_t run_fused_t(ntt_plan_s &p, void *data, uint32_t batch, bool inverse, cudaStream_t st);
+template <class W, int RED>
+cudaError_t run_fused_pwinv_t(ntt_plan_s &p, void *c, const void *a, const void *b, uint32_t batch,
+                              cudaStream_t st);
+cudaError_t launch_fused_pwinv(ntt_plan_s &p, void *c, const void *a, const void *b, uint32_t batch,
+                               cudaStream_t st);
 // cluster form, instantiated in cluster_<reduction>.cu
 template <int RED>
 cudaError_t run_cluster(ntt_plan_s &p, void *data, uint32_t batch, bool inverse, cudaStream_t st);

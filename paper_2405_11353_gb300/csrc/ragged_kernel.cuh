@@ -67,6 +67,8 @@ __device__ __forceinline__ bool ragged_item(const RaggedArgs &ra, const RItem &i
     const RJob &J = ra.jobs[it.job];
     FArgs<W> a;
     a.data = reinterpret_cast<W *>(J.data);
+    a.out = a.data;
+    a.pw_b = nullptr;
     const int which = KIND == TK_CHUNKS ? (INV ? 3 : 2) : (INV ? 1 : 0);
     a.tw = reinterpret_cast<const Tw<W> *>(J.tw[which]);
     a.lc = J.lc;

@@ -438,6 +438,14 @@ cudaError_t launch_fused(ntt_plan_s &p, void *data, uint32_t batch, bool inverse
     });
 }
 
+cudaError_t launch_fused_pwinv(ntt_plan_s &p, void *c, const void *a, const void *b, uint32_t batch,
+                               cudaStream_t st) {
+    return dispatch(p, [&](auto w, auto r) {
+        using W = decltype(w);
+        return run_fused_pwinv_t<W, decltype(r)::value>(p, c, a, b, batch, st);
+    });
+}
+
 cudaError_t launch_pointwise(ntt_plan_s &p, void *c, const void *a, const void *b, uint32_t batch, cudaStream_t st) {
     return dispatch(p, [&](auto w, auto r) {
         using W = decltype(w);

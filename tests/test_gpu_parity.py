@@ -386,6 +386,40 @@ def test_extreme_inputs_all_q_minus_1(nt, orc):
                 p.close()
 
 
+@pytest.mark.parametrize("red", ["shoup", "barrett", "montgomery"])
+def test_pointwise_inverse_fused_and_fallback(nt, orc, red):
+    """c = INTT(a (.) b) through the fused entry point: the two-pass sizes
+    in bit-reversed order take the product inside the first inverse pass
+    (u32 N = 2^15, 2^16, 2^17; u64 N = 2^16); N = 2^12, natural order and
+    NTT_CHECK plans run the two steps.  c aliasing a, aliasing b, or apart."""
+    # (log N, u64, bit-reversed, flags, launches: 2 fused; else the product
+    # (with NTT_CHECK: + a range check of each operand), then the inverse
+    # (+ its range check, + the order permutation, + one or two passes))
+    cases = [(15, False, True, 0, 2), (16, False, True, 0, 2), (17, False, True, 0, 2), (16, True, True, 0, 2),
+             (12, False, True, 0, 2), (16, False, False, 0, 4), (16, False, True, nt.NTT_CHECK, 6)]
+    for i, (n, w64, bitrev, extra, launches) in enumerate(cases):
+        N, batch = 1 << n, 3
+        qs = primes_for(orc, N, w64, 2)
+        psis = [orc.psi(q, N) for q in qs]
+        A = ntt_synth.rns_batch(1700 + i, qs, N, batch)
+        Bm = ntt_synth.rns_batch(1750 + i, qs, N, batch)
+        fa, fb = orc.ntt_batch(A, qs, psis), orc.ntt_batch(Bm, qs, psis)
+        want = orc.ntt_batch(orc.pointwise_batch(fa, fb, qs), qs, psis, inverse=True)
+        p = Plan(nt, N, qs, "fused", red=red, w64=w64, bitrev=bitrev, extra_flags=extra)
+        try:
+            for mode in ("c=a", "c=b", "apart"):
+                da, db = to_dev(reorder(fa, bitrev, orc), w64), to_dev(reorder(fb, bitrev, orc), w64)
+                dc = da if mode == "c=a" else db if mode == "c=b" else torch.zeros_like(da)
+                nt.ntt_pointwise_inverse(p.h, dc, da, db, batch)
+                assert np.array_equal(to_host(dc, w64, A.shape), want), (n, w64, bitrev, extra, mode)
+                if mode == "apart":
+                    assert np.array_equal(to_host(db, w64, A.shape), reorder(fb, bitrev, orc))
+            assert nt.ntt_plan_last_launches(p.h) == launches
+            assert nt.ntt_get_device_status(p.h) == nt.NTT_OK
+        finally:
+            p.close()
+
+
 def test_polymul_host_entry(nt, orc):
     """The host-buffer entry point: copies, transforms and products in one
     call, pipelined in chunks of pairs (1, 3 and 13 pairs: one chunk, chunks
