@@ -292,8 +292,9 @@ def wide_word(nt, torch, dev, reps=50):
 
 def tc_fourstep(nt, torch, dev, reps=20):
     """N = 2^16, 32 primes q < 2^30, u32, 16 polys: the forward transform as
-    the tensor-core four-step form (8-bit digit products, mma.sync u8 -> s32)
-    against the butterfly form on the same data."""
+    the tensor-core four-step form (8-bit digit products on tcgen05, and on
+    the warp-level mma.sync u8 -> s32) against the butterfly form on the
+    same data."""
     qs = nt.ntt_find_primes(30, 17, 32)
     N, B = 1 << 16, 16
     host = ntt_synth.rns_batch(1005, qs, N, B, dtype=np.uint32)
@@ -302,21 +303,27 @@ def tc_fourstep(nt, torch, dev, reps=20):
     sh = stream.cuda_stream
     out = {"workload": "N=2^16, L=32 primes q<2^30, u32, 16 polys: forward transform"}
     macs = 2 * 2 * 256 * 256 * 256 * 16 * B * 32 / 2   # 2 passes x 256^3 per transform x 16 digit pairs
-    for name, variant in (("tensor_core", nt.NTT_TC_FOURSTEP), ("butterfly", nt.NTT_FUSED)):
-        p = nt.ntt_plan_create(N, qs, variant, nt.NTT_ORDER_BITREV)
+    for name, variant, extra in (("tensor_core", nt.NTT_TC_FOURSTEP, 0),
+                                 ("tensor_core_mma_sync", nt.NTT_TC_FOURSTEP, nt.NTT_TC_IMMA),
+                                 ("butterfly", nt.NTT_FUSED, 0)):
+        p = nt.ntt_plan_create(N, qs, variant, nt.NTT_ORDER_BITREV | extra)
         try:
             ms = _time_loop(torch, stream, lambda: nt.ntt_forward(p, d, B, sh), reps)
         finally:
             nt.ntt_plan_destroy(p)
         out[name] = {"value": B * 32 / (ms / 1e3), "unit": "NTT/s", "ms_per_call": ms}
-    out["tensor_core"]["int8_tops"] = macs * 2 / (out["tensor_core"]["ms_per_call"] / 1e3) / 1e12
+    for name in ("tensor_core", "tensor_core_mma_sync"):
+        out[name]["digit_tops"] = macs * 2 / (out[name]["ms_per_call"] / 1e3) / 1e12
+    out["tensor_core"]["instruction"] = "tcgen05.mma kind::f16 (balanced 8-bit digits, fp32 diagonals in TMEM)"
+    out["tensor_core_mma_sync"]["instruction"] = "mma.sync m16n8k32 u8.u8.s32"
     return out
 
 
 def cluster_form(nt, torch, dev, reps=50):
     """N = 2^16, 32 primes q < 2^30, u32, 16 polys: forward and inverse as
-    the two-pass split (default) and as one pass on eight-CTA clusters
-    (NTT_CLUSTER), which reads and writes each word once."""
+    the two-pass split in one streamed launch (default), as two launches
+    (NTT_TWO_LAUNCH), and as one pass on eight-CTA clusters (NTT_CLUSTER),
+    which reads and writes each word once."""
     qs = nt.ntt_find_primes(30, 17, 32)
     N, B = 1 << 16, 16
     host = ntt_synth.rns_batch(1005, qs, N, B, dtype=np.uint32)
@@ -324,7 +331,8 @@ def cluster_form(nt, torch, dev, reps=50):
     stream = torch.cuda.current_stream(dev)
     sh = stream.cuda_stream
     out = {"workload": "N=2^16, L=32 primes q<2^30, u32, 16 polys: forward, inverse"}
-    for name, extra in (("two_pass", 0), ("cluster_one_pass", nt.NTT_CLUSTER)):
+    for name, extra in (("two_pass_one_launch", 0), ("two_pass_two_launches", nt.NTT_TWO_LAUNCH),
+                        ("cluster_one_pass", nt.NTT_CLUSTER)):
         p = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, nt.NTT_ORDER_BITREV | extra)
         try:
             ms_f = _time_loop(torch, stream, lambda: nt.ntt_forward(p, d, B, sh), reps)
@@ -467,7 +475,7 @@ def main():
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": achieved / peak, "traffic": traffic_from_profiles(digest),
-        "kernel": "ntt_forward (column pass + 256-point chunk pass), %d transforms" % n_fwd,
+        "kernel": "ntt_forward: column pass + 256-point chunk pass in one streamed launch, %d transforms" % n_fwd,
         "algorithmic_bytes_per_call": fwd_bytes, "avg_ms": fwd_ms,
         "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
         else "fallback 6.8 TB/s",

@@ -97,6 +97,23 @@ typedef enum {
                                       GB300 it moves half the DRAM bytes but
                                       takes longer: a cluster barrier per
                                       transform and single-buffered tiles) */
+#define NTT_TWO_LAUNCH 0x400u      /* NTT_FUSED, two-pass sizes (N > 2^14 with
+                                      4-byte words, N > 2^13 with 8-byte): run
+                                      the column pass and the chunk pass as two
+                                      launches (the whole batch written to
+                                      memory between them).  Default: one
+                                      launch that streams limb by limb, so a
+                                      limb's intermediate is read back while
+                                      still in L2; results identical.  Calls of
+                                      one default plan use one of 16 counter
+                                      sets in turn: at most 16 calls of one
+                                      plan may overlap on the GPU */
+#define NTT_TC_IMMA 0x800u         /* NTT_TC_FOURSTEP: the digit products on
+                                      the warp-level integer MMA (mma.sync
+                                      u8 x u8 -> s32) instead of tcgen05
+                                      (fp16 digits, fp32 accumulators in
+                                      tensor memory); results identical, kept
+                                      for comparison */
 #define NTT_TEST_STALL 0x8000u     /* test hook, fused plans only: in every
                                       forward call one CTA's first tile waits
                                       for 16 bytes that never arrive, so its

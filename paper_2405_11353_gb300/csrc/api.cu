@@ -15,7 +15,8 @@ using u128 = unsigned __int128;
 namespace {
 
 constexpr uint32_t kKnownFlags =
-    NTT_WORD64 | NTT_ORDER_BITREV | NTT_RED_MASK | NTT_CHECK | NTT_CLUSTER | NTT_TEST_STALL;
+    NTT_WORD64 | NTT_ORDER_BITREV | NTT_RED_MASK | NTT_CHECK | NTT_CLUSTER | NTT_TWO_LAUNCH |
+    NTT_TC_IMMA | NTT_TEST_STALL;
 constexpr uint32_t kMaxLimbs = 4096;
 
 int red_of(uint32_t flags) {
@@ -70,7 +71,8 @@ ntt_status upload(void **dptr, const std::vector<uint8_t> &h) {
 void free_plan_memory(ntt_plan_s *p) {
     void *ptrs[] = {p->d_limb,      p->d_w_fwd,     p->d_w_inv,   p->d_twist,    p->d_untwist,
                     p->d_main_fwd,  p->d_main_inv,  p->d_chunk_fwd, p->d_chunk_inv, p->d_tc,
-                    p->d_clu_fwd,   p->d_clu_inv,   p->d_scratch,  p->d_status};
+                    p->d_clu_fwd,   p->d_clu_inv,   p->d_scratch,  p->d_status,
+                    p->d_stream_ctr, p->d_tc5};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (p->aux_ready) {
@@ -114,6 +116,30 @@ ntt_status validate(uint32_t N, const uint64_t *q, uint32_t L, uint32_t flags) {
 //   forward twiddle        [u][n2] = psi^(n2 (2 k1 + 1))
 //   inverse twiddle        [u][n2] = psi^(-n2 (2 k1 + 1))
 // each matrix as four 8-bit digit planes; twiddles as Shoup pairs.
+// IEEE half-precision bits of a small integer (|d| <= 2048: exact).
+uint16_t half_bits(int d) {
+    if (d == 0) return 0;
+    const uint16_t sign = d < 0 ? 0x8000u : 0u;
+    uint32_t a = (uint32_t)(d < 0 ? -d : d), e = 0;
+    while ((a >> (e + 1)) != 0) ++e;
+    const uint32_t mant = (a << (10 - e)) & 0x3FFu;
+    return (uint16_t)(sign | ((e + 15) << 10) | mant);
+}
+
+// Matrices of the tensor-core form as balanced 8-bit digits in fp16
+// (tc5.cu): v = sum_d c_d 256^d, c_d = byte d of (v + 0x80808080) - 128.
+void build_tc5_digits(const std::vector<uint8_t> &tc, uint32_t L, std::vector<uint8_t> &out) {
+    out.assign((size_t)4 * L * 4 * 65536 * 2, 0);
+    uint16_t *h = reinterpret_cast<uint16_t *>(out.data());
+    for (size_t ml = 0; ml < (size_t)4 * L; ++ml)
+        for (size_t e = 0; e < 65536; ++e) {
+            uint32_t v = 0;
+            for (int d = 0; d < 4; ++d) v |= (uint32_t)tc[(ml * 4 + d) * 65536 + e] << (8 * d);
+            const uint32_t y = v + 0x80808080u;
+            for (int d = 0; d < 4; ++d) h[(ml * 4 + d) * 65536 + e] = half_bits((int)((y >> (8 * d)) & 255u) - 128);
+        }
+}
+
 void build_tc_tables(ntt_plan_s *p, std::vector<uint8_t> &out) {
     const uint32_t L = p->L, N = p->N;
     const size_t mat_bytes = (size_t)4 * L * 4 * 65536, tw_bytes = (size_t)2 * L * 65536 * 8;
@@ -255,7 +281,11 @@ ntt_status build_tables(ntt_plan_s *p) {
         }
     }
     std::vector<uint8_t> tcb;
-    if (p->variant == NTT_TC_FOURSTEP) build_tc_tables(p, tcb);
+    std::vector<uint8_t> tc5b;
+    if (p->variant == NTT_TC_FOURSTEP) {
+        build_tc_tables(p, tcb);
+        if (!p->tc_imma) build_tc5_digits(tcb, L, tc5b);
+    }
     if (clu_tabs) {
         // cluster form (cluster.cuh), word index g = 8192 k + 1024 r + j; per
         // (limb, CTA c) a slice of 8192 + 16 pairs: block (c, r) of 1024
@@ -302,6 +332,7 @@ ntt_status build_tables(ntt_plan_s *p) {
     std::memcpy(lcb.data(), lc.data(), lcb.size());
     ntt_status s;
     if (!tcb.empty() && (s = upload(&p->d_tc, tcb)) != NTT_OK) return s;
+    if (!tc5b.empty() && (s = upload(&p->d_tc5, tc5b)) != NTT_OK) return s;
     if ((s = upload((void **)&p->d_limb, lcb)) != NTT_OK) return s;
     if (variant_tabs) {
         if ((s = upload(&p->d_w_fwd, wf)) != NTT_OK) return s;
@@ -323,12 +354,18 @@ ntt_status build_tables(ntt_plan_s *p) {
     }
     if (cudaMalloc((void **)&p->d_status, sizeof(uint32_t)) != cudaSuccess) { cudaGetLastError(); return NTT_ERR_OOM; }
     if (cudaMemset(p->d_status, 0, sizeof(uint32_t)) != cudaSuccess) return NTT_ERR_CUDA;
+    if (chunk_tabs) {
+        const size_t bytes = (size_t)nttgb::kStreamRing * nttgb::stream_set_words(L) * sizeof(uint32_t);
+        if (cudaMalloc((void **)&p->d_stream_ctr, bytes) != cudaSuccess) { cudaGetLastError(); return NTT_ERR_OOM; }
+        if (cudaMemset(p->d_stream_ctr, 0, bytes) != cudaSuccess) return NTT_ERR_CUDA;
+    }
     return NTT_OK;
 }
 
 bool needs_scratch(const ntt_plan_s &p) {
     switch (p.variant) {
     case NTT_PEASE: case NTT_PEASE_NC: case NTT_STOCKHAM: case NTT_SIXSTEP: return true;
+    case NTT_TC_FOURSTEP: return !p.tc_imma;     // tcgen05 passes run out of place
     default: return false;
     }
 }
@@ -348,6 +385,7 @@ ntt_status run_transform(ntt_plan_t plan, void *d_data, uint32_t batch, ntt_stre
         view.psi.clear();
         ntt_status s = run_transform(&view, d_data, batch, stream, inverse, 0);
         plan->last_launches = view.last_launches;
+        plan->stream_seq = view.stream_seq;
         // the view may have grown (freed and replaced) the scratch buffer
         plan->d_scratch = view.d_scratch;
         plan->scratch_bytes = view.scratch_bytes;
@@ -365,7 +403,9 @@ ntt_status run_transform(ntt_plan_t plan, void *d_data, uint32_t batch, ntt_stre
         if (p.variant == NTT_TC_FOURSTEP) {
             // works in bit-reversed order, like the fused kernels
             if (inverse && !p.bitrev_order) e = nttgb::launch_bitrev_permute(p, d_data, batch, st);
-            if (e == cudaSuccess) e = nttgb::launch_tc(p, d_data, batch, inverse, st);
+            if (e == cudaSuccess)
+                e = p.tc_imma ? nttgb::launch_tc(p, d_data, batch, inverse, st)
+                              : nttgb::launch_tc5(p, d_data, batch, inverse, st);
             if (e == cudaSuccess && !inverse && !p.bitrev_order) e = nttgb::launch_bitrev_permute(p, d_data, batch, st);
         } else if (p.variant != NTT_FUSED || p.fused_mode == nttgb::FUSED_STAGES) {
             ntt_variant v = p.variant == NTT_FUSED ? NTT_FLAT : p.variant;
@@ -480,6 +520,7 @@ ntt_status create_plan(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t
     p->word64 = (flags & NTT_WORD64) != 0;
     p->bitrev_order = (flags & NTT_ORDER_BITREV) != 0;
     p->check = (flags & NTT_CHECK) != 0;
+    p->tc_imma = (flags & NTT_TC_IMMA) != 0;
     p->q.assign(q, q + L);
     p->psi.resize(L);
     for (uint32_t l = 0; l < L; ++l) {
@@ -500,6 +541,7 @@ ntt_status create_plan(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t
             p->fused_mode = nttgb::FUSED_CLUSTER;
         else {
             p->fused_mode = nttgb::FUSED_TWO_PASS;
+            p->two_launch = (flags & NTT_TWO_LAUNCH) != 0;
             p->s2 = nttgb::kChunkLog;
             p->s1 = p->logN - p->s2;
         }

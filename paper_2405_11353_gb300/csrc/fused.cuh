@@ -48,7 +48,7 @@ template <class W> struct FArgs {
     uint64_t ntiles;
     uint32_t logN, L, logK, s2;   // N2 = 2^s2 (cols / chunks)
     uint32_t final_pass;      // fully reduce output; inverse: fold N^-1
-    uint32_t stall_tx;        // test hook: extra bytes CTA 0 expects on its first tile
+    uint32_t stall_tx;        // test hook: extra bytes the first tile of a call waits for
     CUtensorMap tmap;         // column passes: the data as rows of N2 words
 };
 
@@ -366,6 +366,9 @@ template <class W, int LOGS, int KIND, int P = 0> __host__ __device__ constexpr 
 struct PipeState {
     uint32_t uses[2];
     uint32_t tw_phase;
+    // uses[s] with a run-time s, without indexing (which would put the
+    // state in local memory)
+    __device__ __forceinline__ uint32_t use(uint32_t s) const { return s ? uses[1] : uses[0]; }
 };
 
 // Process tiles [t_begin, t_end) of one pass.  One thread keeps the next
@@ -478,28 +481,36 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     if (tid == 0) {
         fence_proxy_async();   // the buffers may have been read by a previous call
         // (test hook: the first barrier waits for bytes no copy delivers)
-        if (a.stall_tx && blockIdx.x == 0) mbar_add_tx(&bar[0], a.stall_tx);
+        // (per-plan launches: CTA 0; one-launch two-pass form: the item
+        // holding the first tile)
+        if (a.stall_tx && (P == 0 ? blockIdx.x == 0 : t_begin == 0)) mbar_add_tx(&bar[0], a.stall_tx);
         for (uint32_t s = 0; s < NS && t_begin + s < t_end; ++s) { issue(ahead, s); cur_next(ahead); }
         if (t_begin + NS < t_end) prefetch(ahead);
     }
     uint32_t tw_key = 0xffffffffu;  // (limb, group) of the staged twiddles
     uint32_t &tw_phase = ps.tw_phase;
     bool ok = true;
+    // limb constants, reloaded only when the limb changes (tiles run
+    // polynomial-fastest, so rarely)
+    uint32_t kk_l = 0xffffffffu;
+    Lc<W> kk;
+    Tw<W> tn{}, twn{};
 
     uint32_t i = 0;
     for (uint32_t tile = t_begin; tile < t_end; ++tile, ++i, cur_next(cur)) {
         const uint32_t s = i % NS;
-        const uint32_t parity = (ps.uses[s] + i / NS) & 1u;
+        const uint32_t parity = (ps.use(s) + i / NS) & 1u;
         const uint32_t pos0 = cur.g * K;
         const uint64_t t = KIND == TK_SINGLE ? cur_t(cur) + k : cur_t(cur);
         const bool valid = t < a.ntrans;
         const uint32_t l = KIND == TK_SINGLE ? (uint32_t)((valid ? t : 0) % L) : cur.l;
-        Lc<W> kk;
-        kk.load(a.lc + l);
-        Tw<W> tn{}, twn{};
-        if (INV && a.final_pass) {
-            tn.w = (W)a.lc[l].ninv_w; tn.c = (W)a.lc[l].ninv_c;
-            twn.w = (W)a.lc[l].ninv_w1_w; twn.c = (W)a.lc[l].ninv_w1_c;
+        if (l != kk_l) {
+            kk.load(a.lc + l);
+            if (INV && a.final_pass) {
+                tn.w = (W)a.lc[l].ninv_w; tn.c = (W)a.lc[l].ninv_c;
+                twn.w = (W)a.lc[l].ninv_w1_w; twn.c = (W)a.lc[l].ninv_w1_c;
+            }
+            kk_l = l;
         }
         const Tw<W> *twb;
         if (TWS) {
@@ -519,6 +530,20 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
             twb = tws + (KIND == TK_CHUNKS ? k * CP : 0);
         } else {
             twb = KIND == TK_CHUNKS ? tw_src(l, 0) + (size_t)(pos0 + k) * CP : a.tw + (size_t)l * N;
+        }
+        // fused pointwise product (inverse chunk pass): b's 16 words at this
+        // thread's positions, loaded before the tile wait so they overlap it
+        constexpr bool PW = KIND == TK_CHUNKS && INV && R0::RR == 4 && R0::LO == 0;
+        constexpr int NV = 16 / (16 / (int)sizeof(W));
+        using V16 = typename std::conditional<sizeof(W) == 4, uint4, ulonglong2>::type;
+        V16 bv[PW ? NV : 1];
+        const bool use_pw = PW && a.pw_b && valid;
+        if constexpr (PW) {
+            if (use_pw) {
+                const V16 *bq = reinterpret_cast<const V16 *>(a.pw_b + t * N + ((size_t)(pos0 + k) << S2) + R0::A(tau));
+#pragma unroll
+                for (int v = 0; v < NV; ++v) bv[v] = __ldg(bq + v);
+            }
         }
         // ---- round 0 from the staged tile
         ok = ok && mbar_wait_bounded(&bar[s], parity);
@@ -564,24 +589,19 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
                 for (int e = 0; e < 16; ++e) x[e] = sb[k * SP + (A0 | R0::E(e))];
             }
         }
-        if constexpr (KIND == TK_CHUNKS && INV && R0::RR == 4 && R0::LO == 0) {
-            // fused pointwise product: the inverse of a (.) b reads b's 16
-            // words at the same positions
-            if (a.pw_b && valid) {
-                const W *bq = a.pw_b + t * N + ((size_t)(pos0 + k) << S2) + R0::A(tau);
-                constexpr int V = 16 / sizeof(W);
+        if constexpr (PW) {
+            // the inverse of a (.) b: multiply by b's words first
+            if (use_pw) {
 #pragma unroll
-                for (int v = 0; v < 16 / V; ++v) {
-                    if (sizeof(W) == 4) {
-                        uint4 w4 = __ldg(reinterpret_cast<const uint4 *>(bq) + v);
-                        x[4 * v] = mul_var<RED>(x[4 * v], (W)w4.x, kk);
-                        x[4 * v + 1] = mul_var<RED>(x[4 * v + 1], (W)w4.y, kk);
-                        x[4 * v + 2] = mul_var<RED>(x[4 * v + 2], (W)w4.z, kk);
-                        x[4 * v + 3] = mul_var<RED>(x[4 * v + 3], (W)w4.w, kk);
+                for (int v = 0; v < NV; ++v) {
+                    if constexpr (sizeof(W) == 4) {
+                        x[4 * v] = mul_var<RED>(x[4 * v], (W)bv[v].x, kk);
+                        x[4 * v + 1] = mul_var<RED>(x[4 * v + 1], (W)bv[v].y, kk);
+                        x[4 * v + 2] = mul_var<RED>(x[4 * v + 2], (W)bv[v].z, kk);
+                        x[4 * v + 3] = mul_var<RED>(x[4 * v + 3], (W)bv[v].w, kk);
                     } else {
-                        ulonglong2 w2 = __ldg(reinterpret_cast<const ulonglong2 *>(bq) + v);
-                        x[2 * v] = mul_var<RED>(x[2 * v], (W)w2.x, kk);
-                        x[2 * v + 1] = mul_var<RED>(x[2 * v + 1], (W)w2.y, kk);
+                        x[2 * v] = mul_var<RED>(x[2 * v], (W)bv[v].x, kk);
+                        x[2 * v + 1] = mul_var<RED>(x[2 * v + 1], (W)bv[v].y, kk);
                     }
                 }
             }
@@ -645,7 +665,7 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
         if (tid == 0) {
             for (uint32_t j = i; j < i + NS && j < n_local; ++j) {
                 const long long t0 = clock64();
-                while (!mbar_try_wait(&bar[j % NS], (ps.uses[j % NS] + j / NS) & 1u))
+                while (!mbar_try_wait(&bar[j % NS], (ps.use(j % NS) + j / NS) & 1u))
                     if (clock64() - t0 > (1ll << 30)) break;
             }
             if (TWS && tw_phase > 0) {

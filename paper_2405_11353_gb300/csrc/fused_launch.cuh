@@ -4,8 +4,11 @@
 #pragma once
 #include <cstring>
 
+#include <cstdlib>
+
 #include "fused.cuh"
 #include "plan.hpp"
+#include "stream.cuh"
 
 namespace nttgb {
 
@@ -129,12 +132,22 @@ template <class W, int KIND, bool INV> size_t smem_for(int logS) {
 // threads each.
 inline uint32_t ilog2(uint32_t x) { uint32_t r = 0; while ((1u << r) < x) ++r; return r; }
 
-// One pass over `data` in place, or (out, pw_b set: the inverse chunk pass
-// of the fused pointwise + inverse) from `data` times pw_b into `out`.
-template <class W, int RED, bool INV, int KIND>
-cudaError_t run_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, int logS, bool final_pass,
-                     cudaStream_t st, W *out = nullptr, const W *pw_b = nullptr) {
-    FArgs<W> a;
+template <class W, int KIND, int P> uint32_t tile_k_p(int logS) {
+    switch (logS) {
+#define NTTGB_CASE(s) case s: return tile_k<W, s, KIND, P>();
+        NTTGB_CASE(4) NTTGB_CASE(5) NTTGB_CASE(6) NTTGB_CASE(7) NTTGB_CASE(8) NTTGB_CASE(9)
+        NTTGB_CASE(10) NTTGB_CASE(11) NTTGB_CASE(12) NTTGB_CASE(13) NTTGB_CASE(14)
+#undef NTTGB_CASE
+    }
+    return 1;
+}
+
+// Arguments of one pass over `data` (tiles of K sub-transforms of 2^logS
+// words), in place, or (out, pw_b set: the inverse chunk pass of the fused
+// pointwise + inverse) from `data` times pw_b into `out`.
+template <class W, bool INV, int KIND>
+cudaError_t fill_pass(FArgs<W> &a, ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, int logS,
+                      bool final_pass, uint32_t K, W *out, const W *pw_b) {
     std::memset(&a, 0, sizeof(a));
     a.data = data;
     a.out = out ? out : data;
@@ -148,8 +161,6 @@ cudaError_t run_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, in
     a.s2 = p.s2;
     a.final_pass = final_pass ? 1u : 0u;
     a.stall_tx = (p.flags & NTT_TEST_STALL) && !INV && KIND != TK_CHUNKS ? 16u : 0u;
-    const uint32_t T = (1u << logS) / 16;
-    const uint32_t K = tile_k_for<W, KIND>(logS);
     if (KIND == TK_SINGLE) a.ntiles = (ntrans + K - 1) / K;
     else if (KIND == TK_COLS) a.ntiles = ntrans * ((1u << p.s2) / K);
     else a.ntiles = ntrans * ((1u << (p.logN - p.s2)) / K);
@@ -168,9 +179,88 @@ cudaError_t run_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, in
                                        K * (1u << logS) / RW);
         if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
+}
+
+// One pass as its own launch.
+template <class W, int RED, bool INV, int KIND>
+cudaError_t run_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, int logS, bool final_pass,
+                     cudaStream_t st, W *out = nullptr, const W *pw_b = nullptr) {
+    FArgs<W> a;
+    const uint32_t T = (1u << logS) / 16;
+    const uint32_t K = tile_k_for<W, KIND>(logS);
+    cudaError_t e = fill_pass<W, INV, KIND>(a, p, data, tw, ntrans, logS, final_pass, K, out, pw_b);
+    if (e != cudaSuccess) return e;
     size_t smem = smem_for<W, KIND, INV>(logS);
     ++p.last_launches;
     return pass_dispatch<W, RED, INV, KIND>(logS, a, K * T, smem, st);
+}
+
+// Tuning of the one-launch two-pass form: tiles per work item and the lag
+// (in rounds of one limb) between a limb's first and second pass; unset or
+// 0 = the defaults below.  Read at each call from NTT_STREAM_TILES /
+// NTT_STREAM_LAG (any value gives the same result; only the speed changes).
+inline uint32_t stream_env(const char *name) {
+    const char *v = std::getenv(name);
+    return v ? (uint32_t)std::strtoul(v, nullptr, 10) : 0u;
+}
+
+// Both passes of a two-pass transform in one launch (stream.cuh).
+template <class W, int RED, bool INV>
+cudaError_t run_stream(ntt_plan_s &p, W *data, uint64_t ntrans, cudaStream_t st, W *out, const W *pw_b) {
+    const uint32_t env_tiles = stream_env("NTT_STREAM_TILES");
+    const uint32_t env_lag = stream_env("NTT_STREAM_LAG");
+    StreamArgs<W> sa;
+    std::memset(&sa, 0, sizeof(sa));
+    const uint32_t Kc = tile_k_p<W, TK_COLS, 1>((int)p.s1);
+    const uint32_t Kh = tile_k<W, kN2Log, TK_CHUNKS, 1>();
+    const uint64_t B = ntrans / p.L;
+    const uint64_t tpl_cols = B * ((1u << p.s2) / Kc), tpl_chunks = B * ((1u << p.s1) / Kh);
+    if (tpl_cols * p.L >= (1ull << 32) || tpl_chunks * p.L >= (1ull << 32)) return cudaErrorInvalidValue;
+    W *o = out ? out : data;
+    cudaError_t e;
+    if (!INV) {
+        e = fill_pass<W, false, TK_COLS>(sa.pass[0], p, data, p.d_main_fwd, ntrans, (int)p.s1, false, Kc, nullptr,
+                                         nullptr);
+        if (e == cudaSuccess)
+            e = fill_pass<W, false, TK_CHUNKS>(sa.pass[1], p, data, p.d_chunk_fwd, ntrans, (int)p.s2, true, Kh,
+                                               nullptr, nullptr);
+        sa.tiles_per_limb[0] = (uint32_t)tpl_cols;
+        sa.tiles_per_limb[1] = (uint32_t)tpl_chunks;
+    } else {
+        e = fill_pass<W, true, TK_CHUNKS>(sa.pass[0], p, data, p.d_chunk_inv, ntrans, (int)p.s2, false, Kh, o, pw_b);
+        if (e == cudaSuccess)
+            e = fill_pass<W, true, TK_COLS>(sa.pass[1], p, o, p.d_main_inv, ntrans, (int)p.s1, true, Kc, nullptr,
+                                            nullptr);
+        sa.tiles_per_limb[0] = (uint32_t)tpl_chunks;
+        sa.tiles_per_limb[1] = (uint32_t)tpl_cols;
+    }
+    if (e != cudaSuccess) return e;
+    // work items of 4 tiles (4 KiB ... 32 KiB each)
+    const uint32_t g = env_tiles ? env_tiles : 4u;
+    uint32_t slots = 0;
+    for (int i = 0; i < 2; ++i) {
+        sa.tiles_per_item[i] = g < sa.tiles_per_limb[i] ? g : sa.tiles_per_limb[i];
+        sa.items_per_limb[i] = (sa.tiles_per_limb[i] + sa.tiles_per_item[i] - 1) / sa.tiles_per_item[i];
+        slots += sa.items_per_limb[i];
+    }
+    sa.L = p.L;
+    // the second pass of a limb starts about two grids of items after its
+    // first pass (so its first-pass tiles are done), plus one round; the
+    // intermediate then held in L2 is about lag rounds of one limb
+    int resident = 0;
+    e = stream_resident<W, RED, INV>((int)p.s1, &resident);
+    if (e != cudaSuccess) return e;
+    sa.lag = env_lag ? env_lag : (2u * (uint32_t)resident + slots - 1) / slots + 1;
+    sa.ctr = p.d_stream_ctr + (size_t)(p.stream_seq++ % kStreamRing) * stream_set_words(p.L);
+    ++p.last_launches;
+    switch (p.s1) {
+    case 6: return stream_launch<W, RED, INV, 6>(sa, st);
+    case 7: return stream_launch<W, RED, INV, 7>(sa, st);
+    case 8: return stream_launch<W, RED, INV, 8>(sa, st);
+    case 9: return stream_launch<W, RED, INV, 9>(sa, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <class W, int RED>
@@ -181,6 +271,10 @@ cudaError_t run_fused_t(ntt_plan_s &p, void *data_v, uint32_t batch, bool invers
     if (p.fused_mode == FUSED_SINGLE) {
         if (!inverse) return run_pass<W, RED, false, TK_SINGLE>(p, data, p.d_main_fwd, ntrans, p.logN, true, st);
         return run_pass<W, RED, true, TK_SINGLE>(p, data, p.d_main_inv, ntrans, p.logN, true, st);
+    }
+    if (!p.two_launch) {
+        if (!inverse) return run_stream<W, RED, false>(p, data, ntrans, st, nullptr, nullptr);
+        return run_stream<W, RED, true>(p, data, ntrans, st, nullptr, nullptr);
     }
     if (!inverse) {
         e = run_pass<W, RED, false, TK_COLS>(p, data, p.d_main_fwd, ntrans, p.s1, false, st);
@@ -200,6 +294,9 @@ cudaError_t run_fused_pwinv_t(ntt_plan_s &p, void *c, const void *a, const void 
                               cudaStream_t st) {
     const uint64_t ntrans = (uint64_t)batch * p.L;
     W *cw = reinterpret_cast<W *>(c);
+    if (!p.two_launch)
+        return run_stream<W, RED, true>(p, const_cast<W *>(reinterpret_cast<const W *>(a)), ntrans, st, cw,
+                                        reinterpret_cast<const W *>(b));
     cudaError_t e = run_pass<W, RED, true, TK_CHUNKS>(p, const_cast<W *>(reinterpret_cast<const W *>(a)),
                                                       p.d_chunk_inv, ntrans, p.s2, false, st, cw,
                                                       reinterpret_cast<const W *>(b));

@@ -21,6 +21,11 @@ constexpr int kChunkLog = 8;      // pass-B sub-transform size 256
 // One pass on a cluster of eight CTAs (cluster.cuh, flag NTT_CLUSTER):
 // N = 2^16, 4-byte words.
 constexpr int kClusterLogN = 16;
+// One-launch two-pass form (stream.cuh): a plan keeps kStreamRing counter
+// sets of stream_set_words(L) words (L limb counts, queue head, exit count,
+// abort flag), used by its calls in turn.
+constexpr uint32_t kStreamRing = 16;
+inline constexpr uint32_t stream_set_words(uint32_t L) { return ((L + 3) + 31) & ~31u; }
 // ntt_polymul_host splits its pairs into at most this many pipelined chunks.
 constexpr uint32_t kHostChunks = 8;
 
@@ -47,11 +52,18 @@ struct ntt_plan_s {
     void *d_chunk_fwd = nullptr; // pass-B per-chunk layout of psi^bitrev
     void *d_chunk_inv = nullptr;
     void *d_tc = nullptr;        // tensor-core four-step tables (see tc.cu)
+    void *d_tc5 = nullptr;       // their matrices as fp16 balanced digits (tc5.cu)
+    bool tc_imma = false;        // NTT_TC_IMMA: warp-level mma.sync form
     // cluster form (cluster.cuh): [L][8][8192 + 16] twiddle pairs each
     void *d_clu_fwd = nullptr;
     void *d_clu_inv = nullptr;
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
+    // two-pass plans: progress counters of the one-launch form (stream.cuh),
+    // a ring of sets, one per call
+    uint32_t *d_stream_ctr = nullptr;
+    uint32_t stream_seq = 0;
+    bool two_launch = false;     // NTT_TWO_LAUNCH: the passes as two launches
     uint32_t *d_status = nullptr;
     uint32_t last_launches = 0;
 
@@ -76,6 +88,7 @@ cudaError_t launch_pointwise(ntt_plan_s &p, void *c, const void *a, const void *
 cudaError_t launch_bitrev_permute(ntt_plan_s &p, void *data, uint32_t batch, cudaStream_t st);
 cudaError_t launch_check_range(ntt_plan_s &p, const void *data, uint32_t batch, cudaStream_t st);
 cudaError_t launch_tc(ntt_plan_s &p, void *data, uint32_t batch, bool inverse, cudaStream_t st);
+cudaError_t launch_tc5(ntt_plan_s &p, void *data, uint32_t batch, bool inverse, cudaStream_t st);
 
 ntt_status ensure_scratch(ntt_plan_s &p, uint32_t batch, cudaStream_t st);
 

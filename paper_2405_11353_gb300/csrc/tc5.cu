@@ -1,0 +1,484 @@
+// tc5.cu -- the tensor-core four-step form on the fifth-generation tensor
+// cores (tcgen05.mma, accumulators in tensor memory).
+//
+// Same split as tc.cu (Sec. II "Six-step": the N = 2^16 transform as 256-point
+// sub-transforms, each a dense 256 x 256 matrix product mod q, with the
+// inter-step twiddles in an epilogue), same tables of matrices and output
+// order.  What differs is how a product mod q is made exact on hardware whose
+// only 8-bit-class tcgen05 kinds are floating point on this target:
+//
+//   * Both operands are split into four BALANCED 8-bit digits,
+//     x = sum_i d_i 256^i with d_i in [-128, 128): the digits of a data word
+//     are the bytes of x + 0x80808080 minus 128, those of a matrix entry are
+//     precomputed.  Every digit is an fp16 integer (exact).
+//   * The 16 digit products are accumulated by diagonal s = i + j into seven
+//     fp32 accumulators in tensor memory.  A diagonal sums at most 4 x 256
+//     products of magnitude <= 128 * 128 = 2^14, so every partial sum is an
+//     integer of magnitude <= 2^24: exactly representable, so fp32
+//     accumulation loses nothing, in any order.
+//   * The epilogue reads the diagonals back (tcgen05.ld), recombines
+//     sum_s D_s (2^(8 s) mod q) in 64-bit integers (|.| < 7 2^24 q < 2^57),
+//     adds a multiple of q above 2^57 to make it positive and reduces mod q
+//     (Barrett), then applies
+//     the inter-step twiddle (Shoup) where the pass has one.
+//
+// GEMM view, D[m][n] = sum_k A[m][k] B[n][k], both operands K-major in shared
+// memory (128-byte swizzle, tile M = 128, N = 64, K chunks of 64):
+//   column pass  A = matrix [u][n1] (TMA), B = data column block [n2][n1]
+//                (converted by the CTA), D = out[u][n2];
+//   row pass     A = data row block [r][n2] (converted), B = matrix [v][n2]
+//                (TMA), D = out[r][v].
+// Each pass reads src and writes dst (out of place: a tile's output rows are
+// other tiles' input rows).
+//
+// Roles in a CTA (one per SM: 192 KiB of shared memory, 448 of the 512
+// tensor-memory columns): warps 0-7 convert data digits into the stage
+// buffers and run the epilogue (warp w reads tensor-memory lanes
+// 32 (w % 4) ..); warp 8 lane 0 issues the TMA copies of the matrix digits;
+// warp 9 lane 0 issues the MMAs.  Two stage buffers, mbarriers between the
+// roles, every wait bounded (about a second of SM clock) -- on expiry the
+// call records NTT_ERR_TIMEOUT, all roles leave their loops, and the CTA
+// waits (bounded) for its copies and products in flight before it frees its
+// tensor memory.
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "fused.cuh"
+#include "plan.hpp"
+
+namespace nttgb {
+
+constexpr uint32_t kT5M = 128, kT5N = 64, kT5KC = 64;
+constexpr uint32_t kT5Dig = 4, kT5Diag = 7;
+constexpr uint32_t kT5StageA = kT5Dig * kT5M * 128;   // 64 KiB
+constexpr uint32_t kT5StageB = kT5Dig * kT5N * 128;   // 32 KiB
+constexpr uint32_t kT5Stage = kT5StageA + kT5StageB;
+constexpr uint32_t kT5ConvWarps = 8;
+constexpr uint32_t kT5Threads = (kT5ConvWarps + 2) * 32;
+constexpr uint32_t kT5TmemCols = 512;
+constexpr size_t kT5Smem = 2 * (size_t)kT5Stage + 1024 + 256;
+
+struct Tc5Args {
+    const uint32_t *src;
+    uint32_t *dst;
+    CUtensorMap cmap;               // matrix digit planes, fp16 (k: 256, rows), box 64 x 64, 128-byte swizzle
+    uint32_t mat_row0;              // cmap row of (this pass's matrix, limb 0, digit 0, row 0)
+    const Tw<uint32_t> *tw;         // [L][256][256] epilogue twiddles, or null
+    const LimbConst *lc;
+    const uint32_t *wdiag;          // [L][8]: 2^(8 s) mod q for s < 7
+    uint32_t *status;
+    uint32_t L;
+    uint32_t ntiles;                // 8 per transform
+};
+
+namespace {
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ void t5_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void t5_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D (tmem) (+)= A (smem) * B (smem)^T, kind::f16, cta_group::1
+__device__ __forceinline__ void t5_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// arrive on `bar` once every MMA this thread issued before has completed
+__device__ __forceinline__ void t5_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void t5_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void t5_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
+// 1 KiB one after another (stride 1024 bytes), start at `saddr`.
+__device__ __forceinline__ uint64_t t5_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);          // start address
+    d |= (uint64_t)1u << 16;                          // leading byte offset (unused when swizzled)
+    d |= (uint64_t)(1024u >> 4) << 32;                // stride byte offset
+    d |= (uint64_t)1u << 46;                          // descriptor version
+    d |= (uint64_t)2u << 61;                          // 128-byte swizzle
+    return d;
+}
+// Instruction descriptor, kind::f16: fp16 A and B, fp32 D, both K-major,
+// M = 128, N = 64.
+constexpr uint32_t kT5Idesc = (1u << 4) | (0u << 7) | (0u << 10) | ((kT5N >> 3) << 17) | ((kT5M >> 4) << 24);
+
+// byte offset of 16-byte unit `unit` (0..7) of row `row` in a K-major
+// 128-byte-swizzled operand
+__device__ __forceinline__ uint32_t t5_swz(uint32_t row, uint32_t unit) {
+    return (row >> 3) * 1024u + (row & 7u) * 128u + ((unit ^ (row & 7u)) << 4);
+}
+
+// Balanced digits of eight words as fp16, packed for one 16-byte unit per
+// digit plane: out[d] holds digit d of words 0..7.
+__device__ __forceinline__ void t5_digits(const uint32_t (&x)[8], uint4 (&out)[4]) {
+    uint32_t y[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) y[i] = x[i] + 0x80808080u;
+    const __half2 bias = __halves2half2(__ushort_as_half((unsigned short)0x6480u),
+                                        __ushort_as_half((unsigned short)0x6480u));   // 1152
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const uint32_t sel = (uint32_t)d | ((uint32_t)d << 4) | ((uint32_t)(4 + d) << 8) | ((uint32_t)(4 + d) << 12);
+        uint32_t w[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            uint32_t t = __byte_perm(y[2 * p], y[2 * p + 1], sel);
+            t = (t & 0x00FF00FFu) | 0x64006400u;           // fp16 1024 + byte, twice
+            __half2 h = __hsub2(*reinterpret_cast<__half2 *>(&t), bias);
+            w[p] = *reinterpret_cast<uint32_t *>(&h);
+        }
+        out[d] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// Wait for phase `parity` of `bar`, bounded; false on expiry or abort.
+__device__ __forceinline__ bool t5_wait(uint64_t *bar, uint32_t parity, volatile uint32_t *abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > (1ll << 31)) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void t5_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+struct T5Tile {
+    uint32_t t, mb, nb, l;
+};
+__device__ __forceinline__ T5Tile t5_tile(uint32_t tile, uint32_t L) {
+    T5Tile r;
+    r.t = tile >> 3;
+    r.mb = (tile >> 2) & 1u;
+    r.nb = tile & 3u;
+    r.l = r.t % L;
+    return r;
+}
+
+}  // namespace
+
+template <bool ROWP>
+__global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ Tc5Args a) {
+    extern __shared__ __align__(1024) unsigned char t5_smem_raw[];
+    unsigned char *base = t5_smem_raw + ((1024u - (smem_addr(t5_smem_raw) & 1023u)) & 1023u);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + 2 * (size_t)kT5Stage);
+    uint64_t *full_c = bars, *full_d = bars + 2, *empty = bars + 4, *acc_full = bars + 6, *acc_empty = bars + 7,
+             *drain = bars + 8;
+    __shared__ uint32_t s_tmem;
+    __shared__ uint32_t s_abort;
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr uint32_t NCONV = kT5ConvWarps * 32;
+
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&full_c[s], 1);
+            mbar_init(&full_d[s], NCONV);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, NCONV);
+        mbar_init(drain, 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                     "r"(kT5TmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    t5_fence_before();
+    __syncthreads();
+    t5_fence_after();
+    const uint32_t tmem = s_tmem;
+    volatile uint32_t *abort_flag = &s_abort;
+    const uint32_t ntiles = a.ntiles;
+    // the operand regions of stage s
+    auto stage_a = [&](uint32_t s) { return base + (size_t)s * kT5Stage; };
+    auto stage_b = [&](uint32_t s) { return base + (size_t)s * kT5Stage + kT5StageA; };
+    // the data operand (converted here) and the matrix operand (TMA)
+    auto data_op = [&](uint32_t s) { return ROWP ? stage_a(s) : stage_b(s); };
+    auto mat_op = [&](uint32_t s) { return ROWP ? stage_b(s) : stage_a(s); };
+    constexpr uint32_t DROWS = ROWP ? kT5M : kT5N;     // rows of the data operand
+    constexpr uint32_t MROWS = ROWP ? kT5N : kT5M;     // rows of the matrix operand
+    bool ok = true;
+
+    if (warp == kT5ConvWarps) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            uint32_t g = 0, issued[2] = {0, 0};
+            for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                const T5Tile T = t5_tile(tile, a.L);
+                const uint32_t mrow0 = a.mat_row0 + T.l * kT5Dig * 256 + (ROWP ? T.nb * kT5N : T.mb * kT5M);
+                for (uint32_t c = 0; c < 4 && ok; ++c, ++g) {
+                    const uint32_t s = g & 1u;
+                    if (g >= 2 && !t5_wait(&empty[s], ((g - 2) >> 1) & 1u, abort_flag)) { ok = false; break; }
+                    unsigned char *dst = mat_op(s);
+                    mbar_expect_tx(&full_c[s], kT5Dig * MROWS * 128);
+                    for (uint32_t d = 0; d < kT5Dig; ++d)
+                        for (uint32_t r0 = 0; r0 < MROWS; r0 += 64)
+                            tma_2d_g2s(dst + (d * MROWS + r0) * 128, &a.cmap, (int)(c * kT5KC),
+                                       (int)(mrow0 + d * 256 + r0), &full_c[s]);
+                    if (s) ++issued[1]; else ++issued[0];
+                }
+            }
+            if (!ok) {
+                atomicExch(const_cast<uint32_t *>(abort_flag), 1u);
+                // copies still in flight land before the CTA leaves
+                for (uint32_t s = 0; s < 2; ++s) {
+                    const uint32_t n = s ? issued[1] : issued[0];
+                    if (!n) continue;
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(&full_c[s], (n - 1) & 1u) && clock64() - t0 < (1ll << 30)) {
+                    }
+                }
+            }
+        }
+    } else if (warp == kT5ConvWarps + 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t g = 0, ti = 0;
+            for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++ti) {
+                if (ti > 0) {
+                    if (!t5_wait(acc_empty, (ti - 1) & 1u, abort_flag)) { ok = false; break; }
+                    t5_fence_after();
+                }
+                uint32_t started = 0;     // diagonals that hold a first product
+                for (uint32_t c = 0; c < 4 && ok; ++c, ++g) {
+                    const uint32_t s = g & 1u, ph = (g >> 1) & 1u;
+                    if (!t5_wait(&full_c[s], ph, abort_flag) || !t5_wait(&full_d[s], ph, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    t5_fence_after();
+                    const uint32_t a0 = smem_addr(stage_a(s)), b0 = smem_addr(stage_b(s));
+#pragma unroll 1
+                    for (uint32_t ks = 0; ks < kT5KC / 16; ++ks) {
+#pragma unroll
+                        for (uint32_t i = 0; i < kT5Dig; ++i) {
+#pragma unroll
+                            for (uint32_t j = 0; j < kT5Dig; ++j) {
+                                const uint32_t dg = i + j;
+                                const uint64_t ad = t5_desc(a0 + i * (kT5M * 128) + ks * 32);
+                                const uint64_t bd = t5_desc(b0 + j * (kT5N * 128) + ks * 32);
+                                t5_mma(tmem + dg * kT5N, ad, bd, kT5Idesc, (started >> dg) & 1u);
+                                started |= 1u << dg;
+                            }
+                        }
+                    }
+                    t5_commit(&empty[s]);
+                }
+                if (ok) t5_commit(acc_full);
+            }
+            if (!ok) atomicExch(const_cast<uint32_t *>(abort_flag), 1u);
+            // every product issued has completed before the CTA frees the
+            // tensor memory
+            t5_commit(drain);
+            const long long t0 = clock64();
+            while (!mbar_try_wait(drain, 0) && clock64() - t0 < (1ll << 31)) {
+            }
+        }
+    } else {
+        // ------------------------------------- converters and epilogue
+        const uint32_t ct = tid;              // 0 .. 255
+        uint32_t g = 0, ti = 0;
+        for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++ti) {
+            const T5Tile T = t5_tile(tile, a.L);
+            const uint32_t *src = a.src + (size_t)T.t * 65536;
+            for (uint32_t c = 0; c < 4; ++c, ++g) {
+                const uint32_t s = g & 1u;
+                // this chunk's words, loaded before the buffer is free
+                constexpr uint32_t TASKS = DROWS * 8 / NCONV;    // 16-byte units per thread
+                uint32_t xw[TASKS][8];
+#pragma unroll
+                for (uint32_t q = 0; q < TASKS; ++q) {
+                    const uint32_t task = ct + q * NCONV;
+                    if (ROWP) {
+                        // unit u of data row r: words k = 8u .. 8u + 7 of the chunk
+                        const uint32_t r = task >> 3, u = task & 7u;
+                        const uint4 *p = reinterpret_cast<const uint4 *>(src + (size_t)(T.mb * kT5M + r) * 256 +
+                                                                         c * kT5KC + 8 * u);
+                        const uint4 v0 = __ldg(p), v1 = __ldg(p + 1);
+                        xw[q][0] = v0.x; xw[q][1] = v0.y; xw[q][2] = v0.z; xw[q][3] = v0.w;
+                        xw[q][4] = v1.x; xw[q][5] = v1.y; xw[q][6] = v1.z; xw[q][7] = v1.w;
+                    } else {
+                        // column n (lanes along n), sum rows k = 8u .. 8u + 7 of the chunk
+                        const uint32_t n = task & 63u, u = task >> 6;
+                        const uint32_t *p = src + (size_t)(c * kT5KC + 8 * u) * 256 + T.nb * kT5N + n;
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) xw[q][e] = __ldg(p + (size_t)e * 256);
+                    }
+                }
+                if (g >= 2 && !t5_wait(&empty[s], ((g - 2) >> 1) & 1u, abort_flag)) { ok = false; break; }
+                unsigned char *dst = data_op(s);
+#pragma unroll
+                for (uint32_t q = 0; q < TASKS; ++q) {
+                    const uint32_t task = ct + q * NCONV;
+                    const uint32_t row = ROWP ? task >> 3 : task & 63u, u = ROWP ? task & 7u : task >> 6;
+                    uint4 dg[4];
+                    t5_digits(xw[q], dg);
+                    const uint32_t off = t5_swz(row, u);
+#pragma unroll
+                    for (uint32_t d = 0; d < kT5Dig; ++d)
+                        *reinterpret_cast<uint4 *>(dst + d * (DROWS * 128) + off) = dg[d];
+                }
+                // generic-proxy stores, read next by the tensor cores
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                t5_arrive(&full_d[s]);
+            }
+            if (!ok) break;
+            // ---- epilogue: the seven diagonals of this thread's row
+            if (!t5_wait(acc_full, ti & 1u, abort_flag)) { ok = false; break; }
+            t5_fence_after();
+            const uint32_t row = 32 * (warp & 3u) + lane;        // tensor-memory lane = output row
+            const uint32_t colh = (warp >> 2) * 32;              // this warp's 32 of the 64 columns
+            Lc<uint32_t> kk;
+            kk.load(a.lc + T.l);
+            uint32_t w7[kT5Diag];
+#pragma unroll
+            for (uint32_t d = 0; d < kT5Diag; ++d) w7[d] = __ldg(a.wdiag + 8 * T.l + d);
+            // a multiple of q above 7 * 2^24 * q > |sum|: makes the sum positive
+            const uint64_t off = (uint64_t)kk.q * ((1ull << 57) / kk.q + 1);
+            const uint32_t orow = T.mb * kT5M + row;
+            uint32_t *out = a.dst + (size_t)T.t * 65536 + (size_t)orow * 256 + T.nb * kT5N + colh;
+            const Tw<uint32_t> *twr =
+                a.tw ? a.tw + (size_t)T.l * 65536 + (size_t)orow * 256 + T.nb * kT5N + colh : nullptr;
+#pragma unroll 1
+            for (uint32_t grp = 0; grp < 2; ++grp) {
+                uint32_t f[kT5Diag][16];
+#pragma unroll
+                for (uint32_t d = 0; d < kT5Diag; ++d)
+                    t5_ld16(tmem + ((32u * (warp & 3u)) << 16) + d * kT5N + colh + 16 * grp, f[d]);
+                t5_wait_ld();
+                uint32_t v[16];
+#pragma unroll
+                for (int cc = 0; cc < 16; ++cc) {
+                    int64_t comb = 0;
+#pragma unroll
+                    for (uint32_t d = 0; d < kT5Diag; ++d)
+                        comb += (int64_t)__float2int_rn(__uint_as_float(f[d][cc])) * (int64_t)w7[d];
+                    uint32_t r = csub<uint32_t>(barrett_lazy((uint64_t)comb + off, kk), kk.q);
+                    if (twr) r = mul_full<RED_SHOUP>(r, ldtw(twr + 16 * grp + cc), kk);
+                    v[cc] = r;
+                }
+                uint4 *o = reinterpret_cast<uint4 *>(out + 16 * grp);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) o[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+            t5_fence_before();
+            t5_arrive(acc_empty);
+        }
+        if (!ok) atomicExch(const_cast<uint32_t *>(abort_flag), 1u);
+    }
+    // ---------------------------------------------------------- teardown
+    t5_fence_before();
+    __syncthreads();
+    if (tid == 0 && *abort_flag) atomicOr(a.status, 2u);
+    if (warp == 0) {
+        t5_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kT5TmemCols)
+                     : "memory");
+    }
+}
+
+}  // namespace nttgb
+
+namespace nttgb {
+
+namespace {
+cudaError_t make_t5_cmap(CUtensorMap *m, const void *tab, uint64_t rows) {
+    using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeFn encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return cudaErrorNotSupported;
+        encode = reinterpret_cast<EncodeFn>(fn);
+    }
+    cuuint64_t dims[2] = {256, rows};
+    cuuint64_t strides[1] = {256 * 2};
+    cuuint32_t box[2] = {64, 64};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(tab), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <bool ROWP> cudaError_t t5_launch(const Tc5Args &a, cudaStream_t st) {
+    static int sms = 0;
+    if (!sms) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc5<ROWP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT5Smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const unsigned grid = a.ntiles < (uint32_t)sms ? a.ntiles : (unsigned)sms;
+    k_tc5<ROWP><<<grid, kT5Threads, kT5Smem, st>>>(a);
+    return cudaGetLastError();
+}
+}  // namespace
+
+// Tables (plan->d_tc5): matrix digit planes [4][L][4 digits][256][256] fp16
+// (balanced digits; matrices as in tc.cu: 0 forward column, 1 forward row,
+// 2 inverse row, 3 inverse column; row = output index, column = sum index).
+// Twiddles and the powers 2^(8 s) mod q come from plan->d_tc (tc.cu layout).
+cudaError_t launch_tc5(ntt_plan_s &p, void *data, uint32_t batch, bool inverse, cudaStream_t st) {
+    const uint64_t ntrans = (uint64_t)batch * p.L;
+    if (ntrans * 8 >= (1ull << 32)) return cudaErrorInvalidValue;
+    const uint8_t *mats = reinterpret_cast<const uint8_t *>(p.d_tc);
+    const Tw<uint32_t> *tws = reinterpret_cast<const Tw<uint32_t> *>(mats + (size_t)p.L * 16 * 65536);
+    const uint32_t *pow8 = reinterpret_cast<const uint32_t *>(tws + (size_t)p.L * 2 * 65536);
+    Tc5Args a;
+    std::memset(&a, 0, sizeof(a));
+    cudaError_t e = make_t5_cmap(&a.cmap, p.d_tc5, (uint64_t)4 * p.L * 1024);
+    if (e != cudaSuccess) return e;
+    a.lc = p.d_limb;
+    a.wdiag = pow8;
+    a.status = p.d_status;
+    a.L = p.L;
+    a.ntiles = (uint32_t)(ntrans * 8);
+    uint32_t *d = reinterpret_cast<uint32_t *>(data), *s = reinterpret_cast<uint32_t *>(p.d_scratch);
+    auto row0 = [&](int m) { return (uint32_t)m * p.L * 1024; };
+    if (!inverse) {
+        a.src = d; a.dst = s; a.mat_row0 = row0(0); a.tw = tws;
+        if ((e = t5_launch<false>(a, st)) != cudaSuccess) return e;
+        a.src = s; a.dst = d; a.mat_row0 = row0(1); a.tw = nullptr;
+        e = t5_launch<true>(a, st);
+    } else {
+        a.src = d; a.dst = s; a.mat_row0 = row0(2); a.tw = tws + (size_t)p.L * 65536;
+        if ((e = t5_launch<true>(a, st)) != cudaSuccess) return e;
+        a.src = s; a.dst = d; a.mat_row0 = row0(3); a.tw = nullptr;
+        e = t5_launch<false>(a, st);
+    }
+    p.last_launches += 2;
+    return e;
+}
+
+}  // namespace nttgb

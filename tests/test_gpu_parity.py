@@ -231,18 +231,78 @@ def test_workload_n2p16_L32_u32(nt, orc):
 
 # ----------------------------------------- N = 2^16: two-pass and cluster
 @pytest.mark.parametrize("red", ["shoup", "barrett", "montgomery"])
-@pytest.mark.parametrize("cluster", [False, True])
-def test_n2p16_u32_two_pass_and_cluster(nt, orc, red, cluster):
-    """Both fused forms of N = 2^16 with 4-byte words (the two-pass split;
-    one pass on clusters of eight CTAs), both orders, batch sizes that give
-    clusters one transform, none, or uneven ranges, and limb changes inside
-    a cluster's range."""
+@pytest.mark.parametrize("form", ["stream", "two_launch", "cluster"])
+def test_n2p16_u32_two_pass_and_cluster(nt, orc, red, form):
+    """The fused forms of N = 2^16 with 4-byte words (the two-pass split in
+    one streamed launch or as two launches; one pass on clusters of eight
+    CTAs), both orders, batch sizes that give clusters one transform, none,
+    or uneven ranges, and limb changes inside a cluster's range."""
     N = 1 << 16
-    extra = nt.NTT_CLUSTER if cluster else 0
+    extra = {"stream": 0, "two_launch": nt.NTT_TWO_LAUNCH, "cluster": nt.NTT_CLUSTER}[form]
     qs = primes_for(orc, N, False, 10)
     for i, (batch, L, bitrev) in enumerate([(1, 1, True), (3, 5, False), (10, 10, True), (1, 7, True)]):
         roundtrip_check(nt, orc, N, qs[:L], batch, "fused", red=red, bitrev=bitrev, seed=1600 + i,
                         extra_flags=extra)
+
+
+@pytest.mark.parametrize("tiles,lag", [("1", "1"), ("3", "1"), ("8", "2"), ("64", "1"), ("5", "40")])
+def test_stream_form_item_sizes_and_lags(nt, orc, monkeypatch, tiles, lag):
+    """The one-launch two-pass form under other work-item sizes and lags
+    (the smallest lag makes second-pass items wait on first-pass items still
+    in flight): forward, pointwise-fused inverse and their launch counts, for
+    4- and 8-byte words and every column-pass size (N = 2^14 .. 2^17)."""
+    monkeypatch.setenv("NTT_STREAM_TILES", tiles)
+    monkeypatch.setenv("NTT_STREAM_LAG", lag)
+    for n, w64, L, pairs in [(16, False, 6, 2), (15, False, 3, 1), (17, False, 2, 1), (14, True, 5, 2),
+                             (16, True, 3, 1)]:
+        N = 1 << n
+        qs = primes_for(orc, N, w64, L)
+        psis = [orc.psi(q, N) for q in qs]
+        host = ntt_synth.rns_batch(1700 + n, qs, N, 2 * pairs)
+        p = Plan(nt, N, qs, "fused", w64=w64, bitrev=True)
+        try:
+            d = to_dev(host, w64)
+            p.fwd(d, 2 * pairs)
+            assert nt.ntt_plan_last_launches(p.h) == 1
+            fwd = to_host(d, w64, host.shape)
+            half = pairs * L * N
+            c = torch.empty_like(d[:half])
+            nt.ntt_pointwise_inverse(p.h, c, d[:half], d[half:], pairs)
+            assert nt.ntt_plan_last_launches(p.h) == 1
+            out = to_host(c, w64, (pairs, L, N))
+            assert nt.ntt_get_device_status(p.h) == nt.NTT_OK
+        finally:
+            p.close()
+        A = orc.ntt_batch(host, qs, psis)
+        assert np.array_equal(fwd, reorder(A, True, orc)), (n, w64)
+        P = orc.pointwise_batch(A[:pairs], A[pairs:], qs)
+        assert np.array_equal(out, orc.ntt_batch(P, qs, psis, inverse=True)), (n, w64)
+
+
+def test_stream_and_two_launch_forms_agree_on_the_workload_shape(nt, orc):
+    """N = 2^16, 32 limbs, 16 polynomials: the streamed form and the two
+    launches give the same words, forward and inverse, over five calls in a
+    row (the plan's counter sets are reused and reset by every call)."""
+    N = 1 << 16
+    qs = orc.find_primes(30, 17, 32)
+    host = ntt_synth.rns_batch(1705, qs, N, 16)
+    ps = Plan(nt, N, qs, "fused", bitrev=True)
+    p2 = Plan(nt, N, qs, "fused", bitrev=True, extra_flags=nt.NTT_TWO_LAUNCH)
+    try:
+        a, b = to_dev(host, False), to_dev(host, False)
+        for _ in range(5):
+            ps.fwd(a, 16)
+            p2.fwd(b, 16)
+            assert torch.equal(a, b)
+            ps.inv(a, 16)
+            p2.inv(b, 16)
+            assert torch.equal(a, b)
+        assert nt.ntt_plan_last_launches(p2.h) == 2
+        assert np.array_equal(to_host(a, False, host.shape), host)
+        assert nt.ntt_get_device_status(ps.h) == nt.NTT_OK
+    finally:
+        ps.close()
+        p2.close()
 
 
 def test_n2p16_u32_cluster_polymul_and_launches(nt, orc):
@@ -392,11 +452,13 @@ def test_pointwise_inverse_fused_and_fallback(nt, orc, red):
     in bit-reversed order take the product inside the first inverse pass
     (u32 N = 2^15, 2^16, 2^17; u64 N = 2^16); N = 2^12, natural order and
     NTT_CHECK plans run the two steps.  c aliasing a, aliasing b, or apart."""
-    # (log N, u64, bit-reversed, flags, launches: 2 fused; else the product
-    # (with NTT_CHECK: + a range check of each operand), then the inverse
-    # (+ its range check, + the order permutation, + one or two passes))
-    cases = [(15, False, True, 0, 2), (16, False, True, 0, 2), (17, False, True, 0, 2), (16, True, True, 0, 2),
-             (12, False, True, 0, 2), (16, False, False, 0, 4), (16, False, True, nt.NTT_CHECK, 6)]
+    # (log N, u64, bit-reversed, flags, launches: 1 fused (both passes in
+    # one launch), 2 with NTT_TWO_LAUNCH; else the product (with NTT_CHECK:
+    # + a range check of each operand), then the inverse (+ its range check,
+    # + the order permutation, + its one launch))
+    cases = [(15, False, True, 0, 1), (16, False, True, 0, 1), (17, False, True, 0, 1), (16, True, True, 0, 1),
+             (16, False, True, nt.NTT_TWO_LAUNCH, 2), (16, True, True, nt.NTT_TWO_LAUNCH, 2),
+             (12, False, True, 0, 2), (16, False, False, 0, 3), (16, False, True, nt.NTT_CHECK, 5)]
     for i, (n, w64, bitrev, extra, launches) in enumerate(cases):
         N, batch = 1 << n, 3
         qs = primes_for(orc, N, w64, 2)

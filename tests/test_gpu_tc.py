@@ -1,5 +1,7 @@
-"""The tensor-core four-step form (N = 2^16, 8-bit digit products on the
-integer tensor cores) against the oracle and against the butterfly form."""
+"""The tensor-core four-step form (N = 2^16, 8-bit digit products) against
+the oracle and against the butterfly form, in both of its forms: tcgen05
+(balanced digits in fp16, fp32 diagonals in tensor memory; the default) and
+the warp-level integer MMA (NTT_TC_IMMA)."""
 import numpy as np
 import pytest
 
@@ -33,13 +35,21 @@ def bitrev_rows(X, orc):
     return np.stack([np.stack([orc.bitrev_permute(X[b, l]) for l in range(L)]) for b in range(B)])
 
 
-@pytest.mark.parametrize("L,batch", [(2, 1), (32, 16)])
-def test_tc_forward_inverse_bit_exact(nt, orc, L, batch):
+FORMS = ["tcgen05", "imma"]
+
+
+def form_flags(nt, form):
+    return nt.NTT_TC_IMMA if form == "imma" else 0
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("L,batch", [(2, 1), (3, 5), (32, 16)])
+def test_tc_forward_inverse_bit_exact(nt, orc, form, L, batch):
     N = 1 << 16
     qs = orc.find_primes(30, 17, L)
     psis = [orc.psi(q, N) for q in qs]
     h = ntt_synth.rns_batch(1005, qs, N, batch)
-    p = nt.ntt_plan_create(N, qs, nt.NTT_TC_FOURSTEP, nt.NTT_ORDER_BITREV)
+    p = nt.ntt_plan_create(N, qs, nt.NTT_TC_FOURSTEP, nt.NTT_ORDER_BITREV | form_flags(nt, form))
     try:
         d = dev(h)
         nt.ntt_forward(p, d, batch)
@@ -48,6 +58,7 @@ def test_tc_forward_inverse_bit_exact(nt, orc, L, batch):
         assert np.array_equal(got, want)
         nt.ntt_inverse(p, d, batch)
         assert np.array_equal(host(d, h.shape), h)
+        assert nt.ntt_get_device_status(p) == nt.NTT_OK
     finally:
         nt.ntt_plan_destroy(p)
 
@@ -57,7 +68,7 @@ def test_tc_matches_butterfly_form_and_natural_order(nt, orc):
     qs = orc.find_primes(30, 17, L)
     h = ntt_synth.rns_batch(77, qs, N, batch)
     outs = []
-    for variant, flags in [(nt.NTT_TC_FOURSTEP, 0), (nt.NTT_FUSED, 0)]:
+    for variant, flags in [(nt.NTT_TC_FOURSTEP, 0), (nt.NTT_TC_FOURSTEP, nt.NTT_TC_IMMA), (nt.NTT_FUSED, 0)]:
         p = nt.ntt_plan_create(N, qs, variant, flags)
         try:
             d = dev(h)
@@ -67,24 +78,33 @@ def test_tc_matches_butterfly_form_and_natural_order(nt, orc):
             assert np.array_equal(host(d, h.shape), h)
         finally:
             nt.ntt_plan_destroy(p)
-    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
+    assert np.array_equal(outs[1], outs[2])
     psis = [orc.psi(q, N) for q in qs]
     assert np.array_equal(outs[0], orc.ntt_batch(h, qs, psis))
 
 
-def test_tc_extreme_inputs(nt, orc):
-    """All words q-1: every digit product and diagonal sum at its maximum."""
+@pytest.mark.parametrize("form", FORMS)
+def test_tc_extreme_inputs(nt, orc, form):
+    """Words that put the digits at their extremes: q - 1 (unsigned digits
+    all large), 0x3F7F7F80 (balanced digits -128, -128, -128, 64), 0 and
+    alternating patterns, forward and back."""
     N = 1 << 16
-    qs = orc.find_primes(30, 17, 2)
-    h = np.zeros((1, 2, N), np.uint64)
+    qs = orc.find_primes(30, 17, 4)
+    h = np.zeros((2, 4, N), np.uint64)
     for l, q in enumerate(qs):
         h[0, l] = q - 1
-    p = nt.ntt_plan_create(N, qs, nt.NTT_TC_FOURSTEP, nt.NTT_ORDER_BITREV)
+        h[1, l, 0::2] = 0x3F7F7F80 % q
+        h[1, l, 1::4] = 0
+        h[1, l, 3::4] = 0x00808080
+    p = nt.ntt_plan_create(N, qs, nt.NTT_TC_FOURSTEP, nt.NTT_ORDER_BITREV | form_flags(nt, form))
     try:
         d = dev(h)
-        nt.ntt_forward(p, d, 1)
+        nt.ntt_forward(p, d, 2)
         psis = [orc.psi(q, N) for q in qs]
         assert np.array_equal(host(d, h.shape), bitrev_rows(orc.ntt_batch(h, qs, psis), orc))
+        nt.ntt_inverse(p, d, 2)
+        assert np.array_equal(host(d, h.shape), h)
     finally:
         nt.ntt_plan_destroy(p)
 
