@@ -97,15 +97,19 @@ typedef enum {
                                       GB300 it moves half the DRAM bytes but
                                       takes longer: a cluster barrier per
                                       transform and single-buffered tiles) */
-#define NTT_TWO_LAUNCH 0x400u      /* NTT_FUSED, two-pass sizes (N > 2^14 with
+#define NTT_STREAMED 0x400u        /* NTT_FUSED, two-pass sizes (N > 2^14 with
                                       4-byte words, N > 2^13 with 8-byte): run
-                                      the column pass and the chunk pass as two
-                                      launches (the whole batch written to
-                                      memory between them).  Default: one
-                                      launch that streams limb by limb, so a
-                                      limb's intermediate is read back while
-                                      still in L2; results identical.  Calls of
-                                      one default plan use one of 16 counter
+                                      both passes in one launch that streams
+                                      limb by limb, so each limb's
+                                      intermediate is read back while still
+                                      in L2 (about a quarter less DRAM
+                                      traffic), instead of the default two
+                                      launches with the whole batch written
+                                      to memory between them; results
+                                      identical.  On GB300 the two launches
+                                      are faster (the passes are bound by
+                                      issue and latency, not DRAM).  Calls of
+                                      one streamed plan use one of 16 counter
                                       sets in turn: at most 16 calls of one
                                       plan may overlap on the GPU */
 #define NTT_TC_IMMA 0x800u         /* NTT_TC_FOURSTEP: the digit products on

@@ -43,7 +43,7 @@ NTT_RED_MONTGOMERY = 0x20
 NTT_RED_MASK = 0x30
 NTT_CHECK = 0x100
 NTT_CLUSTER = 0x200
-NTT_TWO_LAUNCH = 0x400
+NTT_STREAMED = 0x400
 NTT_TC_IMMA = 0x800
 NTT_TEST_STALL = 0x8000
 REDUCTIONS = {"shoup": NTT_RED_SHOUP, "barrett": NTT_RED_BARRETT,

@@ -40,11 +40,19 @@ def _digest(extra=""):
     return h.hexdigest()
 
 
-def kernel_digest():
-    """Digest of the kernel sources and headers (relative paths + contents):
-    identifies the code an ncu capture was taken on."""
+# Sources of the fused forward transform with 4-byte words and Shoup
+# twiddles (the streamed two-pass launch the benchmark times).
+FORWARD_U32_SOURCES = ("fused.cuh", "stream.cuh", "fused_launch.cuh", "modarith.cuh", "plan.hpp",
+                       "fused_u32_shoup.cu")
+
+
+def kernel_digest(files=None):
+    """Digest of kernel sources and headers (relative paths + contents):
+    identifies the code an ncu capture was taken on.  `files`: names under
+    csrc/ to cover (default: all of them)."""
     h = hashlib.sha256()
-    for p in _sources() + _headers():
+    paths = _sources() + _headers() if files is None else [os.path.join(CSRC, f) for f in files]
+    for p in sorted(paths):
         h.update(os.path.relpath(p, ROOT).encode())
         with open(p, "rb") as f:
             h.update(f.read())

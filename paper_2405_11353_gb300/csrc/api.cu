@@ -15,7 +15,7 @@ using u128 = unsigned __int128;
 namespace {
 
 constexpr uint32_t kKnownFlags =
-    NTT_WORD64 | NTT_ORDER_BITREV | NTT_RED_MASK | NTT_CHECK | NTT_CLUSTER | NTT_TWO_LAUNCH |
+    NTT_WORD64 | NTT_ORDER_BITREV | NTT_RED_MASK | NTT_CHECK | NTT_CLUSTER | NTT_STREAMED |
     NTT_TC_IMMA | NTT_TEST_STALL;
 constexpr uint32_t kMaxLimbs = 4096;
 
@@ -354,7 +354,7 @@ ntt_status build_tables(ntt_plan_s *p) {
     }
     if (cudaMalloc((void **)&p->d_status, sizeof(uint32_t)) != cudaSuccess) { cudaGetLastError(); return NTT_ERR_OOM; }
     if (cudaMemset(p->d_status, 0, sizeof(uint32_t)) != cudaSuccess) return NTT_ERR_CUDA;
-    if (chunk_tabs) {
+    if (chunk_tabs && p->streamed) {
         const size_t bytes = (size_t)nttgb::kStreamRing * nttgb::stream_set_words(L) * sizeof(uint32_t);
         if (cudaMalloc((void **)&p->d_stream_ctr, bytes) != cudaSuccess) { cudaGetLastError(); return NTT_ERR_OOM; }
         if (cudaMemset(p->d_stream_ctr, 0, bytes) != cudaSuccess) return NTT_ERR_CUDA;
@@ -541,7 +541,7 @@ ntt_status create_plan(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t
             p->fused_mode = nttgb::FUSED_CLUSTER;
         else {
             p->fused_mode = nttgb::FUSED_TWO_PASS;
-            p->two_launch = (flags & NTT_TWO_LAUNCH) != 0;
+            p->streamed = (flags & NTT_STREAMED) != 0;
             p->s2 = nttgb::kChunkLog;
             p->s1 = p->logN - p->s2;
         }

@@ -78,8 +78,9 @@ template <class W> __host__ __device__ constexpr uint32_t cols_phys(uint32_t k, 
 // words (or one transform above that), column strips 16 (4-byte) or 8
 // (8-byte) columns and at least 256 threads, chunk tiles 16 chunks.
 // P = 0: per-plan passes; column strips have 128-byte rows (32 four-byte or
-// 16 eight-byte columns).  P = 1: the ragged kernel, whose CTAs always have
-// 256 threads (4096-word column tiles).
+// 16 eight-byte columns).  P = 1: the ragged kernel and the streamed
+// two-pass launch, whose CTAs always have 256 threads (4096-word column
+// tiles).
 template <class W, int LOGS, int KIND, int P = 0> __host__ __device__ constexpr uint32_t tile_k() {
     return KIND == TK_SINGLE ? (LOGS >= 12 ? 1u : (4096u >> LOGS))
          : KIND == TK_CHUNKS ? 16u
@@ -396,6 +397,14 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     constexpr bool WS = KIND != TK_COLS && T <= 32;
     using R0 = RoundOf<LOGS, INV, 0>;
     using RL = RoundOf<LOGS, INV, R0::NR - 1>;
+    // Per-plan passes (long runs of tiles per CTA, registers to spare):
+    // refill a buffer right after the next tile's first barrier, which saves
+    // a barrier per tile; keep the limb constants in registers across tiles;
+    // load the fused product's second operand before the tile wait.  The
+    // 256-thread item kernels (short runs, three CTAs per SM, one kernel for
+    // every tile kind under a 128-register cap) refill at the end of each
+    // tile and load constants per tile, which keeps them free of spills.
+    constexpr bool LATE_REFILL = P == 0;
     W *stage = reinterpret_cast<W *>(base);
     Tw<W> *tws = reinterpret_cast<Tw<W> *>(stage + (size_t)NS * BW);
     if (t_begin >= t_end) return true;
@@ -487,6 +496,7 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
         for (uint32_t s = 0; s < NS && t_begin + s < t_end; ++s) { issue(ahead, s); cur_next(ahead); }
         if (t_begin + NS < t_end) prefetch(ahead);
     }
+    uint32_t n_issued = t_end - t_begin < NS ? t_end - t_begin : NS;   // local tiles issued so far
     uint32_t tw_key = 0xffffffffu;  // (limb, group) of the staged twiddles
     uint32_t &tw_phase = ps.tw_phase;
     bool ok = true;
@@ -504,7 +514,7 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
         const uint64_t t = KIND == TK_SINGLE ? cur_t(cur) + k : cur_t(cur);
         const bool valid = t < a.ntrans;
         const uint32_t l = KIND == TK_SINGLE ? (uint32_t)((valid ? t : 0) % L) : cur.l;
-        if (l != kk_l) {
+        if (!LATE_REFILL || l != kk_l) {
             kk.load(a.lc + l);
             if (INV && a.final_pass) {
                 tn.w = (W)a.lc[l].ninv_w; tn.c = (W)a.lc[l].ninv_c;
@@ -518,6 +528,10 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
             // thread finished with the old one before the previous refill barrier)
             const uint32_t key = KIND == TK_CHUNKS ? cur.l * per + cur.g : cur.l;
             if (key != tw_key) {
+                // inside a run of tiles, the previous tile may still be
+                // reading the old table (without LATE_REFILL the end-of-tile
+                // barrier has already waited for it)
+                if (LATE_REFILL && i > 0) __syncthreads();
                 if (tid == 0) {
                     fence_proxy_async();
                     mbar_expect_tx(&bar[NS], TWP * (uint32_t)sizeof(Tw<W>));
@@ -538,9 +552,11 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
         using V16 = typename std::conditional<sizeof(W) == 4, uint4, ulonglong2>::type;
         V16 bv[PW ? NV : 1];
         const bool use_pw = PW && a.pw_b && valid;
-        if constexpr (PW) {
+        const V16 *bq = use_pw ? reinterpret_cast<const V16 *>(a.pw_b + t * N + ((size_t)(pos0 + k) << S2) +
+                                                              R0::A(tau))
+                               : nullptr;
+        if constexpr (PW && LATE_REFILL) {
             if (use_pw) {
-                const V16 *bq = reinterpret_cast<const V16 *>(a.pw_b + t * N + ((size_t)(pos0 + k) << S2) + R0::A(tau));
 #pragma unroll
                 for (int v = 0; v < NV; ++v) bv[v] = __ldg(bq + v);
             }
@@ -592,6 +608,10 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
         if constexpr (PW) {
             // the inverse of a (.) b: multiply by b's words first
             if (use_pw) {
+                if constexpr (!LATE_REFILL) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) bv[v] = __ldg(bq + v);
+                }
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     if constexpr (sizeof(W) == 4) {
@@ -606,21 +626,33 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
                 }
             }
         }
-        // every thread has its words (the buffer now serves the exchanges)
+        // every thread has its words (the buffer now serves the exchanges),
+        // and every thread is done with the previous tile: with LATE_REFILL
+        // its buffer takes the tile NS - 1 ahead of this one here
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicOr(a.status, 2u);
             ok = false;
             break;
         }
+        if (LATE_REFILL && tid == 0 && i > 0 && tile + NS - 1 < t_end) {
+            fence_proxy_async();
+            issue(ahead, (i + NS - 1) % NS);
+            cur_next(ahead);
+            ++n_issued;
+            if (tile + NS < t_end) prefetch(ahead);
+        }
         round_bfly<W, RED, INV, LOGS, 0, TWS>(x, tau, twb, kk, INV && a.final_pass, tn, twn);
         later_rounds<W, RED, INV, LOGS, KIND, WS, TWS, 1, P>(x, sb, smb_k, tau, twb, kk, INV && a.final_pass, tn, twn);
-        // the buffer and the twiddles are free: refill with the tile NS ahead
-        __syncthreads();
-        if (tid == 0 && tile + NS < t_end) {
-            fence_proxy_async();
-            issue(ahead, s);
-            cur_next(ahead);
-            if (tile + NS + 1 < t_end) prefetch(ahead);
+        if (!LATE_REFILL) {
+            // the buffer and the twiddles are free: refill with the tile NS ahead
+            __syncthreads();
+            if (tid == 0 && tile + NS < t_end) {
+                fence_proxy_async();
+                issue(ahead, s);
+                cur_next(ahead);
+                ++n_issued;
+                if (tile + NS + 1 < t_end) prefetch(ahead);
+            }
         }
         if (a.final_pass) {
 #pragma unroll
@@ -663,7 +695,7 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
         // i .. i+NS-1 and the twiddle table) land before the CTA goes on,
         // again with a time limit
         if (tid == 0) {
-            for (uint32_t j = i; j < i + NS && j < n_local; ++j) {
+            for (uint32_t j = i; j < n_issued; ++j) {
                 const long long t0 = clock64();
                 while (!mbar_try_wait(&bar[j % NS], (ps.use(j % NS) + j / NS) & 1u))
                     if (clock64() - t0 > (1ll << 30)) break;

@@ -212,8 +212,8 @@ cudaError_t run_stream(ntt_plan_s &p, W *data, uint64_t ntrans, cudaStream_t st,
     const uint32_t env_lag = stream_env("NTT_STREAM_LAG");
     StreamArgs<W> sa;
     std::memset(&sa, 0, sizeof(sa));
-    const uint32_t Kc = tile_k_p<W, TK_COLS, 1>((int)p.s1);
-    const uint32_t Kh = tile_k<W, kN2Log, TK_CHUNKS, 1>();
+    const uint32_t Kc = tile_k_p<W, TK_COLS, stream_p<W>()>((int)p.s1);
+    const uint32_t Kh = tile_k<W, kN2Log, TK_CHUNKS, stream_p<W>()>();
     const uint64_t B = ntrans / p.L;
     const uint64_t tpl_cols = B * ((1u << p.s2) / Kc), tpl_chunks = B * ((1u << p.s1) / Kh);
     if (tpl_cols * p.L >= (1ull << 32) || tpl_chunks * p.L >= (1ull << 32)) return cudaErrorInvalidValue;
@@ -236,8 +236,17 @@ cudaError_t run_stream(ntt_plan_s &p, W *data, uint64_t ntrans, cudaStream_t st,
         sa.tiles_per_limb[1] = (uint32_t)tpl_cols;
     }
     if (e != cudaSuccess) return e;
-    // work items of 4 tiles (4 KiB ... 32 KiB each)
-    const uint32_t g = env_tiles ? env_tiles : 4u;
+    int resident = 0;
+    e = stream_resident<W, RED, INV>((int)p.s1, &resident);
+    if (e != cudaSuccess) return e;
+    // work items of up to 4 tiles (4 KiB ... 32 KiB each), fewer when the
+    // first pass would otherwise have less than two items per CTA
+    uint32_t g = env_tiles;
+    if (!g) {
+        const uint64_t first_tiles = (uint64_t)sa.tiles_per_limb[0] * p.L;
+        const uint64_t per = first_tiles / (2ull * (uint64_t)resident);
+        g = per >= 4 ? 4u : (per >= 2 ? 2u : 1u);
+    }
     uint32_t slots = 0;
     for (int i = 0; i < 2; ++i) {
         sa.tiles_per_item[i] = g < sa.tiles_per_limb[i] ? g : sa.tiles_per_limb[i];
@@ -248,9 +257,6 @@ cudaError_t run_stream(ntt_plan_s &p, W *data, uint64_t ntrans, cudaStream_t st,
     // the second pass of a limb starts about two grids of items after its
     // first pass (so its first-pass tiles are done), plus one round; the
     // intermediate then held in L2 is about lag rounds of one limb
-    int resident = 0;
-    e = stream_resident<W, RED, INV>((int)p.s1, &resident);
-    if (e != cudaSuccess) return e;
     sa.lag = env_lag ? env_lag : (2u * (uint32_t)resident + slots - 1) / slots + 1;
     sa.ctr = p.d_stream_ctr + (size_t)(p.stream_seq++ % kStreamRing) * stream_set_words(p.L);
     ++p.last_launches;
@@ -272,7 +278,7 @@ cudaError_t run_fused_t(ntt_plan_s &p, void *data_v, uint32_t batch, bool invers
         if (!inverse) return run_pass<W, RED, false, TK_SINGLE>(p, data, p.d_main_fwd, ntrans, p.logN, true, st);
         return run_pass<W, RED, true, TK_SINGLE>(p, data, p.d_main_inv, ntrans, p.logN, true, st);
     }
-    if (!p.two_launch) {
+    if (p.streamed) {
         if (!inverse) return run_stream<W, RED, false>(p, data, ntrans, st, nullptr, nullptr);
         return run_stream<W, RED, true>(p, data, ntrans, st, nullptr, nullptr);
     }
@@ -294,7 +300,7 @@ cudaError_t run_fused_pwinv_t(ntt_plan_s &p, void *c, const void *a, const void 
                               cudaStream_t st) {
     const uint64_t ntrans = (uint64_t)batch * p.L;
     W *cw = reinterpret_cast<W *>(c);
-    if (!p.two_launch)
+    if (p.streamed)
         return run_stream<W, RED, true>(p, const_cast<W *>(reinterpret_cast<const W *>(a)), ntrans, st, cw,
                                         reinterpret_cast<const W *>(b));
     cudaError_t e = run_pass<W, RED, true, TK_CHUNKS>(p, const_cast<W *>(reinterpret_cast<const W *>(a)),

@@ -63,7 +63,7 @@ struct ntt_plan_s {
     // a ring of sets, one per call
     uint32_t *d_stream_ctr = nullptr;
     uint32_t stream_seq = 0;
-    bool two_launch = false;     // NTT_TWO_LAUNCH: the passes as two launches
+    bool streamed = false;       // NTT_STREAMED: both passes in one streamed launch
     uint32_t *d_status = nullptr;
     uint32_t last_launches = 0;
 

@@ -12,6 +12,9 @@
 // only ever wait on items earlier in the queue, which CTAs already hold and
 // finish without waiting on later ones, so no launch shape can deadlock.
 //
+// Tiles are those of the per-pass kernels (fused.cuh) in their 256-thread
+// configuration (P = 1).
+//
 // Per call the kernel uses one counter set of the plan (a ring of
 // kStreamRing sets, so that up to that many calls of one plan may overlap):
 // [0, L) first-pass tiles stored per limb, then the queue head, the exit
@@ -21,7 +24,11 @@
 
 namespace nttgb {
 
-constexpr uint32_t kStreamThreads = 256;
+// Tile configuration of the stream kernel: 256-thread CTAs, three per SM
+// (512-thread CTAs with 32-chunk tiles fit only one per SM and ran slower).
+template <class W> __host__ __device__ constexpr int stream_p() { return 1; }
+template <class W> __host__ __device__ constexpr uint32_t stream_threads() { return 256u; }
+template <class W> __host__ __device__ constexpr int stream_min_blocks() { return 3; }
 
 template <class W> struct StreamArgs {
     FArgs<W> pass[2];           // in run order: [0] first pass, [1] second pass
@@ -33,10 +40,10 @@ template <class W> struct StreamArgs {
     uint32_t lag;               // rounds between a limb's first and second pass (>= 1)
 };
 
-// Shared-memory bytes a tile kind uses in the stream kernel (256-thread tiles).
+// Shared-memory bytes a tile kind uses in the stream kernel.
 template <class W, int LOGS, int KIND, bool INV> __host__ __device__ constexpr size_t stream_kind_bytes() {
-    return (size_t)n_stages<W, LOGS, KIND>() * buf_words<W, LOGS, KIND, INV, 1>() * sizeof(W) +
-           (size_t)tw_pairs<W, LOGS, KIND, 1>() * 2 * sizeof(W);
+    return (size_t)n_stages<W, LOGS, KIND>() * buf_words<W, LOGS, KIND, INV, stream_p<W>()>() * sizeof(W) +
+           (size_t)tw_pairs<W, LOGS, KIND, stream_p<W>()>() * 2 * sizeof(W);
 }
 template <class W, int S1, bool INV> __host__ __device__ constexpr size_t stream_bar_offset() {
     constexpr size_t a = stream_kind_bytes<W, S1, TK_COLS, INV>();
@@ -71,7 +78,8 @@ __device__ __forceinline__ bool wait_count(const uint32_t *c, uint32_t target, c
 }
 
 template <class W, int RED, bool INV, int S1>
-__global__ void __launch_bounds__(kStreamThreads, 3) k_stream(const __grid_constant__ StreamArgs<W> sa) {
+__global__ void __launch_bounds__(stream_threads<W>(), stream_min_blocks<W>())
+k_stream(const __grid_constant__ StreamArgs<W> sa) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint32_t s_item;
     __shared__ int s_go;
@@ -95,8 +103,16 @@ __global__ void __launch_bounds__(kStreamThreads, 3) k_stream(const __grid_const
     const uint64_t total = (uint64_t)(L + sa.lag) * slots;
     PipeState ps{{0, 0}, 0};
     bool ok = true;
+    // thread 0 takes the next item while this one runs (its atomic's
+    // latency hides behind the work); holding one item ahead cannot
+    // deadlock: the earliest unfinished item is always one a CTA is running
+    uint32_t ahead = 0;
+    if (tid == 0) ahead = atomicAdd(head, 1u);
     for (;;) {
-        if (tid == 0) s_item = *(volatile uint32_t *)abort_flag ? 0xffffffffu : atomicAdd(head, 1u);
+        if (tid == 0) {
+            s_item = *(volatile uint32_t *)abort_flag ? 0xffffffffu : ahead;
+            if (s_item < total) ahead = atomicAdd(head, 1u);
+        }
         __syncthreads();
         const uint32_t item = s_item;
         __syncthreads();
@@ -114,7 +130,8 @@ __global__ void __launch_bounds__(kStreamThreads, 3) k_stream(const __grid_const
         const uint32_t t0 = limb * tpl + j * tpi;
         const uint32_t t1 = t0 + tpi < (limb + 1) * tpl ? t0 + tpi : (limb + 1) * tpl;
         if (first) {
-            ok = run_tiles<W, RED, INV, LOGS0, KIND0, 1>(sa.pass[0], &sa.pass[0].tmap, t0, t1, base, bar, ps);
+            ok = run_tiles<W, RED, INV, LOGS0, KIND0, stream_p<W>()>(sa.pass[0], &sa.pass[0].tmap, t0, t1, base, bar,
+                                                                    ps);
             if (!ok) break;
             // every thread's stores of this item, then the count
             fence_proxy_async_global();
@@ -129,7 +146,8 @@ __global__ void __launch_bounds__(kStreamThreads, 3) k_stream(const __grid_const
             }
             __syncthreads();
             if (!s_go) { ok = false; break; }
-            ok = run_tiles<W, RED, INV, LOGS1, KIND1, 1>(sa.pass[1], &sa.pass[1].tmap, t0, t1, base, bar, ps);
+            ok = run_tiles<W, RED, INV, LOGS1, KIND1, stream_p<W>()>(sa.pass[1], &sa.pass[1].tmap, t0, t1, base, bar,
+                                                                    ps);
             if (!ok) break;
         }
     }
@@ -153,7 +171,7 @@ template <class W, int RED, bool INV, int S1> cudaError_t stream_config(size_t *
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, (int)kStreamThreads, *smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, (int)stream_threads<W>(), *smem);
 }
 
 // Grid of the stream kernel: every CTA that fits on the GPU at once.
@@ -190,7 +208,7 @@ cudaError_t stream_launch(const StreamArgs<W> &sa, cudaStream_t st) {
     size_t smem = 0;
     cudaError_t e = stream_resident_s1<W, RED, INV, S1>(&resident, &smem);
     if (e != cudaSuccess) return e;
-    k_stream<W, RED, INV, S1><<<resident, kStreamThreads, smem, st>>>(sa);
+    k_stream<W, RED, INV, S1><<<resident, stream_threads<W>(), smem, st>>>(sa);
     return cudaGetLastError();
 }
 

@@ -23,11 +23,12 @@
 //     the inter-step twiddle (Shoup) where the pass has one.
 //
 // GEMM view, D[m][n] = sum_k A[m][k] B[n][k], both operands K-major in shared
-// memory (128-byte swizzle, tile M = 128, N = 64, K chunks of 64):
-//   column pass  A = matrix [u][n1] (TMA), B = data column block [n2][n1]
-//                (converted by the CTA), D = out[u][n2];
-//   row pass     A = data row block [r][n2] (converted), B = matrix [v][n2]
-//                (TMA), D = out[r][v].
+// memory (128-byte swizzle, tile M = 128, N = 64, K chunks of 64); A is 128
+// data rows (converted to digits by the CTA), B 64 matrix rows (TMA):
+//   column pass  A[n2][n1] = src[n1][n2], B = matrix [u][n1],
+//                D[n2][u] -> out[u][n2];
+//   row pass     A[r][n2] = src[r][n2],   B = matrix [v][n2],
+//                D[r][v]  -> out[r][v].
 // Each pass reads src and writes dst (out of place: a tile's output rows are
 // other tiles' input rows).
 //
@@ -214,14 +215,9 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
     const uint32_t tmem = s_tmem;
     volatile uint32_t *abort_flag = &s_abort;
     const uint32_t ntiles = a.ntiles;
-    // the operand regions of stage s
+    // stage s: A = data digit planes (converted here), B = matrix digit planes (TMA)
     auto stage_a = [&](uint32_t s) { return base + (size_t)s * kT5Stage; };
     auto stage_b = [&](uint32_t s) { return base + (size_t)s * kT5Stage + kT5StageA; };
-    // the data operand (converted here) and the matrix operand (TMA)
-    auto data_op = [&](uint32_t s) { return ROWP ? stage_a(s) : stage_b(s); };
-    auto mat_op = [&](uint32_t s) { return ROWP ? stage_b(s) : stage_a(s); };
-    constexpr uint32_t DROWS = ROWP ? kT5M : kT5N;     // rows of the data operand
-    constexpr uint32_t MROWS = ROWP ? kT5N : kT5M;     // rows of the matrix operand
     bool ok = true;
 
     if (warp == kT5ConvWarps) {
@@ -230,16 +226,15 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
             uint32_t g = 0, issued[2] = {0, 0};
             for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
                 const T5Tile T = t5_tile(tile, a.L);
-                const uint32_t mrow0 = a.mat_row0 + T.l * kT5Dig * 256 + (ROWP ? T.nb * kT5N : T.mb * kT5M);
+                const uint32_t mrow0 = a.mat_row0 + T.l * kT5Dig * 256 + T.nb * kT5N;
                 for (uint32_t c = 0; c < 4 && ok; ++c, ++g) {
                     const uint32_t s = g & 1u;
                     if (g >= 2 && !t5_wait(&empty[s], ((g - 2) >> 1) & 1u, abort_flag)) { ok = false; break; }
-                    unsigned char *dst = mat_op(s);
-                    mbar_expect_tx(&full_c[s], kT5Dig * MROWS * 128);
+                    unsigned char *dst = stage_b(s);
+                    mbar_expect_tx(&full_c[s], kT5Dig * kT5N * 128);
                     for (uint32_t d = 0; d < kT5Dig; ++d)
-                        for (uint32_t r0 = 0; r0 < MROWS; r0 += 64)
-                            tma_2d_g2s(dst + (d * MROWS + r0) * 128, &a.cmap, (int)(c * kT5KC),
-                                       (int)(mrow0 + d * 256 + r0), &full_c[s]);
+                        tma_2d_g2s(dst + d * kT5N * 128, &a.cmap, (int)(c * kT5KC), (int)(mrow0 + d * 256),
+                                   &full_c[s]);
                     if (s) ++issued[1]; else ++issued[0];
                 }
             }
@@ -264,7 +259,6 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
                     if (!t5_wait(acc_empty, (ti - 1) & 1u, abort_flag)) { ok = false; break; }
                     t5_fence_after();
                 }
-                uint32_t started = 0;     // diagonals that hold a first product
                 for (uint32_t c = 0; c < 4 && ok; ++c, ++g) {
                     const uint32_t s = g & 1u, ph = (g >> 1) & 1u;
                     if (!t5_wait(&full_c[s], ph, abort_flag) || !t5_wait(&full_d[s], ph, abort_flag)) {
@@ -272,18 +266,21 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
                         break;
                     }
                     t5_fence_after();
-                    const uint32_t a0 = smem_addr(stage_a(s)), b0 = smem_addr(stage_b(s));
-#pragma unroll 1
+                    // descriptors of the stage's digit planes; a digit plane or
+                    // a K step of 16 (32 bytes) moves the start address field
+                    const uint64_t da = t5_desc(smem_addr(stage_a(s))), db = t5_desc(smem_addr(stage_b(s)));
+#pragma unroll
                     for (uint32_t ks = 0; ks < kT5KC / 16; ++ks) {
 #pragma unroll
                         for (uint32_t i = 0; i < kT5Dig; ++i) {
 #pragma unroll
                             for (uint32_t j = 0; j < kT5Dig; ++j) {
-                                const uint32_t dg = i + j;
-                                const uint64_t ad = t5_desc(a0 + i * (kT5M * 128) + ks * 32);
-                                const uint64_t bd = t5_desc(b0 + j * (kT5N * 128) + ks * 32);
-                                t5_mma(tmem + dg * kT5N, ad, bd, kT5Idesc, (started >> dg) & 1u);
-                                started |= 1u << dg;
+                                // the first product of diagonal i + j in the tile
+                                // (smallest i) overwrites the accumulator
+                                const bool first = ks == 0 && (i == 0 || j == kT5Dig - 1);
+                                t5_mma(tmem + (i + j) * kT5N, da + ((i * (kT5M * 128) + ks * 32) >> 4),
+                                       db + ((j * (kT5N * 128) + ks * 32) >> 4), kT5Idesc,
+                                       (c > 0 || !first) ? 1u : 0u);
                             }
                         }
                     }
@@ -301,58 +298,62 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
         }
     } else {
         // ------------------------------------- converters and epilogue
-        const uint32_t ct = tid;              // 0 .. 255
-        uint32_t g = 0, ti = 0;
-        for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++ti) {
+        // Data operand A[m][k] of a tile, m < 128, for chunk c (k in 64 c ..):
+        //   column pass  m = n2 - 128 mb, k = n1: word src[k][128 mb + m]
+        //   row pass     m = r - 128 mb,  k = n2: word src[128 mb + m][k]
+        // 16-byte unit u (k = 8u .. 8u + 7) of row m is task (m, u); each
+        // thread takes TASKS of them (lanes along m for the column pass,
+        // along u for the row pass, so the loads coalesce).
+        constexpr uint32_t TASKS = kT5M * 8 / NCONV;
+        auto task_mu = [&](uint32_t q, uint32_t &m, uint32_t &u) {
+            const uint32_t task = tid + q * NCONV;
+            if (ROWP) { m = task >> 3; u = task & 7u; }
+            else { m = task & 127u; u = task >> 7; }
+        };
+        auto load_chunk = [&](uint32_t tile, uint32_t c, uint32_t (&xw)[TASKS][8]) {
             const T5Tile T = t5_tile(tile, a.L);
             const uint32_t *src = a.src + (size_t)T.t * 65536;
-            for (uint32_t c = 0; c < 4; ++c, ++g) {
-                const uint32_t s = g & 1u;
-                // this chunk's words, loaded before the buffer is free
-                constexpr uint32_t TASKS = DROWS * 8 / NCONV;    // 16-byte units per thread
-                uint32_t xw[TASKS][8];
 #pragma unroll
-                for (uint32_t q = 0; q < TASKS; ++q) {
-                    const uint32_t task = ct + q * NCONV;
-                    if (ROWP) {
-                        // unit u of data row r: words k = 8u .. 8u + 7 of the chunk
-                        const uint32_t r = task >> 3, u = task & 7u;
-                        const uint4 *p = reinterpret_cast<const uint4 *>(src + (size_t)(T.mb * kT5M + r) * 256 +
-                                                                         c * kT5KC + 8 * u);
-                        const uint4 v0 = __ldg(p), v1 = __ldg(p + 1);
-                        xw[q][0] = v0.x; xw[q][1] = v0.y; xw[q][2] = v0.z; xw[q][3] = v0.w;
-                        xw[q][4] = v1.x; xw[q][5] = v1.y; xw[q][6] = v1.z; xw[q][7] = v1.w;
-                    } else {
-                        // column n (lanes along n), sum rows k = 8u .. 8u + 7 of the chunk
-                        const uint32_t n = task & 63u, u = task >> 6;
-                        const uint32_t *p = src + (size_t)(c * kT5KC + 8 * u) * 256 + T.nb * kT5N + n;
+            for (uint32_t q = 0; q < TASKS; ++q) {
+                uint32_t m, u;
+                task_mu(q, m, u);
+                if (ROWP) {
+                    const uint4 *p = reinterpret_cast<const uint4 *>(src + (size_t)(T.mb * kT5M + m) * 256 +
+                                                                     c * kT5KC + 8 * u);
+                    const uint4 v0 = __ldg(p), v1 = __ldg(p + 1);
+                    xw[q][0] = v0.x; xw[q][1] = v0.y; xw[q][2] = v0.z; xw[q][3] = v0.w;
+                    xw[q][4] = v1.x; xw[q][5] = v1.y; xw[q][6] = v1.z; xw[q][7] = v1.w;
+                } else {
+                    const uint32_t *p = src + (size_t)(c * kT5KC + 8 * u) * 256 + T.mb * kT5M + m;
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) xw[q][e] = __ldg(p + (size_t)e * 256);
-                    }
+                    for (int e = 0; e < 8; ++e) xw[q][e] = __ldg(p + (size_t)e * 256);
                 }
-                if (g >= 2 && !t5_wait(&empty[s], ((g - 2) >> 1) & 1u, abort_flag)) { ok = false; break; }
-                unsigned char *dst = data_op(s);
-#pragma unroll
-                for (uint32_t q = 0; q < TASKS; ++q) {
-                    const uint32_t task = ct + q * NCONV;
-                    const uint32_t row = ROWP ? task >> 3 : task & 63u, u = ROWP ? task & 7u : task >> 6;
-                    uint4 dg[4];
-                    t5_digits(xw[q], dg);
-                    const uint32_t off = t5_swz(row, u);
-#pragma unroll
-                    for (uint32_t d = 0; d < kT5Dig; ++d)
-                        *reinterpret_cast<uint4 *>(dst + d * (DROWS * 128) + off) = dg[d];
-                }
-                // generic-proxy stores, read next by the tensor cores
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                t5_arrive(&full_d[s]);
             }
-            if (!ok) break;
-            // ---- epilogue: the seven diagonals of this thread's row
-            if (!t5_wait(acc_full, ti & 1u, abort_flag)) { ok = false; break; }
+        };
+        auto store_chunk = [&](uint32_t s, const uint32_t (&xw)[TASKS][8]) {
+            unsigned char *dst = stage_a(s);
+#pragma unroll
+            for (uint32_t q = 0; q < TASKS; ++q) {
+                uint32_t m, u;
+                task_mu(q, m, u);
+                uint4 dg[4];
+                t5_digits(xw[q], dg);
+                const uint32_t off = t5_swz(m, u);
+#pragma unroll
+                for (uint32_t d = 0; d < kT5Dig; ++d) *reinterpret_cast<uint4 *>(dst + d * (kT5M * 128) + off) = dg[d];
+            }
+            // generic-proxy stores, read next by the tensor cores
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            t5_arrive(&full_d[s]);
+        };
+        // epilogue of tile `tile` (its ti-th): the seven diagonals of this
+        // thread's row m (tensor-memory lane) over 32 of the 64 columns n
+        auto epilogue = [&](uint32_t tile, uint32_t ti) -> bool {
+            if (!t5_wait(acc_full, ti & 1u, abort_flag)) return false;
             t5_fence_after();
-            const uint32_t row = 32 * (warp & 3u) + lane;        // tensor-memory lane = output row
-            const uint32_t colh = (warp >> 2) * 32;              // this warp's 32 of the 64 columns
+            const T5Tile T = t5_tile(tile, a.L);
+            const uint32_t m = 32 * (warp & 3u) + lane;
+            const uint32_t n0 = (warp >> 2) * 32;
             Lc<uint32_t> kk;
             kk.load(a.lc + T.l);
             uint32_t w7[kT5Diag];
@@ -360,35 +361,81 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
             for (uint32_t d = 0; d < kT5Diag; ++d) w7[d] = __ldg(a.wdiag + 8 * T.l + d);
             // a multiple of q above 7 * 2^24 * q > |sum|: makes the sum positive
             const uint64_t off = (uint64_t)kk.q * ((1ull << 57) / kk.q + 1);
-            const uint32_t orow = T.mb * kT5M + row;
-            uint32_t *out = a.dst + (size_t)T.t * 65536 + (size_t)orow * 256 + T.nb * kT5N + colh;
-            const Tw<uint32_t> *twr =
-                a.tw ? a.tw + (size_t)T.l * 65536 + (size_t)orow * 256 + T.nb * kT5N + colh : nullptr;
+            // output word (row, column) of the transform: column pass
+            // out[u][n2] = out[64 nb + n][128 mb + m]; row pass
+            // out[r][v] = out[128 mb + m][64 nb + n]
+            uint32_t *outt = a.dst + (size_t)T.t * 65536;
+            const Tw<uint32_t> *twt = a.tw ? a.tw + (size_t)T.l * 65536 : nullptr;
 #pragma unroll 1
-            for (uint32_t grp = 0; grp < 2; ++grp) {
-                uint32_t f[kT5Diag][16];
+            for (uint32_t grp = 0; grp < 4; ++grp) {
+                uint32_t f[kT5Diag][8];
 #pragma unroll
-                for (uint32_t d = 0; d < kT5Diag; ++d)
-                    t5_ld16(tmem + ((32u * (warp & 3u)) << 16) + d * kT5N + colh + 16 * grp, f[d]);
+                for (uint32_t d = 0; d < kT5Diag; ++d) {
+                    const uint32_t taddr = tmem + ((32u * (warp & 3u)) << 16) + d * kT5N + n0 + 8 * grp;
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                                 : "=r"(f[d][0]), "=r"(f[d][1]), "=r"(f[d][2]), "=r"(f[d][3]), "=r"(f[d][4]),
+                                   "=r"(f[d][5]), "=r"(f[d][6]), "=r"(f[d][7])
+                                 : "r"(taddr));
+                }
+                Tw<uint32_t> tw8[8];
+                if (twt) {
+#pragma unroll
+                    for (int cc = 0; cc < 8; ++cc) {
+                        const uint32_t n = n0 + 8 * grp + cc;
+                        const size_t at = ROWP ? (size_t)(T.mb * kT5M + m) * 256 + T.nb * kT5N + n
+                                               : (size_t)(T.nb * kT5N + n) * 256 + T.mb * kT5M + m;
+                        tw8[cc] = ldtw(twt + at);
+                    }
+                }
                 t5_wait_ld();
-                uint32_t v[16];
+                uint32_t v[8];
 #pragma unroll
-                for (int cc = 0; cc < 16; ++cc) {
+                for (int cc = 0; cc < 8; ++cc) {
                     int64_t comb = 0;
 #pragma unroll
                     for (uint32_t d = 0; d < kT5Diag; ++d)
                         comb += (int64_t)__float2int_rn(__uint_as_float(f[d][cc])) * (int64_t)w7[d];
                     uint32_t r = csub<uint32_t>(barrett_lazy((uint64_t)comb + off, kk), kk.q);
-                    if (twr) r = mul_full<RED_SHOUP>(r, ldtw(twr + 16 * grp + cc), kk);
+                    if (twt) r = mul_full<RED_SHOUP>(r, tw8[cc], kk);
                     v[cc] = r;
                 }
-                uint4 *o = reinterpret_cast<uint4 *>(out + 16 * grp);
+                if (ROWP) {
+                    uint4 *o = reinterpret_cast<uint4 *>(outt + (size_t)(T.mb * kT5M + m) * 256 + T.nb * kT5N + n0 +
+                                                         8 * grp);
+                    o[0] = make_uint4(v[0], v[1], v[2], v[3]);
+                    o[1] = make_uint4(v[4], v[5], v[6], v[7]);
+                } else {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) o[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    for (int cc = 0; cc < 8; ++cc)
+                        outt[(size_t)(T.nb * kT5N + n0 + 8 * grp + cc) * 256 + T.mb * kT5M + m] = v[cc];
+                }
             }
             t5_fence_before();
             t5_arrive(acc_empty);
+            return true;
+        };
+
+        // chunks in order g = 4 (tile index) + c; the words of chunk g + 1
+        // are loaded while chunk g is converted; the epilogue of a tile runs
+        // after the next tile's first chunk is in its stage buffer
+        uint32_t xa[TASKS][8], xb[TASKS][8];
+        const uint32_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+        const uint32_t nchunks = 4 * my_tiles;
+        auto tile_of = [&](uint32_t g) { return blockIdx.x + (g >> 2) * gridDim.x; };
+        if (nchunks) load_chunk(tile_of(0), 0, xa);
+        auto step = [&](uint32_t g, uint32_t (&cur)[TASKS][8], uint32_t (&nxt)[TASKS][8]) -> bool {
+            if (g + 1 < nchunks) load_chunk(tile_of(g + 1), (g + 1) & 3u, nxt);
+            const uint32_t s = g & 1u;
+            if (g >= 2 && !t5_wait(&empty[s], ((g - 2) >> 1) & 1u, abort_flag)) return false;
+            store_chunk(s, cur);
+            if ((g & 3u) == 0 && g > 0 && !epilogue(tile_of(g - 1), (g >> 2) - 1)) return false;
+            return true;
+        };
+        for (uint32_t g = 0; g < nchunks && ok; g += 2) {
+            ok = step(g, xa, xb);
+            if (ok && g + 1 < nchunks) ok = step(g + 1, xb, xa);
         }
+        if (ok && nchunks) ok = epilogue(tile_of(nchunks - 1), my_tiles - 1);
         if (!ok) atomicExch(const_cast<uint32_t *>(abort_flag), 1u);
     }
     // ---------------------------------------------------------- teardown

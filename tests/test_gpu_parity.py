@@ -231,14 +231,14 @@ def test_workload_n2p16_L32_u32(nt, orc):
 
 # ----------------------------------------- N = 2^16: two-pass and cluster
 @pytest.mark.parametrize("red", ["shoup", "barrett", "montgomery"])
-@pytest.mark.parametrize("form", ["stream", "two_launch", "cluster"])
+@pytest.mark.parametrize("form", ["two_launch", "streamed", "cluster"])
 def test_n2p16_u32_two_pass_and_cluster(nt, orc, red, form):
-    """The fused forms of N = 2^16 with 4-byte words (the two-pass split in
-    one streamed launch or as two launches; one pass on clusters of eight
+    """The fused forms of N = 2^16 with 4-byte words (the two-pass split as
+    two launches or in one streamed launch; one pass on clusters of eight
     CTAs), both orders, batch sizes that give clusters one transform, none,
     or uneven ranges, and limb changes inside a cluster's range."""
     N = 1 << 16
-    extra = {"stream": 0, "two_launch": nt.NTT_TWO_LAUNCH, "cluster": nt.NTT_CLUSTER}[form]
+    extra = {"two_launch": 0, "streamed": nt.NTT_STREAMED, "cluster": nt.NTT_CLUSTER}[form]
     qs = primes_for(orc, N, False, 10)
     for i, (batch, L, bitrev) in enumerate([(1, 1, True), (3, 5, False), (10, 10, True), (1, 7, True)]):
         roundtrip_check(nt, orc, N, qs[:L], batch, "fused", red=red, bitrev=bitrev, seed=1600 + i,
@@ -259,7 +259,7 @@ def test_stream_form_item_sizes_and_lags(nt, orc, monkeypatch, tiles, lag):
         qs = primes_for(orc, N, w64, L)
         psis = [orc.psi(q, N) for q in qs]
         host = ntt_synth.rns_batch(1700 + n, qs, N, 2 * pairs)
-        p = Plan(nt, N, qs, "fused", w64=w64, bitrev=True)
+        p = Plan(nt, N, qs, "fused", w64=w64, bitrev=True, extra_flags=nt.NTT_STREAMED)
         try:
             d = to_dev(host, w64)
             p.fwd(d, 2 * pairs)
@@ -280,14 +280,15 @@ def test_stream_form_item_sizes_and_lags(nt, orc, monkeypatch, tiles, lag):
 
 
 def test_stream_and_two_launch_forms_agree_on_the_workload_shape(nt, orc):
-    """N = 2^16, 32 limbs, 16 polynomials: the streamed form and the two
-    launches give the same words, forward and inverse, over five calls in a
-    row (the plan's counter sets are reused and reset by every call)."""
+    """N = 2^16, 32 limbs, 16 polynomials: the streamed form (NTT_STREAMED)
+    and the two launches give the same words, forward and inverse, over
+    five calls in a row (the plan's counter sets are reused and reset by
+    every call)."""
     N = 1 << 16
     qs = orc.find_primes(30, 17, 32)
     host = ntt_synth.rns_batch(1705, qs, N, 16)
-    ps = Plan(nt, N, qs, "fused", bitrev=True)
-    p2 = Plan(nt, N, qs, "fused", bitrev=True, extra_flags=nt.NTT_TWO_LAUNCH)
+    ps = Plan(nt, N, qs, "fused", bitrev=True, extra_flags=nt.NTT_STREAMED)
+    p2 = Plan(nt, N, qs, "fused", bitrev=True)
     try:
         a, b = to_dev(host, False), to_dev(host, False)
         for _ in range(5):
@@ -452,13 +453,13 @@ def test_pointwise_inverse_fused_and_fallback(nt, orc, red):
     in bit-reversed order take the product inside the first inverse pass
     (u32 N = 2^15, 2^16, 2^17; u64 N = 2^16); N = 2^12, natural order and
     NTT_CHECK plans run the two steps.  c aliasing a, aliasing b, or apart."""
-    # (log N, u64, bit-reversed, flags, launches: 1 fused (both passes in
-    # one launch), 2 with NTT_TWO_LAUNCH; else the product (with NTT_CHECK:
-    # + a range check of each operand), then the inverse (+ its range check,
-    # + the order permutation, + its one launch))
-    cases = [(15, False, True, 0, 1), (16, False, True, 0, 1), (17, False, True, 0, 1), (16, True, True, 0, 1),
-             (16, False, True, nt.NTT_TWO_LAUNCH, 2), (16, True, True, nt.NTT_TWO_LAUNCH, 2),
-             (12, False, True, 0, 2), (16, False, False, 0, 3), (16, False, True, nt.NTT_CHECK, 5)]
+    # (log N, u64, bit-reversed, flags, launches: 2 fused (the two passes),
+    # 1 with NTT_STREAMED; else the product (with NTT_CHECK: + a range check
+    # of each operand), then the inverse (+ its range check, + the order
+    # permutation, + its two launches))
+    cases = [(15, False, True, 0, 2), (16, False, True, 0, 2), (17, False, True, 0, 2), (16, True, True, 0, 2),
+             (16, False, True, nt.NTT_STREAMED, 1), (16, True, True, nt.NTT_STREAMED, 1),
+             (12, False, True, 0, 2), (16, False, False, 0, 4), (16, False, True, nt.NTT_CHECK, 6)]
     for i, (n, w64, bitrev, extra, launches) in enumerate(cases):
         N, batch = 1 << n, 3
         qs = primes_for(orc, N, w64, 2)
@@ -564,8 +565,8 @@ def test_limb_prefix_entry_points(nt, orc, variant):
             p.close()
 
 
-@pytest.mark.parametrize("cluster", [False, True])
-def test_bounded_wait_reports_timeout_and_context_survives(nt, orc, cluster):
+@pytest.mark.parametrize("form", ["two_launch", "streamed", "cluster"])
+def test_bounded_wait_reports_timeout_and_context_survives(nt, orc, form):
     """Failure path on the GPU without a fault: with the test hook, one CTA's
     first tile waits for bytes that never arrive; its wait gives up after
     about a second, the call reports NTT_ERR_TIMEOUT, and the next plan on
@@ -573,7 +574,7 @@ def test_bounded_wait_reports_timeout_and_context_survives(nt, orc, cluster):
     N = 1 << 16
     qs = primes_for(orc, N, False, 2)
     host = ntt_synth.rns_batch(61, qs, N, 2)
-    extra = nt.NTT_CLUSTER if cluster else 0
+    extra = {"two_launch": 0, "streamed": nt.NTT_STREAMED, "cluster": nt.NTT_CLUSTER}[form]
     p = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, nt.NTT_ORDER_BITREV | nt.NTT_TEST_STALL | extra)
     try:
         d = to_dev(host, False)
