@@ -354,6 +354,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ragged and wide-word side measurements")
+    ap.add_argument("--extra", default=None,
+                    choices=["ragged", "wide_word_u64", "tc_fourstep", "cluster_form"],
+                    help="run only this side measurement and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -380,6 +383,11 @@ def main():
     if world > 1:
         dist.barrier()
     nt.lib()
+    if args.extra:
+        fn = {"ragged": ragged_vs_plain, "wide_word_u64": wide_word, "tc_fourstep": tc_fourstep,
+              "cluster_form": cluster_form}[args.extra]
+        print(json.dumps({args.extra: fn(nt, torch, dev)}), flush=True)
+        return 0
     from paper_2405_11353_gb300 import build as nb
     digest = nb.kernel_digest(nb.FORWARD_U32_SOURCES)
 
