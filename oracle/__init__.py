@@ -77,6 +77,8 @@ def lib():
                 "orc_pointwise_batch": (None, [u64, ctypes.c_uint32,
                                                ctypes.c_uint32, _u64p, _u64p,
                                                _u64p, _u64p]),
+                "orc_base_conv": (None, [ctypes.c_uint32, _u64p, ctypes.c_uint32,
+                                         _u64p, u64, ctypes.c_uint32, _u64p, _u64p]),
                 "orc_num_threads": (ctypes.c_int, []),
             }
             for name, (res, args) in sig.items():
@@ -227,3 +229,16 @@ def pointwise_batch(a, b, qs):
     c = np.zeros_like(a)
     lib().orc_pointwise_batch(N, L, B, _p(q), _p(a), _p(b), _p(c))
     return c
+
+
+def base_conv(data, qs, ps):
+    """Fast RNS base conversion of [batch][L][N] residues modulo qs to
+    [batch][K][N] residues modulo ps (see orc_base_conv)."""
+    d = _u64(data)
+    B, L, N = d.shape
+    q = _u64(qs)
+    p = _u64(ps)
+    assert q.size == L
+    out = np.zeros((B, p.size, N), dtype=np.uint64)
+    lib().orc_base_conv(L, _p(q), p.size, _p(p), N, B, _p(d), _p(out))
+    return out

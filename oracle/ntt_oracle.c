@@ -21,6 +21,9 @@
  *     radix-2 DIT that the O(N log N) path below follows, with the index
  *     typos read as stated in the comments of orc_ntt_fwd_fast.
  *   - Sec. I: the NTT reduces a polynomial product to a pointwise product.
+ *   - orc_base_conv: the fast RNS base conversion that follows the inverse
+ *     transform in the homomorphic schemes Sec. I motivates; the paper does
+ *     not define it, the definition is stated above the function.
  *
  * Conventions (readings of points the paper leaves open):
  *   - generator g of Z_q^* = the smallest integer >= 2 of multiplicative
@@ -380,6 +383,59 @@ void orc_pointwise_batch(uint64_t N, uint32_t L, uint32_t batch,
         orc_pointwise(q[l], N, a + (size_t)t * N, b + (size_t)t * N,
                       c + (size_t)t * N);
     }
+}
+
+/* ------------------------------------------------- RNS base conversion */
+/*
+ * Fast base conversion of RNS residues (the basis-extension step that
+ * follows the inverse transform in RNS homomorphic schemes, the setting
+ * Sec. I motivates the NTT with; the paper itself defines no conversion).
+ * For a coefficient with residues x_i = x mod q_i (i < L), Q = prod_i q_i
+ * and qhat_i = Q / q_i:
+ *     y_i = x_i * qhat_i^{-1} mod q_i
+ *     z_j = ( sum_i y_i * qhat_i ) mod p_j            (j < K)
+ * with the sum taken exactly; written out here as
+ *     z_j = sum_i y_i * (qhat_i mod p_j)   mod p_j.
+ * The exact sum v = sum_i y_i qhat_i satisfies v = x (mod Q) and
+ * 0 <= v < L Q, so z_j = (x + alpha Q) mod p_j for one integer
+ * 0 <= alpha < L (the conversion is approximate by that multiple of Q).
+ * x: [batch][L][N], z: [batch][K][N]; the q_i pairwise coprime.
+ */
+
+/* qhat_i mod m = prod_{k != i} q_k mod m */
+static uint64_t qhat_mod(uint32_t L, const uint64_t *q, uint32_t i, uint64_t m)
+{
+    uint64_t r = 1 % m;
+    for (uint32_t k = 0; k < L; ++k)
+        if (k != i) r = orc_mulmod(r, q[k] % m, m);
+    return r;
+}
+
+void orc_base_conv(uint32_t L, const uint64_t *q, uint32_t K, const uint64_t *p,
+                   uint64_t N, uint32_t batch, const uint64_t *x, uint64_t *z)
+{
+    uint64_t *qinv = (uint64_t *)malloc(sizeof(uint64_t) * L);
+    uint64_t *qm = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)L * K);
+    for (uint32_t i = 0; i < L; ++i) {
+        qinv[i] = orc_invmod(qhat_mod(L, q, i, q[i]), q[i]);
+        for (uint32_t j = 0; j < K; ++j) qm[(size_t)i * K + j] = qhat_mod(L, q, i, p[j]);
+    }
+    long total = (long)batch * (long)N;
+#pragma omp parallel for schedule(static)
+    for (long t = 0; t < total; ++t) {
+        const uint64_t b = (uint64_t)t / N, n = (uint64_t)t % N;
+        for (uint32_t j = 0; j < K; ++j) {
+            uint64_t acc = 0;
+            for (uint32_t i = 0; i < L; ++i) {
+                const uint64_t xi = x[(b * L + i) * N + n];
+                const uint64_t yi = orc_mulmod(xi, qinv[i], q[i]);
+                acc = orc_addmod(acc, orc_mulmod(yi % p[j], qm[(size_t)i * K + j], p[j]), p[j]);
+            }
+            z[(b * K + j) * N + n] = acc;
+        }
+    }
+    free(qinv);
+    free(qm);
 }
 
 /* Threads an OpenMP region would use (1 without OpenMP). */

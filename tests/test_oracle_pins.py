@@ -320,3 +320,60 @@ def test_synth_residues_in_range():
     # published generator seeded with 0)
     first = [int(v) for v in ntt_synth.splitmix64(0, 3)]
     assert first == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+# ------------------------------------------------------ RNS base conversion
+def test_base_conv_worked_example(orc):
+    g = _read_golden("bconv_q5_7_p11_13.txt")
+    qs, ps = g.pop("q"), g.pop("p")
+    for key, (x0, x1, y0, y1, v, z0, z1) in g.items():
+        x = np.array([[[x0], [x1]]], dtype=np.uint64)
+        assert orc.base_conv(x, qs, ps)[0, :, 0].tolist() == [z0, z1], key
+
+
+def _crt_check(orc, qs, ps, X):
+    """z_j = (X + alpha Q) mod p_j for one alpha in [0, L) (the approximate
+    fast conversion), X given by its residues."""
+    Q = 1
+    for q in qs:
+        Q *= q
+    x = np.array([[[X % q] for q in qs]], dtype=np.uint64)
+    z = [int(v) for v in orc.base_conv(x, qs, ps)[0, :, 0]]
+    # residues reassembled by the library CRT give X back
+    assert int(sympy.ntheory.modular.crt(qs, [int(v) for v in x[0, :, 0]])[0]) == X
+    # alpha from the first target prime, then checked on every one
+    alpha = (z[0] - X) * pow(Q, -1, ps[0]) % ps[0]
+    assert 0 <= alpha < len(qs)
+    assert z == [(X + alpha * Q) % p for p in ps]
+    return alpha
+
+
+def test_base_conv_is_x_plus_small_multiple_of_Q(orc):
+    rng = random.Random(11)
+    qs = orc.find_primes(30, 17, 6)
+    ps = orc.find_primes(31, 17, 5)
+    Q = 1
+    for q in qs:
+        Q *= q
+    alphas = set()
+    for X in [0, 1, 2, Q - 1, Q // 2] + [rng.randrange(Q) for _ in range(200)]:
+        alphas.add(_crt_check(orc, qs, ps, X))
+    assert len(alphas) > 1          # the multiple of Q really varies
+
+
+def test_base_conv_special_cases(orc):
+    rng = random.Random(12)
+    qs = orc.find_primes(30, 17, 4)
+    ps = orc.find_primes(31, 17, 3)
+    x = np.array([[[rng.randrange(q) for _ in range(64)] for q in qs]], dtype=np.uint64)
+    # one source prime: qhat = 1, the conversion is plain reduction
+    z1 = orc.base_conv(x[:, :1], qs[:1], ps)
+    assert np.array_equal(z1[0], np.stack([x[0, 0] % p for p in ps]))
+    # a target prime of the source basis returns that limb (Q = 0 mod q_i)
+    z = orc.base_conv(x, qs, [qs[2], ps[0], qs[0]])
+    assert np.array_equal(z[0, 0], x[0, 2]) and np.array_equal(z[0, 2], x[0, 0])
+    # zero maps to zero; batches convert independently
+    assert not orc.base_conv(np.zeros((2, 4, 8), np.uint64), qs, ps).any()
+    xb = np.concatenate([x, x[:, :, ::-1].copy()])
+    zb = orc.base_conv(xb, qs, ps)
+    assert np.array_equal(zb[1], orc.base_conv(x[:, :, ::-1].copy(), qs, ps)[0])
