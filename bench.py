@@ -319,6 +319,31 @@ def tc_fourstep(nt, torch, dev, reps=20):
     return out
 
 
+def base_conv(nt, torch, dev, reps=50):
+    """Fast RNS base conversion (ntt_bconv) of 8 polynomials, N = 2^16,
+    from 32 primes q < 2^30 to 32 other primes: L x K = 1024 multiply-adds
+    mod p per coefficient, on the integer pipes."""
+    qs = nt.ntt_find_primes(30, 17, 32)
+    ps = nt.ntt_find_primes(29, 17, 32)
+    N, B, L, K = 1 << 16, 8, 32, 32
+    host = ntt_synth.rns_batch(1006, qs, N, B, dtype=np.uint32)
+    x = torch.from_numpy(host.view(np.int32).reshape(-1).copy()).to(dev)
+    z = torch.empty(B * K * N, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    h = nt.ntt_bconv_create(qs, ps, N)
+    try:
+        ms = _time_loop(torch, stream, lambda: nt.ntt_bconv(h, z, x, B, sh), reps)
+    finally:
+        nt.ntt_bconv_destroy(h)
+    coeffs = B * N
+    byts = coeffs * (L + K) * 4
+    return {"workload": "N=2^16, 8 polys, 32 primes q<2^30 -> 32 primes p<2^29",
+            "ms_per_call": ms, "coefficients_per_s": coeffs / (ms / 1e3),
+            "algorithmic_gbs": byts / (ms / 1e3) / 1e9,
+            "mod_mults_per_s": coeffs * L * K / (ms / 1e3)}
+
+
 def cluster_form(nt, torch, dev, reps=50):
     """N = 2^16, 32 primes q < 2^30, u32, 16 polys: forward and inverse as
     the two-pass split in two launches (default), in one streamed launch
@@ -355,7 +380,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ragged and wide-word side measurements")
     ap.add_argument("--extra", default=None,
-                    choices=["ragged", "wide_word_u64", "tc_fourstep", "cluster_form"],
+                    choices=["ragged", "wide_word_u64", "tc_fourstep", "cluster_form", "base_conv"],
                     help="run only this side measurement and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -385,7 +410,7 @@ def main():
     nt.lib()
     if args.extra:
         fn = {"ragged": ragged_vs_plain, "wide_word_u64": wide_word, "tc_fourstep": tc_fourstep,
-              "cluster_form": cluster_form}[args.extra]
+              "cluster_form": cluster_form, "base_conv": base_conv}[args.extra]
         print(json.dumps({args.extra: fn(nt, torch, dev)}), flush=True)
         return 0
     from paper_2405_11353_gb300 import build as nb
@@ -492,7 +517,8 @@ def main():
     extras = {}
     if not args.no_extras:
         for name, fn in (("ragged", ragged_vs_plain), ("wide_word_u64", wide_word),
-                         ("tc_fourstep", tc_fourstep), ("cluster_form", cluster_form)):
+                         ("tc_fourstep", tc_fourstep), ("cluster_form", cluster_form),
+                         ("base_conv", base_conv)):
             try:
                 extras[name] = fn(nt, torch, dev)
             except Exception as exc:     # a side measurement never hides the main line

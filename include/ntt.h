@@ -276,6 +276,35 @@ ntt_status ntt_default_psi(uint64_t q, uint32_t N, uint64_t *psi_out);
 ntt_status ntt_find_primes(uint32_t bits, uint32_t m, uint32_t count,
                            uint64_t *out);
 
+/* ------------------------------------------------ RNS base conversion
+ * Fast base conversion of coefficient residues (the basis-extension step
+ * that follows the inverse transform in RNS homomorphic schemes, the
+ * setting Sec. I motivates the NTT with; the paper defines no conversion).
+ * For every coefficient with residues x_i = x mod q_i (i < L), Q = prod q_i,
+ * qhat_i = Q / q_i:
+ *     y_i = x_i qhat_i^-1 mod q_i,
+ *     z_j = (sum_i y_i qhat_i) mod p_j                      (j < K),
+ * so z_j = (x + alpha Q) mod p_j for one integer 0 <= alpha < L (the fast,
+ * approximate conversion; no correction of alpha is made).  4-byte words:
+ * every q_i and p_j prime, 3 <= prime < 2^30; the q_i distinct;
+ * 1 <= L, K <= 64; N >= 1 coefficients per polynomial (any N). */
+typedef struct ntt_bconv_s *ntt_bconv_t;
+
+/* Build the conversion tables (host arithmetic, one device upload).
+ * NTT_ERR_INVALID_ARG (null, L or K out of range, N = 0, repeated q_i),
+ * NTT_ERR_Q_WIDTH, NTT_ERR_Q_NOT_PRIME, NTT_ERR_OOM. */
+ntt_status ntt_bconv_create(ntt_bconv_t *out, const uint64_t *q, uint32_t L,
+                            const uint64_t *p, uint32_t K, uint32_t N);
+
+/* d_in: [batch][L][N] uint32_t residues (x_i < q_i), d_out: [batch][K][N]
+ * uint32_t, fully reduced; device pointers, 4-byte aligned, not
+ * overlapping.  Enqueued on `stream`, one launch. */
+ntt_status ntt_bconv(ntt_bconv_t plan, void *d_out, const void *d_in,
+                     uint32_t batch, ntt_stream_t stream);
+
+/* Free the tables (after synchronising the device). */
+void ntt_bconv_destroy(ntt_bconv_t plan);
+
 /* ------------------------------------------------------- ragged batches
  * One persistent kernel, captured in a CUDA graph, runs every job of a
  * heterogeneous set (different N, L, word width, direction). */

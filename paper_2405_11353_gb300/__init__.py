@@ -57,6 +57,7 @@ EXPORTS = [
     "ntt_status_string", "ntt_validate", "ntt_default_psi", "ntt_find_primes",
     "ntt_ragged_create", "ntt_ragged_launch", "ntt_ragged_status", "ntt_ragged_destroy",
     "ntt_forward_noalloc", "ntt_forward_prefix", "ntt_inverse_prefix", "ntt_pointwise_inverse",
+    "ntt_bconv_create", "ntt_bconv", "ntt_bconv_destroy",
 ]
 
 
@@ -109,6 +110,9 @@ def lib():
             "ntt_forward_noalloc": (st, [vp, vp, u32, vp]),
             "ntt_forward_prefix": (st, [vp, vp, u32, u32, vp]),
             "ntt_inverse_prefix": (st, [vp, vp, u32, u32, vp]),
+            "ntt_bconv_create": (st, [ctypes.POINTER(vp), u64p, u32, u64p, u32, u32]),
+            "ntt_bconv": (st, [vp, vp, vp, u32, vp]),
+            "ntt_bconv_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -280,3 +284,20 @@ def ntt_ragged_status(r, stream=None):
 
 def ntt_ragged_destroy(r):
     lib().ntt_ragged_destroy(r)
+
+
+def ntt_bconv_create(q, p, N):
+    """Fast RNS base conversion plan from primes q (L) to primes p (K) for
+    polynomials of N coefficients; returns a handle (int)."""
+    h = ctypes.c_void_p()
+    _check(lib().ntt_bconv_create(ctypes.byref(h), _u64arr(q), len(q), _u64arr(p), len(p), N),
+           "ntt_bconv_create")
+    return h.value
+
+
+def ntt_bconv(plan, out, inp, batch, stream=None):
+    _check(lib().ntt_bconv(plan, _ptr(out), _ptr(inp), batch, _stream(stream)), "ntt_bconv")
+
+
+def ntt_bconv_destroy(plan):
+    lib().ntt_bconv_destroy(plan)
