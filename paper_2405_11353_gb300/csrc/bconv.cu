@@ -7,9 +7,11 @@
 //     y_i = x_i qhat_i^-1 mod q_i,   z_j = sum_i y_i (qhat_i mod p_j) mod p_j,
 // qhat_i = prod_{k != i} q_k.  z_j = (x + alpha Q) mod p_j for one integer
 // 0 <= alpha < L.  Per coefficient it is an L-by-K matrix-vector product
-// mod p_j: a thread owns one coefficient, keeps its L values y_i in
-// registers (L up to the template bucket LB) and runs the K rows, four at a
-// time, against the matrix (qhat_i mod p_j) broadcast from shared memory.
+// mod p_j: a thread owns one coefficient at a time (persistent grid, the
+// next coefficient's words loaded while this one is converted), keeps its L
+// values y_i in registers (L up to the template bucket LB) and runs the K
+// rows, four at a time, against the matrix (qhat_i mod p_j) broadcast from
+// shared memory.
 // Products y_i m_ij < 2^60 accumulate in 64 bits, reduced (Barrett, 2^64 /
 // p_j) every 12 terms so the sum never wraps.  Words are 4 bytes (primes
 // below 2^30); reads and writes coalesce along the coefficients.
@@ -56,60 +58,72 @@ __device__ __forceinline__ uint32_t bc_reduce64(uint64_t z, uint32_t p, uint64_t
 }
 
 template <uint32_t LB>
-__global__ void __launch_bounds__(kBcThreads) k_bconv(const uint32_t *__restrict__ x, uint32_t *__restrict__ z,
-                                                       BcTab t, uint32_t L, uint32_t K, uint32_t N,
-                                                       uint64_t total) {
-    // the matrix rows (K x LB words) and the per-prime constants in shared memory
+__global__ void __launch_bounds__(kBcThreads, 2) k_bconv(const uint32_t *__restrict__ x, uint32_t *__restrict__ z,
+                                                          BcTab t, uint32_t L, uint32_t K, uint32_t N,
+                                                          uint64_t total) {
+    // the matrix rows (K x LB words) in shared memory, read as broadcasts
     extern __shared__ __align__(16) uint32_t bc_smem[];
     uint32_t *sm = bc_smem;
     for (uint32_t e = threadIdx.x; e < K * LB; e += blockDim.x) sm[e] = t.m[e];
     __syncthreads();
-    const uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= total) return;
-    const uint64_t b = c / N, n = c % N;
-    const uint32_t *xc = x + b * L * N + n;
-    uint32_t y[LB];
+    // persistent: a thread takes coefficients c, c + stride, ...; the words
+    // of the next one are loaded while the current one is converted
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t xn[LB];
+    auto load = [&](uint64_t cc) {
+        const uint64_t b = cc / N, n = cc % N;
+        const uint32_t *xc = x + b * L * N + n;
 #pragma unroll
-    for (uint32_t i = 0; i < LB; ++i) {
-        y[i] = 0;
-        if (i < L) {
-            const uint32_t xi = __ldg(xc + (size_t)i * N);
-            const uint32_t w = __ldg(t.qinv + 2 * i), wc = __ldg(t.qinv + 2 * i + 1), q = __ldg(t.q + i);
-            uint32_t r = xi * w - __umulhi(xi, wc) * q;      // Shoup, in [0, 2q)
-            y[i] = r >= q ? r - q : r;
+        for (uint32_t i = 0; i < LB; ++i) xn[i] = i < L ? __ldg(xc + (size_t)i * N) : 0u;
+    };
+    if (c < total) load(c);
+    for (; c < total; c += stride) {
+        uint32_t y[LB];
+#pragma unroll
+        for (uint32_t i = 0; i < LB; ++i) {
+            y[i] = 0;
+            if (i < L) {
+                const uint32_t xi = xn[i];
+                const uint32_t w = __ldg(t.qinv + 2 * i), wc = __ldg(t.qinv + 2 * i + 1), q = __ldg(t.q + i);
+                uint32_t r = xi * w - __umulhi(xi, wc) * q;      // Shoup, in [0, 2q)
+                y[i] = r >= q ? r - q : r;
+            }
         }
-    }
-    uint32_t *zc = z + b * K * N + n;
-    for (uint32_t j0 = 0; j0 < K; j0 += 4) {
-        uint64_t acc[4] = {0, 0, 0, 0};
-        uint32_t pj[4];
-        uint64_t muj[4];
-#pragma unroll
-        for (uint32_t r = 0; r < 4; ++r) {
-            const uint32_t j = j0 + r < K ? j0 + r : K - 1;
-            pj[r] = __ldg(t.p + j);
-            muj[r] = __ldg(t.mu + j);
-        }
-#pragma unroll
-        for (uint32_t i0 = 0; i0 < LB; i0 += 4) {
-            if (i0 >= L) break;
+        if (c + stride < total) load(c + stride);
+        const uint64_t b = c / N, n = c % N;
+        uint32_t *zc = z + b * K * N + n;
+        for (uint32_t j0 = 0; j0 < K; j0 += 4) {
+            uint64_t acc[4] = {0, 0, 0, 0};
+            uint32_t pj[4];
+            uint64_t muj[4];
 #pragma unroll
             for (uint32_t r = 0; r < 4; ++r) {
                 const uint32_t j = j0 + r < K ? j0 + r : K - 1;
-                const uint4 mv = *reinterpret_cast<const uint4 *>(sm + j * LB + i0);
-                acc[r] += (uint64_t)y[i0] * mv.x + (uint64_t)y[i0 + 1] * mv.y + (uint64_t)y[i0 + 2] * mv.z +
-                          (uint64_t)y[i0 + 3] * mv.w;
+                pj[r] = __ldg(t.p + j);
+                muj[r] = __ldg(t.mu + j);
             }
-            // at most 12 products (< 2^60 each) since the last reduction,
-            // plus a remainder < 2^30: no wrap before the next one
-            if ((i0 / 4) % 3 == 2) {
 #pragma unroll
-                for (uint32_t r = 0; r < 4; ++r) acc[r] = bc_reduce64(acc[r], pj[r], muj[r]);
+            for (uint32_t i0 = 0; i0 < LB; i0 += 4) {
+                if (i0 >= L) break;
+#pragma unroll
+                for (uint32_t r = 0; r < 4; ++r) {
+                    const uint32_t j = j0 + r < K ? j0 + r : K - 1;
+                    const uint4 mv = *reinterpret_cast<const uint4 *>(sm + j * LB + i0);
+                    acc[r] += (uint64_t)y[i0] * mv.x + (uint64_t)y[i0 + 1] * mv.y + (uint64_t)y[i0 + 2] * mv.z +
+                              (uint64_t)y[i0 + 3] * mv.w;
+                }
+                // at most 12 products (< 2^60 each) since the last reduction,
+                // plus a remainder < 2^30: no wrap before the next one
+                if ((i0 / 4) % 3 == 2) {
+#pragma unroll
+                    for (uint32_t r = 0; r < 4; ++r) acc[r] = bc_reduce64(acc[r], pj[r], muj[r]);
+                }
             }
+#pragma unroll
+            for (uint32_t r = 0; r < 4; ++r)
+                if (j0 + r < K) zc[(size_t)(j0 + r) * N] = bc_reduce64(acc[r], pj[r], muj[r]);
         }
-#pragma unroll
-        for (uint32_t r = 0; r < 4; ++r)
-            if (j0 + r < K) zc[(size_t)(j0 + r) * N] = bc_reduce64(acc[r], pj[r], muj[r]);
     }
 }
 
@@ -127,8 +141,19 @@ template <uint32_t LB> cudaError_t bc_launch(const ntt_bconv_s &p, const uint32_
         cudaError_t e = cudaFuncSetAttribute(k_bconv<LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    const uint64_t blocks = (total + kBcThreads - 1) / kBcThreads;
-    if (blocks >= (1ull << 31)) return cudaErrorInvalidValue;
+    // persistent grid: the CTAs that fit at once (or fewer, for small calls)
+    static int resident = 0;
+    if (!resident) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bconv<LB>, kBcThreads,
+                                                                      (size_t)kBcMaxK * LB * sizeof(uint32_t));
+        if (e != cudaSuccess) return e;
+        resident = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    uint64_t blocks = (total + kBcThreads - 1) / kBcThreads;
+    if (blocks > (uint64_t)resident) blocks = (uint64_t)resident;
     k_bconv<LB><<<(unsigned)blocks, kBcThreads, smem, st>>>(x, z, t, p.L, p.K, p.N, total);
     return cudaGetLastError();
 }
