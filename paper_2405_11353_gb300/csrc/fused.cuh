@@ -76,14 +76,19 @@ template <class W> __host__ __device__ constexpr uint32_t cols_phys(uint32_t k, 
 // Sub-transforms per CTA (compile-time, so every shared-memory address is
 // a per-round base plus an immediate offset): single-pass tiles hold 4096
 // words (or one transform above that), column strips 16 (4-byte) or 8
-// (8-byte) columns and at least 256 threads, chunk tiles 16 chunks.
+// (8-byte) columns and at least 256 threads, chunk tiles 16 chunks, or 2
+// chunks in the per-pass forward chunk kernel (P = 0): one warp per CTA, so
+// the per-tile barriers are warp barriers and the many small CTAs of an SM
+// run independently.  The per-pass inverse chunk kernel (P = 3: its tiles
+// land through a 128-byte-swizzled copy and need 1 KiB alignment) keeps
+// 16-chunk tiles.
 // P = 0: per-plan passes; column strips have 128-byte rows (32 four-byte or
 // 16 eight-byte columns).  P = 1: the ragged kernel and the streamed
 // two-pass launch, whose CTAs always have 256 threads (4096-word column
-// tiles).
+// tiles).  P = 3: the per-pass inverse chunk kernel (as P = 0 otherwise).
 template <class W, int LOGS, int KIND, int P = 0> __host__ __device__ constexpr uint32_t tile_k() {
     return KIND == TK_SINGLE ? (LOGS >= 12 ? 1u : (4096u >> LOGS))
-         : KIND == TK_CHUNKS ? 16u
+         : KIND == TK_CHUNKS ? (P == 0 ? 2u : 16u)
          : P == 1 ? (4096u >> LOGS)
          : ((256u >> (LOGS - 4)) > (128u / sizeof(W)) ? (256u >> (LOGS - 4)) : (128u / (uint32_t)sizeof(W)));
 }
@@ -343,12 +348,18 @@ template <class W, int LOGS, int KIND, bool INV, int P = 0> __host__ __device__ 
     return KIND == TK_COLS ? (tile_k<W, LOGS, KIND, P>() << LOGS)
                            : tile_k<W, LOGS, KIND, P>() * stage_pitch<W, LOGS, KIND, INV>();
 }
+// Alignment of the stage buffers: 1 KiB where a 128-byte-swizzled tensor
+// copy lands in them (and in the item kernels, which mix tile kinds), else
+// 128 bytes (tensor copies without swizzle, bulk copies).
+template <class W, int LOGS, int KIND, bool INV, int P = 0> __host__ __device__ constexpr uint32_t stage_align() {
+    return (P != 0 || (KIND == TK_CHUNKS && INV)) ? 1024u : 128u;
+}
 template <class W, int LOGS, int KIND, bool INV, int P = 0> __host__ __device__ constexpr uint32_t buf_words() {
-    // multiple of 256 words keeps every buffer 1 KiB aligned
+    constexpr size_t A = stage_align<W, LOGS, KIND, INV, P>() / sizeof(W);
     return (uint32_t)(((tile_words<W, LOGS, KIND, INV, P>() > xchg_words<W, LOGS, KIND, P>()
                             ? tile_words<W, LOGS, KIND, INV, P>()
                             : xchg_words<W, LOGS, KIND, P>()) +
-                       255) & ~size_t(255));
+                       A - 1) & ~(A - 1));
 }
 // Two buffers per CTA: the next tile lands while the current one computes.
 template <class W, int LOGS, int KIND> __host__ __device__ constexpr uint32_t n_stages() { return 2u; }
@@ -404,7 +415,7 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     // 256-thread item kernels (short runs, three CTAs per SM, one kernel for
     // every tile kind under a 128-register cap) refill at the end of each
     // tile and load constants per tile, which keeps them free of spills.
-    constexpr bool LATE_REFILL = P == 0;
+    constexpr bool LATE_REFILL = P == 0 || P == 3;
     W *stage = reinterpret_cast<W *>(base);
     Tw<W> *tws = reinterpret_cast<Tw<W> *>(stage + (size_t)NS * BW);
     if (t_begin >= t_end) return true;
@@ -712,15 +723,22 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     return true;
 }
 
+// Tile configuration of a per-plan pass (see tile_k).
+template <bool INV, int KIND> __host__ __device__ constexpr int pass_p() {
+    return (INV && KIND == TK_CHUNKS) ? 3 : 0;
+}
+
 // Per-plan fused pass: CTA c processes tiles [c T / G, (c+1) T / G).
 template <class W, int RED, bool INV, int LOGS, int KIND>
 __global__ void __launch_bounds__(sizeof(W) == 4 ? 1024 : 512)
 k_fused(const __grid_constant__ FArgs<W> a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     constexpr uint32_t NS = n_stages<W, LOGS, KIND>();
-    constexpr uint32_t BW = buf_words<W, LOGS, KIND, INV, 0>();
-    constexpr uint32_t TWP = tw_pairs<W, LOGS, KIND, 0>();
-    unsigned char *base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+    constexpr int PP = pass_p<INV, KIND>();
+    constexpr uint32_t BW = buf_words<W, LOGS, KIND, INV, PP>();
+    constexpr uint32_t TWP = tw_pairs<W, LOGS, KIND, PP>();
+    constexpr uint32_t AL = stage_align<W, LOGS, KIND, INV, PP>();
+    unsigned char *base = smem_raw + ((AL - (smem_addr(smem_raw) & (AL - 1))) & (AL - 1));
     uint64_t *bar = reinterpret_cast<uint64_t *>(base + (size_t)NS * BW * sizeof(W) + (size_t)TWP * 2 * sizeof(W));
     if (threadIdx.x == 0) {
         for (uint32_t s = 0; s <= NS; ++s) mbar_init(&bar[s], 1);
@@ -730,12 +748,12 @@ k_fused(const __grid_constant__ FArgs<W> a) {
     PipeState ps{{0, 0}, 0};
     const uint32_t t_begin = (uint32_t)((uint64_t)blockIdx.x * a.ntiles / gridDim.x);
     const uint32_t t_end = (uint32_t)((uint64_t)(blockIdx.x + 1) * a.ntiles / gridDim.x);
-    run_tiles<W, RED, INV, LOGS, KIND, 0>(a, &a.tmap, t_begin, t_end, base, bar, ps);
+    run_tiles<W, RED, INV, LOGS, KIND, PP>(a, &a.tmap, t_begin, t_end, base, bar, ps);
 }
 
 template <class W, int LOGS, int KIND, bool INV, int P = 0> __host__ __device__ constexpr size_t fused_smem_bytes() {
     return (size_t)n_stages<W, LOGS, KIND>() * buf_words<W, LOGS, KIND, INV, P>() * sizeof(W) +
-           (size_t)tw_pairs<W, LOGS, KIND, P>() * 2 * sizeof(W) + 8 * 4 + 16 + 1024;
+           (size_t)tw_pairs<W, LOGS, KIND, P>() * 2 * sizeof(W) + 8 * 4 + 16 + stage_align<W, LOGS, KIND, INV, P>();
 }
 
 }  // namespace nttgb

@@ -108,9 +108,10 @@ cudaError_t pass_dispatch(int logS, const FArgs<W> &a, uint32_t threads, size_t 
     }
 }
 
-template <class W, int KIND> uint32_t tile_k_for(int logS) {
+template <class W, int KIND, bool INV> uint32_t tile_k_for(int logS) {
+    constexpr int PP = pass_p<INV, KIND>();
     switch (logS) {
-#define NTTGB_CASE(s) case s: return tile_k<W, s, KIND>();
+#define NTTGB_CASE(s) case s: return tile_k<W, s, KIND, PP>();
         NTTGB_CASE(4) NTTGB_CASE(5) NTTGB_CASE(6) NTTGB_CASE(7) NTTGB_CASE(8) NTTGB_CASE(9)
         NTTGB_CASE(10) NTTGB_CASE(11) NTTGB_CASE(12) NTTGB_CASE(13) NTTGB_CASE(14)
 #undef NTTGB_CASE
@@ -119,8 +120,9 @@ template <class W, int KIND> uint32_t tile_k_for(int logS) {
 }
 
 template <class W, int KIND, bool INV> size_t smem_for(int logS) {
+    constexpr int PP = pass_p<INV, KIND>();
     switch (logS) {
-#define NTTGB_CASE(s) case s: return fused_smem_bytes<W, s, KIND, INV>();
+#define NTTGB_CASE(s) case s: return fused_smem_bytes<W, s, KIND, INV, PP>();
         NTTGB_CASE(4) NTTGB_CASE(5) NTTGB_CASE(6) NTTGB_CASE(7) NTTGB_CASE(8) NTTGB_CASE(9)
         NTTGB_CASE(10) NTTGB_CASE(11) NTTGB_CASE(12) NTTGB_CASE(13) NTTGB_CASE(14)
 #undef NTTGB_CASE
@@ -188,7 +190,7 @@ cudaError_t run_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, in
                      cudaStream_t st, W *out = nullptr, const W *pw_b = nullptr) {
     FArgs<W> a;
     const uint32_t T = (1u << logS) / 16;
-    const uint32_t K = tile_k_for<W, KIND>(logS);
+    const uint32_t K = tile_k_for<W, KIND, INV>(logS);
     cudaError_t e = fill_pass<W, INV, KIND>(a, p, data, tw, ntrans, logS, final_pass, K, out, pw_b);
     if (e != cudaSuccess) return e;
     size_t smem = smem_for<W, KIND, INV>(logS);
