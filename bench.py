@@ -514,6 +514,18 @@ def main():
         else "fallback 6.8 TB/s",
     }
 
+    # the same call against the integer multiply pipe: every butterfly of the
+    # Shoup form takes three 32-bit multiplies (hi(x w'), x w, qh q); the
+    # SM issues 64 of them per clock (half its 128 integer/fp32 lanes)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    muls = 3 * n_fwd * (N // 2) * 16
+    int_peak = 64 * sm_count * mhz * 1e6
+    int_roofline = {"bound": "alu", "achieved": muls / (fwd_ms / 1e3) / 1e12, "peak": int_peak / 1e12,
+                    "unit": "T int32 multiplies/s", "frac": muls / (fwd_ms / 1e3) / int_peak,
+                    "multiplies_per_call": muls,
+                    "peak_source": "64 multiplies/clk/SM x %d SMs x %.0f MHz (sampled)" % (sm_count, mhz)}
+
     extras = {}
     if not args.no_extras:
         for name, fn in (("ragged", ragged_vs_plain), ("wide_word_u64", wide_word),
@@ -542,6 +554,7 @@ def main():
                        "parallelism": "replicas x%d" % world},
             "per_call_ms": {"forward_16polys": fwd_ms, "pointwise_inverse_8pairs": pwinv_ms},
             "roofline": roofline,
+            "int_roofline": int_roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "NTT/s",
                     "h2d_bytes_per_step": POLYS * L * N * WORD,

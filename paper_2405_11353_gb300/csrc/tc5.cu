@@ -12,7 +12,10 @@
 //     are the bytes of x + 0x80808080 minus 128, those of a matrix entry are
 //     precomputed.  Every digit is an fp16 integer (exact).
 //   * The 16 digit products are accumulated by diagonal s = i + j into seven
-//     fp32 accumulators in tensor memory.  A diagonal sums at most 4 x 256
+//     fp32 accumulators in tensor memory: one M = 128, N = 256 product per
+//     data digit i against the four matrix digit planes at once (they are
+//     contiguous rows of one operand) lands A_i B_j in diagonal i + j; the
+//     accumulators are zeroed once and again by each epilogue after reading.  A diagonal sums at most 4 x 256
 //     products of magnitude <= 128 * 128 = 2^14, so every partial sum is an
 //     integer of magnitude <= 2^24: exactly representable, so fp32
 //     accumulation loses nothing, in any order.
@@ -32,12 +35,13 @@
 // Each pass reads src and writes dst (out of place: a tile's output rows are
 // other tiles' input rows).
 //
-// Roles in a CTA (one per SM: 192 KiB of shared memory, 448 of the 512
+// Roles in a CTA (one per SM: 224 KiB of shared memory, 448 of the 512
 // tensor-memory columns): warps 0-7 convert data digits into the stage
 // buffers and run the epilogue (warp w reads tensor-memory lanes
 // 32 (w % 4) ..); warp 8 lane 0 issues the TMA copies of the matrix digits;
-// warp 9 lane 0 issues the MMAs.  Two stage buffers, mbarriers between the
-// roles, every wait bounded (about a second of SM clock) -- on expiry the
+// warp 9 lane 0 issues the MMAs.  Two data stage buffers (64 KiB) and three
+// matrix stage buffers (32 KiB; the copies run further ahead), mbarriers
+// between the roles, every wait bounded (about a second of SM clock) -- on expiry the
 // call records NTT_ERR_TIMEOUT, all roles leave their loops, and the CTA
 // waits (bounded) for its copies and products in flight before it frees its
 // tensor memory.
@@ -56,11 +60,12 @@ constexpr uint32_t kT5M = 128, kT5N = 64, kT5KC = 64;
 constexpr uint32_t kT5Dig = 4, kT5Diag = 7;
 constexpr uint32_t kT5StageA = kT5Dig * kT5M * 128;   // 64 KiB
 constexpr uint32_t kT5StageB = kT5Dig * kT5N * 128;   // 32 KiB
-constexpr uint32_t kT5Stage = kT5StageA + kT5StageB;
+constexpr uint32_t kT5NA = 2, kT5NB = 3;              // data / matrix stage buffers
 constexpr uint32_t kT5ConvWarps = 8;
 constexpr uint32_t kT5Threads = (kT5ConvWarps + 2) * 32;
 constexpr uint32_t kT5TmemCols = 512;
-constexpr size_t kT5Smem = 2 * (size_t)kT5Stage + 1024 + 256;
+constexpr size_t kT5SmemData = (size_t)kT5NA * kT5StageA + (size_t)kT5NB * kT5StageB;   // 224 KiB
+constexpr size_t kT5Smem = kT5SmemData + 1024 + 256;
 
 struct Tc5Args {
     const uint32_t *src;
@@ -120,6 +125,19 @@ __device__ __forceinline__ uint64_t t5_desc(uint32_t saddr) {
 // Instruction descriptor, kind::f16: fp16 A and B, fp32 D, both K-major,
 // M = 128, N = 64.
 constexpr uint32_t kT5Idesc = (1u << 4) | (0u << 7) | (0u << 10) | ((kT5N >> 3) << 17) | ((kT5M >> 4) << 24);
+// The four matrix digit planes of a stage lie one after another, so they
+// form one 256-row B operand: a single M = 128, N = 256 product of data
+// digit plane i with all of them adds A_i B_j to the accumulator of
+// diagonal i + j for j = 0..3 at once (columns 64 (i + j), contiguous).
+constexpr uint32_t kT5IdescAll = (1u << 4) | (0u << 7) | (0u << 10) | (((kT5Dig * kT5N) >> 3) << 17) |
+                                 ((kT5M >> 4) << 24);
+
+__device__ __forceinline__ void t5_st_zero8(uint32_t taddr) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+                 "r"(0u)
+                 : "memory");
+}
+__device__ __forceinline__ void t5_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // byte offset of 16-byte unit `unit` (0..7) of row `row` in a K-major
 // 128-byte-swizzled operand
@@ -183,17 +201,22 @@ template <bool ROWP>
 __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ Tc5Args a) {
     extern __shared__ __align__(1024) unsigned char t5_smem_raw[];
     unsigned char *base = t5_smem_raw + ((1024u - (smem_addr(t5_smem_raw) & 1023u)) & 1023u);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(base + 2 * (size_t)kT5Stage);
-    uint64_t *full_c = bars, *full_d = bars + 2, *empty = bars + 4, *acc_full = bars + 6, *acc_empty = bars + 7,
-             *drain = bars + 8;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + kT5SmemData);
+    // full_c / empty_b: matrix stages (TMA in, products done), full_d /
+    // empty: data stages (digits written, products done)
+    uint64_t *full_c = bars, *empty_b = bars + 3, *full_d = bars + 6, *empty = bars + 8, *acc_full = bars + 10,
+             *acc_empty = bars + 11, *drain = bars + 12;
     __shared__ uint32_t s_tmem;
     __shared__ uint32_t s_abort;
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr uint32_t NCONV = kT5ConvWarps * 32;
 
     if (tid == 0) {
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < (int)kT5NB; ++s) {
             mbar_init(&full_c[s], 1);
+            mbar_init(&empty_b[s], 1);
+        }
+        for (int s = 0; s < (int)kT5NA; ++s) {
             mbar_init(&full_d[s], NCONV);
             mbar_init(&empty[s], 1);
         }
@@ -216,36 +239,37 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
     volatile uint32_t *abort_flag = &s_abort;
     const uint32_t ntiles = a.ntiles;
     // stage s: A = data digit planes (converted here), B = matrix digit planes (TMA)
-    auto stage_a = [&](uint32_t s) { return base + (size_t)s * kT5Stage; };
-    auto stage_b = [&](uint32_t s) { return base + (size_t)s * kT5Stage + kT5StageA; };
+    auto stage_a = [&](uint32_t s) { return base + (size_t)s * kT5StageA; };
+    auto stage_b = [&](uint32_t s) { return base + (size_t)kT5NA * kT5StageA + (size_t)s * kT5StageB; };
     bool ok = true;
 
     if (warp == kT5ConvWarps) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
-            uint32_t g = 0, issued[2] = {0, 0};
+            uint32_t g = 0;
             for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
                 const T5Tile T = t5_tile(tile, a.L);
                 const uint32_t mrow0 = a.mat_row0 + T.l * kT5Dig * 256 + T.nb * kT5N;
                 for (uint32_t c = 0; c < 4 && ok; ++c, ++g) {
-                    const uint32_t s = g & 1u;
-                    if (g >= 2 && !t5_wait(&empty[s], ((g - 2) >> 1) & 1u, abort_flag)) { ok = false; break; }
+                    const uint32_t s = g % kT5NB;
+                    if (g >= kT5NB && !t5_wait(&empty_b[s], ((g - kT5NB) / kT5NB) & 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
                     unsigned char *dst = stage_b(s);
                     mbar_expect_tx(&full_c[s], kT5Dig * kT5N * 128);
                     for (uint32_t d = 0; d < kT5Dig; ++d)
                         tma_2d_g2s(dst + d * kT5N * 128, &a.cmap, (int)(c * kT5KC), (int)(mrow0 + d * 256),
                                    &full_c[s]);
-                    if (s) ++issued[1]; else ++issued[0];
                 }
             }
             if (!ok) {
                 atomicExch(const_cast<uint32_t *>(abort_flag), 1u);
-                // copies still in flight land before the CTA leaves
-                for (uint32_t s = 0; s < 2; ++s) {
-                    const uint32_t n = s ? issued[1] : issued[0];
-                    if (!n) continue;
+                // copies still in flight land before the CTA leaves: chunk
+                // h used stage h % 3 for its ((h / 3) + 1)-th phase
+                for (uint32_t h = g >= kT5NB ? g - kT5NB : 0; h < g; ++h) {
                     const long long t0 = clock64();
-                    while (!mbar_try_wait(&full_c[s], (n - 1) & 1u) && clock64() - t0 < (1ll << 30)) {
+                    while (!mbar_try_wait(&full_c[h % kT5NB], (h / kT5NB) & 1u) && clock64() - t0 < (1ll << 30)) {
                     }
                 }
             }
@@ -255,36 +279,29 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
         if (lane == 0) {
             uint32_t g = 0, ti = 0;
             for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++ti) {
-                if (ti > 0) {
-                    if (!t5_wait(acc_empty, (ti - 1) & 1u, abort_flag)) { ok = false; break; }
-                    t5_fence_after();
-                }
+                // accumulators zeroed (at the start, then by each epilogue)
+                if (!t5_wait(acc_empty, ti & 1u, abort_flag)) { ok = false; break; }
+                t5_fence_after();
                 for (uint32_t c = 0; c < 4 && ok; ++c, ++g) {
-                    const uint32_t s = g & 1u, ph = (g >> 1) & 1u;
-                    if (!t5_wait(&full_c[s], ph, abort_flag) || !t5_wait(&full_d[s], ph, abort_flag)) {
+                    const uint32_t s = g & 1u, sb = g % kT5NB;
+                    if (!t5_wait(&full_c[sb], (g / kT5NB) & 1u, abort_flag) ||
+                        !t5_wait(&full_d[s], (g >> 1) & 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
                     t5_fence_after();
-                    // descriptors of the stage's digit planes; a digit plane or
+                    // descriptors of the stages' digit planes; a digit plane or
                     // a K step of 16 (32 bytes) moves the start address field
-                    const uint64_t da = t5_desc(smem_addr(stage_a(s))), db = t5_desc(smem_addr(stage_b(s)));
+                    const uint64_t da = t5_desc(smem_addr(stage_a(s))), db = t5_desc(smem_addr(stage_b(sb)));
 #pragma unroll
                     for (uint32_t ks = 0; ks < kT5KC / 16; ++ks) {
 #pragma unroll
-                        for (uint32_t i = 0; i < kT5Dig; ++i) {
-#pragma unroll
-                            for (uint32_t j = 0; j < kT5Dig; ++j) {
-                                // the first product of diagonal i + j in the tile
-                                // (smallest i) overwrites the accumulator
-                                const bool first = ks == 0 && (i == 0 || j == kT5Dig - 1);
-                                t5_mma(tmem + (i + j) * kT5N, da + ((i * (kT5M * 128) + ks * 32) >> 4),
-                                       db + ((j * (kT5N * 128) + ks * 32) >> 4), kT5Idesc,
-                                       (c > 0 || !first) ? 1u : 0u);
-                            }
-                        }
+                        for (uint32_t i = 0; i < kT5Dig; ++i)
+                            t5_mma(tmem + i * kT5N, da + ((i * (kT5M * 128) + ks * 32) >> 4), db + ((ks * 32) >> 4),
+                                   kT5IdescAll, 1u);
                     }
                     t5_commit(&empty[s]);
+                    t5_commit(&empty_b[sb]);
                 }
                 if (ok) t5_commit(acc_full);
             }
@@ -388,6 +405,10 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
                     }
                 }
                 t5_wait_ld();
+                // the next tile accumulates onto zeros
+#pragma unroll
+                for (uint32_t d = 0; d < kT5Diag; ++d)
+                    t5_st_zero8(tmem + ((32u * (warp & 3u)) << 16) + d * kT5N + n0 + 8 * grp);
                 uint32_t v[8];
 #pragma unroll
                 for (int cc = 0; cc < 8; ++cc) {
@@ -410,6 +431,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
                         outt[(size_t)(T.nb * kT5N + n0 + 8 * grp + cc) * 256 + T.mb * kT5M + m] = v[cc];
                 }
             }
+            t5_wait_st();
             t5_fence_before();
             t5_arrive(acc_empty);
             return true;
@@ -423,6 +445,14 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
         const uint32_t nchunks = 4 * my_tiles;
         auto tile_of = [&](uint32_t g) { return blockIdx.x + (g >> 2) * gridDim.x; };
         if (nchunks) load_chunk(tile_of(0), 0, xa);
+        // the accumulators start at zero (every product accumulates):
+        // this thread's row, its 32 of the 64 columns of each diagonal
+        for (uint32_t d = 0; d < kT5Diag; ++d)
+            for (uint32_t c8 = 0; c8 < 4; ++c8)
+                t5_st_zero8(tmem + ((32u * (warp & 3u)) << 16) + d * kT5N + (warp >> 2) * 32 + 8 * c8);
+        t5_wait_st();
+        t5_fence_before();
+        t5_arrive(acc_empty);
         auto step = [&](uint32_t g, uint32_t (&cur)[TASKS][8], uint32_t (&nxt)[TASKS][8]) -> bool {
             if (g + 1 < nchunks) load_chunk(tile_of(g + 1), (g + 1) & 3u, nxt);
             const uint32_t s = g & 1u;
