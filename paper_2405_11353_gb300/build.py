@@ -42,8 +42,7 @@ def _digest(extra=""):
 
 # Sources of the fused forward transform with 4-byte words and Shoup
 # twiddles (the streamed two-pass launch the benchmark times).
-FORWARD_U32_SOURCES = ("fused.cuh", "stream.cuh", "fused_launch.cuh", "modarith.cuh", "plan.hpp",
-                       "fused_u32_shoup.cu")
+FORWARD_U32_SOURCES = ("fused.cuh", "stream.cuh", "fused_launch.cuh", "modarith.cuh", "fused_u32_shoup.cu")
 
 
 def kernel_digest(files=None):
