@@ -78,6 +78,7 @@ struct Tc5Args {
     uint32_t *status;
     uint32_t L;
     uint32_t ntiles;                // 8 per transform
+    uint32_t stall_tx;              // test hook: extra bytes CTA 0's first matrix copy waits for
 };
 
 namespace {
@@ -258,6 +259,8 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
                     }
                     unsigned char *dst = stage_b(s);
                     mbar_expect_tx(&full_c[s], kT5Dig * kT5N * 128);
+                    // (test hook: this copy's barrier waits for bytes that never come)
+                    if (a.stall_tx && g == 0 && blockIdx.x == 0) mbar_add_tx(&full_c[s], a.stall_tx);
                     for (uint32_t d = 0; d < kT5Dig; ++d)
                         tma_2d_g2s(dst + d * kT5N * 128, &a.cmap, (int)(c * kT5KC), (int)(mrow0 + d * 256),
                                    &full_c[s]);
@@ -541,12 +544,13 @@ cudaError_t launch_tc5(ntt_plan_s &p, void *data, uint32_t batch, bool inverse, 
     a.status = p.d_status;
     a.L = p.L;
     a.ntiles = (uint32_t)(ntrans * 8);
+    a.stall_tx = (p.flags & NTT_TEST_STALL) && !inverse ? 16u : 0u;
     uint32_t *d = reinterpret_cast<uint32_t *>(data), *s = reinterpret_cast<uint32_t *>(p.d_scratch);
     auto row0 = [&](int m) { return (uint32_t)m * p.L * 1024; };
     if (!inverse) {
         a.src = d; a.dst = s; a.mat_row0 = row0(0); a.tw = tws;
         if ((e = t5_launch<false>(a, st)) != cudaSuccess) return e;
-        a.src = s; a.dst = d; a.mat_row0 = row0(1); a.tw = nullptr;
+        a.src = s; a.dst = d; a.mat_row0 = row0(1); a.tw = nullptr; a.stall_tx = 0;
         e = t5_launch<true>(a, st);
     } else {
         a.src = d; a.dst = s; a.mat_row0 = row0(2); a.tw = tws + (size_t)p.L * 65536;

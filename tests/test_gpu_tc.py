@@ -116,3 +116,30 @@ def test_tc_rejects_unsupported(nt, orc):
             nt.ntt_plan_create(N, qs if N == 1 << 16 else orc.find_primes(30, 15, 1),
                                nt.NTT_TC_FOURSTEP, flags)
         assert e.value.status == nt.NTT_ERR_UNSUPPORTED
+
+
+def test_tc_bounded_wait_reports_timeout_and_context_survives(nt, orc):
+    """Failure path of the tcgen05 kernel without a fault: with the test
+    hook, CTA 0's first matrix copy waits for bytes that never arrive; the
+    MMA thread's wait gives up after about a second, every role leaves its
+    loop, the CTA frees its tensor memory, the call reports
+    NTT_ERR_TIMEOUT, and the next plan on the same context is bit-exact."""
+    N = 1 << 16
+    qs = orc.find_primes(30, 17, 2)
+    h = ntt_synth.rns_batch(63, qs, N, 2)
+    p = nt.ntt_plan_create(N, qs, nt.NTT_TC_FOURSTEP, nt.NTT_ORDER_BITREV | nt.NTT_TEST_STALL)
+    try:
+        d = dev(h)
+        nt.ntt_forward(p, d, 2)
+        assert nt.ntt_get_device_status(p) == nt.NTT_ERR_TIMEOUT
+    finally:
+        nt.ntt_plan_destroy(p)
+    p = nt.ntt_plan_create(N, qs, nt.NTT_TC_FOURSTEP, nt.NTT_ORDER_BITREV)
+    try:
+        d = dev(h)
+        nt.ntt_forward(p, d, 2)
+        psis = [orc.psi(q, N) for q in qs]
+        assert np.array_equal(host(d, h.shape), bitrev_rows(orc.ntt_batch(h, qs, psis), orc))
+        assert nt.ntt_get_device_status(p) == nt.NTT_OK
+    finally:
+        nt.ntt_plan_destroy(p)
