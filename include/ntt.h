@@ -118,13 +118,14 @@ typedef enum {
                                       (fp16 digits, fp32 accumulators in
                                       tensor memory); results identical, kept
                                       for comparison */
-#define NTT_TEST_STALL 0x8000u     /* test hook, fused plans only: in every
-                                      forward call one CTA's first tile waits
-                                      for 16 bytes that never arrive, so its
-                                      bounded wait runs out (about a second)
-                                      and ntt_get_device_status then reports
-                                      NTT_ERR_TIMEOUT; the results of that
-                                      call are not valid */
+#define NTT_TEST_STALL 0x8000u     /* test hook, fused and tensor-core
+                                      plans: in every forward call one CTA's
+                                      first tile (or first matrix copy)
+                                      waits for 16 bytes that never arrive,
+                                      so its bounded wait runs out (about a
+                                      second) and ntt_get_device_status then
+                                      reports NTT_ERR_TIMEOUT; the results of
+                                      that call are not valid */
 
 /*
  * Create a plan for batches of L-limb polynomials of N coefficients.
@@ -275,6 +276,18 @@ ntt_status ntt_default_psi(uint64_t q, uint32_t N, uint64_t *psi_out);
  * fewer exist or bits is outside 3..62. */
 ntt_status ntt_find_primes(uint32_t bits, uint32_t m, uint32_t count,
                            uint64_t *out);
+
+/* ------------------------------------------------ integer roofline
+ * Measures the rate of 32-bit integer multiply-adds (the denominator the
+ * butterfly kernels are reported against; not part of the paper's method):
+ * launches blocks x 256 threads (blocks = 8 per SM, written to *blocks_out),
+ * each running 8 independent chains of `iters` mad.lo.u32 (high = 0) or
+ * mad.hi.u32 (high = 1) steps, i.e. blocks x 256 x 8 x iters operations;
+ * the caller times the launch on `stream`.  d_scratch receives one word per
+ * thread (scratch_bytes >= blocks x 1 KiB, else NTT_ERR_INVALID_ARG). */
+ntt_status ntt_measure_int_mad_rate(int high, uint32_t iters, void *d_scratch,
+                                    size_t scratch_bytes, uint32_t *blocks_out,
+                                    ntt_stream_t stream);
 
 /* ------------------------------------------------ RNS base conversion
  * Fast base conversion of coefficient residues (the basis-extension step

@@ -57,7 +57,7 @@ EXPORTS = [
     "ntt_status_string", "ntt_validate", "ntt_default_psi", "ntt_find_primes",
     "ntt_ragged_create", "ntt_ragged_launch", "ntt_ragged_status", "ntt_ragged_destroy",
     "ntt_forward_noalloc", "ntt_forward_prefix", "ntt_inverse_prefix", "ntt_pointwise_inverse",
-    "ntt_bconv_create", "ntt_bconv", "ntt_bconv_destroy",
+    "ntt_bconv_create", "ntt_bconv", "ntt_bconv_destroy", "ntt_measure_int_mad_rate",
 ]
 
 
@@ -113,6 +113,7 @@ def lib():
             "ntt_bconv_create": (st, [ctypes.POINTER(vp), u64p, u32, u64p, u32, u32]),
             "ntt_bconv": (st, [vp, vp, vp, u32, vp]),
             "ntt_bconv_destroy": (None, [vp]),
+            "ntt_measure_int_mad_rate": (st, [ctypes.c_int, u32, vp, ctypes.c_size_t, ctypes.POINTER(u32), vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -301,3 +302,13 @@ def ntt_bconv(plan, out, inp, batch, stream=None):
 
 def ntt_bconv_destroy(plan):
     lib().ntt_bconv_destroy(plan)
+
+
+def ntt_measure_int_mad_rate(high, iters, scratch, stream=None):
+    """Launch the integer multiply-add rate kernel; returns the operation
+    count of the launch (the caller times it)."""
+    blocks = ctypes.c_uint32()
+    nbytes = scratch.numel() * scratch.element_size()
+    _check(lib().ntt_measure_int_mad_rate(1 if high else 0, iters, _ptr(scratch), nbytes, ctypes.byref(blocks),
+                                          _stream(stream)), "ntt_measure_int_mad_rate")
+    return blocks.value * 256 * 8 * iters
