@@ -137,7 +137,7 @@ def job_rate(units_per_step_per_rank, world, steps, elapsed_ms):
 
 
 # ----------------------------------------------------------------- oracle arm
-def oracle_sample(qs, seconds=12.0, max_reps=50):
+def oracle_sample(qs, seconds=12.0, max_reps=200):
     """The CPU oracle (O(N log N) path, OpenMP over transforms) running the
     step's pipeline on one pair of polynomials x all limbs, repeated for
     about `seconds`.  Returns (NTTs/s, threads, description)."""
@@ -335,6 +335,55 @@ def tc_fourstep(nt, torch, dev, reps=20):
     return out
 
 
+def variants_n1024(nt, torch, dev, reps=50):
+    """The paper's comparison of dataflow variants on the N = 1024, q = 12289,
+    64-polynomial workload: forward + inverse per variant (the per-stage
+    variant kernels, and the fused path)."""
+    N, B, qs = 1024, 64, [12289]
+    host = ntt_synth.rns_batch(1001, qs, N, B, dtype=np.uint32)
+    d = torch.from_numpy(host.view(np.int32).reshape(-1).copy()).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    out = {"workload": "N=1024, q=12289, u32, 64 polys: forward + inverse (128 transforms)"}
+    for name in ("dit", "dif", "flat", "pease", "pease_nc", "stockham", "sixstep", "fused"):
+        p = nt.ntt_plan_create(N, qs, nt.VARIANTS[name], 0)
+        try:
+            nt.ntt_plan_reserve(p, B, sh)
+
+            def step():
+                nt.ntt_forward(p, d, B, sh)
+                nt.ntt_inverse(p, d, B, sh)
+            ms = _time_loop(torch, stream, step, reps)
+        finally:
+            nt.ntt_plan_destroy(p)
+        out[name] = {"ms_per_step": ms, "value": 2 * B / (ms / 1e3), "unit": "NTT/s"}
+    return out
+
+
+def rns_n2p14(nt, torch, dev, reps=50):
+    """N = 2^14, 8 primes q < 2^30 (= 1 mod 2^15), 128 polynomials: forward
+    of all 128, 64 pointwise products fused into the inverse (single-pass
+    fused kernels)."""
+    qs = nt.ntt_find_primes(30, 15, 8)
+    N, B = 1 << 14, 128
+    host = ntt_synth.rns_batch(1002, qs, N, B, dtype=np.uint32)
+    d = torch.from_numpy(host.view(np.int32).reshape(-1).copy()).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    half = (B // 2) * 8 * N
+    p = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, nt.NTT_ORDER_BITREV)
+    try:
+        def step():
+            nt.ntt_forward(p, d, B, sh)
+            nt.ntt_pointwise_inverse(p, d, d, d[half:], B // 2, sh)
+        ms = _time_loop(torch, stream, step, reps)
+    finally:
+        nt.ntt_plan_destroy(p)
+    n = (B + B // 2) * 8
+    return {"workload": "N=2^14, L=8, u32, 128 polys: forward x128, pointwise x64 + inverse x64",
+            "ms_per_step": ms, "value": n / (ms / 1e3), "unit": "NTT/s"}
+
+
 def base_conv(nt, torch, dev, reps=50):
     """Fast RNS base conversion (ntt_bconv) of 8 polynomials, N = 2^16,
     from 32 primes q < 2^30 to 32 other primes: L x K = 1024 multiply-adds
@@ -396,7 +445,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ragged and wide-word side measurements")
     ap.add_argument("--extra", default=None,
-                    choices=["ragged", "wide_word_u64", "tc_fourstep", "cluster_form", "base_conv"],
+                    choices=["ragged", "wide_word_u64", "tc_fourstep", "cluster_form", "base_conv",
+                             "variants_n1024", "rns_n2p14"],
                     help="run only this side measurement and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -426,7 +476,8 @@ def main():
     nt.lib()
     if args.extra:
         fn = {"ragged": ragged_vs_plain, "wide_word_u64": wide_word, "tc_fourstep": tc_fourstep,
-              "cluster_form": cluster_form, "base_conv": base_conv}[args.extra]
+              "cluster_form": cluster_form, "base_conv": base_conv, "variants_n1024": variants_n1024,
+              "rns_n2p14": rns_n2p14}[args.extra]
         print(json.dumps({args.extra: fn(nt, torch, dev)}), flush=True)
         return 0
     from paper_2405_11353_gb300 import build as nb
@@ -546,7 +597,8 @@ def main():
     if not args.no_extras:
         for name, fn in (("ragged", ragged_vs_plain), ("wide_word_u64", wide_word),
                          ("tc_fourstep", tc_fourstep), ("cluster_form", cluster_form),
-                         ("base_conv", base_conv)):
+                         ("base_conv", base_conv), ("variants_n1024", variants_n1024),
+                         ("rns_n2p14", rns_n2p14)):
             try:
                 extras[name] = fn(nt, torch, dev)
             except Exception as exc:     # a side measurement never hides the main line

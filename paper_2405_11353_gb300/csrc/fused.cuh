@@ -469,6 +469,9 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
             mbar_expect_tx(&bar[s], K * S * (uint32_t)sizeof(W));
             const uint64_t row0 = (t * N + ((size_t)pos0 << S2)) / RW;
             tma_2d_g2s(dst, tmap, 0, (int)row0, &bar[s]);
+            // the fused product's second operand (read by plain loads) into
+            // L2 while this tile's copy is in flight
+            if (a.pw_b) prefetch_l2(a.pw_b + t * N + ((size_t)pos0 << S2), K * S * (uint32_t)sizeof(W));
         } else if (KIND == TK_CHUNKS) {
             mbar_expect_tx(&bar[s], K * S * (uint32_t)sizeof(W));
             const W *src = a.data + t * N + ((size_t)pos0 << S2);
