@@ -485,7 +485,15 @@ def main():
 
     qs = nt.ntt_find_primes(BITS, M, L)
     flags = nt.NTT_ORDER_BITREV | nt.NTT_RED_SHOUP
+    # the autotuner picks the two-pass form of each direction for the two
+    # batch sizes of the step (forward of 16 polynomials, product + inverse
+    # of 8) before the plan is made
+    tuning = {"forward_batch%d" % POLYS: nt.ntt_autotune(N, qs, flags, POLYS),
+              "inverse_batch%d" % PAIRS: nt.ntt_autotune(N, qs, flags, PAIRS)}
     plan = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, flags)
+    form_names = {v: k for k, v in nt.FORMS.items()}
+    forms = {"forward": form_names.get(nt.ntt_plan_form(plan, POLYS)),
+             "product_inverse": form_names.get(nt.ntt_plan_form(plan, PAIRS, True))}
     host = ntt_synth.rns_batch(1005 + 7919 * rank, qs, N, POLYS, dtype=np.uint32)
     words = POLYS * L * N
     half = PAIRS * L * N
@@ -575,7 +583,7 @@ def main():
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": achieved / peak, "traffic": traffic_from_profiles(digest),
-        "kernel": "ntt_forward: column pass + 256-point chunk pass (two launches), %d transforms" % n_fwd,
+        "kernel": "ntt_forward: column pass + 256-point chunk pass (%s form), %d transforms" % (forms["forward"], n_fwd),
         "algorithmic_bytes_per_call": fwd_bytes, "avg_ms": fwd_ms,
         "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
         else "fallback 6.8 TB/s",
@@ -618,9 +626,11 @@ def main():
             "dtype": "u32", "data": "synthetic (seeded SplitMix64 residues, uniform in [0,q))",
             "config": {"workload": WORKLOAD, "N": N, "L": L, "polys": POLYS, "word": "u32",
                        "variant": "fused", "reduction": "shoup", "order": "bitrev",
+                       "two_pass_forms": forms,
                        "l2": "4 rotating input copies (512 MiB) > 129 MB L2",
                        "parallelism": "replicas x%d" % world},
             "per_call_ms": {"forward_16polys": fwd_ms, "pointwise_inverse_8pairs": pwinv_ms},
+            "autotune": tuning,
             "roofline": roofline,
             "int_roofline": int_roofline,
             "cpu_baseline": cpu,

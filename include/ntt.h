@@ -106,12 +106,11 @@ typedef enum {
                                       traffic), instead of the default two
                                       launches with the whole batch written
                                       to memory between them; results
-                                      identical.  On GB300 the two launches
-                                      are faster (the passes are bound by
-                                      issue and latency, not DRAM).  Calls of
-                                      one streamed plan use one of 16 counter
-                                      sets in turn: at most 16 calls of one
-                                      plan may overlap on the GPU */
+                                      identical (NTT_FORM_STREAMED below).
+                                      Calls in the streamed form use one of
+                                      16 counter sets of the plan in turn:
+                                      at most 16 such calls of one plan may
+                                      overlap on the GPU */
 #define NTT_TC_IMMA 0x800u         /* NTT_TC_FOURSTEP: the digit products on
                                       the warp-level integer MMA (mma.sync
                                       u8 x u8 -> s32) instead of tcgen05
@@ -276,6 +275,51 @@ ntt_status ntt_default_psi(uint64_t q, uint32_t N, uint64_t *psi_out);
  * fewer exist or bits is outside 3..62. */
 ntt_status ntt_find_primes(uint32_t bits, uint32_t m, uint32_t count,
                            uint64_t *out);
+
+/* ------------------------------------------------------------ autotuner
+ * The two-pass fused path (N > 2^14 with 4-byte words, N > 2^13 with
+ * 8-byte) runs each direction in one of three forms: */
+#define NTT_FORM_SMALL 0      /* chunk pass on one-warp CTAs (2-chunk tiles) */
+#define NTT_FORM_WIDE 1       /* chunk pass on 256-thread CTAs (16-chunk tiles) */
+#define NTT_FORM_STREAMED 2   /* both passes in one streamed launch */
+/* Defaults: NTT_FORM_SMALL forward, NTT_FORM_WIDE inverse (NTT_FORM_STREAMED
+ * both ways under NTT_STREAMED); results are identical in every form. */
+typedef struct {
+    float forward_ms[3];      /* per form, ms per call */
+    float inverse_ms[3];
+    int32_t forward_form;     /* the fastest */
+    int32_t inverse_form;
+} ntt_tune_result;
+
+/* Time the three forms of both directions for (N, q[0..L), flags, batch)
+ * on the current device (a scratch buffer of batch x L x N zero words,
+ * allocated and freed here) and record the fastest per direction in the
+ * process-wide tuning table, keyed by (N, word size, L, reduction, order,
+ * floor(log2 batch)).  Plans created afterwards with that shape use the
+ * recorded forms for calls in that batch bucket (NTT_STREAMED plans keep
+ * their form).  If the environment variable NTT_TUNE_DB names a file, the
+ * table is read from it at first use and rewritten after each tuning (one
+ * JSON object per line).  flags: as ntt_plan_create, without NTT_STREAMED,
+ * NTT_CHECK or NTT_TEST_STALL.  NTT_ERR_UNSUPPORTED for sizes outside the
+ * two-pass range.  result may be NULL. */
+ntt_status ntt_autotune(uint32_t N, const uint64_t *q, uint32_t L,
+                        uint32_t flags, uint32_t batch, ntt_stream_t stream,
+                        ntt_tune_result *result);
+
+/* The form a plan uses for calls with this batch (0: forward, else
+ * inverse), or -1 when the plan is not on the two-pass fused path. */
+int32_t ntt_plan_form(ntt_plan_t plan, uint32_t batch, int inverse);
+
+/* Host-only access to the tuning table (no GPU needed): record forms for a
+ * shape by hand (saved to NTT_TUNE_DB like a tuning; NTT_ERR_INVALID_ARG for
+ * a form outside 0..2 or batch 0), read the form recorded for a shape and
+ * direction (-1: none), and empty the in-memory table (the file is not
+ * read again in this process).  Plans copy the table at creation. */
+ntt_status ntt_tune_set(uint32_t N, uint32_t L, uint32_t flags, uint32_t batch,
+                        int32_t forward_form, int32_t inverse_form);
+int32_t ntt_tune_get(uint32_t N, uint32_t L, uint32_t flags, uint32_t batch,
+                     int inverse);
+void ntt_tune_clear(void);
 
 /* ------------------------------------------------ integer roofline
  * Measures the rate of 32-bit integer multiply-adds (the denominator the

@@ -58,6 +58,7 @@ EXPORTS = [
     "ntt_ragged_create", "ntt_ragged_launch", "ntt_ragged_status", "ntt_ragged_destroy",
     "ntt_forward_noalloc", "ntt_forward_prefix", "ntt_inverse_prefix", "ntt_pointwise_inverse",
     "ntt_bconv_create", "ntt_bconv", "ntt_bconv_destroy", "ntt_measure_int_mad_rate",
+    "ntt_autotune", "ntt_plan_form", "ntt_tune_set", "ntt_tune_get", "ntt_tune_clear",
 ]
 
 
@@ -73,6 +74,14 @@ class NttJob(ctypes.Structure):
                 ("word64", ctypes.c_uint32), ("inverse", ctypes.c_int32),
                 ("reserved", ctypes.c_uint32)]
 
+
+class NttTuneResult(ctypes.Structure):
+    _fields_ = [("forward_ms", ctypes.c_float * 3), ("inverse_ms", ctypes.c_float * 3),
+                ("forward_form", ctypes.c_int32), ("inverse_form", ctypes.c_int32)]
+
+
+NTT_FORM_SMALL, NTT_FORM_WIDE, NTT_FORM_STREAMED = 0, 1, 2
+FORMS = {"small": NTT_FORM_SMALL, "wide": NTT_FORM_WIDE, "streamed": NTT_FORM_STREAMED}
 
 _lib = None
 
@@ -114,6 +123,11 @@ def lib():
             "ntt_bconv": (st, [vp, vp, vp, u32, vp]),
             "ntt_bconv_destroy": (None, [vp]),
             "ntt_measure_int_mad_rate": (st, [ctypes.c_int, u32, vp, ctypes.c_size_t, ctypes.POINTER(u32), vp]),
+            "ntt_autotune": (st, [u32, u64p, u32, u32, u32, vp, ctypes.POINTER(NttTuneResult)]),
+            "ntt_plan_form": (ctypes.c_int32, [vp, u32, ctypes.c_int]),
+            "ntt_tune_set": (st, [u32, u32, u32, u32, ctypes.c_int32, ctypes.c_int32]),
+            "ntt_tune_get": (ctypes.c_int32, [u32, u32, u32, u32, ctypes.c_int]),
+            "ntt_tune_clear": (None, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -312,3 +326,30 @@ def ntt_measure_int_mad_rate(high, iters, scratch, stream=None):
     _check(lib().ntt_measure_int_mad_rate(1 if high else 0, iters, _ptr(scratch), nbytes, ctypes.byref(blocks),
                                           _stream(stream)), "ntt_measure_int_mad_rate")
     return blocks.value * 256 * 8 * iters
+
+
+def ntt_autotune(N, q, flags, batch, stream=None):
+    """Time the three two-pass forms for this shape, record the fastest;
+    returns {"forward_ms": [...], "inverse_ms": [...], "forward_form",
+    "inverse_form"}."""
+    r = NttTuneResult()
+    _check(lib().ntt_autotune(N, _u64arr(q), len(q), flags, batch, _stream(stream), ctypes.byref(r)),
+           "ntt_autotune")
+    return {"forward_ms": list(r.forward_ms), "inverse_ms": list(r.inverse_ms),
+            "forward_form": r.forward_form, "inverse_form": r.inverse_form}
+
+
+def ntt_plan_form(plan, batch, inverse=False):
+    return lib().ntt_plan_form(plan, batch, 1 if inverse else 0)
+
+
+def ntt_tune_set(N, L, flags, batch, forward_form, inverse_form):
+    _check(lib().ntt_tune_set(N, L, flags, batch, forward_form, inverse_form), "ntt_tune_set")
+
+
+def ntt_tune_get(N, L, flags, batch, inverse=False):
+    return lib().ntt_tune_get(N, L, flags, batch, 1 if inverse else 0)
+
+
+def ntt_tune_clear():
+    lib().ntt_tune_clear()

@@ -354,7 +354,7 @@ ntt_status build_tables(ntt_plan_s *p) {
     }
     if (cudaMalloc((void **)&p->d_status, sizeof(uint32_t)) != cudaSuccess) { cudaGetLastError(); return NTT_ERR_OOM; }
     if (cudaMemset(p->d_status, 0, sizeof(uint32_t)) != cudaSuccess) return NTT_ERR_CUDA;
-    if (chunk_tabs && p->streamed) {
+    if (chunk_tabs) {
         const size_t bytes = (size_t)nttgb::kStreamRing * nttgb::stream_set_words(L) * sizeof(uint32_t);
         if (cudaMalloc((void **)&p->d_stream_ctr, bytes) != cudaSuccess) { cudaGetLastError(); return NTT_ERR_OOM; }
         if (cudaMemset(p->d_stream_ctr, 0, bytes) != cudaSuccess) return NTT_ERR_CUDA;
@@ -546,6 +546,7 @@ ntt_status create_plan(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t
             p->s1 = p->logN - p->s2;
         }
     }
+    nttgb::apply_tuning(*p);
     cudaGetDevice(&p->device);
     s = build_tables(p);
     if (s != NTT_OK) { free_plan_memory(p); delete p; cudaGetLastError(); return s; }

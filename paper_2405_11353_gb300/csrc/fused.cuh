@@ -77,15 +77,18 @@ template <class W> __host__ __device__ constexpr uint32_t cols_phys(uint32_t k, 
 // a per-round base plus an immediate offset): single-pass tiles hold 4096
 // words (or one transform above that), column strips 16 (4-byte) or 8
 // (8-byte) columns and at least 256 threads, chunk tiles 16 chunks, or 2
-// chunks in the per-pass forward chunk kernel (P = 0): one warp per CTA, so
-// the per-tile barriers are warp barriers and the many small CTAs of an SM
-// run independently.  The per-pass inverse chunk kernel (P = 3: its tiles
-// land through a 128-byte-swizzled copy and need 1 KiB alignment) keeps
-// 16-chunk tiles.
+// chunks in the per-pass chunk kernels with P = 0: one warp per CTA, so the
+// per-tile barriers are warp barriers and the many small CTAs of an SM run
+// independently.  With P = 3 the per-pass chunk kernels keep 16-chunk
+// tiles (256 threads); which one a plan uses per direction is its form
+// (default: 2-chunk tiles forward, 16-chunk tiles inverse, whose copies
+// land through the 128-byte swizzle and need 1 KiB alignment; the
+// autotuner can choose otherwise).
 // P = 0: per-plan passes; column strips have 128-byte rows (32 four-byte or
 // 16 eight-byte columns).  P = 1: the ragged kernel and the streamed
 // two-pass launch, whose CTAs always have 256 threads (4096-word column
-// tiles).  P = 3: the per-pass inverse chunk kernel (as P = 0 otherwise).
+// tiles).  P = 3: per-pass chunk kernels with 16-chunk tiles (as P = 0
+// otherwise).
 template <class W, int LOGS, int KIND, int P = 0> __host__ __device__ constexpr uint32_t tile_k() {
     return KIND == TK_SINGLE ? (LOGS >= 12 ? 1u : (4096u >> LOGS))
          : KIND == TK_CHUNKS ? (P == 0 ? 2u : 16u)
@@ -726,18 +729,13 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     return true;
 }
 
-// Tile configuration of a per-plan pass (see tile_k).
-template <bool INV, int KIND> __host__ __device__ constexpr int pass_p() {
-    return (INV && KIND == TK_CHUNKS) ? 3 : 0;
-}
-
 // Per-plan fused pass: CTA c processes tiles [c T / G, (c+1) T / G).
-template <class W, int RED, bool INV, int LOGS, int KIND>
+// PP: the tile configuration (see tile_k): 0, or 3 for 16-chunk tiles.
+template <class W, int RED, bool INV, int LOGS, int KIND, int PP>
 __global__ void __launch_bounds__(sizeof(W) == 4 ? 1024 : 512)
 k_fused(const __grid_constant__ FArgs<W> a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     constexpr uint32_t NS = n_stages<W, LOGS, KIND>();
-    constexpr int PP = pass_p<INV, KIND>();
     constexpr uint32_t BW = buf_words<W, LOGS, KIND, INV, PP>();
     constexpr uint32_t TWP = tw_pairs<W, LOGS, KIND, PP>();
     constexpr uint32_t AL = stage_align<W, LOGS, KIND, INV, PP>();

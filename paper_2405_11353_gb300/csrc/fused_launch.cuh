@@ -14,9 +14,9 @@ namespace nttgb {
 
 static_assert(kN2Log == (uint32_t)kChunkLog, "two-pass split must match the plan's chunk size");
 
-template <class W, int RED, bool INV, int LOGS, int KIND>
+template <class W, int RED, bool INV, int LOGS, int KIND, int PP>
 cudaError_t launch_pass(const FArgs<W> &a, uint32_t threads, size_t smem, cudaStream_t st) {
-    auto kern = k_fused<W, RED, INV, LOGS, KIND>;
+    auto kern = k_fused<W, RED, INV, LOGS, KIND, PP>;
     // persistent grid: as many CTAs as fit on the GPU at once
     static int resident = 0;
     if (!resident) {
@@ -93,7 +93,7 @@ inline cudaError_t make_rows_tmap(CUtensorMap *m, void *data, bool w64, uint64_t
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <class W, int RED, bool INV, int KIND, int LOGS = 4>
+template <class W, int RED, bool INV, int KIND, int PP, int LOGS = 4>
 cudaError_t pass_dispatch(int logS, const FArgs<W> &a, uint32_t threads, size_t smem, cudaStream_t st) {
     constexpr int MAXS = KIND == TK_SINGLE ? (sizeof(W) == 4 ? kSingleMaxLog32 : kSingleMaxLog64)
                                            : (KIND == TK_COLS ? 9 : kChunkLog);
@@ -102,14 +102,13 @@ cudaError_t pass_dispatch(int logS, const FArgs<W> &a, uint32_t threads, size_t 
         return cudaErrorInvalidValue;
     } else {
         if constexpr (LOGS >= MINS) {
-            if (logS == LOGS) return launch_pass<W, RED, INV, LOGS, KIND>(a, threads, smem, st);
+            if (logS == LOGS) return launch_pass<W, RED, INV, LOGS, KIND, PP>(a, threads, smem, st);
         }
-        return pass_dispatch<W, RED, INV, KIND, LOGS + 1>(logS, a, threads, smem, st);
+        return pass_dispatch<W, RED, INV, KIND, PP, LOGS + 1>(logS, a, threads, smem, st);
     }
 }
 
-template <class W, int KIND, bool INV> uint32_t tile_k_for(int logS) {
-    constexpr int PP = pass_p<INV, KIND>();
+template <class W, int KIND, int PP> uint32_t tile_k_for(int logS) {
     switch (logS) {
 #define NTTGB_CASE(s) case s: return tile_k<W, s, KIND, PP>();
         NTTGB_CASE(4) NTTGB_CASE(5) NTTGB_CASE(6) NTTGB_CASE(7) NTTGB_CASE(8) NTTGB_CASE(9)
@@ -119,8 +118,7 @@ template <class W, int KIND, bool INV> uint32_t tile_k_for(int logS) {
     return 1;
 }
 
-template <class W, int KIND, bool INV> size_t smem_for(int logS) {
-    constexpr int PP = pass_p<INV, KIND>();
+template <class W, int KIND, bool INV, int PP> size_t smem_for(int logS) {
     switch (logS) {
 #define NTTGB_CASE(s) case s: return fused_smem_bytes<W, s, KIND, INV, PP>();
         NTTGB_CASE(4) NTTGB_CASE(5) NTTGB_CASE(6) NTTGB_CASE(7) NTTGB_CASE(8) NTTGB_CASE(9)
@@ -184,18 +182,28 @@ cudaError_t fill_pass(FArgs<W> &a, ntt_plan_s &p, W *data, const void *tw, uint6
     return cudaSuccess;
 }
 
-// One pass as its own launch.
-template <class W, int RED, bool INV, int KIND>
+// One pass as its own launch; PP: tile configuration (0, or 3 for
+// 16-chunk tiles in a chunk pass).
+template <class W, int RED, bool INV, int KIND, int PP = 0>
 cudaError_t run_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, int logS, bool final_pass,
                      cudaStream_t st, W *out = nullptr, const W *pw_b = nullptr) {
     FArgs<W> a;
     const uint32_t T = (1u << logS) / 16;
-    const uint32_t K = tile_k_for<W, KIND, INV>(logS);
+    const uint32_t K = tile_k_for<W, KIND, PP>(logS);
     cudaError_t e = fill_pass<W, INV, KIND>(a, p, data, tw, ntrans, logS, final_pass, K, out, pw_b);
     if (e != cudaSuccess) return e;
-    size_t smem = smem_for<W, KIND, INV>(logS);
+    size_t smem = smem_for<W, KIND, INV, PP>(logS);
     ++p.last_launches;
-    return pass_dispatch<W, RED, INV, KIND>(logS, a, K * T, smem, st);
+    return pass_dispatch<W, RED, INV, KIND, PP>(logS, a, K * T, smem, st);
+}
+
+// The chunk pass in the plan's form for this direction.
+template <class W, int RED, bool INV>
+cudaError_t run_chunk_pass(ntt_plan_s &p, int form, W *data, const void *tw, uint64_t ntrans, bool final_pass,
+                           cudaStream_t st, W *out = nullptr, const W *pw_b = nullptr) {
+    if (form == FORM_SMALL)
+        return run_pass<W, RED, INV, TK_CHUNKS, 0>(p, data, tw, ntrans, (int)p.s2, final_pass, st, out, pw_b);
+    return run_pass<W, RED, INV, TK_CHUNKS, 3>(p, data, tw, ntrans, (int)p.s2, final_pass, st, out, pw_b);
 }
 
 // Tuning of the one-launch two-pass form: tiles per work item and the lag
@@ -210,7 +218,7 @@ inline uint32_t stream_env(const char *name) {
 // Both passes of a two-pass transform in one launch (stream.cuh).
 template <class W, int RED, bool INV>
 cudaError_t run_stream(ntt_plan_s &p, W *data, uint64_t ntrans, cudaStream_t st, W *out, const W *pw_b) {
-    const uint32_t env_tiles = stream_env("NTT_STREAM_TILES");
+    const uint32_t env_tiles = p.stream_tiles ? p.stream_tiles : stream_env("NTT_STREAM_TILES");
     const uint32_t env_lag = stream_env("NTT_STREAM_LAG");
     StreamArgs<W> sa;
     std::memset(&sa, 0, sizeof(sa));
@@ -280,16 +288,17 @@ cudaError_t run_fused_t(ntt_plan_s &p, void *data_v, uint32_t batch, bool invers
         if (!inverse) return run_pass<W, RED, false, TK_SINGLE>(p, data, p.d_main_fwd, ntrans, p.logN, true, st);
         return run_pass<W, RED, true, TK_SINGLE>(p, data, p.d_main_inv, ntrans, p.logN, true, st);
     }
-    if (p.streamed) {
+    const int form = p.form_for(batch, inverse);
+    if (form == FORM_STREAMED) {
         if (!inverse) return run_stream<W, RED, false>(p, data, ntrans, st, nullptr, nullptr);
         return run_stream<W, RED, true>(p, data, ntrans, st, nullptr, nullptr);
     }
     if (!inverse) {
         e = run_pass<W, RED, false, TK_COLS>(p, data, p.d_main_fwd, ntrans, p.s1, false, st);
         if (e != cudaSuccess) return e;
-        return run_pass<W, RED, false, TK_CHUNKS>(p, data, p.d_chunk_fwd, ntrans, p.s2, true, st);
+        return run_chunk_pass<W, RED, false>(p, form, data, p.d_chunk_fwd, ntrans, true, st);
     }
-    e = run_pass<W, RED, true, TK_CHUNKS>(p, data, p.d_chunk_inv, ntrans, p.s2, false, st);
+    e = run_chunk_pass<W, RED, true>(p, form, data, p.d_chunk_inv, ntrans, false, st);
     if (e != cudaSuccess) return e;
     return run_pass<W, RED, true, TK_COLS>(p, data, p.d_main_inv, ntrans, p.s1, true, st);
 }
@@ -302,12 +311,13 @@ cudaError_t run_fused_pwinv_t(ntt_plan_s &p, void *c, const void *a, const void 
                               cudaStream_t st) {
     const uint64_t ntrans = (uint64_t)batch * p.L;
     W *cw = reinterpret_cast<W *>(c);
-    if (p.streamed)
+    const int form = p.form_for(batch, true);
+    if (form == FORM_STREAMED)
         return run_stream<W, RED, true>(p, const_cast<W *>(reinterpret_cast<const W *>(a)), ntrans, st, cw,
                                         reinterpret_cast<const W *>(b));
-    cudaError_t e = run_pass<W, RED, true, TK_CHUNKS>(p, const_cast<W *>(reinterpret_cast<const W *>(a)),
-                                                      p.d_chunk_inv, ntrans, p.s2, false, st, cw,
-                                                      reinterpret_cast<const W *>(b));
+    cudaError_t e = run_chunk_pass<W, RED, true>(p, form, const_cast<W *>(reinterpret_cast<const W *>(a)),
+                                                 p.d_chunk_inv, ntrans, false, st, cw,
+                                                 reinterpret_cast<const W *>(b));
     if (e != cudaSuccess) return e;
     return run_pass<W, RED, true, TK_COLS>(p, cw, p.d_main_inv, ntrans, p.s1, true, st);
 }

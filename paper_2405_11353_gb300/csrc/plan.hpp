@@ -11,6 +11,10 @@
 namespace nttgb {
 
 enum FusedMode : int { FUSED_STAGES = 0, FUSED_SINGLE = 1, FUSED_TWO_PASS = 2, FUSED_CLUSTER = 3 };
+// Forms of a two-pass direction: chunk pass on one-warp CTAs (2-chunk
+// tiles), on 256-thread CTAs (16-chunk tiles), or both passes in one
+// streamed launch.
+enum TwoPassForm : int { FORM_SMALL = 0, FORM_WIDE = 1, FORM_STREAMED = 2 };
 
 // Largest transform done in one pass of the fused kernel (one CTA holds the
 // whole transform in shared memory): 2^14 words of 4 bytes, 2^13 of 8.
@@ -64,6 +68,19 @@ struct ntt_plan_s {
     uint32_t *d_stream_ctr = nullptr;
     uint32_t stream_seq = 0;
     bool streamed = false;       // NTT_STREAMED: both passes in one streamed launch
+    uint32_t stream_tiles = 0;   // tiles per streamed work item (0: default)
+    // Two-pass form per direction and batch bucket (floor(log2 batch)),
+    // from the tuning table at plan creation; -1: the default (FORM_SMALL
+    // forward, FORM_WIDE inverse; FORM_STREAMED under NTT_STREAMED).
+    int8_t tuned_form[2][32];
+    int form_for(uint32_t batch, bool inverse) const {
+        uint32_t b = 0;
+        while (b < 31 && (2u << b) <= batch) ++b;
+        const int t = tuned_form[inverse ? 1 : 0][b];
+        if (t >= 0) return t;
+        if (streamed) return nttgb::FORM_STREAMED;
+        return inverse ? nttgb::FORM_WIDE : nttgb::FORM_SMALL;
+    }
     uint32_t *d_status = nullptr;
     uint32_t last_launches = 0;
 
@@ -91,6 +108,8 @@ cudaError_t launch_tc(ntt_plan_s &p, void *data, uint32_t batch, bool inverse, c
 cudaError_t launch_tc5(ntt_plan_s &p, void *data, uint32_t batch, bool inverse, cudaStream_t st);
 
 ntt_status ensure_scratch(ntt_plan_s &p, uint32_t batch, cudaStream_t st);
+// Copy the autotuner's table entries for the plan's shape into the plan (tune.cu).
+void apply_tuning(ntt_plan_s &p);
 
 // Plan builder (ntt_plan_create_ex with a cap on the single-pass size).
 ntt_status create_plan(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t L, ntt_variant variant,

@@ -1,0 +1,102 @@
+"""Two-pass forms chosen by the tuning table, and the autotuner itself:
+every combination of forward and inverse form is bit-exact against the
+oracle, and a tuning run records forms that the next plan uses."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import ntt_synth  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def nt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2405_11353_gb300 as nt
+    torch.cuda.init()
+    yield nt
+    nt.ntt_tune_clear()
+
+
+def to_dev(h, w64):
+    a = np.ascontiguousarray(h.astype(np.uint64 if w64 else np.uint32))
+    return torch.from_numpy(a.view(np.int64 if w64 else np.int32).reshape(-1).copy()).cuda()
+
+
+def to_host(t, w64, shape):
+    return t.cpu().numpy().view(np.uint64 if w64 else np.uint32).reshape(shape).astype(np.uint64)
+
+
+def bitrev_rows(X, orc):
+    B, L, N = X.shape
+    return np.stack([np.stack([orc.bitrev_permute(X[b, l]) for l in range(L)]) for b in range(B)])
+
+
+@pytest.mark.parametrize("n,w64", [(16, False), (15, True)])
+def test_every_form_pair_bit_exact(nt, orc, n, w64):
+    N, L, pairs = 1 << n, 3, 2
+    qs = orc.find_primes(60 if w64 else 30, 18, L)
+    psis = [orc.psi(q, N) for q in qs]
+    host = ntt_synth.rns_batch(2300 + n, qs, N, 2 * pairs)
+    A = orc.ntt_batch(host, qs, psis)
+    want_prod = orc.ntt_batch(orc.pointwise_batch(A[:pairs], A[pairs:], qs), qs, psis, inverse=True)
+    flags = nt.NTT_ORDER_BITREV | (nt.NTT_WORD64 if w64 else 0)
+    try:
+        for fwd in range(3):
+            for inv in range(3):
+                nt.ntt_tune_set(N, L, flags, 2 * pairs, fwd, inv)     # forward batch
+                nt.ntt_tune_set(N, L, flags, pairs, fwd, inv)         # product batch
+                p = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, flags)
+                try:
+                    assert nt.ntt_plan_form(p, 2 * pairs) == fwd
+                    assert nt.ntt_plan_form(p, pairs, True) == inv
+                    d = to_dev(host, w64)
+                    nt.ntt_forward(p, d, 2 * pairs)
+                    assert nt.ntt_plan_last_launches(p) == (1 if fwd == 2 else 2)
+                    assert np.array_equal(to_host(d, w64, host.shape), bitrev_rows(A, orc)), (fwd, inv)
+                    half = pairs * L * N
+                    c = torch.empty_like(d[:half])
+                    nt.ntt_pointwise_inverse(p, c, d[:half], d[half:], pairs)
+                    assert np.array_equal(to_host(c, w64, (pairs, L, N)), want_prod), (fwd, inv)
+                    nt.ntt_inverse(p, d, 2 * pairs)
+                    assert np.array_equal(to_host(d, w64, host.shape), host), (fwd, inv)
+                    assert nt.ntt_get_device_status(p) == nt.NTT_OK
+                finally:
+                    nt.ntt_plan_destroy(p)
+    finally:
+        nt.ntt_tune_clear()
+
+
+def test_autotune_records_forms_the_next_plan_uses(nt, orc):
+    N, L, batch = 1 << 16, 5, 4
+    qs = orc.find_primes(30, 17, L)
+    flags = nt.NTT_ORDER_BITREV
+    try:
+        r = nt.ntt_autotune(N, qs, flags, batch)
+        assert r["forward_form"] in (0, 1, 2) and r["inverse_form"] in (0, 1, 2)
+        assert all(ms > 0 for ms in r["forward_ms"] + r["inverse_ms"])
+        assert r["forward_ms"][r["forward_form"]] == min(r["forward_ms"])
+        assert nt.ntt_tune_get(N, L, flags, batch) == r["forward_form"]
+        p = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, flags)
+        try:
+            assert nt.ntt_plan_form(p, batch) == r["forward_form"]
+            assert nt.ntt_plan_form(p, batch, True) == r["inverse_form"]
+            assert nt.ntt_plan_form(p, 4 * batch) == nt.NTT_FORM_SMALL        # untuned bucket: default
+            psis = [orc.psi(q, N) for q in qs]
+            host = ntt_synth.rns_batch(2310, qs, N, batch)
+            d = to_dev(host, False)
+            nt.ntt_forward(p, d, batch)
+            assert np.array_equal(to_host(d, False, host.shape), bitrev_rows(orc.ntt_batch(host, qs, psis), orc))
+            nt.ntt_inverse(p, d, batch)
+            assert np.array_equal(to_host(d, False, host.shape), host)
+        finally:
+            nt.ntt_plan_destroy(p)
+        with pytest.raises(nt.NttError) as e:
+            nt.ntt_autotune(1 << 12, qs, flags, 2)                           # single-pass size
+        assert e.value.status == nt.NTT_ERR_UNSUPPORTED
+    finally:
+        nt.ntt_tune_clear()

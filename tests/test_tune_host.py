@@ -1,0 +1,55 @@
+"""The autotuner's table on the host (no GPU): forms recorded by hand are
+read back, written to the NTT_TUNE_DB file as one JSON object per line, and
+read again by a fresh process."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def nt():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2405_11353_gb300 as nt
+    return nt
+
+
+def _run(code, db):
+    env = dict(os.environ, NTT_TUNE_DB=db, PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    return r.stdout.strip()
+
+
+def test_tune_table_set_get_persist(nt, tmp_path):
+    db = str(tmp_path / "tune.jsonl")
+    out = _run("import paper_2405_11353_gb300 as nt\n"
+               "f = nt.NTT_ORDER_BITREV\n"
+               "nt.ntt_tune_set(1 << 16, 32, f, 16, nt.NTT_FORM_WIDE, nt.NTT_FORM_SMALL)\n"
+               "nt.ntt_tune_set(1 << 15, 4, f | nt.NTT_WORD64, 3, nt.NTT_FORM_STREAMED, nt.NTT_FORM_STREAMED)\n"
+               "print(nt.ntt_tune_get(1 << 16, 32, f, 16), nt.ntt_tune_get(1 << 16, 32, f, 31, True),\n"
+               "      nt.ntt_tune_get(1 << 16, 32, f, 32), nt.ntt_tune_get(1 << 16, 32, 0, 16))\n", db)
+    # batches 16..31 share a bucket; batch 32 and natural order are other keys
+    assert out == "1 0 -1 -1"
+    lines = [json.loads(x) for x in open(db)]
+    assert len(lines) == 2
+    row = [x for x in lines if x["N"] == 1 << 16][0]
+    assert (row["word_bytes"], row["L"], row["bitrev"], row["batch_log2"]) == (4, 32, 1, 4)
+    assert (row["forward_form"], row["inverse_form"]) == (1, 0)
+    out = _run("import paper_2405_11353_gb300 as nt\n"
+               "print(nt.ntt_tune_get(1 << 15, 4, nt.NTT_ORDER_BITREV | nt.NTT_WORD64, 2, True),\n"
+               "      nt.ntt_tune_get(1 << 16, 32, nt.NTT_ORDER_BITREV, 20))\n"
+               "nt.ntt_tune_clear()\n"
+               "print(nt.ntt_tune_get(1 << 16, 32, nt.NTT_ORDER_BITREV, 20))\n", db)
+    assert out.split() == ["2", "1", "-1"]
+
+
+def test_tune_set_rejects_bad_forms(nt):
+    for fwd, inv, batch in [(3, 0, 4), (0, -1, 4), (0, 0, 0)]:
+        with pytest.raises(nt.NttError):
+            nt.ntt_tune_set(1 << 16, 2, 0, batch, fwd, inv)
