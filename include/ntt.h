@@ -383,10 +383,19 @@ typedef struct {
  * into a CUDA graph.  All forward jobs complete before any inverse job
  * starts, so a set holding a forward and an inverse job on the same buffer
  * is a round trip.  flags: NTT_ORDER_BITREV (required: the ragged kernel
- * works in bit-reversed evaluation order) and NTT_RED_*.  The job array
- * and its q arrays are copied; the data buffers must stay valid. */
+ * works in bit-reversed evaluation order), NTT_RED_* and
+ * NTT_RAGGED_TUNE.  The job array and its q arrays are copied; the data
+ * buffers must stay valid (their contents are not touched here). */
+#define NTT_RAGGED_TUNE 0x1000u   /* autotune the work-item size: time items
+                                     of 2, 4, 8 and 16 tiles (three launches
+                                     each) on zeroed scratch copies of the
+                                     jobs' buffers, allocated and freed here,
+                                     and capture the fastest; default 8 */
 ntt_status ntt_ragged_create(ntt_ragged_t *out, const ntt_job *jobs,
                              uint32_t n_jobs, uint32_t flags);
+
+/* Tiles per work item the ragged set was captured with. */
+uint32_t ntt_ragged_item_tiles(ntt_ragged_t r);
 
 /* Replay the captured graph on `stream`. */
 ntt_status ntt_ragged_launch(ntt_ragged_t r, ntt_stream_t stream);

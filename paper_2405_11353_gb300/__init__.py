@@ -45,6 +45,7 @@ NTT_CHECK = 0x100
 NTT_CLUSTER = 0x200
 NTT_STREAMED = 0x400
 NTT_TC_IMMA = 0x800
+NTT_RAGGED_TUNE = 0x1000
 NTT_TEST_STALL = 0x8000
 REDUCTIONS = {"shoup": NTT_RED_SHOUP, "barrett": NTT_RED_BARRETT,
               "montgomery": NTT_RED_MONTGOMERY}
@@ -59,6 +60,7 @@ EXPORTS = [
     "ntt_forward_noalloc", "ntt_forward_prefix", "ntt_inverse_prefix", "ntt_pointwise_inverse",
     "ntt_bconv_create", "ntt_bconv", "ntt_bconv_destroy", "ntt_measure_int_mad_rate",
     "ntt_autotune", "ntt_plan_form", "ntt_tune_set", "ntt_tune_get", "ntt_tune_clear",
+    "ntt_ragged_item_tiles",
 ]
 
 
@@ -128,6 +130,7 @@ def lib():
             "ntt_tune_set": (st, [u32, u32, u32, u32, ctypes.c_int32, ctypes.c_int32]),
             "ntt_tune_get": (ctypes.c_int32, [u32, u32, u32, u32, ctypes.c_int]),
             "ntt_tune_clear": (None, []),
+            "ntt_ragged_item_tiles": (u32, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -353,3 +356,7 @@ def ntt_tune_get(N, L, flags, batch, inverse=False):
 
 def ntt_tune_clear():
     lib().ntt_tune_clear()
+
+
+def ntt_ragged_item_tiles(r):
+    return lib().ntt_ragged_item_tiles(r)

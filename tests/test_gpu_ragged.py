@@ -175,3 +175,38 @@ def test_ragged_other_reductions(nt, orc, red):
     for h, qs, t, w64, N in hosts:
         want = bitrev_rows(orc.ntt_batch(h, qs, [orc.psi(q, N) for q in qs]), orc)
         assert np.array_equal(back(t, w64, h.shape), want)
+
+
+def test_ragged_autotuned_item_size(nt, orc):
+    """NTT_RAGGED_TUNE: the work-item size is timed on scratch copies (the
+    jobs' buffers are untouched by the creation), one of 2/4/8/16 tiles is
+    captured, and the launch is bit-exact (forward jobs of every kind)."""
+    specs = [(12, False, 3, 2), (13, True, 2, 1), (14, False, 4, 3), (16, False, 5, 2), (16, True, 3, 1),
+             (17, False, 2, 1)]
+    hosts, tens, jobs = [], [], []
+    for i, (n, w64, L, batch) in enumerate(specs):
+        qs = primes(orc, w64)[:L]
+        h = ntt_synth.rns_batch(900 + i, qs, 1 << n, batch)
+        t = dev(h, w64)
+        hosts.append((h, qs, n, w64))
+        tens.append(t)
+        jobs.append(dict(data=t, q=qs, N=1 << n, batch=batch, word64=w64, inverse=False))
+    r = nt.ntt_ragged_create(jobs, nt.NTT_ORDER_BITREV | nt.NTT_RAGGED_TUNE)
+    try:
+        assert nt.ntt_ragged_item_tiles(r) in (2, 4, 8, 16)
+        torch.cuda.synchronize()
+        for (h, qs, n, w64), t in zip(hosts, tens):
+            assert np.array_equal(back(t, w64, h.shape), h)            # creation left the data alone
+        nt.ntt_ragged_launch(r)
+        assert nt.ntt_ragged_status(r) == nt.NTT_OK
+        torch.cuda.synchronize()
+    finally:
+        nt.ntt_ragged_destroy(r)
+    for (h, qs, n, w64), t in zip(hosts, tens):
+        psis = [orc.psi(q, 1 << n) for q in qs]
+        assert np.array_equal(back(t, w64, h.shape), bitrev_rows(orc.ntt_batch(h, qs, psis), orc)), (n, w64)
+    r = nt.ntt_ragged_create(jobs, nt.NTT_ORDER_BITREV)
+    try:
+        assert nt.ntt_ragged_item_tiles(r) == 8                     # the default without tuning
+    finally:
+        nt.ntt_ragged_destroy(r)
