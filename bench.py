@@ -446,6 +446,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ragged and wide-word side measurements")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner (default two-pass forms), e.g. for launch lists under ncu")
     ap.add_argument("--extra", default=None,
                     choices=["ragged", "wide_word_u64", "tc_fourstep", "cluster_form", "base_conv",
                              "variants_n1024", "rns_n2p14"],
@@ -490,8 +492,10 @@ def main():
     # the autotuner picks the two-pass form of each direction for the two
     # batch sizes of the step (forward of 16 polynomials, product + inverse
     # of 8) before the plan is made
-    tuning = {"forward_batch%d" % POLYS: nt.ntt_autotune(N, qs, flags, POLYS),
-              "inverse_batch%d" % PAIRS: nt.ntt_autotune(N, qs, flags, PAIRS)}
+    tuning = None
+    if not args.no_tune:
+        tuning = {"forward_batch%d" % POLYS: nt.ntt_autotune(N, qs, flags, POLYS),
+                  "inverse_batch%d" % PAIRS: nt.ntt_autotune(N, qs, flags, PAIRS)}
     plan = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, flags)
     form_names = {v: k for k, v in nt.FORMS.items()}
     forms = {"forward": form_names.get(nt.ntt_plan_form(plan, POLYS)),
