@@ -386,6 +386,21 @@ def rns_n2p14(nt, torch, dev, reps=50):
             "ms_per_step": ms, "value": n / (ms / 1e3), "unit": "NTT/s"}
 
 
+def autotune_survey(nt, torch, dev):
+    """The autotuner on other two-pass shapes: which form wins per
+    direction (0: one-warp chunk CTAs, 1: 16-chunk CTAs, 2: streamed)."""
+    sh = torch.cuda.current_stream(dev).cuda_stream
+    out = {}
+    for name, n, w64, L, batch in (("u32_n2p15_L8_b32", 15, False, 8, 32), ("u32_n2p16_L32_b2", 16, False, 32, 2),
+                                   ("u32_n2p17_L16_b8", 17, False, 16, 8), ("u64_n2p16_L24_b8", 16, True, 24, 8),
+                                   ("u64_n2p14_L8_b64", 14, True, 8, 64)):
+        qs = nt.ntt_find_primes(60 if w64 else 30, 18, L)
+        flags = nt.NTT_ORDER_BITREV | (nt.NTT_WORD64 if w64 else 0)
+        out[name] = nt.ntt_autotune(1 << n, qs, flags, batch, sh)
+    nt.ntt_tune_clear()
+    return out
+
+
 def base_conv(nt, torch, dev, reps=50):
     """Fast RNS base conversion (ntt_bconv) of 8 polynomials, N = 2^16,
     from 32 primes q < 2^30 to 32 other primes: L x K = 1024 multiply-adds
@@ -450,7 +465,7 @@ def main():
                     help="skip the autotuner (default two-pass forms), e.g. for launch lists under ncu")
     ap.add_argument("--extra", default=None,
                     choices=["ragged", "wide_word_u64", "tc_fourstep", "cluster_form", "base_conv",
-                             "variants_n1024", "rns_n2p14"],
+                             "variants_n1024", "rns_n2p14", "autotune_survey"],
                     help="run only this side measurement and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -481,7 +496,7 @@ def main():
     if args.extra:
         fn = {"ragged": ragged_vs_plain, "wide_word_u64": wide_word, "tc_fourstep": tc_fourstep,
               "cluster_form": cluster_form, "base_conv": base_conv, "variants_n1024": variants_n1024,
-              "rns_n2p14": rns_n2p14}[args.extra]
+              "rns_n2p14": rns_n2p14, "autotune_survey": autotune_survey}[args.extra]
         print(json.dumps({args.extra: fn(nt, torch, dev)}), flush=True)
         return 0
     from paper_2405_11353_gb300 import build as nb
@@ -612,7 +627,7 @@ def main():
         for name, fn in (("ragged", ragged_vs_plain), ("wide_word_u64", wide_word),
                          ("tc_fourstep", tc_fourstep), ("cluster_form", cluster_form),
                          ("base_conv", base_conv), ("variants_n1024", variants_n1024),
-                         ("rns_n2p14", rns_n2p14)):
+                         ("rns_n2p14", rns_n2p14), ("autotune_survey", autotune_survey)):
             try:
                 extras[name] = fn(nt, torch, dev)
             except Exception as exc:     # a side measurement never hides the main line
