@@ -451,6 +451,44 @@ def cluster_form(nt, torch, dev, reps=50):
     return out
 
 
+def tw_otf(nt, torch, dev, reps=50):
+    """The chunk-pass twiddles read from the per-chunk tables (default) or
+    made on the fly from 8 seeds per chunk and 256 roots per limb
+    (NTT_TW_OTF), on the headline data: forward of 16 polynomials and the
+    pointwise product fused into the inverse of 8, four rotating copies of
+    the input (512 MiB > L2), with each plan's device table bytes."""
+    qs = nt.ntt_find_primes(30, 17, 32)
+    N, B, L = 1 << 16, 16, 32
+    host = ntt_synth.rns_batch(1005, qs, N, B, dtype=np.uint32)
+    src = torch.from_numpy(host.view(np.int32).reshape(-1).copy()).to(dev)
+    copies = [src.clone() for _ in range(4)]
+    half = B // 2 * L * N
+    c = torch.empty(half, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    out = {"workload": "N=2^16, L=32 primes q<2^30, u32, 16 polys: forward x16; pointwise x8 + inverse x8"}
+    for name, extra in (("tables", 0), ("on_the_fly", nt.NTT_TW_OTF)):
+        # each plan in its fastest forms for these batches (autotuned)
+        for b in (B, B // 2):
+            nt.ntt_autotune(N, qs, nt.NTT_ORDER_BITREV | extra, b, sh)
+        p = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, nt.NTT_ORDER_BITREV | extra)
+        names = {v: k for k, v in nt.FORMS.items()}
+        forms = {"forward": names[nt.ntt_plan_form(p, B)], "product_inverse": names[nt.ntt_plan_form(p, B // 2, True)]}
+        try:
+            it = iter(range(1 << 30))
+            ms_f = _time_loop(torch, stream, lambda: nt.ntt_forward(p, copies[next(it) % 4], B, sh), reps)
+            ms_p = _time_loop(torch, stream, lambda: nt.ntt_pointwise_inverse(
+                p, c, copies[next(it) % 4][:half], copies[next(it) % 4][half:], B // 2, sh), reps)
+            status = nt.ntt_get_device_status(p)
+            out[name] = {"forward_ms": ms_f, "pointwise_inverse_ms": ms_p,
+                         "forward_value": B * L / (ms_f / 1e3), "unit": "NTT/s",
+                         "table_bytes": nt.ntt_plan_table_bytes(p), "two_pass_forms": forms,
+                         "device_status": status}
+        finally:
+            nt.ntt_plan_destroy(p)
+    return out
+
+
 # ------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -465,7 +503,7 @@ def main():
                     help="skip the autotuner (default two-pass forms), e.g. for launch lists under ncu")
     ap.add_argument("--extra", default=None,
                     choices=["ragged", "wide_word_u64", "tc_fourstep", "cluster_form", "base_conv",
-                             "variants_n1024", "rns_n2p14", "autotune_survey"],
+                             "variants_n1024", "rns_n2p14", "autotune_survey", "tw_otf"],
                     help="run only this side measurement and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -496,7 +534,7 @@ def main():
     if args.extra:
         fn = {"ragged": ragged_vs_plain, "wide_word_u64": wide_word, "tc_fourstep": tc_fourstep,
               "cluster_form": cluster_form, "base_conv": base_conv, "variants_n1024": variants_n1024,
-              "rns_n2p14": rns_n2p14, "autotune_survey": autotune_survey}[args.extra]
+              "rns_n2p14": rns_n2p14, "autotune_survey": autotune_survey, "tw_otf": tw_otf}[args.extra]
         print(json.dumps({args.extra: fn(nt, torch, dev)}), flush=True)
         return 0
     from paper_2405_11353_gb300 import build as nb
@@ -627,7 +665,7 @@ def main():
         for name, fn in (("ragged", ragged_vs_plain), ("wide_word_u64", wide_word),
                          ("tc_fourstep", tc_fourstep), ("cluster_form", cluster_form),
                          ("base_conv", base_conv), ("variants_n1024", variants_n1024),
-                         ("rns_n2p14", rns_n2p14), ("autotune_survey", autotune_survey)):
+                         ("rns_n2p14", rns_n2p14), ("autotune_survey", autotune_survey), ("tw_otf", tw_otf)):
             try:
                 extras[name] = fn(nt, torch, dev)
             except Exception as exc:     # a side measurement never hides the main line

@@ -117,6 +117,24 @@ typedef enum {
                                       (fp16 digits, fp32 accumulators in
                                       tensor memory); results identical, kept
                                       for comparison */
+#define NTT_TW_OTF 0x2000u         /* NTT_FUSED, 4-byte words, Shoup
+                                      twiddles (else NTT_ERR_UNSUPPORTED):
+                                      the second pass of a two-pass plan
+                                      (N > 2^14) makes its twiddles on the
+                                      fly instead of reading the per-chunk
+                                      tables.  Entry 2^s + i of chunk r is
+                                      psi^bitrev(2^s (N1 + r) + i) =
+                                      A_s(r) * B_s(i), A_s(r) =
+                                      psi^(2^(7-s) (1 + 2 bitrev(r))) (8
+                                      words per chunk), B_s(i) =
+                                      psi^(2^(n-s) bitrev_s(i)) (255 pairs
+                                      per limb): one modular product and
+                                      its Shoup quotient per entry, when a
+                                      CTA stages a chunk's table.  The
+                                      chunk tables (N + N/32 pairs per limb
+                                      and direction) are not built; results
+                                      identical.  No effect on single-pass
+                                      sizes; not with NTT_STREAMED */
 #define NTT_TEST_STALL 0x8000u     /* test hook, fused and tensor-core
                                       plans: in every forward call one CTA's
                                       first tile (or first matrix copy)
@@ -257,6 +275,11 @@ ntt_status ntt_plan_get_psi(ntt_plan_t plan, uint64_t *psi_out);
  * call on this plan launched (for launch accounting). */
 uint32_t ntt_plan_last_launches(ntt_plan_t plan);
 
+/* Bytes of device memory the plan holds for its tables (twiddles, limb
+ * constants, tensor-core matrices), without the scratch buffer, its status
+ * word and progress counters; 0 for a null plan. */
+uint64_t ntt_plan_table_bytes(ntt_plan_t plan);
+
 /* Human-readable name of a status code (static string). */
 const char *ntt_status_string(ntt_status s);
 
@@ -295,9 +318,10 @@ typedef struct {
  * on the current device (a scratch buffer of batch x L x N zero words,
  * allocated and freed here) and record the fastest per direction in the
  * process-wide tuning table, keyed by (N, word size, L, reduction, order,
- * floor(log2 batch)).  Plans created afterwards with that shape use the
- * recorded forms for calls in that batch bucket (NTT_STREAMED plans keep
- * their form).  If the environment variable NTT_TUNE_DB names a file, the
+ * NTT_TW_OTF or not, floor(log2 batch)).  Plans created afterwards with
+ * that shape use the recorded forms for calls in that batch bucket
+ * (NTT_STREAMED plans keep their form).  NTT_TW_OTF plans have no streamed
+ * form: its time is reported as -1 and it is never chosen.  If the environment variable NTT_TUNE_DB names a file, the
  * table is read from it at first use and rewritten after each tuning (one
  * JSON object per line).  flags: as ntt_plan_create, without NTT_STREAMED,
  * NTT_CHECK or NTT_TEST_STALL.  NTT_ERR_UNSUPPORTED for sizes outside the

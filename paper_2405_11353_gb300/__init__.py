@@ -46,6 +46,7 @@ NTT_CLUSTER = 0x200
 NTT_STREAMED = 0x400
 NTT_TC_IMMA = 0x800
 NTT_RAGGED_TUNE = 0x1000
+NTT_TW_OTF = 0x2000
 NTT_TEST_STALL = 0x8000
 REDUCTIONS = {"shoup": NTT_RED_SHOUP, "barrett": NTT_RED_BARRETT,
               "montgomery": NTT_RED_MONTGOMERY}
@@ -60,7 +61,7 @@ EXPORTS = [
     "ntt_forward_noalloc", "ntt_forward_prefix", "ntt_inverse_prefix", "ntt_pointwise_inverse",
     "ntt_bconv_create", "ntt_bconv", "ntt_bconv_destroy", "ntt_measure_int_mad_rate",
     "ntt_autotune", "ntt_plan_form", "ntt_tune_set", "ntt_tune_get", "ntt_tune_clear",
-    "ntt_ragged_item_tiles",
+    "ntt_ragged_item_tiles", "ntt_plan_table_bytes",
 ]
 
 
@@ -110,6 +111,7 @@ def lib():
             "ntt_get_device_status": (st, [vp, vp]),
             "ntt_plan_get_psi": (st, [vp, u64p]),
             "ntt_plan_last_launches": (u32, [vp]),
+            "ntt_plan_table_bytes": (u64, [vp]),
             "ntt_status_string": (ctypes.c_char_p, [st]),
             "ntt_validate": (st, [u32, u64p, u32, u32]),
             "ntt_default_psi": (st, [u64, u32, u64p]),
@@ -243,6 +245,10 @@ def ntt_plan_get_psi(plan, L):
 
 def ntt_plan_last_launches(plan):
     return int(lib().ntt_plan_last_launches(plan))
+
+
+def ntt_plan_table_bytes(plan):
+    return int(lib().ntt_plan_table_bytes(plan))
 
 
 def ntt_status_string(status):

@@ -16,7 +16,7 @@ namespace {
 
 constexpr uint32_t kKnownFlags =
     NTT_WORD64 | NTT_ORDER_BITREV | NTT_RED_MASK | NTT_CHECK | NTT_CLUSTER | NTT_STREAMED |
-    NTT_TC_IMMA | NTT_TEST_STALL;
+    NTT_TC_IMMA | NTT_TW_OTF | NTT_TEST_STALL;
 constexpr uint32_t kMaxLimbs = 4096;
 
 int red_of(uint32_t flags) {
@@ -62,7 +62,9 @@ void put_pair(std::vector<uint8_t> &out, size_t idx, uint64_t v, uint64_t c, boo
     }
 }
 
-ntt_status upload(void **dptr, const std::vector<uint8_t> &h) {
+// Device copy of a host table; its size is added to *total.
+ntt_status upload(void **dptr, const std::vector<uint8_t> &h, uint64_t *total) {
+    *total += h.size();
     if (cudaMalloc(dptr, h.size()) != cudaSuccess) { *dptr = nullptr; cudaGetLastError(); return NTT_ERR_OOM; }
     if (cudaMemcpy(*dptr, h.data(), h.size(), cudaMemcpyHostToDevice) != cudaSuccess) return NTT_ERR_CUDA;
     return NTT_OK;
@@ -72,7 +74,8 @@ void free_plan_memory(ntt_plan_s *p) {
     void *ptrs[] = {p->d_limb,      p->d_w_fwd,     p->d_w_inv,   p->d_twist,    p->d_untwist,
                     p->d_main_fwd,  p->d_main_inv,  p->d_chunk_fwd, p->d_chunk_inv, p->d_tc,
                     p->d_clu_fwd,   p->d_clu_inv,   p->d_scratch,  p->d_status,
-                    p->d_stream_ctr, p->d_tc5};
+                    p->d_stream_ctr, p->d_tc5, p->d_seed_fwd, p->d_seed_inv,
+                    p->d_root_fwd,  p->d_root_inv};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (p->aux_ready) {
@@ -192,23 +195,34 @@ ntt_status build_tables(ntt_plan_s *p) {
                               p->fused_mode == nttgb::FUSED_STAGES;
     const bool clu_tabs = p->variant == NTT_FUSED && p->fused_mode == nttgb::FUSED_CLUSTER;
     const bool fused_tabs = p->variant == NTT_FUSED && p->fused_mode != nttgb::FUSED_STAGES && !clu_tabs;
-    const bool chunk_tabs = fused_tabs && p->fused_mode == nttgb::FUSED_TWO_PASS;
+    const bool two_pass = fused_tabs && p->fused_mode == nttgb::FUSED_TWO_PASS;
+    const bool chunk_tabs = two_pass && !p->tw_otf;
+    const bool otf_tabs = two_pass && p->tw_otf;
 
     std::vector<LimbConst> lc(L);
     std::vector<uint8_t> wf, wi, tw, ut, mf, mi, cf, ci;
     const size_t tab_bytes = (size_t)L * N * pair_bytes;
     if (variant_tabs) { wf.resize(tab_bytes); wi.resize(tab_bytes); tw.resize(tab_bytes); ut.resize(tab_bytes); }
-    if (fused_tabs) { mf.resize(tab_bytes); mi.resize(tab_bytes); }
     const uint32_t N1 = 1u << p->s1, N2 = 1u << p->s2;
+    // fused main tables: [L][N] (single pass), or [L][N1] for the column
+    // pass of two-pass plans (the chunk pass has its own tables or seeds)
+    const uint32_t NM = two_pass ? N1 : N;
+    if (fused_tabs) { mf.resize((size_t)L * NM * pair_bytes); mi.resize(mf.size()); }
     const uint32_t CP = w64 ? nttgb::chunk_tab_pitch<uint64_t>() : nttgb::chunk_tab_pitch<uint32_t>();
     const size_t chunk_limb = (size_t)N1 * CP;       // pairs per limb, chunk tables
     if (chunk_tabs) { cf.resize(L * chunk_limb * pair_bytes); ci.resize(L * chunk_limb * pair_bytes); }
+    // NTT_TW_OTF (4-byte words): per limb, 8 stage seeds per chunk and the
+    // 256-entry root table of the chunk stages (see the kernels' staging)
+    std::vector<uint8_t> sf, si, rf, ri;
+    if (otf_tabs) {
+        sf.resize((size_t)L * N1 * 8 * 4); si.resize(sf.size());
+        rf.resize((size_t)L * N2 * 8); ri.resize(rf.size());
+    }
     std::vector<uint8_t> kf, ki;   // cluster form tables (below)
     if (clu_tabs) { kf.resize((size_t)L * 8 * (8192 + 16) * pair_bytes); ki.resize(kf.size()); }
     // main-table position of entry i (see level_pos in modarith.cuh)
     auto main_pos = [&](uint32_t i) -> uint32_t {
-        if (p->fused_mode == nttgb::FUSED_SINGLE) return nttgb::level_pos(i, n);
-        return i < N1 ? nttgb::level_pos(i, p->s1) : i;
+        return nttgb::level_pos(i, p->fused_mode == nttgb::FUSED_SINGLE ? n : p->s1);
     };
 
     std::vector<uint64_t> pw(N), pwi(N);
@@ -252,10 +266,12 @@ ntt_status build_tables(ntt_plan_s *p) {
             }
         }
         if (fused_tabs) {
-            for (uint32_t i = 0; i < N; ++i) {
+            // entry i < NM: psi^bitrev_n(i) (for two-pass plans i < N1, the
+            // column pass's stages)
+            for (uint32_t i = 0; i < NM; ++i) {
                 uint32_t r = H::bitrev(i, (int)n);
-                enc(pw[r], v, cc); put_pair(mf, base + main_pos(i), v, cc, w64);
-                enc(pwi[r], v, cc); put_pair(mi, base + main_pos(i), v, cc, w64);
+                enc(pw[r], v, cc); put_pair(mf, (size_t)l * NM + main_pos(i), v, cc, w64);
+                enc(pwi[r], v, cc); put_pair(mi, (size_t)l * NM + main_pos(i), v, cc, w64);
             }
         }
         if (chunk_tabs) {
@@ -278,6 +294,41 @@ ntt_status build_tables(ntt_plan_s *p) {
                         enc(pwi[e], v, cc); put_pair(ci, at, v, cc, w64);
                     }
             }
+        }
+    }
+    if (otf_tabs) {
+        // chunk r, stage s (0 = first of the pass), entry i < 2^s: with
+        // m = 2^s (N1 + r) + i, bitrev_n(m) = 2^(7-s) (1 + 2 bitrev_s1(r)) +
+        // 2^(n-s) bitrev_s(i) (the bit fields of m are disjoint), so
+        // psi^bitrev(m) = A_s(r) * B_s(i):
+        //   seeds [l][r][s]        A_s(r), plain words
+        //   roots [l][level_pos]   B_s(i) as Shoup pairs, entry 2^s + i in
+        //                          the chunk tables' level-transposed order
+        std::vector<uint64_t> pw2(N), pwi2(N);
+        for (uint32_t l = 0; l < L; ++l) {
+            const uint64_t q = p->q[l], psi = p->psi[l], psi_inv = H::invm(psi, q);
+            Enc enc{q, W, p->red, (uint64_t)(uint32_t)H::inv_pow2_64(q)};
+            pw2[0] = 1; pwi2[0] = 1;
+            for (uint32_t i = 1; i < N; ++i) { pw2[i] = H::mulm(pw2[i - 1], psi, q); pwi2[i] = H::mulm(pwi2[i - 1], psi_inv, q); }
+            uint32_t *sfw = reinterpret_cast<uint32_t *>(sf.data()) + (size_t)l * N1 * 8;
+            uint32_t *siw = reinterpret_cast<uint32_t *>(si.data()) + (size_t)l * N1 * 8;
+            for (uint32_t r = 0; r < N1; ++r)
+                for (uint32_t s = 0; s < p->s2; ++s) {
+                    const uint64_t e = (1ull << (p->s2 - 1 - s)) * (1 + 2 * (uint64_t)H::bitrev(r, (int)p->s1));
+                    sfw[r * 8 + s] = (uint32_t)pw2[e];
+                    siw[r * 8 + s] = (uint32_t)pwi2[e];
+                }
+            const size_t rb = (size_t)l * N2;
+            uint64_t v, cc;
+            put_pair(rf, rb, 0, 0, w64);
+            put_pair(ri, rb, 0, 0, w64);
+            for (uint32_t s = 0; s < p->s2; ++s)
+                for (uint32_t ip = 0; ip < (1u << s); ++ip) {
+                    const uint64_t e = (1ull << (n - s)) * (uint64_t)H::bitrev(ip, (int)s);
+                    const size_t at = rb + nttgb::level_pos((1u << s) + ip, p->s2);
+                    enc(pw2[e], v, cc); put_pair(rf, at, v, cc, w64);
+                    enc(pwi2[e], v, cc); put_pair(ri, at, v, cc, w64);
+                }
         }
     }
     std::vector<uint8_t> tcb;
@@ -331,30 +382,36 @@ ntt_status build_tables(ntt_plan_s *p) {
     std::vector<uint8_t> lcb(sizeof(LimbConst) * L);
     std::memcpy(lcb.data(), lc.data(), lcb.size());
     ntt_status s;
-    if (!tcb.empty() && (s = upload(&p->d_tc, tcb)) != NTT_OK) return s;
-    if (!tc5b.empty() && (s = upload(&p->d_tc5, tc5b)) != NTT_OK) return s;
-    if ((s = upload((void **)&p->d_limb, lcb)) != NTT_OK) return s;
+    if (!tcb.empty() && (s = upload(&p->d_tc, tcb, &p->table_bytes)) != NTT_OK) return s;
+    if (!tc5b.empty() && (s = upload(&p->d_tc5, tc5b, &p->table_bytes)) != NTT_OK) return s;
+    if ((s = upload((void **)&p->d_limb, lcb, &p->table_bytes)) != NTT_OK) return s;
     if (variant_tabs) {
-        if ((s = upload(&p->d_w_fwd, wf)) != NTT_OK) return s;
-        if ((s = upload(&p->d_w_inv, wi)) != NTT_OK) return s;
-        if ((s = upload(&p->d_twist, tw)) != NTT_OK) return s;
-        if ((s = upload(&p->d_untwist, ut)) != NTT_OK) return s;
+        if ((s = upload(&p->d_w_fwd, wf, &p->table_bytes)) != NTT_OK) return s;
+        if ((s = upload(&p->d_w_inv, wi, &p->table_bytes)) != NTT_OK) return s;
+        if ((s = upload(&p->d_twist, tw, &p->table_bytes)) != NTT_OK) return s;
+        if ((s = upload(&p->d_untwist, ut, &p->table_bytes)) != NTT_OK) return s;
     }
     if (fused_tabs) {
-        if ((s = upload(&p->d_main_fwd, mf)) != NTT_OK) return s;
-        if ((s = upload(&p->d_main_inv, mi)) != NTT_OK) return s;
+        if ((s = upload(&p->d_main_fwd, mf, &p->table_bytes)) != NTT_OK) return s;
+        if ((s = upload(&p->d_main_inv, mi, &p->table_bytes)) != NTT_OK) return s;
     }
     if (clu_tabs) {
-        if ((s = upload(&p->d_clu_fwd, kf)) != NTT_OK) return s;
-        if ((s = upload(&p->d_clu_inv, ki)) != NTT_OK) return s;
+        if ((s = upload(&p->d_clu_fwd, kf, &p->table_bytes)) != NTT_OK) return s;
+        if ((s = upload(&p->d_clu_inv, ki, &p->table_bytes)) != NTT_OK) return s;
     }
     if (chunk_tabs) {
-        if ((s = upload(&p->d_chunk_fwd, cf)) != NTT_OK) return s;
-        if ((s = upload(&p->d_chunk_inv, ci)) != NTT_OK) return s;
+        if ((s = upload(&p->d_chunk_fwd, cf, &p->table_bytes)) != NTT_OK) return s;
+        if ((s = upload(&p->d_chunk_inv, ci, &p->table_bytes)) != NTT_OK) return s;
+    }
+    if (otf_tabs) {
+        if ((s = upload(&p->d_seed_fwd, sf, &p->table_bytes)) != NTT_OK) return s;
+        if ((s = upload(&p->d_seed_inv, si, &p->table_bytes)) != NTT_OK) return s;
+        if ((s = upload(&p->d_root_fwd, rf, &p->table_bytes)) != NTT_OK) return s;
+        if ((s = upload(&p->d_root_inv, ri, &p->table_bytes)) != NTT_OK) return s;
     }
     if (cudaMalloc((void **)&p->d_status, sizeof(uint32_t)) != cudaSuccess) { cudaGetLastError(); return NTT_ERR_OOM; }
     if (cudaMemset(p->d_status, 0, sizeof(uint32_t)) != cudaSuccess) return NTT_ERR_CUDA;
-    if (chunk_tabs) {
+    if (two_pass) {
         const size_t bytes = (size_t)nttgb::kStreamRing * nttgb::stream_set_words(L) * sizeof(uint32_t);
         if (cudaMalloc((void **)&p->d_stream_ctr, bytes) != cudaSuccess) { cudaGetLastError(); return NTT_ERR_OOM; }
         if (cudaMemset(p->d_stream_ctr, 0, bytes) != cudaSuccess) return NTT_ERR_CUDA;
@@ -509,6 +566,11 @@ ntt_status create_plan(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t
     if (variant == NTT_TC_FOURSTEP &&
         (N != (1u << 16) || (flags & NTT_WORD64) || (flags & NTT_RED_MASK) != NTT_RED_SHOUP))
         return NTT_ERR_UNSUPPORTED;
+    // twiddles made on the fly: the fused path's chunk pass, 4-byte words,
+    // Shoup pairs; not with the streamed one-launch form
+    if ((flags & NTT_TW_OTF) && (variant != NTT_FUSED || (flags & NTT_WORD64) ||
+                                 (flags & NTT_RED_MASK) != NTT_RED_SHOUP || (flags & NTT_STREAMED)))
+        return NTT_ERR_UNSUPPORTED;
     ntt_plan_s *p = new (std::nothrow) ntt_plan_s();
     if (!p) return NTT_ERR_OOM;
     p->N = N;
@@ -542,6 +604,7 @@ ntt_status create_plan(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t
         else {
             p->fused_mode = nttgb::FUSED_TWO_PASS;
             p->streamed = (flags & NTT_STREAMED) != 0;
+            p->tw_otf = (flags & NTT_TW_OTF) != 0;
             p->s2 = nttgb::kChunkLog;
             p->s1 = p->logN - p->s2;
         }
@@ -715,5 +778,7 @@ ntt_status ntt_plan_get_psi(ntt_plan_t plan, uint64_t *psi_out) {
 }
 
 uint32_t ntt_plan_last_launches(ntt_plan_t plan) { return plan ? plan->last_launches : 0; }
+
+uint64_t ntt_plan_table_bytes(ntt_plan_t plan) { return plan ? plan->table_bytes : 0; }
 
 }  // extern "C"

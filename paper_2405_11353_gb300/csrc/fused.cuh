@@ -41,7 +41,11 @@ template <class W> struct FArgs {
                               // the fused pointwise + inverse first pass)
     const W *pw_b;            // inverse chunk pass: multiply each word by this
                               // operand's word first (Eq. 3), or null
-    const Tw<W> *tw;          // [L][N] table of this pass
+    const Tw<W> *tw;          // table of this pass: [L][2^LOGS] pairs (single
+                              // and column passes), [L][N1][pitch] (chunks)
+    const W *tw_seed;         // chunk passes with twiddles made on the fly
+    const Tw<W> *tw_root;     // (4-byte words, Shoup): [L][N1][8] stage
+                              // seeds, [L][256] root pairs; else null
     const LimbConst *lc;
     uint32_t *status;         // plan status word (bit 1: timeout)
     uint64_t ntrans;          // batch * L
@@ -394,7 +398,7 @@ struct PipeState {
 // twiddles (staged in shared memory) for many consecutive tiles.  `bar`
 // holds NS tile barriers and one twiddle barrier, initialised by the caller.
 // Returns false if a wait ran out of time (the abort has been recorded).
-template <class W, int RED, bool INV, int LOGS, int KIND, int P>
+template <class W, int RED, bool INV, int LOGS, int KIND, int P, bool OTF_K = false>
 __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *tmap, uint32_t t_begin,
                                           uint32_t t_end, unsigned char *base, uint64_t *bar, PipeState &ps) {
     constexpr uint32_t S = 1u << LOGS;
@@ -419,6 +423,10 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     // every tile kind under a 128-register cap) refill at the end of each
     // tile and load constants per tile, which keeps them free of spills.
     constexpr bool LATE_REFILL = P == 0 || P == 3;
+    // chunk tables made on the fly from the plan's seeds (OTF_K: the
+    // per-plan chunk kernels of NTT_TW_OTF plans, 4-byte words, Shoup)
+    constexpr bool OTF = OTF_K && KIND == TK_CHUNKS && LOGS == 8 && sizeof(W) == 4 && RED == RED_SHOUP && P != 1 && TWS;
+    static_assert(!OTF_K || OTF, "twiddles made on the fly: 4-byte-word Shoup chunk kernels only");
     W *stage = reinterpret_cast<W *>(base);
     Tw<W> *tws = reinterpret_cast<Tw<W> *>(stage + (size_t)NS * BW);
     if (t_begin >= t_end) return true;
@@ -454,10 +462,11 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     auto cur_t = [&](const Cur &c) -> uint64_t {
         return KIND == TK_SINGLE ? (uint64_t)c.p : (uint64_t)c.p * L + c.l;
     };
-    // twiddle table of limb l (column pass) or of the chunks of group g
+    // twiddle table of limb l (column pass: [L][N1] tables) or of the
+    // chunks of group g
     auto tw_src = [&](uint32_t l, uint32_t g) -> const Tw<W> * {
         if (KIND == TK_CHUNKS) return a.tw + (size_t)l * N1 * CP + (size_t)g * K * CP;
-        return a.tw + (size_t)l * N;
+        return a.tw + (size_t)l * S;
     };
     auto issue = [&](const Cur &c, uint32_t s) {
         const uint64_t t = cur_t(c);
@@ -549,13 +558,49 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
                 // reading the old table (without LATE_REFILL the end-of-tile
                 // barrier has already waited for it)
                 if (LATE_REFILL && i > 0) __syncthreads();
-                if (tid == 0) {
-                    fence_proxy_async();
-                    mbar_expect_tx(&bar[NS], TWP * (uint32_t)sizeof(Tw<W>));
-                    bulk_g2s(tws, tw_src(cur.l, cur.g), TWP * (uint32_t)sizeof(Tw<W>), &bar[NS]);
+                if constexpr (OTF) {
+                    // (the launcher checks that the plan supplies seeds)
+                    // the K chunk tables of this tile from their seeds:
+                    // entry j of chunk r at stage level lv = floor(log2 j)
+                    // is A_lv(r) * B[j] (see the plan's table builder)
+                    // (every thread makes S / T = 16 entries, in two
+                    // batches of 8 whose loads are all issued first, so
+                    // their latencies overlap)
+                    constexpr uint32_t NT = K * T, PER = K * S / NT, BATCH = 8;
+                    static_assert(PER % BATCH == 0, "entries per thread");
+                    const W *sd = a.tw_seed + ((size_t)cur.l * N1 + pos0) * 8;
+                    const Tw<W> *rt = a.tw_root + (size_t)cur.l * S;
+#pragma unroll 1
+                    for (uint32_t b0 = 0; b0 < PER; b0 += BATCH) {
+                        W sa[BATCH];
+                        Tw<W> rb[BATCH];
+#pragma unroll
+                        for (uint32_t i2 = 0; i2 < BATCH; ++i2) {
+                            const uint32_t e = tid + (b0 + i2) * NT, j = e & (S - 1);
+                            sa[i2] = __ldg(sd + (e >> LOGS) * 8 + (j ? 31 - __clz(j) : 0));
+                            rb[i2] = ldtw(rt + j);
+                        }
+#pragma unroll
+                        for (uint32_t i2 = 0; i2 < BATCH; ++i2) {
+                            const uint32_t e = tid + (b0 + i2) * NT, j = e & (S - 1);
+                            Tw<W> tv{0, 0};
+                            if (j != 0) {
+                                tv.w = mul_full<RED_SHOUP, W>(sa[i2], rb[i2], kk);
+                                tv.c = shoup_quotient(tv.w, kk);
+                            }
+                            tws[(e >> LOGS) * CP + j] = tv;
+                        }
+                    }
+                    __syncthreads();
+                } else {
+                    if (tid == 0) {
+                        fence_proxy_async();
+                        mbar_expect_tx(&bar[NS], TWP * (uint32_t)sizeof(Tw<W>));
+                        bulk_g2s(tws, tw_src(cur.l, cur.g), TWP * (uint32_t)sizeof(Tw<W>), &bar[NS]);
+                    }
+                    ok = ok && mbar_wait_bounded(&bar[NS], tw_phase & 1u);
+                    ++tw_phase;
                 }
-                ok = ok && mbar_wait_bounded(&bar[NS], tw_phase & 1u);
-                ++tw_phase;
                 tw_key = key;
             }
             twb = tws + (KIND == TK_CHUNKS ? k * CP : 0);
@@ -731,7 +776,7 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
 
 // Per-plan fused pass: CTA c processes tiles [c T / G, (c+1) T / G).
 // PP: the tile configuration (see tile_k): 0, or 3 for 16-chunk tiles.
-template <class W, int RED, bool INV, int LOGS, int KIND, int PP>
+template <class W, int RED, bool INV, int LOGS, int KIND, int PP, bool OTF_K = false>
 __global__ void __launch_bounds__(sizeof(W) == 4 ? 1024 : 512)
 k_fused(const __grid_constant__ FArgs<W> a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -749,7 +794,7 @@ k_fused(const __grid_constant__ FArgs<W> a) {
     PipeState ps{{0, 0}, 0};
     const uint32_t t_begin = (uint32_t)((uint64_t)blockIdx.x * a.ntiles / gridDim.x);
     const uint32_t t_end = (uint32_t)((uint64_t)(blockIdx.x + 1) * a.ntiles / gridDim.x);
-    run_tiles<W, RED, INV, LOGS, KIND, PP>(a, &a.tmap, t_begin, t_end, base, bar, ps);
+    run_tiles<W, RED, INV, LOGS, KIND, PP, OTF_K>(a, &a.tmap, t_begin, t_end, base, bar, ps);
 }
 
 template <class W, int LOGS, int KIND, bool INV, int P = 0> __host__ __device__ constexpr size_t fused_smem_bytes() {

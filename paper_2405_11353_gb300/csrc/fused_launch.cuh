@@ -14,9 +14,9 @@ namespace nttgb {
 
 static_assert(kN2Log == (uint32_t)kChunkLog, "two-pass split must match the plan's chunk size");
 
-template <class W, int RED, bool INV, int LOGS, int KIND, int PP>
+template <class W, int RED, bool INV, int LOGS, int KIND, int PP, bool OTF_K = false>
 cudaError_t launch_pass(const FArgs<W> &a, uint32_t threads, size_t smem, cudaStream_t st) {
-    auto kern = k_fused<W, RED, INV, LOGS, KIND, PP>;
+    auto kern = k_fused<W, RED, INV, LOGS, KIND, PP, OTF_K>;
     // persistent grid: as many CTAs as fit on the GPU at once
     static int resident = 0;
     if (!resident) {
@@ -93,7 +93,7 @@ inline cudaError_t make_rows_tmap(CUtensorMap *m, void *data, bool w64, uint64_t
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <class W, int RED, bool INV, int KIND, int PP, int LOGS = 4>
+template <class W, int RED, bool INV, int KIND, int PP, bool OTF_K = false, int LOGS = 4>
 cudaError_t pass_dispatch(int logS, const FArgs<W> &a, uint32_t threads, size_t smem, cudaStream_t st) {
     constexpr int MAXS = KIND == TK_SINGLE ? (sizeof(W) == 4 ? kSingleMaxLog32 : kSingleMaxLog64)
                                            : (KIND == TK_COLS ? 9 : kChunkLog);
@@ -102,9 +102,9 @@ cudaError_t pass_dispatch(int logS, const FArgs<W> &a, uint32_t threads, size_t 
         return cudaErrorInvalidValue;
     } else {
         if constexpr (LOGS >= MINS) {
-            if (logS == LOGS) return launch_pass<W, RED, INV, LOGS, KIND, PP>(a, threads, smem, st);
+            if (logS == LOGS) return launch_pass<W, RED, INV, LOGS, KIND, PP, OTF_K>(a, threads, smem, st);
         }
-        return pass_dispatch<W, RED, INV, KIND, PP, LOGS + 1>(logS, a, threads, smem, st);
+        return pass_dispatch<W, RED, INV, KIND, PP, OTF_K, LOGS + 1>(logS, a, threads, smem, st);
     }
 }
 
@@ -154,6 +154,13 @@ cudaError_t fill_pass(FArgs<W> &a, ntt_plan_s &p, W *data, const void *tw, uint6
     a.pw_b = pw_b;
     a.status = p.d_status;
     a.tw = reinterpret_cast<const Tw<W> *>(tw);
+    if (KIND == TK_CHUNKS && p.tw_otf && sizeof(W) == 4) {
+        // chunk twiddles made on the fly from seeds (NTT_TW_OTF)
+        a.tw_seed = reinterpret_cast<const W *>(INV ? p.d_seed_inv : p.d_seed_fwd);
+        a.tw_root = reinterpret_cast<const Tw<W> *>(INV ? p.d_root_inv : p.d_root_fwd);
+    }
+    // every pass reads a table or, for chunk passes, makes one from seeds
+    if (!a.tw && !(KIND == TK_CHUNKS && a.tw_seed && a.tw_root)) return cudaErrorInvalidValue;
     a.lc = p.d_limb;
     a.ntrans = ntrans;
     a.logN = p.logN;
@@ -184,7 +191,7 @@ cudaError_t fill_pass(FArgs<W> &a, ntt_plan_s &p, W *data, const void *tw, uint6
 
 // One pass as its own launch; PP: tile configuration (0, or 3 for
 // 16-chunk tiles in a chunk pass).
-template <class W, int RED, bool INV, int KIND, int PP = 0>
+template <class W, int RED, bool INV, int KIND, int PP = 0, bool OTF_K = false>
 cudaError_t run_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, int logS, bool final_pass,
                      cudaStream_t st, W *out = nullptr, const W *pw_b = nullptr) {
     FArgs<W> a;
@@ -194,13 +201,24 @@ cudaError_t run_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, in
     if (e != cudaSuccess) return e;
     size_t smem = smem_for<W, KIND, INV, PP>(logS);
     ++p.last_launches;
-    return pass_dispatch<W, RED, INV, KIND, PP>(logS, a, K * T, smem, st);
+    if (OTF_K != (a.tw_seed != nullptr)) return cudaErrorInvalidValue;   // kernel and plan must agree
+    return pass_dispatch<W, RED, INV, KIND, PP, OTF_K>(logS, a, K * T, smem, st);
 }
 
 // The chunk pass in the plan's form for this direction.
 template <class W, int RED, bool INV>
 cudaError_t run_chunk_pass(ntt_plan_s &p, int form, W *data, const void *tw, uint64_t ntrans, bool final_pass,
                            cudaStream_t st, W *out = nullptr, const W *pw_b = nullptr) {
+    if constexpr (sizeof(W) == 4 && RED == RED_SHOUP) {
+        // NTT_TW_OTF plans: kernels that make the chunk tables from seeds
+        if (p.tw_otf) {
+            if (form == FORM_SMALL)
+                return run_pass<W, RED, INV, TK_CHUNKS, 0, true>(p, data, tw, ntrans, (int)p.s2, final_pass, st, out,
+                                                                 pw_b);
+            return run_pass<W, RED, INV, TK_CHUNKS, 3, true>(p, data, tw, ntrans, (int)p.s2, final_pass, st, out,
+                                                             pw_b);
+        }
+    }
     if (form == FORM_SMALL)
         return run_pass<W, RED, INV, TK_CHUNKS, 0>(p, data, tw, ntrans, (int)p.s2, final_pass, st, out, pw_b);
     return run_pass<W, RED, INV, TK_CHUNKS, 3>(p, data, tw, ntrans, (int)p.s2, final_pass, st, out, pw_b);

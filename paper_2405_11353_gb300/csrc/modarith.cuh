@@ -176,6 +176,19 @@ template <int RED, class W> __device__ __forceinline__ void gs_bfly_last(W &u, W
     v = mul_lazy<RED>(d, twn, k);
 }
 
+// Shoup quotient of a twiddle made on the device: floor(w 2^32 / q) for
+// w < q < 2^30, from mu = floor(2^64 / q) = vh 2^32 + vl.  The Barrett
+// estimate floor(w 2^32 mu / 2^64) = w vh + hi(w vl) is floor(w 2^32 / q)
+// or one less (w 2^32 / 2^64 < 1/4); it is below 2^32, so it may be formed
+// modulo 2^32, and so may the remainder w 2^32 - e q, which lies in
+// [0, 2q): one comparison settles it.
+__device__ __forceinline__ uint32_t shoup_quotient(uint32_t w, const Lc<uint32_t> &k) {
+    const uint32_t vh = (uint32_t)(k.mu >> 32), vl = (uint32_t)k.mu;
+    uint32_t e = w * vh + __umulhi(w, vl);
+    const uint32_t r = 0u - e * k.q;
+    return r >= k.q ? e + 1 : e;
+}
+
 // Fully reduced add / sub (Algorithm 4 with the >= reading), a, b in [0, q).
 template <class W> __device__ __forceinline__ W add_mod(W a, W b, W q) { return csub<W>(a + b, q); }
 template <class W> __device__ __forceinline__ W sub_mod(W a, W b, W q) { return csub<W>(a - b + q, q); }

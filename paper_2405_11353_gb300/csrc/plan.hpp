@@ -50,11 +50,17 @@ struct ntt_plan_s {
     void *d_w_inv = nullptr;     // omega^-e
     void *d_twist = nullptr;     // psi^n
     void *d_untwist = nullptr;   // N^-1 psi^-n
-    // fused tables, [L][N] twiddle pairs each
+    // fused tables: [L][N] twiddle pairs each for single-pass plans, [L][N1]
+    // (the column pass's entries) for two-pass plans
     void *d_main_fwd = nullptr;  // psi^bitrev(i)
     void *d_main_inv = nullptr;  // psi^-bitrev(i)
     void *d_chunk_fwd = nullptr; // pass-B per-chunk layout of psi^bitrev
     void *d_chunk_inv = nullptr;
+    // NTT_TW_OTF two-pass plans instead of the chunk tables: [L][N1][8]
+    // stage seeds (words) and [L][256] root pairs per direction
+    bool tw_otf = false;
+    void *d_seed_fwd = nullptr, *d_seed_inv = nullptr;
+    void *d_root_fwd = nullptr, *d_root_inv = nullptr;
     void *d_tc = nullptr;        // tensor-core four-step tables (see tc.cu)
     void *d_tc5 = nullptr;       // their matrices as fp16 balanced digits (tc5.cu)
     bool tc_imma = false;        // NTT_TC_IMMA: warp-level mma.sync form
@@ -77,12 +83,13 @@ struct ntt_plan_s {
         uint32_t b = 0;
         while (b < 31 && (2u << b) <= batch) ++b;
         const int t = tuned_form[inverse ? 1 : 0][b];
-        if (t >= 0) return t;
+        if (t >= 0 && !(tw_otf && t == nttgb::FORM_STREAMED)) return t;
         if (streamed) return nttgb::FORM_STREAMED;
         return inverse ? nttgb::FORM_WIDE : nttgb::FORM_SMALL;
     }
     uint32_t *d_status = nullptr;
     uint32_t last_launches = 0;
+    uint64_t table_bytes = 0;    // device bytes of the tables above
 
     // ntt_polymul_host pipeline: copy streams and events, made on first use
     bool aux_ready = false;

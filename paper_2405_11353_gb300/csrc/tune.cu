@@ -7,7 +7,9 @@
 // size, the limb count and the batch, so ntt_autotune times all three on
 // the current device for one shape and records the fastest per direction
 // in a process-wide table keyed by (N, word size, L, reduction, order,
-// floor(log2 batch)).  ntt_plan_create copies the table's entries for its
+// twiddles made on the fly or read, floor(log2 batch)).  Plans whose chunk
+// twiddles are made on the fly (NTT_TW_OTF) have no streamed form: its time
+// is reported as -1 and it is never chosen.  ntt_plan_create copies the table's entries for its
 // shape into the plan; each call then looks up its batch bucket.  The
 // table is also kept in the JSON-lines file named by NTT_TUNE_DB, read at
 // first use and rewritten after every tuning, so tuning survives the
@@ -28,9 +30,10 @@ namespace nttgb {
 namespace {
 
 struct TuneKey {
-    uint32_t N, word, L, red, bitrev, bucket;
+    uint32_t N, word, L, red, bitrev, bucket, otf;
     bool operator<(const TuneKey &o) const {
-        return std::tie(N, word, L, red, bitrev, bucket) < std::tie(o.N, o.word, o.L, o.red, o.bitrev, o.bucket);
+        return std::tie(N, word, L, red, bitrev, bucket, otf) <
+               std::tie(o.N, o.word, o.L, o.red, o.bitrev, o.bucket, o.otf);
     }
 };
 struct TuneVal {
@@ -59,13 +62,25 @@ void load_locked() {
     while (std::fgets(line, sizeof(line), f)) {
         TuneKey k;
         TuneVal v;
-        const int n = std::sscanf(line,
-                                  "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
-                                  "\"batch_log2\": %u, \"forward_form\": %d, \"inverse_form\": %d, "
-                                  "\"forward_ms\": [%f, %f, %f], \"inverse_ms\": [%f, %f, %f]}",
-                                  &k.N, &k.word, &k.L, &k.red, &k.bitrev, &k.bucket, &v.form[0], &v.form[1],
-                                  &v.ms[0][0], &v.ms[0][1], &v.ms[0][2], &v.ms[1][0], &v.ms[1][1], &v.ms[1][2]);
-        if (n != 14 || k.bucket > 31 || v.form[0] < 0 || v.form[0] > 2 || v.form[1] < 0 || v.form[1] > 2) continue;
+        int n = std::sscanf(line,
+                            "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
+                            "\"tw_otf\": %u, \"batch_log2\": %u, \"forward_form\": %d, \"inverse_form\": %d, "
+                            "\"forward_ms\": [%f, %f, %f], \"inverse_ms\": [%f, %f, %f]}",
+                            &k.N, &k.word, &k.L, &k.red, &k.bitrev, &k.otf, &k.bucket, &v.form[0], &v.form[1],
+                            &v.ms[0][0], &v.ms[0][1], &v.ms[0][2], &v.ms[1][0], &v.ms[1][1], &v.ms[1][2]);
+        if (n != 15) {
+            // lines written before the twiddle-mode field existed
+            k.otf = 0;
+            n = 1 + std::sscanf(line,
+                                "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
+                                "\"batch_log2\": %u, \"forward_form\": %d, \"inverse_form\": %d, "
+                                "\"forward_ms\": [%f, %f, %f], \"inverse_ms\": [%f, %f, %f]}",
+                                &k.N, &k.word, &k.L, &k.red, &k.bitrev, &k.bucket, &v.form[0], &v.form[1],
+                                &v.ms[0][0], &v.ms[0][1], &v.ms[0][2], &v.ms[1][0], &v.ms[1][1], &v.ms[1][2]);
+        }
+        if (n != 15 || k.bucket > 31 || k.otf > 1 || v.form[0] < 0 || v.form[0] > 2 || v.form[1] < 0 ||
+            v.form[1] > 2)
+            continue;
         g_table[k] = v;
     }
     std::fclose(f);
@@ -81,16 +96,17 @@ void save_locked() {
         const TuneVal &v = e.second;
         std::fprintf(f,
                      "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
-                     "\"batch_log2\": %u, \"forward_form\": %d, \"inverse_form\": %d, "
+                     "\"tw_otf\": %u, \"batch_log2\": %u, \"forward_form\": %d, \"inverse_form\": %d, "
                      "\"forward_ms\": [%.6f, %.6f, %.6f], \"inverse_ms\": [%.6f, %.6f, %.6f]}\n",
-                     k.N, k.word, k.L, k.red, k.bitrev, k.bucket, v.form[0], v.form[1], v.ms[0][0], v.ms[0][1],
+                     k.N, k.word, k.L, k.red, k.bitrev, k.otf, k.bucket, v.form[0], v.form[1], v.ms[0][0], v.ms[0][1],
                      v.ms[0][2], v.ms[1][0], v.ms[1][1], v.ms[1][2]);
     }
     std::fclose(f);
 }
 
 TuneKey key_of(const ntt_plan_s &p, uint32_t bucket) {
-    return TuneKey{p.N, (uint32_t)p.word_bytes(), p.L, (uint32_t)p.red, p.bitrev_order ? 1u : 0u, bucket};
+    return TuneKey{p.N, (uint32_t)p.word_bytes(), p.L, (uint32_t)p.red, p.bitrev_order ? 1u : 0u, bucket,
+                   p.tw_otf ? 1u : 0u};
 }
 
 }  // namespace
@@ -139,6 +155,10 @@ ntt_status ntt_autotune(uint32_t N, const uint64_t *q, uint32_t L, uint32_t flag
     // time every form of each direction on zero words (valid residues)
     for (int dir = 0; dir < 2 && ok; ++dir) {
         for (int form = 0; form < 3 && ok; ++form) {
+            if (form == nttgb::FORM_STREAMED && p->tw_otf) {
+                v.ms[dir][form] = -1.f;
+                continue;
+            }
             p->tuned_form[dir][bucket] = (int8_t)form;
             auto call = [&]() {
                 return dir == 0 ? ntt_forward(p, d, batch, stream) : ntt_inverse(p, d, batch, stream);
@@ -159,7 +179,7 @@ ntt_status ntt_autotune(uint32_t N, const uint64_t *q, uint32_t L, uint32_t flag
         }
         int best = 0;
         for (int form = 1; form < 3; ++form)
-            if (v.ms[dir][form] < v.ms[dir][best]) best = form;
+            if (v.ms[dir][form] >= 0.f && v.ms[dir][form] < v.ms[dir][best]) best = form;
         v.form[dir] = best;
     }
     if (e0) cudaEventDestroy(e0);
@@ -195,7 +215,7 @@ nttgb::TuneKey key_from_flags(uint32_t N, uint32_t L, uint32_t flags, uint32_t b
                          : (flags & NTT_RED_MASK) == NTT_RED_BARRETT   ? nttgb::RED_BARRETT
                                                                        : nttgb::RED_SHOUP;
     return nttgb::TuneKey{N, (flags & NTT_WORD64) ? 8u : 4u, L, red, (flags & NTT_ORDER_BITREV) ? 1u : 0u,
-                          nttgb::bucket_of(batch)};
+                          nttgb::bucket_of(batch), (flags & NTT_TW_OTF) ? 1u : 0u};
 }
 }  // namespace
 

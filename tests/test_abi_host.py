@@ -96,3 +96,19 @@ def test_default_psi_matches_oracle(nt, orc):
     cases += [(q, 1 << 17) for q in orc.find_primes(60, 18, 4)]
     for q, N in cases:
         assert nt.ntt_default_psi(q, N) == orc.psi(q, N), (q, N)
+
+
+def test_otf_flag_combinations_rejected_before_touching_cuda(nt):
+    """NTT_TW_OTF needs the fused variant, 4-byte words, Shoup twiddles and
+    the two-launch forms."""
+    q = 1073479681   # 30-bit, 1 mod 2^18
+    q60 = 1152921504606830593
+    for N, qs, variant, flags in [(1 << 16, [q], nt.NTT_DIT, 0),
+                                  (1024, [q60], nt.NTT_FUSED, nt.NTT_WORD64),
+                                  (1 << 16, [q], nt.NTT_FUSED, nt.NTT_RED_BARRETT),
+                                  (1 << 16, [q], nt.NTT_FUSED, nt.NTT_RED_MONTGOMERY),
+                                  (1 << 16, [q], nt.NTT_FUSED, nt.NTT_STREAMED),
+                                  (1 << 16, [q], nt.NTT_TC_FOURSTEP, 0)]:
+        with pytest.raises(nt.NttError) as e:
+            nt.ntt_plan_create(N, qs, variant, flags | nt.NTT_TW_OTF)
+        assert e.value.status == nt.NTT_ERR_UNSUPPORTED, (variant, flags)

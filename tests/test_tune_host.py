@@ -53,3 +53,23 @@ def test_tune_set_rejects_bad_forms(nt):
     for fwd, inv, batch in [(3, 0, 4), (0, -1, 4), (0, 0, 0)]:
         with pytest.raises(nt.NttError):
             nt.ntt_tune_set(1 << 16, 2, 0, batch, fwd, inv)
+
+
+def test_tune_table_keys_twiddle_mode_and_reads_older_lines(nt, tmp_path):
+    """NTT_TW_OTF plans have their own entries, written with a tw_otf field;
+    lines without it (an older table) load as table-twiddle entries."""
+    db = str(tmp_path / "tune.jsonl")
+    with open(db, "w") as f:
+        f.write('{"N": 32768, "word_bytes": 4, "L": 8, "reduction": 0, "bitrev": 1, "batch_log2": 2, '
+                '"forward_form": 1, "inverse_form": 2, "forward_ms": [-1.0, -1.0, -1.0], '
+                '"inverse_ms": [-1.0, -1.0, -1.0]}\n')
+    out = _run("import paper_2405_11353_gb300 as nt\n"
+               "f = nt.NTT_ORDER_BITREV\n"
+               "print(nt.ntt_tune_get(1 << 15, 8, f, 4), nt.ntt_tune_get(1 << 15, 8, f, 4, True),\n"
+               "      nt.ntt_tune_get(1 << 15, 8, f | nt.NTT_TW_OTF, 4))\n"
+               "nt.ntt_tune_set(1 << 15, 8, f | nt.NTT_TW_OTF, 4, nt.NTT_FORM_SMALL, nt.NTT_FORM_WIDE)\n"
+               "print(nt.ntt_tune_get(1 << 15, 8, f | nt.NTT_TW_OTF, 4, True), nt.ntt_tune_get(1 << 15, 8, f, 4))\n",
+               db)
+    assert out.split() == ["1", "2", "-1", "1", "1"]
+    rows = [json.loads(x) for x in open(db)]
+    assert sorted(r["tw_otf"] for r in rows) == [0, 1]
