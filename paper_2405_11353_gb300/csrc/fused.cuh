@@ -563,32 +563,39 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
                     // the K chunk tables of this tile from their seeds:
                     // entry j of chunk r at stage level lv = floor(log2 j)
                     // is A_lv(r) * B[j] (see the plan's table builder)
-                    // (every thread makes S / T = 16 entries, in two
-                    // batches of 8 whose loads are all issued first, so
-                    // their latencies overlap)
-                    constexpr uint32_t NT = K * T, PER = K * S / NT, BATCH = 8;
-                    static_assert(PER % BATCH == 0, "entries per thread");
+                    // (thread tid makes entries j = tid + NT m of every
+                    // chunk of the tile: one root pair and one stage level
+                    // per j serve the K chunks; the loads of MB values of j
+                    // are all issued before their products, so their
+                    // latencies overlap)
+                    constexpr uint32_t NT = K * T, JPT = S / NT, MB = JPT < 4 ? JPT : 4;
+                    static_assert(NT <= S && S % NT == 0 && JPT % MB == 0, "threads per chunk table");
                     const W *sd = a.tw_seed + ((size_t)cur.l * N1 + pos0) * 8;
                     const Tw<W> *rt = a.tw_root + (size_t)cur.l * S;
 #pragma unroll 1
-                    for (uint32_t b0 = 0; b0 < PER; b0 += BATCH) {
-                        W sa[BATCH];
-                        Tw<W> rb[BATCH];
+                    for (uint32_t m0 = 0; m0 < JPT; m0 += MB) {
+                        Tw<W> rb[MB];
+                        W sa[MB][K];
 #pragma unroll
-                        for (uint32_t i2 = 0; i2 < BATCH; ++i2) {
-                            const uint32_t e = tid + (b0 + i2) * NT, j = e & (S - 1);
-                            sa[i2] = __ldg(sd + (e >> LOGS) * 8 + (j ? 31 - __clz(j) : 0));
-                            rb[i2] = ldtw(rt + j);
+                        for (uint32_t m = 0; m < MB; ++m) {
+                            const uint32_t j = tid + (m0 + m) * NT;
+                            const uint32_t lv = j ? 31 - __clz(j) : 0;
+                            rb[m] = ldtw(rt + j);
+#pragma unroll
+                            for (uint32_t c2 = 0; c2 < K; ++c2) sa[m][c2] = __ldg(sd + c2 * 8 + lv);
                         }
 #pragma unroll
-                        for (uint32_t i2 = 0; i2 < BATCH; ++i2) {
-                            const uint32_t e = tid + (b0 + i2) * NT, j = e & (S - 1);
-                            Tw<W> tv{0, 0};
-                            if (j != 0) {
-                                tv.w = mul_full<RED_SHOUP, W>(sa[i2], rb[i2], kk);
-                                tv.c = shoup_quotient(tv.w, kk);
+                        for (uint32_t m = 0; m < MB; ++m) {
+                            const uint32_t j = tid + (m0 + m) * NT;
+#pragma unroll
+                            for (uint32_t c2 = 0; c2 < K; ++c2) {
+                                Tw<W> tv{0, 0};
+                                if (j != 0) {
+                                    tv.w = mul_full<RED_SHOUP, W>(sa[m][c2], rb[m], kk);
+                                    tv.c = shoup_quotient(tv.w, kk);
+                                }
+                                tws[c2 * CP + j] = tv;
                             }
-                            tws[(e >> LOGS) * CP + j] = tv;
                         }
                     }
                     __syncthreads();
