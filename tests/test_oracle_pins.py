@@ -377,3 +377,25 @@ def test_base_conv_special_cases(orc):
     xb = np.concatenate([x, x[:, :, ::-1].copy()])
     zb = orc.base_conv(xb, qs, ps)
     assert np.array_equal(zb[1], orc.base_conv(x[:, :, ::-1].copy(), qs, ps)[0])
+
+
+def test_chunk_twiddle_factorization(orc):
+    """The identity the on-the-fly chunk twiddles rest on: for the two-pass
+    split N = N1 x 256, entry 2^s + i of chunk r, psi^bitrev_n(2^s (N1 + r) + i),
+    equals A_s(r) B_s(i) with A_s(r) = psi^(2^(7-s) (1 + 2 bitrev(r))) and
+    B_s(i) = psi^(2^(n-s) bitrev_s(i)).  Checked over every (r, s, i) for
+    N = 2^13 and, for a sample of chunks, N = 2^17."""
+    def brv(x, b):
+        return int(format(x, "0%db" % b)[::-1], 2) if b else 0
+
+    for n, chunks in ((13, range(32)), (17, (0, 1, 77, 300, 511))):
+        N, s1 = 1 << n, n - 8
+        q = orc.find_primes(30, 18, 1)[0]
+        psi = orc.psi(q, N)
+        for r in chunks:
+            for s in range(8):
+                a = orc.powmod(psi, (1 << (7 - s)) * (1 + 2 * brv(r, s1)), q)
+                for i in range(1 << s):
+                    b = orc.powmod(psi, (1 << (n - s)) * brv(i, s), q)
+                    want = orc.powmod(psi, brv((1 << s) * ((1 << s1) + r) + i, n), q)
+                    assert orc.mulmod(a, b, q) == want, (n, r, s, i)
