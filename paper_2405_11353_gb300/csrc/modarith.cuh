@@ -6,6 +6,7 @@
 // Algorithm 5 the precomputed-quotient product after HEAX):
 //
 //   Shoup      w' = floor(w 2^W / q);  qh = hi(x w');  r = lo(x w) - lo(qh q)
+//              (written lo(x w) + lo(qh (-q)): one multiply-add)
 //              r in [0, 2q) for every x < 2^W (Algorithm 5 without its final
 //              correction -- the lazy form).
 //   Montgomery w_m = w R mod q, c = w_m q^-1 mod R (R = 2^W);  m = lo(x c);
@@ -57,11 +58,13 @@ template <class W> __device__ __forceinline__ W csub(W x, W c) { return umin<W>(
 
 template <class W> struct Lc {
     W q, two_q, qinv, r2, r2c;
+    W nq;               // -q mod 2^W: lo(x w) - lo(qh q) as one multiply-add
     uint64_t mu;
     uint32_t bits;
     __device__ __forceinline__ void load(const LimbConst *p) {
         q = (W)p->q; two_q = (W)p->two_q; qinv = (W)p->qinv;
         r2 = (W)p->r2; r2c = (W)p->r2c; mu = p->mu; bits = p->bits;
+        nq = (W)0 - q;
     }
 };
 
@@ -92,7 +95,7 @@ __device__ __forceinline__ uint64_t barrett_lazy64(uint64_t zlo, uint64_t zhi, c
 template <int RED> __device__ __forceinline__ uint32_t mul_lazy(uint32_t x, Tw<uint32_t> t, const Lc<uint32_t> &k) {
     if (RED == RED_SHOUP) {
         uint32_t qh = __umulhi(x, t.c);
-        return x * t.w - qh * k.q;
+        return x * t.w + qh * k.nq;
     } else if (RED == RED_MONTGOMERY) {
         uint32_t m = x * t.c;
         uint32_t t1 = __umulhi(x, t.w);
@@ -106,7 +109,7 @@ template <int RED> __device__ __forceinline__ uint32_t mul_lazy(uint32_t x, Tw<u
 template <int RED> __device__ __forceinline__ uint64_t mul_lazy(uint64_t x, Tw<uint64_t> t, const Lc<uint64_t> &k) {
     if (RED == RED_SHOUP) {
         uint64_t qh = __umul64hi(x, t.c);
-        return x * t.w - qh * k.q;
+        return x * t.w + qh * k.nq;
     } else if (RED == RED_MONTGOMERY) {
         uint64_t m = x * t.c;
         uint64_t t1 = __umul64hi(x, t.w);
