@@ -267,6 +267,13 @@ __device__ __forceinline__ void prefetch_tensor_2d(const void *tmap, int x, int 
                  : "memory");
 }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// Programmatic dependent launch: let the next launch on the stream be
+// scheduled once every CTA of this grid has started (its CTAs then take
+// the SM slots this grid frees and run their set-up), and wait until the
+// previous grid on the stream has completed and its writes are visible.
+// Without the launch attribute both are no-ops.
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Rounds J = 1 .. NR-1 of one sub-transform (round 0 is done by the caller
 // on the words read from the staged tile); rounds exchange through the
@@ -398,7 +405,7 @@ struct PipeState {
 // twiddles (staged in shared memory) for many consecutive tiles.  `bar`
 // holds NS tile barriers and one twiddle barrier, initialised by the caller.
 // Returns false if a wait ran out of time (the abort has been recorded).
-template <class W, int RED, bool INV, int LOGS, int KIND, int P, bool OTF_K = false>
+template <class W, int RED, bool INV, int LOGS, int KIND, int P, bool OTF_K = false, bool DEP = false>
 __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *tmap, uint32_t t_begin,
                                           uint32_t t_end, unsigned char *base, uint64_t *bar, PipeState &ps) {
     constexpr uint32_t S = 1u << LOGS;
@@ -513,6 +520,23 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
 
     Cur ahead = cur_at(t_begin);   // next tile to issue (thread 0)
     Cur cur = ahead;               // tile being processed
+    uint32_t tw_key = 0xffffffffu;  // (limb, group) of the staged twiddles
+    bool tw_pending = false;        // the first table was requested early
+    if constexpr (DEP) {
+        // launched as a dependent of the previous launch on the stream:
+        // request the first tile's twiddle table (no data) before waiting
+        // for that launch to end
+        if constexpr (TWS && !OTF) {
+            if (tid == 0) {
+                fence_proxy_async();
+                mbar_expect_tx(&bar[NS], TWP * (uint32_t)sizeof(Tw<W>));
+                bulk_g2s(tws, tw_src(cur.l, cur.g), TWP * (uint32_t)sizeof(Tw<W>), &bar[NS]);
+            }
+            tw_key = KIND == TK_CHUNKS ? cur.l * per + cur.g : cur.l;
+            tw_pending = true;
+        }
+        griddep_wait();
+    }
     if (tid == 0) {
         fence_proxy_async();   // the buffers may have been read by a previous call
         // (test hook: the first barrier waits for bytes no copy delivers)
@@ -523,7 +547,6 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
         if (t_begin + NS < t_end) prefetch(ahead);
     }
     uint32_t n_issued = t_end - t_begin < NS ? t_end - t_begin : NS;   // local tiles issued so far
-    uint32_t tw_key = 0xffffffffu;  // (limb, group) of the staged twiddles
     uint32_t &tw_phase = ps.tw_phase;
     bool ok = true;
     // limb constants, reloaded only when the limb changes (tiles run
@@ -553,7 +576,12 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
             // restage the twiddles when the tile needs another table (every
             // thread finished with the old one before the previous refill barrier)
             const uint32_t key = KIND == TK_CHUNKS ? cur.l * per + cur.g : cur.l;
-            if (key != tw_key) {
+            if (tw_pending) {
+                // the first tile's table, requested before the dependency wait
+                ok = ok && mbar_wait_bounded(&bar[NS], tw_phase & 1u);
+                ++tw_phase;
+                tw_pending = false;
+            } else if (key != tw_key) {
                 // inside a run of tiles, the previous tile may still be
                 // reading the old table (without LATE_REFILL the end-of-tile
                 // barrier has already waited for it)
@@ -797,11 +825,14 @@ k_fused(const __grid_constant__ FArgs<W> a) {
         for (uint32_t s = 0; s <= NS; ++s) mbar_init(&bar[s], 1);
         fence_mbar_init();
     }
+    // the next launch may be scheduled now; run_tiles waits for the
+    // previous one before its first data access
+    griddep_launch_dependents();
     __syncthreads();
     PipeState ps{{0, 0}, 0};
     const uint32_t t_begin = (uint32_t)((uint64_t)blockIdx.x * a.ntiles / gridDim.x);
     const uint32_t t_end = (uint32_t)((uint64_t)(blockIdx.x + 1) * a.ntiles / gridDim.x);
-    run_tiles<W, RED, INV, LOGS, KIND, PP, OTF_K>(a, &a.tmap, t_begin, t_end, base, bar, ps);
+    run_tiles<W, RED, INV, LOGS, KIND, PP, OTF_K, true>(a, &a.tmap, t_begin, t_end, base, bar, ps);
 }
 
 template <class W, int LOGS, int KIND, bool INV, int P = 0> __host__ __device__ constexpr size_t fused_smem_bytes() {

@@ -36,8 +36,20 @@ cudaError_t launch_pass(const FArgs<W> &a, uint32_t threads, size_t smem, cudaSt
     }
     unsigned grid = a.ntiles < (uint64_t)resident ? (unsigned)a.ntiles : (unsigned)resident;
     if (grid == 0) grid = 1;
-    kern<<<grid, threads, smem, st>>>(a);
-    return cudaGetLastError();
+    // programmatic dependent launch: the kernel may be scheduled while the
+    // previous launch on the stream drains; it waits for that launch's
+    // results before touching data (griddep_wait in k_fused)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
 // Tensor map of the data viewed as (ntrans * N1) rows of N2 words, with a
