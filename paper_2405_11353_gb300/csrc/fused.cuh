@@ -522,6 +522,19 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     Cur cur = ahead;               // tile being processed
     uint32_t tw_key = 0xffffffffu;  // (limb, group) of the staged twiddles
     bool tw_pending = false;        // the first table was requested early
+    // limb constants, reloaded only when the limb changes (tiles run
+    // polynomial-fastest, so rarely)
+    uint32_t kk_l = 0xffffffffu;
+    Lc<W> kk;
+    Tw<W> tn{}, twn{};
+    auto load_limb = [&](uint32_t l) {
+        kk.load(a.lc + l);
+        if (INV && a.final_pass) {
+            tn.w = (W)a.lc[l].ninv_w; tn.c = (W)a.lc[l].ninv_c;
+            twn.w = (W)a.lc[l].ninv_w1_w; twn.c = (W)a.lc[l].ninv_w1_c;
+        }
+        kk_l = l;
+    };
     if constexpr (DEP) {
         // launched as a dependent of the previous launch on the stream:
         // request the first tile's twiddle table (no data) before waiting
@@ -534,6 +547,11 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
             }
             tw_key = KIND == TK_CHUNKS ? cur.l * per + cur.g : cur.l;
             tw_pending = true;
+        }
+        // and the first tile's limb constants and tensor map
+        if constexpr (KIND != TK_SINGLE && LATE_REFILL) load_limb(cur.l);
+        if constexpr (KIND == TK_COLS || SWZ) {
+            if (tid == 0) asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
         }
         griddep_wait();
     }
@@ -549,11 +567,6 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     uint32_t n_issued = t_end - t_begin < NS ? t_end - t_begin : NS;   // local tiles issued so far
     uint32_t &tw_phase = ps.tw_phase;
     bool ok = true;
-    // limb constants, reloaded only when the limb changes (tiles run
-    // polynomial-fastest, so rarely)
-    uint32_t kk_l = 0xffffffffu;
-    Lc<W> kk;
-    Tw<W> tn{}, twn{};
 
     uint32_t i = 0;
     for (uint32_t tile = t_begin; tile < t_end; ++tile, ++i, cur_next(cur)) {
@@ -563,14 +576,7 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
         const uint64_t t = KIND == TK_SINGLE ? cur_t(cur) + k : cur_t(cur);
         const bool valid = t < a.ntrans;
         const uint32_t l = KIND == TK_SINGLE ? (uint32_t)((valid ? t : 0) % L) : cur.l;
-        if (!LATE_REFILL || l != kk_l) {
-            kk.load(a.lc + l);
-            if (INV && a.final_pass) {
-                tn.w = (W)a.lc[l].ninv_w; tn.c = (W)a.lc[l].ninv_c;
-                twn.w = (W)a.lc[l].ninv_w1_w; twn.c = (W)a.lc[l].ninv_w1_c;
-            }
-            kk_l = l;
-        }
+        if (!LATE_REFILL || l != kk_l) load_limb(l);
         const Tw<W> *twb;
         if (TWS) {
             // restage the twiddles when the tile needs another table (every
