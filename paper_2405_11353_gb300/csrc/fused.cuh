@@ -817,8 +817,22 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
 
 // Per-plan fused pass: CTA c processes tiles [c T / G, (c+1) T / G).
 // PP: the tile configuration (see tile_k): 0, or 3 for 16-chunk tiles.
+// Launch bounds: inverse column passes of up to 256 points with 4-byte
+// words (512 threads) and Shoup or Montgomery twiddles are held to the
+// registers that let three CTAs share an SM, as their shared memory allows
+// (40 a thread, no spills); 512-point column passes take 1024 threads.
+template <class W, int RED, int LOGS, int KIND, bool INV> __host__ __device__ constexpr bool fused_cols3() {
+    return KIND == TK_COLS && INV && sizeof(W) == 4 && RED != RED_BARRETT && LOGS <= 8;
+}
+template <class W, int RED, int LOGS, int KIND, bool INV> __host__ __device__ constexpr int fused_max_threads() {
+    return fused_cols3<W, RED, LOGS, KIND, INV>() ? 512 : (sizeof(W) == 4 ? 1024 : 512);
+}
+template <class W, int RED, int LOGS, int KIND, bool INV> __host__ __device__ constexpr int fused_min_blocks() {
+    return fused_cols3<W, RED, LOGS, KIND, INV>() ? 3 : 1;
+}
 template <class W, int RED, bool INV, int LOGS, int KIND, int PP, bool OTF_K = false>
-__global__ void __launch_bounds__(sizeof(W) == 4 ? 1024 : 512)
+__global__ void __launch_bounds__(fused_max_threads<W, RED, LOGS, KIND, INV>(),
+                                  fused_min_blocks<W, RED, LOGS, KIND, INV>())
 k_fused(const __grid_constant__ FArgs<W> a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     constexpr uint32_t NS = n_stages<W, LOGS, KIND>();
