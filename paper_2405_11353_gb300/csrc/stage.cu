@@ -42,6 +42,31 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Programmatic dependent launch (as in the fused kernels): every kernel
+// here lets the next launch on the stream be scheduled once all its CTAs
+// have started, then waits for the previous launch's results before it
+// touches data, so the launch latency of one stage hides behind the
+// previous one.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void dep_begin() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+void launch_dep(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, args...);   // errors surface through cudaGetLastError
+}
+
 inline unsigned grid_for(uint64_t work, int threads = kThreads) {
     uint64_t g = (work + threads - 1) / threads;
     if (g > 152ull * 32) g = 152ull * 32;
@@ -64,6 +89,7 @@ template <class W> __device__ __forceinline__ Lc<W> limb_k(const LimbConst *lc, 
 template <class W, int RED>
 __global__ void k_scale(W *__restrict__ x, const Tw<W> *__restrict__ tab, const LimbConst *__restrict__ lc,
                         uint32_t logN, uint32_t L, uint64_t total) {
+    dep_begin();
     const uint32_t N = 1u << logN;
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < total;
          g += (uint64_t)gridDim.x * blockDim.x) {
@@ -78,6 +104,7 @@ __global__ void k_scale(W *__restrict__ x, const Tw<W> *__restrict__ tab, const 
 // in-place bit-reversal permutation of every transform
 template <class W>
 __global__ void k_bitrev(W *__restrict__ x, uint32_t logN, uint64_t total) {
+    dep_begin();
     const uint32_t N = 1u << logN;
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < total;
          g += (uint64_t)gridDim.x * blockDim.x) {
@@ -94,6 +121,7 @@ __global__ void k_bitrev(W *__restrict__ x, uint32_t logN, uint64_t total) {
 
 template <class W>
 __global__ void k_copy(W *__restrict__ dst, const W *__restrict__ src, uint64_t total) {
+    dep_begin();
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < total;
          g += (uint64_t)gridDim.x * blockDim.x)
         dst[g] = src[g];
@@ -103,6 +131,7 @@ __global__ void k_copy(W *__restrict__ dst, const W *__restrict__ src, uint64_t 
 template <class W, int RED>
 __global__ void k_pointwise_vec(W *c, const W *a, const W *b, const LimbConst *__restrict__ lc,
                                 uint32_t logN, uint32_t L, uint64_t nvec) {
+    dep_begin();
     constexpr int V = 16 / sizeof(W);
     using Vec = typename std::conditional<sizeof(W) == 4, uint4, ulonglong2>::type;
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < nvec;
@@ -123,6 +152,7 @@ __global__ void k_pointwise_vec(W *c, const W *a, const W *b, const LimbConst *_
 template <class W, int RED>
 __global__ void k_pointwise_scalar(W *c, const W *a, const W *b, const LimbConst *__restrict__ lc,
                                    uint32_t logN, uint32_t L, uint64_t total) {
+    dep_begin();
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < total;
          g += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t l = (uint32_t)((g >> logN) % L);
@@ -134,6 +164,7 @@ __global__ void k_pointwise_scalar(W *c, const W *a, const W *b, const LimbConst
 template <class W>
 __global__ void k_check_range(const W *__restrict__ x, const LimbConst *__restrict__ lc, uint32_t logN,
                               uint32_t L, uint64_t total, uint32_t *status) {
+    dep_begin();
     bool bad = false;
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < total;
          g += (uint64_t)gridDim.x * blockDim.x) {
@@ -150,6 +181,7 @@ enum { ST_DIT = 0, ST_DIF = 1, ST_FLAT = 2 };
 template <class W, int RED, int KIND>
 __global__ void k_stage_inplace(W *__restrict__ x, const Tw<W> *__restrict__ wt, const LimbConst *__restrict__ lc,
                                 uint32_t logN, uint32_t L, uint32_t s, uint64_t total_bf) {
+    dep_begin();
     const uint32_t N = 1u << logN;
     const uint32_t half = 1u << (s - 1);
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < total_bf;
@@ -187,6 +219,7 @@ template <class W, int RED>
 __global__ void k_stage_cg(W *__restrict__ dst, const W *__restrict__ src, const Tw<W> *__restrict__ wt,
                            const LimbConst *__restrict__ lc, uint32_t logN, uint32_t L, uint32_t s,
                            uint64_t total_bf) {
+    dep_begin();
     const uint32_t N = 1u << logN;
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < total_bf;
          g += (uint64_t)gridDim.x * blockDim.x) {
@@ -211,6 +244,7 @@ template <class W, int RED>
 __global__ void k_stage_stockham(W *__restrict__ dst, const W *__restrict__ src, const Tw<W> *__restrict__ wt,
                                  const LimbConst *__restrict__ lc, uint32_t logN, uint32_t L, uint32_t s,
                                  uint64_t total_bf) {
+    dep_begin();
     const uint32_t N = 1u << logN;
     const uint32_t stride = 1u << (s - 1);
     const uint32_t m = N >> s;
@@ -237,6 +271,7 @@ __global__ void k_stage_stockham(W *__restrict__ dst, const W *__restrict__ src,
 template <class W>
 __global__ void k_transpose(W *__restrict__ dst, const W *__restrict__ src, uint32_t logR, uint32_t logC,
                             uint64_t ntrans) {
+    dep_begin();
     __shared__ W tile[32][33];
     const uint32_t R = 1u << logR, C = 1u << logC;
     const uint32_t tilesC = (C + 31) / 32, tilesR = (R + 31) / 32;
@@ -266,6 +301,7 @@ __global__ void k_transpose(W *__restrict__ dst, const W *__restrict__ src, uint
 template <class W, int RED>
 __global__ void k_rows(W *__restrict__ x, const Tw<W> *__restrict__ wt, const LimbConst *__restrict__ lc,
                        uint32_t logN, uint32_t L, uint32_t logRow, uint64_t nrows_total, int twiddle) {
+    dep_begin();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     W *sm = reinterpret_cast<W *>(smem_raw);
     const uint32_t N = 1u << logN, Rl = 1u << logRow;
@@ -319,50 +355,50 @@ cudaError_t run_variant_t(ntt_plan_s &p, ntt_variant variant, void *data_v, uint
     const unsigned ge = grid_for(total), gb = grid_for(total_bf);
 
     // inverse input in bit-reversed order -> natural first
-    if (inverse && p.bitrev_order) { k_bitrev<W><<<ge, kThreads, 0, st>>>(data, logN, total); ++nl; }
-    if (!inverse) { k_scale<W, RED><<<ge, kThreads, 0, st>>>(data, twist, lc, logN, L, total); ++nl; }
+    if (inverse && p.bitrev_order) { launch_dep(k_bitrev<W>, ge, kThreads, 0, st, data, logN, total); ++nl; }
+    if (!inverse) { launch_dep(k_scale<W, RED>, ge, kThreads, 0, st, data, twist, lc, logN, L, total); ++nl; }
 
     switch (variant) {
     case NTT_DIT:
     case NTT_FLAT:
-        k_bitrev<W><<<ge, kThreads, 0, st>>>(data, logN, total); ++nl;
+        launch_dep(k_bitrev<W>, ge, kThreads, 0, st, data, logN, total); ++nl;
         for (uint32_t s = 1; s <= logN; ++s) {
             if (variant == NTT_DIT)
-                k_stage_inplace<W, RED, ST_DIT><<<gb, kThreads, 0, st>>>(data, wt, lc, logN, L, s, total_bf);
+                launch_dep(k_stage_inplace<W, RED, ST_DIT>, gb, kThreads, 0, st, data, wt, lc, logN, L, s, total_bf);
             else
-                k_stage_inplace<W, RED, ST_FLAT><<<gb, kThreads, 0, st>>>(data, wt, lc, logN, L, s, total_bf);
+                launch_dep(k_stage_inplace<W, RED, ST_FLAT>, gb, kThreads, 0, st, data, wt, lc, logN, L, s, total_bf);
             ++nl;
         }
         break;
     case NTT_DIF:
         for (uint32_t s = logN; s >= 1; --s) {
-            k_stage_inplace<W, RED, ST_DIF><<<gb, kThreads, 0, st>>>(data, wt, lc, logN, L, s, total_bf); ++nl;
+            launch_dep(k_stage_inplace<W, RED, ST_DIF>, gb, kThreads, 0, st, data, wt, lc, logN, L, s, total_bf); ++nl;
         }
-        k_bitrev<W><<<ge, kThreads, 0, st>>>(data, logN, total); ++nl;
+        launch_dep(k_bitrev<W>, ge, kThreads, 0, st, data, logN, total); ++nl;
         break;
     case NTT_PEASE:
     case NTT_PEASE_NC: {
-        k_bitrev<W><<<ge, kThreads, 0, st>>>(data, logN, total); ++nl;
+        launch_dep(k_bitrev<W>, ge, kThreads, 0, st, data, logN, total); ++nl;
         W *src = data, *dst = scr;
         for (uint32_t s = 1; s <= logN; ++s) {
-            k_stage_cg<W, RED><<<gb, kThreads, 0, st>>>(dst, src, wt, lc, logN, L, s, total_bf); ++nl;
+            launch_dep(k_stage_cg<W, RED>, gb, kThreads, 0, st, dst, src, wt, lc, logN, L, s, total_bf); ++nl;
             if (variant == NTT_PEASE) {
                 // Algorithm 3: the new values are copied back before the next stage
-                k_copy<W><<<ge, kThreads, 0, st>>>(src, dst, total); ++nl;
+                launch_dep(k_copy<W>, ge, kThreads, 0, st, src, dst, total); ++nl;
             } else {
                 W *t = src; src = dst; dst = t;   // Pease_nc: swap the roles
             }
         }
-        if (variant == NTT_PEASE_NC && src != data) { k_copy<W><<<ge, kThreads, 0, st>>>(data, src, total); ++nl; }
+        if (variant == NTT_PEASE_NC && src != data) { launch_dep(k_copy<W>, ge, kThreads, 0, st, data, src, total); ++nl; }
         break;
     }
     case NTT_STOCKHAM: {
         W *src = data, *dst = scr;
         for (uint32_t s = 1; s <= logN; ++s) {
-            k_stage_stockham<W, RED><<<gb, kThreads, 0, st>>>(dst, src, wt, lc, logN, L, s, total_bf); ++nl;
+            launch_dep(k_stage_stockham<W, RED>, gb, kThreads, 0, st, dst, src, wt, lc, logN, L, s, total_bf); ++nl;
             W *t = src; src = dst; dst = t;
         }
-        if (src != data) { k_copy<W><<<ge, kThreads, 0, st>>>(data, src, total); ++nl; }
+        if (src != data) { launch_dep(k_copy<W>, ge, kThreads, 0, st, data, src, total); ++nl; }
         break;
     }
     case NTT_SIXSTEP: {
@@ -373,28 +409,28 @@ cudaError_t run_variant_t(ntt_plan_s &p, ntt_variant variant, void *data_v, uint
             uint64_t nrows = ntrans << (logN - logRow);
             unsigned thr = (1u << logRow) / 2 < 32 ? 32 : ((1u << logRow) / 2 > 256 ? 256 : (1u << logRow) / 2);
             unsigned g = nrows > 152ull * 32 ? 152u * 32 : (unsigned)nrows;
-            k_rows<W, RED><<<g, thr, sizeof(W) << logRow, st>>>(x, wt, lc, logN, L, logRow, nrows, tw);
+            launch_dep(k_rows<W, RED>, g, thr, sizeof(W) << logRow, st, x, wt, lc, logN, L, logRow, nrows, tw);
             ++nl;
         };
         // 1. A[n1][n2] (N1 x N2) -> T1[n2][n1]
-        k_transpose<W><<<gt, tb, 0, st>>>(scr, data, l1, l2, ntrans); ++nl;
+        launch_dep(k_transpose<W>, gt, tb, 0, st, scr, data, l1, l2, ntrans); ++nl;
         // 2-3. N1-point transforms of the N2 rows, times omega^(n2 k1)
         rows(scr, l1, 1);
         // 4. T1 (N2 x N1) -> T2[k1][n2]
-        k_transpose<W><<<gt, tb, 0, st>>>(data, scr, l2, l1, ntrans); ++nl;
+        launch_dep(k_transpose<W>, gt, tb, 0, st, data, scr, l2, l1, ntrans); ++nl;
         // 5. N2-point transforms of the N1 rows
         rows(data, l2, 0);
         // 6. T2 (N1 x N2) -> X[k2][k1] = X[k1 + N1 k2]
-        k_transpose<W><<<gt, tb, 0, st>>>(scr, data, l1, l2, ntrans); ++nl;
-        k_copy<W><<<ge, kThreads, 0, st>>>(data, scr, total); ++nl;
+        launch_dep(k_transpose<W>, gt, tb, 0, st, scr, data, l1, l2, ntrans); ++nl;
+        launch_dep(k_copy<W>, ge, kThreads, 0, st, data, scr, total); ++nl;
         break;
     }
     default:
         return cudaErrorInvalidValue;
     }
 
-    if (inverse) { k_scale<W, RED><<<ge, kThreads, 0, st>>>(data, untwist, lc, logN, L, total); ++nl; }
-    if (!inverse && p.bitrev_order) { k_bitrev<W><<<ge, kThreads, 0, st>>>(data, logN, total); ++nl; }
+    if (inverse) { launch_dep(k_scale<W, RED>, ge, kThreads, 0, st, data, untwist, lc, logN, L, total); ++nl; }
+    if (!inverse && p.bitrev_order) { launch_dep(k_bitrev<W>, ge, kThreads, 0, st, data, logN, total); ++nl; }
     return cudaGetLastError();
 }
 
@@ -454,10 +490,10 @@ cudaError_t launch_pointwise(ntt_plan_s &p, void *c, const void *a, const void *
         constexpr int V = 16 / sizeof(W);
         if (p.N % V == 0) {
             uint64_t nvec = total / V;
-            k_pointwise_vec<W, RED><<<grid_for(nvec), kThreads, 0, st>>>(
+            launch_dep(k_pointwise_vec<W, RED>, grid_for(nvec), kThreads, 0, st, 
                 (W *)c, (const W *)a, (const W *)b, p.d_limb, p.logN, p.L, nvec);
         } else {
-            k_pointwise_scalar<W, RED><<<grid_for(total), kThreads, 0, st>>>(
+            launch_dep(k_pointwise_scalar<W, RED>, grid_for(total), kThreads, 0, st, 
                 (W *)c, (const W *)a, (const W *)b, p.d_limb, p.logN, p.L, total);
         }
         ++p.last_launches;
@@ -467,8 +503,8 @@ cudaError_t launch_pointwise(ntt_plan_s &p, void *c, const void *a, const void *
 
 cudaError_t launch_bitrev_permute(ntt_plan_s &p, void *data, uint32_t batch, cudaStream_t st) {
     const uint64_t total = (uint64_t)batch * p.L * p.N;
-    if (p.word64) k_bitrev<uint64_t><<<grid_for(total), kThreads, 0, st>>>((uint64_t *)data, p.logN, total);
-    else k_bitrev<uint32_t><<<grid_for(total), kThreads, 0, st>>>((uint32_t *)data, p.logN, total);
+    if (p.word64) launch_dep(k_bitrev<uint64_t>, grid_for(total), kThreads, 0, st, (uint64_t *)data, p.logN, total);
+    else launch_dep(k_bitrev<uint32_t>, grid_for(total), kThreads, 0, st, (uint32_t *)data, p.logN, total);
     ++p.last_launches;
     return cudaGetLastError();
 }
@@ -476,10 +512,10 @@ cudaError_t launch_bitrev_permute(ntt_plan_s &p, void *data, uint32_t batch, cud
 cudaError_t launch_check_range(ntt_plan_s &p, const void *data, uint32_t batch, cudaStream_t st) {
     const uint64_t total = (uint64_t)batch * p.L * p.N;
     if (p.word64)
-        k_check_range<uint64_t><<<grid_for(total), kThreads, 0, st>>>((const uint64_t *)data, p.d_limb, p.logN,
+        launch_dep(k_check_range<uint64_t>, grid_for(total), kThreads, 0, st, (const uint64_t *)data, p.d_limb, p.logN,
                                                                      p.L, total, p.d_status);
     else
-        k_check_range<uint32_t><<<grid_for(total), kThreads, 0, st>>>((const uint32_t *)data, p.d_limb, p.logN,
+        launch_dep(k_check_range<uint32_t>, grid_for(total), kThreads, 0, st, (const uint32_t *)data, p.d_limb, p.logN,
                                                                      p.L, total, p.d_status);
     ++p.last_launches;
     return cudaGetLastError();
