@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of libnttgb: validation, plan building, dispatch.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -427,6 +428,36 @@ bool needs_scratch(const ntt_plan_s &p) {
     }
 }
 
+// A view of a fused plan (single-pass or two-pass) restricted to its limbs
+// l0 .. l0 + lw - 1: every device table is per limb, so the view is the
+// plan with its limb count cut and its table pointers advanced by l0 limbs.
+// It shares the plan's status word and counter sets.
+ntt_plan_s limb_window(const ntt_plan_s &p, uint32_t l0, uint32_t lw) {
+    ntt_plan_s v = p;
+    v.q.clear();
+    v.psi.clear();
+    v.L = lw;
+    const size_t pair = p.word64 ? 16 : 8;
+    const size_t main_limb = p.fused_mode == nttgb::FUSED_TWO_PASS ? ((size_t)1 << p.s1) : (size_t)p.N;
+    auto adv = [&](void *ptr, size_t bytes_per_limb) -> void * {
+        return ptr ? reinterpret_cast<uint8_t *>(ptr) + (size_t)l0 * bytes_per_limb : nullptr;
+    };
+    v.d_limb = p.d_limb + l0;
+    v.d_main_fwd = adv(p.d_main_fwd, main_limb * pair);
+    v.d_main_inv = adv(p.d_main_inv, main_limb * pair);
+    if (p.fused_mode == nttgb::FUSED_TWO_PASS) {
+        const size_t N1 = (size_t)1 << p.s1;
+        const size_t CP = p.word64 ? nttgb::chunk_tab_pitch<uint64_t>() : nttgb::chunk_tab_pitch<uint32_t>();
+        v.d_chunk_fwd = adv(p.d_chunk_fwd, N1 * CP * pair);
+        v.d_chunk_inv = adv(p.d_chunk_inv, N1 * CP * pair);
+        v.d_seed_fwd = adv(p.d_seed_fwd, N1 * 8 * 4);
+        v.d_seed_inv = adv(p.d_seed_inv, N1 * 8 * 4);
+        v.d_root_fwd = adv(p.d_root_fwd, ((size_t)1 << p.s2) * 8);
+        v.d_root_inv = adv(p.d_root_inv, ((size_t)1 << p.s2) * 8);
+    }
+    return v;
+}
+
 ntt_status run_transform(ntt_plan_t plan, void *d_data, uint32_t batch, ntt_stream_t stream, bool inverse,
                          uint32_t limbs = 0) {
     if (!plan || !d_data || batch == 0) return NTT_ERR_INVALID_ARG;
@@ -708,11 +739,14 @@ ntt_status ntt_polymul_host(ntt_plan_t plan, void *h_out, const void *h_in, void
     if (!aligned16(d_work)) return NTT_ERR_ALIGNMENT;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     ntt_plan_s &p = *plan;
-    // Chunks of g pairs run as a three-stage pipeline: host-to-device copies
-    // on one stream, the transforms on the caller's stream, device-to-host
-    // copies on a third, chained by events, so the copies of one chunk
-    // overlap the arithmetic of the others.  Chunk c's inputs land at
-    // d_work + c * 2g polynomials as [a | b].
+    // Chunks run as a three-stage pipeline: host-to-device copies on one
+    // stream, the transforms on the caller's stream, device-to-host copies
+    // on a third, chained by events, so the copies of one chunk overlap the
+    // arithmetic of the others and each other.  A chunk is g whole pairs, or
+    // -- fused plans with one or two pairs -- a window of lw limbs of one
+    // pair (the limbs are independent), so that even one pair is pipelined.
+    // Chunk (pair p0, limbs l0..) keeps its inputs at d_work + 2 (p0 L + l0) N
+    // words as [a | b].
     if (!p.aux_ready) {
         if (cudaStreamCreateWithFlags(&p.aux_h2d, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&p.aux_d2h, cudaStreamNonBlocking) != cudaSuccess) {
@@ -723,9 +757,19 @@ ntt_status ntt_polymul_host(ntt_plan_t plan, void *h_out, const void *h_in, void
             if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); return NTT_ERR_CUDA; }
         p.aux_ready = true;
     }
-    const size_t poly = (size_t)p.L * p.N * p.word_bytes();
-    const uint32_t g = (pairs + nttgb::kHostChunks - 1) / nttgb::kHostChunks;
-    const uint32_t chunks = (pairs + g - 1) / g;
+    const uint32_t K = nttgb::kHostChunks, KMIN = nttgb::kHostMinChunks;
+    const size_t limb = (size_t)p.N * p.word_bytes(), poly = (size_t)p.L * limb;
+    const bool windows = pairs * 2 <= KMIN && p.L > 1 && p.variant == NTT_FUSED &&
+                         (p.fused_mode == nttgb::FUSED_SINGLE || p.fused_mode == nttgb::FUSED_TWO_PASS);
+    uint32_t g = 1, lw = p.L;
+    if (windows) {
+        const uint32_t per_pair = (KMIN / pairs < p.L) ? KMIN / pairs : p.L;   // windows per pair
+        lw = (p.L + per_pair - 1) / per_pair;
+    } else {
+        g = (pairs + K - 1) / K;
+    }
+    const uint32_t wpp = (p.L + lw - 1) / lw;                 // windows per pair
+    const uint32_t chunks = windows ? pairs * wpp : (pairs + g - 1) / g;
     const uint8_t *hi = reinterpret_cast<const uint8_t *>(h_in);
     uint8_t *ho = reinterpret_cast<uint8_t *>(h_out);
     uint8_t *d = reinterpret_cast<uint8_t *>(d_work);
@@ -735,20 +779,36 @@ ntt_status ntt_polymul_host(ntt_plan_t plan, void *h_out, const void *h_in, void
     uint32_t launches = 0;
     ntt_status s = NTT_OK;
     for (uint32_t c = 0; c < chunks && ok && s == NTT_OK; ++c) {
-        const uint32_t p0 = c * g, gc = pairs - p0 < g ? pairs - p0 : g;
-        uint8_t *dc = d + (size_t)2 * p0 * poly;
+        // pairs p0 .. p0 + gc - 1, limbs l0 .. l0 + lc - 1
+        const uint32_t p0 = windows ? c / wpp : c * g;
+        const uint32_t gc = windows ? 1 : (pairs - p0 < g ? pairs - p0 : g);
+        const uint32_t l0 = windows ? (c % wpp) * lw : 0;
+        const uint32_t lc = windows ? (p.L - l0 < lw ? p.L - l0 : lw) : p.L;
+        const size_t part = (size_t)gc * lc * limb;           // one operand of the chunk
+        uint8_t *dc = d + 2 * ((size_t)p0 * poly + (size_t)l0 * limb);
         cudaEvent_t e_in = ev[2 + 2 * c], e_done = ev[3 + 2 * c];
-        ok = cudaMemcpyAsync(dc, hi + (size_t)p0 * poly, gc * poly, cudaMemcpyHostToDevice, p.aux_h2d) == cudaSuccess &&
-             cudaMemcpyAsync(dc + gc * poly, hi + ((size_t)pairs + p0) * poly, gc * poly, cudaMemcpyHostToDevice,
+        ok = cudaMemcpyAsync(dc, hi + (size_t)p0 * poly + l0 * limb, part, cudaMemcpyHostToDevice, p.aux_h2d) ==
+                 cudaSuccess &&
+             cudaMemcpyAsync(dc + part, hi + ((size_t)pairs + p0) * poly + l0 * limb, part, cudaMemcpyHostToDevice,
                              p.aux_h2d) == cudaSuccess &&
              cudaEventRecord(e_in, p.aux_h2d) == cudaSuccess && cudaStreamWaitEvent(st, e_in, 0) == cudaSuccess;
         if (!ok) break;
-        s = ntt_forward(plan, dc, 2 * gc, stream);
-        launches += p.last_launches;
-        if (s == NTT_OK) { s = ntt_pointwise_inverse(plan, dc, dc, dc + gc * poly, gc, stream); launches += p.last_launches; }
+        if (windows && lc != p.L) {
+            // the limb window as a plan of its own: every table is per limb
+            ntt_plan_s view = limb_window(p, l0, lc);
+            s = ntt_forward(&view, dc, 2, stream);
+            launches += view.last_launches;
+            if (s == NTT_OK) { s = ntt_pointwise_inverse(&view, dc, dc, dc + part, 1, stream); launches += view.last_launches; }
+            p.stream_seq = view.stream_seq;
+        } else {
+            s = ntt_forward(plan, dc, 2 * gc, stream);
+            launches += p.last_launches;
+            if (s == NTT_OK) { s = ntt_pointwise_inverse(plan, dc, dc, dc + part, gc, stream); launches += p.last_launches; }
+        }
         if (s != NTT_OK) break;
         ok = cudaEventRecord(e_done, st) == cudaSuccess && cudaStreamWaitEvent(p.aux_d2h, e_done, 0) == cudaSuccess &&
-             cudaMemcpyAsync(ho + (size_t)p0 * poly, dc, gc * poly, cudaMemcpyDeviceToHost, p.aux_d2h) == cudaSuccess;
+             cudaMemcpyAsync(ho + (size_t)p0 * poly + l0 * limb, dc, part, cudaMemcpyDeviceToHost, p.aux_d2h) ==
+                 cudaSuccess;
     }
     // the caller's stream resumes after the last copy out (also on an error,
     // so no work of this call outlives what the caller waits for)

@@ -513,6 +513,35 @@ def test_polymul_host_entry(nt, orc):
         p.close()
 
 
+def test_polymul_host_limb_windows(nt, orc):
+    """One or two pairs are pipelined as windows of limbs (an uneven last
+    window with 5 limbs), on a two-pass size in both orders and on a
+    single-pass size; every product coefficient against the oracle's
+    transform pipeline, a sample against the schoolbook product."""
+    for n, L, bitrev in ((16, 5, True), (15, 5, False), (12, 3, True)):
+        N = 1 << n
+        qs = primes_for(orc, N, False, L)
+        psis = [orc.psi(q, N) for q in qs]
+        p = Plan(nt, N, qs, "fused", bitrev=bitrev)
+        try:
+            for pairs in (1, 2):
+                host = ntt_synth.rns_batch(3000 + n + pairs, qs, N, 2 * pairs).astype(np.uint32)
+                h_in = torch.from_numpy(host.view(np.int32).copy()).pin_memory()
+                h_out = torch.zeros(pairs * L * N, dtype=torch.int32).pin_memory()
+                work = torch.empty(2 * pairs * L * N, dtype=torch.int32, device="cuda")
+                nt.ntt_polymul_host(p.h, h_out, h_in, work, pairs)
+                torch.cuda.synchronize()
+                got = h_out.numpy().view(np.uint32).reshape(pairs, L, N).astype(np.uint64)
+                A = orc.ntt_batch(host, qs, psis)
+                want = orc.ntt_batch(orc.pointwise_batch(A[:pairs], A[pairs:], qs), qs, psis, inverse=True)
+                assert np.array_equal(got, want), (n, L, pairs)
+                assert int(got[0, L - 1, N - 1]) == orc.negacyclic_mul_at(host[0, L - 1], host[pairs, L - 1],
+                                                                        qs[L - 1], N - 1)
+            assert nt.ntt_get_device_status(p.h) == nt.NTT_OK
+        finally:
+            p.close()
+
+
 def test_two_streams(nt, orc):
     N = 1 << 14
     qs = primes_for(orc, N, False, 2)
