@@ -542,6 +542,35 @@ def test_polymul_host_limb_windows(nt, orc):
             p.close()
 
 
+def test_dependent_launches_around_other_kernels(nt, orc):
+    """The library's passes are dependent launches: each waits for the
+    previous launch on the stream before it touches data.  Interleave them
+    with PyTorch kernels on the same stream (which read their output and
+    write their input) and with back-to-back calls on one buffer, for the
+    two-pass, single-pass and per-stage (variant) paths."""
+    for N, variant, L, batch in ((1 << 16, "fused", 3, 2), (1 << 12, "fused", 2, 3), (1 << 10, "stockham", 2, 2)):
+        qs = primes_for(orc, N, False, L)
+        psis = [orc.psi(q, N) for q in qs]
+        host = ntt_synth.rns_batch(3100 + N.bit_length(), qs, N, batch)
+        want = reorder(orc.ntt_batch(host, qs, psis), True, orc) if variant == "fused" else \
+            orc.ntt_batch(host, qs, psis)
+        p = Plan(nt, N, qs, variant, bitrev=(variant == "fused"))
+        try:
+            d = to_dev(host, False)
+            for _ in range(3):
+                p.fwd(d, batch)
+                e = d.clone()                     # a PyTorch kernel reads the transform
+                assert np.array_equal(to_host(e, False, host.shape), want)
+                p.inv(e, batch)
+                d.copy_(e)                        # ... and writes the next input
+                p.fwd(d, batch)
+                p.inv(d, batch)                   # back to back on one buffer
+            assert np.array_equal(to_host(d, False, host.shape), host)
+            assert nt.ntt_get_device_status(p.h) == nt.NTT_OK
+        finally:
+            p.close()
+
+
 def test_two_streams(nt, orc):
     N = 1 << 14
     qs = primes_for(orc, N, False, 2)
