@@ -161,6 +161,22 @@ def oracle_sample(qs, seconds=12.0, max_reps=200):
     return done / dt, oracle.num_threads(), desc
 
 
+def oracle_naive_n1024(polys=256):
+    """For the record: the oracle's O(N^2) definition (Horner at each
+    psi^(2k+1)) on `polys` transforms at N = 1024, q = 12289.  (One
+    transform at N = 2^16 would be 4.3e9 modular products, minutes of CPU;
+    it is not timed.)"""
+    import oracle
+    q = 12289
+    psi = oracle.psi(q, 1024)
+    host = ntt_synth.rns_batch(1001, [q], 1024, polys)
+    t0 = time.perf_counter()
+    oracle.ntt_batch(host, [q], [psi], fast=False)
+    dt = time.perf_counter() - t0
+    return {"value": polys / dt, "unit": "NTT/s",
+            "sample": "oracle O(N^2) forward, N=1024, q=12289, %d transforms in %.2f s" % (polys, dt)}
+
+
 def run_reference(args):
     """The oracle as the reference arm: each step is the step's pipeline on
     one pair of polynomials x all 32 limbs (96 NTTs).  When K such steps
@@ -674,7 +690,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, desc = oracle_sample(qs)
-        cpu = {"value": v, "unit": "NTT/s", "cores": cores, "kind": "oracle", "sample": desc}
+        cpu = {"value": v, "unit": "NTT/s", "cores": cores, "kind": "oracle", "sample": desc,
+               "naive_n1024": oracle_naive_n1024()}
 
     nt.ntt_plan_destroy(plan)
     if rank == 0:
