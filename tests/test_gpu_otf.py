@@ -179,3 +179,33 @@ def test_otf_table_bytes(nt, orc):
     finally:
         nt.ntt_plan_destroy(pa)
         nt.ntt_plan_destroy(pb)
+
+
+def test_otf_with_range_check_and_natural_order(nt, orc):
+    """NTT_TW_OTF with NTT_CHECK (the product then runs apart from the
+    inverse) and in natural order (a permutation around the passes): the
+    product of two polynomials against the oracle's pipeline, and a word
+    >= q reported."""
+    N, L = 1 << 15, 2
+    qs = orc.find_primes(30, 17, L)
+    psis = [orc.psi(q, N) for q in qs]
+    host = ntt_synth.rns_batch(2140, qs, N, 2)
+    for flags in (nt.NTT_TW_OTF | nt.NTT_CHECK | nt.NTT_ORDER_BITREV, nt.NTT_TW_OTF):
+        p = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, flags)
+        try:
+            d = to_dev(host)
+            nt.ntt_forward(p, d, 2)
+            c = torch.empty_like(d[:L * N])
+            nt.ntt_pointwise_inverse(p, c, d[:L * N], d[L * N:], 1)
+            got = to_host(c, (1, L, N))
+            assert nt.ntt_get_device_status(p) == nt.NTT_OK
+            if flags & nt.NTT_CHECK:
+                bad = to_dev(host)
+                bad[5] = qs[0]                     # one word equal to q
+                nt.ntt_forward(p, bad, 2)
+                assert nt.ntt_get_device_status(p) == nt.NTT_ERR_INPUT_RANGE
+        finally:
+            nt.ntt_plan_destroy(p)
+        A = orc.ntt_batch(host, qs, psis)
+        want = orc.ntt_batch(orc.pointwise_batch(A[:1], A[1:], qs), qs, psis, inverse=True)
+        assert np.array_equal(got, want), flags
