@@ -402,7 +402,7 @@ def rns_n2p14(nt, torch, dev, reps=50):
             "ms_per_step": ms, "value": n / (ms / 1e3), "unit": "NTT/s"}
 
 
-def autotune_survey(nt, torch, dev):
+def autotune_shapes(nt, torch, dev):
     """The autotuner on other two-pass shapes: which form wins per
     direction (0: one-warp chunk CTAs, 1: 16-chunk CTAs, 2: streamed)."""
     sh = torch.cuda.current_stream(dev).cuda_stream
@@ -519,7 +519,7 @@ def main():
                     help="skip the autotuner (default two-pass forms), e.g. for launch lists under ncu")
     ap.add_argument("--extra", default=None,
                     choices=["ragged", "wide_word_u64", "tc_fourstep", "cluster_form", "base_conv",
-                             "variants_n1024", "rns_n2p14", "autotune_survey", "tw_otf"],
+                             "variants_n1024", "rns_n2p14", "autotune_shapes", "tw_otf"],
                     help="run only this side measurement and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -550,7 +550,7 @@ def main():
     if args.extra:
         fn = {"ragged": ragged_vs_plain, "wide_word_u64": wide_word, "tc_fourstep": tc_fourstep,
               "cluster_form": cluster_form, "base_conv": base_conv, "variants_n1024": variants_n1024,
-              "rns_n2p14": rns_n2p14, "autotune_survey": autotune_survey, "tw_otf": tw_otf}[args.extra]
+              "rns_n2p14": rns_n2p14, "autotune_shapes": autotune_shapes, "tw_otf": tw_otf}[args.extra]
         print(json.dumps({args.extra: fn(nt, torch, dev)}), flush=True)
         return 0
     from paper_2405_11353_gb300 import build as nb
@@ -681,7 +681,7 @@ def main():
         for name, fn in (("ragged", ragged_vs_plain), ("wide_word_u64", wide_word),
                          ("tc_fourstep", tc_fourstep), ("cluster_form", cluster_form),
                          ("base_conv", base_conv), ("variants_n1024", variants_n1024),
-                         ("rns_n2p14", rns_n2p14), ("autotune_survey", autotune_survey), ("tw_otf", tw_otf)):
+                         ("rns_n2p14", rns_n2p14), ("autotune_shapes", autotune_shapes), ("tw_otf", tw_otf)):
             try:
                 extras[name] = fn(nt, torch, dev)
             except Exception as exc:     # a side measurement never hides the main line
