@@ -225,9 +225,10 @@ ntt_status ntt_pointwise_inverse(ntt_plan_t plan, void *d_c, const void *d_a,
  * (x^N + 1, q).  d_work is a device buffer of at least 2*pairs*L*N words
  * (its contents are overwritten).  The products are computed as up to 8
  * chunks of pairs (fused plans with one or two pairs: windows of limbs of
- * each pair, about 4 chunks in all) in a pipeline: each chunk's host-to-device copy, its
- * forward NTTs, pointwise product and inverse NTT, and its device-to-host
- * copy, with the copies on two streams the plan owns and the transforms on
+ * each pair, about 4 chunks in all) in a pipeline: each chunk's
+ * host-to-device copy, its forward NTTs, pointwise product and inverse NTT,
+ * and its device-to-host copy, with the copies on two streams the plan
+ * owns and the transforms on
  * `stream`, so copies of one chunk overlap the arithmetic of others.  The
  * call is ordered after earlier work on `stream`, and later work on `stream`
  * after all of it; the caller synchronises `stream` before reading h_out.
