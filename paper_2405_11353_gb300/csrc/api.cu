@@ -1,7 +1,6 @@
 // api.cu -- the C ABI of libnttgb: validation, plan building, dispatch.
 #include <cuda_runtime.h>
 
-#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
