@@ -246,19 +246,21 @@ ntt_status ntt_polymul_host(ntt_plan_t plan, void *h_out, const void *h_in,
  * memory -- a framework that owns all device memory through its own pool, a
  * latency-bound loop that cannot afford cudaMalloc's implicit device
  * synchronisation, a plugin under a fixed memory budget -- it runs the
- * forward transform with the Stockham dataflow (Sec. II) using, as its
- * ping-pong buffer, a fixed 8 MiB device array that is part of the library
- * (held by every GPU that loads the library until the process exits).  The
- * caller passes the data; no cudaMalloc, cudaFree or other allocating call
- * is made.  Same result and order as ntt_forward on the same plan.
- *   - Plans with the fused variant and N >= 16 have no per-stage tables:
- *     NTT_ERR_UNSUPPORTED.
+ * forward transform with the Stockham dataflow using, as its ping-pong
+ * buffer, a fixed 8 MiB device array that is part of the library (held by
+ * every GPU that loads the library until the process exits).  The caller
+ * passes the data; no cudaMalloc, cudaFree or other allocating call is
+ * made.  Same result, order and NTT_CHECK behaviour as ntt_forward on the
+ * same plan; ntt_plan_last_launches counts its launches.
+ *   - Plans without per-stage tables -- the fused variant with N >= 16 and
+ *     the tensor-core four-step variant -- get NTT_ERR_UNSUPPORTED.
  *   - batch * L * N * word bytes must not exceed 8 MiB, else
  *     NTT_ERR_SCRATCH_LIMIT (e.g. at most one 32-limb polynomial of 2^16
  *     u32 words per call).
  *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) and caches it; make that first call before any
- *     stream capture.
+ *     (cudaGetSymbolAddress) and caches it per CUDA context; make that first
+ *     call, and the first call after a cudaDeviceReset, before any stream
+ *     capture.
  *   - All calls share the array and it keeps the last call's contents
  *     (nothing in it needs to start at zero); calls whose work overlaps on
  *     the GPU race on it.

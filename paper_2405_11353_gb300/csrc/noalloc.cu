@@ -20,8 +20,14 @@
 // Host code cannot use the array's name as a device address: in host code
 // it names a host-side stand-in.  The first call on each device therefore
 // looks up the array's device address with cudaGetSymbolAddress (with that
-// device current) and keeps it; later calls reuse it.  That first call
-// should come before any stream capture.
+// device current) and keeps it, with the device's SM count; later calls
+// reuse both.  That first call should come before any stream capture.  The
+// address belongs to the CUDA context it was looked up in: after
+// cudaDeviceReset the device gets a new primary context, the library's
+// module is loaded again and the array may sit elsewhere, so the cache is
+// keyed on the current context and the address is looked up again when the
+// context changes (that next call, too, should come before any capture).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -40,30 +46,66 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 std::mutex g_mu;
-void *g_addr[kMaxDevices] = {};
+struct DevCache {
+    CUcontext ctx;     // the context the address was looked up in
+    void *addr;        // device address of g_noalloc_scratch there
+    unsigned max_grid; // 32 CTAs of kThreads per SM
+};
+DevCache g_cache[kMaxDevices] = {};
 
-// Device address of g_noalloc_scratch on the current device (looked up once).
-cudaError_t scratch_address(void **out) {
+constexpr int kThreads = 256;
+
+// The driver's cuCtxGetCurrent, reached through the runtime (the library
+// does not link the driver library, so it loads on machines without one).
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &f, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(f);
+    }
+    return fn;
+}
+
+// Device address of g_noalloc_scratch on the current device, and the grid
+// limit for its kernels (looked up once per device and context).
+cudaError_t scratch_address(void **out, unsigned *max_grid) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    CtxGetCurrentFn get_ctx = ctx_get_current();
+    if (!get_ctx) return cudaErrorNotSupported;
+    // the context the kernels will run in (none is current before the
+    // runtime's first call on this thread: the symbol lookup below makes the
+    // device's primary context current)
+    CUcontext ctx = nullptr;
+    if (get_ctx(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    DevCache &c = g_cache[dev];
+    if (!ctx || !c.addr || c.ctx != ctx) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_addr[dev] = p;
+        if (get_ctx(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        c.ctx = ctx;
+        c.addr = p;
+        c.max_grid = (unsigned)(sms > 0 ? sms : 1) * 32u;
     }
-    *out = g_addr[dev];
+    *out = c.addr;
+    *max_grid = c.max_grid;
     return cudaSuccess;
 }
 
-constexpr int kThreads = 256;
-
-unsigned grid_for(uint64_t work) {
+unsigned grid_for(uint64_t work, unsigned max_grid) {
     uint64_t g = (work + kThreads - 1) / kThreads;
-    if (g > 152ull * 32) g = 152ull * 32;
+    if (g > max_grid) g = max_grid;
     return g ? (unsigned)g : 1u;
 }
 
@@ -131,22 +173,31 @@ __global__ void k_bitrev_na(W *__restrict__ x, uint32_t logN, uint64_t total) {
     }
 }
 
+// Counts its launches in p.last_launches.
 template <class W, int RED>
-cudaError_t run_noalloc(ntt_plan_s &p, W *data, W *scr, uint32_t batch, cudaStream_t st) {
+cudaError_t run_noalloc(ntt_plan_s &p, W *data, W *scr, uint32_t batch, unsigned mg, cudaStream_t st) {
     const uint32_t logN = p.logN, L = p.L, N = p.N;
     const uint64_t total = (uint64_t)batch * L * N;
     const uint64_t total_bf = total / 2;
     const Tw<W> *wt = reinterpret_cast<const Tw<W> *>(p.d_w_fwd);
     const Tw<W> *twist = reinterpret_cast<const Tw<W> *>(p.d_twist);
-    k_twist_na<W, RED><<<grid_for(total), kThreads, 0, st>>>(data, twist, p.d_limb, logN, L, total);
+    k_twist_na<W, RED><<<grid_for(total, mg), kThreads, 0, st>>>(data, twist, p.d_limb, logN, L, total);
+    ++p.last_launches;
     W *src = data, *dst = scr;
     for (uint32_t s = 1; s <= logN; ++s) {
-        k_stockham_na<W, RED><<<grid_for(total_bf), kThreads, 0, st>>>(dst, src, wt, p.d_limb, logN, L, s,
-                                                                        total_bf);
+        k_stockham_na<W, RED><<<grid_for(total_bf, mg), kThreads, 0, st>>>(dst, src, wt, p.d_limb, logN, L, s,
+                                                                            total_bf);
+        ++p.last_launches;
         W *t = src; src = dst; dst = t;
     }
-    if (src != data) k_copy_na<W><<<grid_for(total), kThreads, 0, st>>>(data, src, total);
-    if (p.bitrev_order) k_bitrev_na<W><<<grid_for(total), kThreads, 0, st>>>(data, logN, total);
+    if (src != data) {
+        k_copy_na<W><<<grid_for(total, mg), kThreads, 0, st>>>(data, src, total);
+        ++p.last_launches;
+    }
+    if (p.bitrev_order) {
+        k_bitrev_na<W><<<grid_for(total, mg), kThreads, 0, st>>>(data, logN, total);
+        ++p.last_launches;
+    }
     return cudaGetLastError();
 }
 
@@ -157,25 +208,32 @@ extern "C" ntt_status ntt_forward_noalloc(ntt_plan_t plan, void *d_data, uint32_
     if ((reinterpret_cast<uintptr_t>(d_data) & 15u) != 0) return NTT_ERR_ALIGNMENT;
     ntt_plan_s &p = *plan;
     // the Stockham dataflow needs the per-stage tables, which every plan
-    // except the fused one (N >= 16) builds
+    // builds except the fused ones with N >= 16 and the tensor-core
+    // four-step ones
     if (!p.d_w_fwd || !p.d_twist) return NTT_ERR_UNSUPPORTED;
     const size_t bytes = (size_t)batch * p.L * p.N * p.word_bytes();
     if (bytes > kNoAllocScratchBytes) return NTT_ERR_SCRATCH_LIMIT;
     void *scr = nullptr;
-    if (scratch_address(&scr) != cudaSuccess) { cudaGetLastError(); return NTT_ERR_CUDA; }
+    unsigned mg = 0;
+    if (scratch_address(&scr, &mg) != cudaSuccess) { cudaGetLastError(); return NTT_ERR_CUDA; }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t e;
+    p.last_launches = 0;
+    cudaError_t e = cudaSuccess;
+    // NTT_CHECK: record input words >= q in the plan's status word, as
+    // ntt_forward does (the check writes only that existing word)
+    if (p.check) e = nttgb::launch_check_range(p, d_data, batch, st);
+    if (e != cudaSuccess) { cudaGetLastError(); return NTT_ERR_CUDA; }
     if (p.word64) {
         switch (p.red) {
-        case RED_SHOUP: e = run_noalloc<uint64_t, RED_SHOUP>(p, (uint64_t *)d_data, (uint64_t *)scr, batch, st); break;
-        case RED_BARRETT: e = run_noalloc<uint64_t, RED_BARRETT>(p, (uint64_t *)d_data, (uint64_t *)scr, batch, st); break;
-        default: e = run_noalloc<uint64_t, RED_MONTGOMERY>(p, (uint64_t *)d_data, (uint64_t *)scr, batch, st); break;
+        case RED_SHOUP: e = run_noalloc<uint64_t, RED_SHOUP>(p, (uint64_t *)d_data, (uint64_t *)scr, batch, mg, st); break;
+        case RED_BARRETT: e = run_noalloc<uint64_t, RED_BARRETT>(p, (uint64_t *)d_data, (uint64_t *)scr, batch, mg, st); break;
+        default: e = run_noalloc<uint64_t, RED_MONTGOMERY>(p, (uint64_t *)d_data, (uint64_t *)scr, batch, mg, st); break;
         }
     } else {
         switch (p.red) {
-        case RED_SHOUP: e = run_noalloc<uint32_t, RED_SHOUP>(p, (uint32_t *)d_data, (uint32_t *)scr, batch, st); break;
-        case RED_BARRETT: e = run_noalloc<uint32_t, RED_BARRETT>(p, (uint32_t *)d_data, (uint32_t *)scr, batch, st); break;
-        default: e = run_noalloc<uint32_t, RED_MONTGOMERY>(p, (uint32_t *)d_data, (uint32_t *)scr, batch, st); break;
+        case RED_SHOUP: e = run_noalloc<uint32_t, RED_SHOUP>(p, (uint32_t *)d_data, (uint32_t *)scr, batch, mg, st); break;
+        case RED_BARRETT: e = run_noalloc<uint32_t, RED_BARRETT>(p, (uint32_t *)d_data, (uint32_t *)scr, batch, mg, st); break;
+        default: e = run_noalloc<uint32_t, RED_MONTGOMERY>(p, (uint32_t *)d_data, (uint32_t *)scr, batch, mg, st); break;
         }
     }
     if (e != cudaSuccess) { cudaGetLastError(); return NTT_ERR_CUDA; }

@@ -309,6 +309,36 @@ def test_batch_wrappers(orc):
     assert np.array_equal(got, out.reshape(12, N)[t.astype(int), k.astype(int)])
 
 
+def test_pointwise_batch_limb_by_limb(orc):
+    """orc_pointwise_batch on [batch][L][N] arrays at odd L and batch: every
+    (polynomial, limb) block equals orc_pointwise with that limb's prime
+    (itself pinned by the q = 17 worked example below), so a wrong limb
+    index (t % L) or a wrong block stride fails.  The primes differ in
+    every limb, and one block is also checked against Python integers."""
+    import ntt_synth
+    g = _read_golden("q17_n4.txt")
+    assert orc.pointwise(g["A"], g["B"], 17).tolist() == g["C"]
+    for B, L, N, bits in ((3, 5, 16, 30), (5, 3, 64, 60), (1, 7, 8, 30), (7, 1, 32, 60)):
+        qs = orc.find_primes(bits, 8, L)
+        assert len(set(qs)) == L
+        a = ntt_synth.rns_batch(71 + B, qs, N, B)
+        b = ntt_synth.rns_batch(97 + B, qs, N, B)
+        c = orc.pointwise_batch(a, b, qs)
+        assert c.shape == (B, L, N)
+        for p in range(B):
+            for l in range(L):
+                assert np.array_equal(c[p, l], orc.pointwise(a[p, l], b[p, l], qs[l])), (B, L, p, l)
+        p, l = B - 1, L - 1
+        assert [int(v) for v in c[p, l]] == [int(x) * int(y) % qs[l] for x, y in zip(a[p, l], b[p, l])]
+    # a limb index taken from the wrong prime would change these: the same
+    # residues multiplied under two different primes give different products
+    qs = orc.find_primes(30, 8, 2)
+    a = np.full((1, 2, 4), (1 << 29) + 12345, dtype=np.uint64)
+    c = orc.pointwise_batch(a, a, qs)
+    assert [int(c[0, l, 0]) for l in range(2)] == [((1 << 29) + 12345) ** 2 % q for q in qs]
+    assert int(c[0, 0, 0]) != int(c[0, 1, 0])
+
+
 def test_synth_residues_in_range():
     import ntt_synth
     for q in (12289, (1 << 30) - 35, 1152921504606830593):
