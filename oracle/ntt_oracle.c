@@ -171,6 +171,13 @@ int orc_find_primes(int bits, int m, int count, uint64_t *out)
 
 /* ------------------------------------------------- definitional O(N^2) */
 
+/* One Horner step acc * x + c, reduced once: acc, x < q < 2^62 and
+ * c < 2^64, so the 128-bit sum is exact before the `%`. */
+static uint64_t horner_step(uint64_t acc, uint64_t x, uint64_t c, uint64_t q)
+{
+    return (uint64_t)(((u128)acc * (u128)x + (u128)c) % (u128)q);
+}
+
 /* X[k] = sum_{n<N} a[n] psi^{(2k+1) n}: the polynomial a evaluated at the
  * root psi^(2k+1) of x^N + 1, by Horner's rule. */
 uint64_t orc_ntt_fwd_at(uint64_t q, uint64_t psi, uint64_t N,
@@ -179,7 +186,7 @@ uint64_t orc_ntt_fwd_at(uint64_t q, uint64_t psi, uint64_t N,
     uint64_t x = orc_powmod(psi, 2 * k + 1, q);
     uint64_t acc = 0;
     for (uint64_t n = N; n-- > 0;)
-        acc = orc_addmod(orc_mulmod(acc, x, q), a[n] % q, q);
+        acc = horner_step(acc, x, a[n], q);
     return acc;
 }
 
@@ -191,7 +198,7 @@ uint64_t orc_ntt_inv_at(uint64_t q, uint64_t psi, uint64_t N,
     uint64_t y = orc_powmod(psi_inv, 2 * n, q);
     uint64_t acc = 0;
     for (uint64_t k = N; k-- > 0;)
-        acc = orc_addmod(orc_mulmod(acc, y, q), X[k] % q, q);
+        acc = horner_step(acc, y, X[k], q);
     acc = orc_mulmod(acc, orc_powmod(psi_inv, n, q), q);
     return orc_mulmod(acc, orc_invmod(N % q, q), q);
 }
