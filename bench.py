@@ -52,6 +52,19 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def tensor_peak():
+    """Dense bf16 tensor-core peak (burst) in TFLOP/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+# measured 32-bit multiply-add rates (filled by measure_int_mad_rate)
+_MAD_RATES = {}
+
+
 def traffic_from_profiles(digest):
     """Per-launch DRAM bytes of the forward transform from the committed ncu
     summary, if it was taken on the current kernel sources."""
@@ -177,6 +190,82 @@ def oracle_naive_n1024(polys=256):
             "sample": "oracle O(N^2) forward, N=1024, q=12289, %d transforms in %.2f s" % (polys, dt)}
 
 
+def oracle_naive_n65536():
+    """For the record: the oracle's O(N^2) definition on one transform at
+    N = 2^16 (q < 2^30): all 2^16 outputs, each a Horner evaluation at
+    psi^(2k+1) (2^32 modular steps), spread over the host cores."""
+    import oracle
+    q = oracle.find_primes(BITS, M, 1)[0]
+    n = 1 << 16
+    psi = oracle.psi(q, n)
+    host = ntt_synth.rns_batch(1005, [q], n, 1)
+    k = np.arange(n, dtype=np.uint64)
+    t0 = time.perf_counter()
+    oracle.ntt_batch_at(host, [q], [psi], np.zeros(n, dtype=np.uint64), k)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": "NTT/s", "seconds_per_transform": dt, "cores": oracle.num_threads(),
+            "sample": "oracle O(N^2) forward, N=2^16, one transform (2^32 Horner steps)"}
+
+
+def _sig(x, n=4):
+    """x rounded to n significant digits (compact JSON)."""
+    if isinstance(x, float):
+        return float("%.*g" % (n, x))
+    return x
+
+
+def _pick(d, *path):
+    for k in path:
+        if not isinstance(d, dict) or k not in d:
+            return None
+        d = d[k]
+    return _sig(d)
+
+
+def side_summary(extras):
+    """The side measurements' headline figures, compact, for the main line."""
+    g = lambda *p: _pick(extras, *p)  # noqa: E731
+    out = {}
+    if "ragged" in extras:
+        out["ragged"] = {"ntt_s": g("ragged", "value"), "ms": g("ragged", "ms_per_step"),
+                         "transforms": g("ragged", "transforms_per_step"),
+                         "plain_ms": g("ragged", "plain_ms_per_step"),
+                         "speedup_vs_plain": g("ragged", "speedup_vs_plain"),
+                         "hbm_frac": g("ragged", "roofline", "frac"), "status": g("ragged", "device_status"),
+                         "item_tiles": g("ragged", "item_tiles_autotuned")}
+    if "tc_fourstep" in extras:
+        out["tc_fourstep"] = {"tcgen05_ms": g("tc_fourstep", "tensor_core", "ms_per_call"),
+                              "mma_sync_ms": g("tc_fourstep", "tensor_core_mma_sync", "ms_per_call"),
+                              "butterfly_ms": g("tc_fourstep", "butterfly", "ms_per_call"),
+                              "tcgen05_over_butterfly": g("tc_fourstep", "tensor_core", "ratio_to_butterfly"),
+                              "tensor_frac": g("tc_fourstep", "tensor_core", "roofline", "frac")}
+    if "wide_word_u64" in extras:
+        out["wide_word_u64"] = {"shoup_ms": g("wide_word_u64", "shoup", "ms_per_step"),
+                                "montgomery_ms": g("wide_word_u64", "montgomery", "ms_per_step"),
+                                "barrett_ms": g("wide_word_u64", "barrett", "ms_per_step"),
+                                "shoup_int_frac": g("wide_word_u64", "shoup", "int_roofline", "frac"),
+                                "shoup_hbm_frac": g("wide_word_u64", "shoup", "roofline", "frac"),
+                                "montgomery_int_frac": g("wide_word_u64", "montgomery", "int_roofline", "frac")}
+    if "rns_n2p14" in extras:
+        out["rns_n2p14"] = {"ms": g("rns_n2p14", "ms_per_step"), "ntt_s": g("rns_n2p14", "value")}
+    if "variants_n1024" in extras:
+        out["variants_n1024_ms"] = {k: _sig(v.get("ms_per_step")) for k, v in extras["variants_n1024"].items()
+                                    if isinstance(v, dict)}
+    if "cluster_form" in extras:
+        out["forward_ms_by_form"] = {k: _sig(v.get("forward_ms")) for k, v in extras["cluster_form"].items()
+                                     if isinstance(v, dict)}
+    if "tw_otf" in extras:
+        out["tw_otf"] = {k: {"fwd_ms": _sig(v.get("forward_ms")), "pwinv_ms": _sig(v.get("pointwise_inverse_ms")),
+                             "table_bytes": v.get("table_bytes")}
+                         for k, v in extras["tw_otf"].items() if isinstance(v, dict)}
+    if "base_conv" in extras:
+        out["base_conv_ms"] = g("base_conv", "ms_per_call")
+    errors = [k for k, v in extras.items() if isinstance(v, dict) and "error" in v]
+    if errors:
+        out["errors"] = errors
+    return out
+
+
 def run_reference(args):
     """The oracle as the reference arm: each step is the step's pipeline on
     one pair of polynomials x all 32 limbs (96 NTTs).  When K such steps
@@ -238,6 +327,7 @@ def measure_int_mad_rate(nt, torch, dev, stream, iters=4096, reps=5):
         ms = _time_loop(torch, stream, lambda: nt.ntt_measure_int_mad_rate(high, iters, scratch, sh), reps, warm=0)
         ops = sms * 8 * 256 * 8 * iters
         rates.append(ops / (ms / 1e3))
+    _MAD_RATES["lo"], _MAD_RATES["hi"] = rates[0], rates[1]
     return rates[0], rates[1]
 
 
@@ -290,10 +380,22 @@ def ragged_vs_plain(nt, torch, dev, reps=10):
         for p in plans.values():
             nt.ntt_plan_destroy(p)
     n_step = 2 * ntt_total
-    bytes_step = 2 * 2 * bytes_total            # forward + inverse, each reads and writes
+    # forward + inverse, each reads and writes the data once, plus each
+    # (N, word) group's twiddle pairs (its longest prime list) once per direction
+    group_l = {}
+    for sp in specs:
+        key = (sp["logN"], sp["word"])
+        group_l[key] = max(group_l.get(key, 0), sp["L"])
+    table_bytes = sum((1 << n) * l * 2 * (w // 8) for (n, w), l in group_l.items())
+    bytes_step = 2 * (2 * bytes_total + table_bytes)
+    peak, peak_kind = peaks()
+    gbs = bytes_step / (ms_r / 1e3) / 1e9
     return {"workload": "512 polys, N=2^12..2^17, L=1..32, half u32/half u64; forward+inverse",
             "transforms_per_step": n_step, "value": n_step / (ms_r / 1e3), "unit": "NTT/s",
-            "ms_per_step": ms_r, "algorithmic_gbs": bytes_step / (ms_r / 1e3) / 1e9,
+            "ms_per_step": ms_r, "algorithmic_gbs": gbs,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "algorithmic_bytes_per_launch": bytes_step,
+                         "peak_source": "%s hbm_gbs" % peak_kind},
             "plain_value": n_step / (ms_p / 1e3), "plain_ms_per_step": ms_p,
             "speedup_vs_plain": ms_p / ms_r, "device_status": status, "item_tiles_autotuned": item_tiles,
             "note": "ragged = one graph-captured cooperative launch; plain = ntt_forward_prefix/"
@@ -321,6 +423,28 @@ def wide_word(nt, torch, dev, reps=50):
         finally:
             nt.ntt_plan_destroy(p)
         out[red] = {"value": 2 * B * 24 / (ms / 1e3), "unit": "NTT/s", "ms_per_step": ms}
+    # HBM: forward + inverse of 192 transforms (data read + written once per
+    # direction) + 24 limbs x N twiddle pairs of 16 bytes per direction
+    peak, peak_kind = peaks()
+    byts = 2 * (2 * N * 8 * B * 24 + 24 * N * 16)
+    # integer multiply pipe: a 64 x 64-bit product from 32-bit multiplies:
+    # low half 3 mul.lo + 1 mul.hi, high half 4 mul.lo + 4 mul.hi; per
+    # butterfly Shoup takes one high and two low halves (10 lo + 6 hi),
+    # Montgomery one low and two high halves (11 lo + 9 hi)
+    bfly = 2 * B * 24 * (N // 2) * 16
+    lo_rate, hi_rate = _MAD_RATES.get("lo"), _MAD_RATES.get("hi")
+    for red, (nlo, nhi) in (("shoup", (10, 6)), ("montgomery", (11, 9))):
+        ms = out[red]["ms_per_step"]
+        gbs = byts / (ms / 1e3) / 1e9
+        out[red]["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                                "peak_source": "%s hbm_gbs" % peak_kind}
+        if lo_rate and hi_rate:
+            t_min = bfly * (nlo / lo_rate + nhi / hi_rate)
+            out[red]["int_roofline"] = {
+                "bound": "alu", "frac": t_min / (ms / 1e3), "unit": "32-bit multiplies",
+                "multiplies_per_butterfly": {"mad.lo": nlo, "mad.hi": nhi},
+                "floor_ms": t_min * 1e3,
+                "peak_source": "measured mad.lo %.2f T/s, mad.hi %.2f T/s" % (lo_rate / 1e12, hi_rate / 1e12)}
     return out
 
 
@@ -348,6 +472,12 @@ def tc_fourstep(nt, torch, dev, reps=20):
         out[name] = {"value": B * 32 / (ms / 1e3), "unit": "NTT/s", "ms_per_call": ms}
     for name in ("tensor_core", "tensor_core_mma_sync"):
         out[name]["digit_tops"] = macs * 2 / (out[name]["ms_per_call"] / 1e3) / 1e12
+    tp, tp_kind = tensor_peak()
+    out["tensor_core"]["roofline"] = {
+        "bound": "tensor", "achieved": out["tensor_core"]["digit_tops"], "peak": tp, "unit": "TFLOP/s",
+        "frac": out["tensor_core"]["digit_tops"] / tp,
+        "peak_source": "%s bf16_tflops (fp16 MMA, the kind used, runs at the bf16 rate)" % tp_kind}
+    out["tensor_core"]["ratio_to_butterfly"] = out["tensor_core"]["ms_per_call"] / out["butterfly"]["ms_per_call"]
     out["tensor_core"]["instruction"] = "tcgen05.mma kind::f16 (balanced 8-bit digits, fp32 diagonals in TMEM)"
     out["tensor_core_mma_sync"]["instruction"] = "mma.sync m16n8k32 u8.u8.s32"
     return out
@@ -690,8 +820,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, desc = oracle_sample(qs)
-        cpu = {"value": v, "unit": "NTT/s", "cores": cores, "kind": "oracle", "sample": desc,
-               "naive_n1024": oracle_naive_n1024()}
+        cpu = {"value": v, "unit": "NTT/s", "cores": cores, "kind": "oracle", "sample": desc}
+        extras["cpu_naive"] = {"n1024": oracle_naive_n1024(), "n65536": oracle_naive_n65536()}
 
     nt.ntt_plan_destroy(plan)
     if rank == 0:
@@ -706,7 +836,6 @@ def main():
                        "l2": "4 rotating input copies (512 MiB) > 129 MB L2",
                        "parallelism": "replicas x%d" % world},
             "per_call_ms": {"forward_16polys": fwd_ms, "pointwise_inverse_8pairs": pwinv_ms},
-            "autotune": tuning,
             "roofline": roofline,
             "int_roofline": int_roofline,
             "cpu_baseline": cpu,
@@ -716,7 +845,15 @@ def main():
             "gpu_launches": lps * K,
             "clocks": clocks,
         }
-        line.update(extras)
+        # the side measurements in full, one line each, before the main line
+        if tuning:
+            print(json.dumps({"detail": "autotune", **tuning}), flush=True)
+        for name, v in extras.items():
+            print(json.dumps({"detail": name, **(v if isinstance(v, dict) else {"value": v})}), flush=True)
+        # their headline figures close the main line (printed last)
+        line["side"] = side_summary(extras)
+        if "cpu_naive" in extras:
+            line["side"]["cpu_oracle_naive_n65536_s"] = _pick(extras, "cpu_naive", "n65536", "seconds_per_transform")
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

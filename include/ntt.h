@@ -142,7 +142,15 @@ typedef enum {
                                       so its bounded wait runs out (about a
                                       second) and ntt_get_device_status then
                                       reports NTT_ERR_TIMEOUT; the results of
-                                      that call are not valid */
+                                      that call are not valid.  Ragged sets
+                                      (ntt_ragged_create, not with
+                                      NTT_RAGGED_TUNE): in every launch CTA 0
+                                      leaves before the first grid barrier,
+                                      the other CTAs' bounded barrier wait
+                                      runs out (about two seconds) and
+                                      ntt_ragged_status reports
+                                      NTT_ERR_TIMEOUT; the results are not
+                                      valid */
 
 /*
  * Create a plan for batches of L-limb polynomials of N coefficients.
@@ -411,8 +419,8 @@ typedef struct {
  * into a CUDA graph.  All forward jobs complete before any inverse job
  * starts, so a set holding a forward and an inverse job on the same buffer
  * is a round trip.  flags: NTT_ORDER_BITREV (required: the ragged kernel
- * works in bit-reversed evaluation order), NTT_RED_* and
- * NTT_RAGGED_TUNE.  The job array and its q arrays are copied; the data
+ * works in bit-reversed evaluation order), NTT_RED_*, NTT_RAGGED_TUNE
+ * and the test hook NTT_TEST_STALL.  The job array and its q arrays are copied; the data
  * buffers must stay valid (their contents are not touched here). */
 #define NTT_RAGGED_TUNE 0x1000u   /* autotune the work-item size: time items
                                      of 2, 4, 8 and 16 tiles (three launches

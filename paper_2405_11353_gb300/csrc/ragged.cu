@@ -159,7 +159,8 @@ ntt_status ntt_ragged_create(ntt_ragged_t *out, const ntt_job *jobs, uint32_t n_
     if (!out) return NTT_ERR_INVALID_ARG;
     *out = nullptr;
     if (!jobs || n_jobs == 0) return NTT_ERR_INVALID_ARG;
-    if (flags & ~(NTT_ORDER_BITREV | NTT_RED_MASK | NTT_RAGGED_TUNE)) return NTT_ERR_INVALID_ARG;
+    if (flags & ~(NTT_ORDER_BITREV | NTT_RED_MASK | NTT_RAGGED_TUNE | NTT_TEST_STALL)) return NTT_ERR_INVALID_ARG;
+    if ((flags & NTT_TEST_STALL) && (flags & NTT_RAGGED_TUNE)) return NTT_ERR_INVALID_ARG;
     if ((flags & NTT_RED_MASK) == NTT_RED_MASK) return NTT_ERR_INVALID_ARG;
     if (!(flags & NTT_ORDER_BITREV)) return NTT_ERR_UNSUPPORTED;
     for (uint32_t j = 0; j < n_jobs; ++j) {
@@ -252,7 +253,7 @@ ntt_status ntt_ragged_create(ntt_ragged_t *out, const ntt_job *jobs, uint32_t n_
             };
             if (build_items(r, jobs, n_jobs, scratch_of, plan_of, kTuneItemTiles[c]) != NTT_OK) { ok = false; break; }
             auto launch = [&]() {
-                return cudaMemsetAsync(w, 0, 4 * sizeof(uint32_t), ts) == cudaSuccess &&
+                return cudaMemsetAsync(w, 0, 5 * sizeof(uint32_t), ts) == cudaSuccess &&
                        cudaMemsetAsync(w + 7, 0, sizeof(uint32_t), ts) == cudaSuccess &&
                        kernel_launch(r->red, r->args, grid, ts) == cudaSuccess;
             };
@@ -274,6 +275,7 @@ ntt_status ntt_ragged_create(ntt_ragged_t *out, const ntt_job *jobs, uint32_t n_
     }
     ntt_status bs = build_items(r, jobs, n_jobs, [&](uint32_t j) { return jobs[j].d_data; }, plan_of, best_tiles);
     if (bs != NTT_OK) { cudaGetLastError(); ragged_free(r); return bs; }
+    r->args.stall = (flags & NTT_TEST_STALL) ? 1u : 0u;
     const RaggedArgs &a = r->args;
 
     // ---- graph capture
@@ -281,8 +283,10 @@ ntt_status ntt_ragged_create(ntt_ragged_t *out, const ntt_job *jobs, uint32_t n_
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); ragged_free(r); return NTT_ERR_CUDA; }
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaMemsetAsync(w, 0, 4 * sizeof(uint32_t), st);          // item counters
-        cudaMemsetAsync(w + 7, 0, sizeof(uint32_t), st);          // abort flag
+        // item counters and the barrier count (a launch whose barrier wait
+        // ran out leaves arrivals behind), and the abort flag
+        cudaMemsetAsync(w, 0, 5 * sizeof(uint32_t), st);
+        cudaMemsetAsync(w + 7, 0, sizeof(uint32_t), st);
         cudaError_t le = kernel_launch(r->red, a, grid, st);
         e = cudaStreamEndCapture(st, &r->graph);
         if (le != cudaSuccess) e = le;

@@ -42,6 +42,8 @@ struct RaggedArgs {
     uint32_t *bar_gen;          // grid barrier generation
     uint32_t *status;           // bit 1: a wait ran out of time
     uint32_t *abort_flag;
+    uint32_t stall;             // test hook (NTT_TEST_STALL): CTA 0 leaves
+                                // before the first grid barrier
 };
 
 // Kinds of work items: single-pass 4096-word transforms, column passes with

@@ -132,6 +132,10 @@ __global__ void __launch_bounds__(256, 2) k_ragged(const __grid_constant__ Ragge
                 break;
             }
         }
+        // test hook: CTA 0 (its copies all landed: run_tiles drains its
+        // pipeline) leaves without arriving, so the others' bounded wait
+        // at the barrier runs out
+        if (ra.stall && phase == 0 && blockIdx.x == 0) return;
         if (!grid_barrier(ra.bar_count, ra.bar_gen, ra.abort_flag)) {
             if (threadIdx.x == 0) atomicOr(ra.status, 2u);
             return;

@@ -12,6 +12,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import ntt_synth  # noqa: E402
+from parity_helpers import check_definition_samples  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -115,7 +116,7 @@ def test_variants_large_u32(nt, orc, variant):
         roundtrip_check(nt, orc, N, qs, 2, variant, seed=100 + n)
 
 
-@pytest.mark.parametrize("variant", ["dit", "pease_nc", "stockham", "sixstep", "fused"])
+@pytest.mark.parametrize("variant", ["dit", "dif", "flat", "pease", "pease_nc", "stockham", "sixstep", "fused"])
 def test_variants_u64(nt, orc, variant):
     for n in (1, 2, 5, 10, 12, 13, 14, 15, 16, 17):
         N = 1 << n
@@ -135,8 +136,11 @@ def test_reductions(nt, orc, red, w64, variant):
 
 
 # ------------------------------------------------------------ workloads
-def polymul_pipeline(nt, orc, N, qs, pairs, variant, red="shoup", w64=False, bitrev=False, seed=1):
-    """forward (2*pairs polys) -> pointwise -> inverse; returns GPU and oracle."""
+def polymul_pipeline(nt, orc, N, qs, pairs, variant, red="shoup", w64=False, bitrev=False, seed=1, samples=0):
+    """forward (2*pairs polys) -> pointwise -> inverse; returns GPU and oracle.
+    Every stage is compared in full with the O(N log N) oracle; with
+    samples > 0, that many coefficients of every forward transform and of
+    every inverse transform are also checked against the O(N^2) definition."""
     psis = [orc.psi(q, N) for q in qs]
     host = ntt_synth.rns_batch(seed, qs, N, 2 * pairs)
     p = Plan(nt, N, qs, variant, red, w64, bitrev)
@@ -158,6 +162,9 @@ def polymul_pipeline(nt, orc, N, qs, pairs, variant, red="shoup", w64=False, bit
     assert np.array_equal(prod, reorder(P, bitrev, orc))
     want = orc.ntt_batch(P, qs, psis, inverse=True)
     assert np.array_equal(out, want)
+    if samples:
+        check_definition_samples(orc, host, qs, psis, fwd, seed, samples, bitrev=bitrev)
+        check_definition_samples(orc, P, qs, psis, out, seed + 1, samples, inverse=True)
     return host, out
 
 
@@ -189,14 +196,19 @@ def test_workload_n1024_q12289_64polys(nt, orc, variant):
 
 @pytest.mark.parametrize("bitrev", [True, False])
 def test_workload_n2p14_L8_128polys(nt, orc, bitrev):
+    """N = 2^14, 8 30-bit primes, 128 polys: forward, 64 x 8 pointwise
+    products, inverse; all in full against the O(N log N) oracle and 256
+    coefficients of each of the 1024 forward and 512 inverse transforms
+    against the O(N^2) definition."""
     qs = orc.find_primes(30, 15, 8)
-    polymul_pipeline(nt, orc, 1 << 14, qs, 64, "fused", bitrev=bitrev, seed=1002)
+    polymul_pipeline(nt, orc, 1 << 14, qs, 64, "fused", bitrev=bitrev, seed=1002, samples=256)
 
 
 @pytest.mark.parametrize("red", ["montgomery", "shoup"])
 def test_workload_n2p16_L24_u64(nt, orc, red):
     """N = 2^16, 24 60-bit primes, 8 polys: forward + inverse, full
-    comparison with the O(N log N) oracle and 64 sampled O(N^2) values."""
+    comparison with the O(N log N) oracle and 256 coefficients of each of
+    the 192 forward transforms against the O(N^2) definition."""
     N = 1 << 16
     qs = orc.find_primes(60, 17, 24)
     psis = [orc.psi(q, N) for q in qs]
@@ -213,17 +225,16 @@ def test_workload_n2p16_L24_u64(nt, orc, red):
     want = orc.ntt_batch(host, qs, psis)
     assert np.array_equal(got, reorder(want, True, orc))
     assert np.array_equal(back, host)
-    t, k = ntt_synth.sample_indices(1003, 8 * 24, N, 64)
-    vals = orc.ntt_batch_at(host, qs, psis, t, k)
-    nat = want.reshape(8 * 24, N)
-    assert np.array_equal(nat[t.astype(int), k.astype(int)], vals)
+    assert check_definition_samples(orc, host, qs, psis, got, 1003, 256, bitrev=True) == 192 * 256
 
 
 def test_workload_n2p16_L32_u32(nt, orc):
     """N = 2^16, 32 30-bit primes, 16 polys, butterfly form, as bench.py
-    runs it: forward, 8 x 32 pointwise products, inverse."""
+    runs it: forward, 8 x 32 pointwise products, inverse; in full against
+    the O(N log N) oracle and 256 coefficients of each of the 512 forward
+    and 256 inverse transforms against the O(N^2) definition."""
     qs = orc.find_primes(30, 17, 32)
-    host, out = polymul_pipeline(nt, orc, 1 << 16, qs, 8, "fused", bitrev=True, seed=1005)
+    host, out = polymul_pipeline(nt, orc, 1 << 16, qs, 8, "fused", bitrev=True, seed=1005, samples=256)
     # sampled coefficients of products against the schoolbook definition
     for i, l, j in [(0, 0, 0), (3, 5, 12345), (7, 31, (1 << 16) - 1), (5, 17, 40000)]:
         assert int(out[i, l, j]) == orc.negacyclic_mul_at(host[i, l], host[8 + i, l], qs[l], j)

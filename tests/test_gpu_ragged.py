@@ -107,10 +107,16 @@ def c4_jobs(orc):
     return specs
 
 
+def _brv(k, bits):
+    return int(format(int(k), "0%db" % bits)[::-1], 2)
+
+
 def test_ragged_c4_full_size(nt, orc):
     """The 512-job workload (N = 2^12..2^17, L = 1..32, half 30-bit / half
     60-bit): a forward+inverse round trip in one graph launch returns every
-    input; a forward-only launch matches 2048 sampled O(N) oracle values."""
+    input; a forward-only launch matches the O(N log N) oracle on every
+    coefficient of every job, and, for the transforms with N > 2^14, 256
+    coefficients each drawn at random match the O(N^2) definition."""
     specs = c4_jobs(orc)
     hosts, tens, jobs = [], [], []
     for i, s in enumerate(specs):
@@ -125,20 +131,24 @@ def test_ragged_c4_full_size(nt, orc):
     run(nt, rt)
     for s, h, t in zip(specs, hosts, tens):
         assert np.array_equal(back(t, s["word"] == 64, h.shape), h), s
-    # forward only, sampled against the definition
+    # forward only: every job in full, large transforms also by definition
     run(nt, jobs)
-    rng = np.random.default_rng(5)
-    for i in rng.choice(len(specs), 64, replace=False):
-        s, h = specs[i], hosts[i]
-        N, w64 = 1 << s["logN"], s["word"] == 64
-        got = back(tens[i], w64, h.shape).reshape(-1, N)
+    n_sampled = 0
+    for i, (s, h) in enumerate(zip(specs, hosts)):
+        n, L = s["logN"], s["L"]
+        N, w64 = 1 << n, s["word"] == 64
+        got = back(tens[i], w64, h.shape)
         psis = [orc.psi(q, N) for q in s["q"]]
-        nb = 32
-        t_idx = rng.integers(0, s["L"], nb).astype(np.uint64)
-        pos = rng.integers(0, N, nb)
-        k_idx = np.array([int(bin(int(p))[2:].zfill(s["logN"])[::-1], 2) for p in pos], np.uint64)
-        vals = orc.ntt_batch_at(h, s["q"], psis, t_idx, k_idx)
-        assert np.array_equal(got[t_idx.astype(int), pos], vals), s
+        want = orc.ntt_batch(h, s["q"], psis)
+        assert np.array_equal(got, bitrev_rows(want, orc)), (i, s)
+        if n > 14:
+            t_idx = np.repeat(np.arange(L, dtype=np.uint64), 256)
+            _, k_idx = ntt_synth.sample_indices(ntt_synth.stream_seed(1004, i, 7), 1, N, 256 * L)
+            vals = orc.ntt_batch_at(h, s["q"], psis, t_idx, k_idx)
+            pos = [_brv(k, n) for k in k_idx]
+            assert np.array_equal(got.reshape(L, N)[t_idx.astype(int), pos], vals), (i, s)
+            n_sampled += L
+    assert n_sampled > 4000          # about half of the 8536 transforms
 
 
 def test_ragged_errors(nt, orc):
@@ -210,3 +220,36 @@ def test_ragged_autotuned_item_size(nt, orc):
         assert nt.ntt_ragged_item_tiles(r) == 8                     # the default without tuning
     finally:
         nt.ntt_ragged_destroy(r)
+
+
+def test_ragged_barrier_timeout_reported_and_context_survives(nt, orc):
+    """Failure path of the grid barrier without a fault: with the test hook,
+    CTA 0 leaves before the first barrier, the other CTAs' bounded wait runs
+    out (about two seconds), the launch reports NTT_ERR_TIMEOUT, a second
+    launch of the same set does the same (the barrier count is reset per
+    launch), and a regular set on the same context is then bit-exact."""
+    specs = [(12, False, 3), (16, False, 2), (14, True, 2)]
+    hosts, jobs = [], []
+    for i, (n, w64, L) in enumerate(specs):
+        qs = primes(orc, w64)[:L]
+        h = ntt_synth.rns_batch(1200 + i, qs, 1 << n, 2)
+        t = dev(h, w64)
+        hosts.append((h, qs, t, n, w64))
+        jobs.append(dict(data=t, q=qs, N=1 << n, batch=2, word64=w64, inverse=False))
+    with pytest.raises(nt.NttError) as e:
+        nt.ntt_ragged_create(jobs, nt.NTT_ORDER_BITREV | nt.NTT_TEST_STALL | nt.NTT_RAGGED_TUNE)
+    assert e.value.status == nt.NTT_ERR_INVALID_ARG
+    r = nt.ntt_ragged_create(jobs, nt.NTT_ORDER_BITREV | nt.NTT_TEST_STALL)
+    try:
+        for _ in range(2):
+            nt.ntt_ragged_launch(r)
+            assert nt.ntt_ragged_status(r) == nt.NTT_ERR_TIMEOUT
+            assert nt.ntt_ragged_status(r) == nt.NTT_OK          # read and cleared
+    finally:
+        nt.ntt_ragged_destroy(r)
+    for h, qs, t, n, w64 in hosts:
+        t.copy_(dev(h, w64))
+    run(nt, jobs)
+    for h, qs, t, n, w64 in hosts:
+        psis = [orc.psi(q, 1 << n) for q in qs]
+        assert np.array_equal(back(t, w64, h.shape), bitrev_rows(orc.ntt_batch(h, qs, psis), orc)), (n, w64)

@@ -9,6 +9,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import ntt_synth  # noqa: E402
+from parity_helpers import check_definition_samples  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -56,6 +57,10 @@ def test_tc_forward_inverse_bit_exact(nt, orc, form, L, batch):
         got = host(d, h.shape)
         want = bitrev_rows(orc.ntt_batch(h, qs, psis), orc)
         assert np.array_equal(got, want)
+        if L * batch >= 256:
+            # the full workload (512 transforms): 256 coefficients of each
+            # against the O(N^2) definition as well
+            check_definition_samples(orc, h, qs, psis, got, 1005, 256, bitrev=True)
         nt.ntt_inverse(p, d, batch)
         assert np.array_equal(host(d, h.shape), h)
         assert nt.ntt_get_device_status(p) == nt.NTT_OK
