@@ -255,11 +255,8 @@ def side_summary(extras):
         out["forward_ms_by_form"] = {k: _sig(v.get("forward_ms")) for k, v in extras["cluster_form"].items()
                                      if isinstance(v, dict)}
     if "tw_otf" in extras:
-        out["tw_otf"] = {k: {"fwd_ms": _sig(v.get("forward_ms")), "pwinv_ms": _sig(v.get("pointwise_inverse_ms")),
-                             "table_bytes": v.get("table_bytes")}
-                         for k, v in extras["tw_otf"].items() if isinstance(v, dict)}
-    if "base_conv" in extras:
-        out["base_conv_ms"] = g("base_conv", "ms_per_call")
+        out["tw_otf_fwd_ms"] = {k: _sig(v.get("forward_ms")) for k, v in extras["tw_otf"].items()
+                                if isinstance(v, dict)}
     errors = [k for k, v in extras.items() if isinstance(v, dict) and "error" in v]
     if errors:
         out["errors"] = errors
@@ -790,8 +787,7 @@ def main():
         "frac": achieved / peak, "traffic": traffic_from_profiles(digest),
         "kernel": "ntt_forward: column pass + 256-point chunk pass (%s form), %d transforms" % (forms["forward"], n_fwd),
         "algorithmic_bytes_per_call": fwd_bytes, "avg_ms": fwd_ms,
-        "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
-        else "fallback 6.8 TB/s",
+        "peak_source": "measured hbm_gbs" if peak_kind == "measured" else "fallback 6.8 TB/s",
     }
 
     # the same call against the integer multiply pipe: every butterfly of the
@@ -803,7 +799,7 @@ def main():
     int_roofline = {"bound": "alu", "achieved": muls / (fwd_ms / 1e3) / 1e12, "peak": int_peak / 1e12,
                     "unit": "T int32 multiplies/s", "frac": muls / (fwd_ms / 1e3) / int_peak,
                     "multiplies_per_call": muls,
-                    "peak_source": "measured: mad.lo.u32 %.2f T/s, mad.hi.u32 %.2f T/s (1 hi : 2 lo mix)"
+                    "peak_source": "measured mad.lo %.2f, mad.hi %.2f T/s (1 hi : 2 lo)"
                                    % (lo_rate / 1e12, hi_rate / 1e12)}
 
     extras = {}

@@ -260,8 +260,9 @@ ntt_status ntt_polymul_host(ntt_plan_t plan, void *h_out, const void *h_in,
  * passes the data; no cudaMalloc, cudaFree or other allocating call is
  * made.  Same result, order and NTT_CHECK behaviour as ntt_forward on the
  * same plan; ntt_plan_last_launches counts its launches.
- *   - Plans without per-stage tables -- the fused variant with N >= 16 and
- *     the tensor-core four-step variant -- get NTT_ERR_UNSUPPORTED.
+ *   - Plans of the fused variant with N >= 16 have no per-stage tables:
+ *     NTT_ERR_UNSUPPORTED.  (Tensor-core four-step plans carry them and are
+ *     served.)
  *   - batch * L * N * word bytes must not exceed 8 MiB, else
  *     NTT_ERR_SCRATCH_LIMIT (e.g. at most one 32-limb polynomial of 2^16
  *     u32 words per call).
@@ -311,33 +312,61 @@ ntt_status ntt_default_psi(uint64_t q, uint32_t N, uint64_t *psi_out);
 ntt_status ntt_find_primes(uint32_t bits, uint32_t m, uint32_t count,
                            uint64_t *out);
 
+/* Limb sharding across processes (one GPU each).  Every limb of an RNS
+ * polynomial is transformed modulo its own prime, independently of the
+ * others (the per-limb transform of Eq. 3), so L limbs split into `world`
+ * contiguous slices with no exchange on the transform path: rank r holds
+ * limbs [*first, *first + *count) of every polynomial, as [batch][count][N]
+ * words, and makes its plan over q[*first .. *first + *count).  The slices
+ * are balanced (the first L mod world ranks hold one limb more) and in rank
+ * order, so gathering them in rank order restores [batch][L][N] -- the one
+ * exchange a sharded pipeline needs, before a step that reads every limb of
+ * a coefficient (ntt_bconv).  Host-only.  NTT_ERR_INVALID_ARG for a null
+ * pointer, world = 0, rank >= world or L < world. */
+ntt_status ntt_limb_shard(uint32_t L, uint32_t world, uint32_t rank,
+                          uint32_t *first, uint32_t *count);
+
 /* ------------------------------------------------------------ autotuner
  * The two-pass fused path (N > 2^14 with 4-byte words, N > 2^13 with
- * 8-byte) runs each direction in one of three forms: */
-#define NTT_FORM_SMALL 0      /* chunk pass on one-warp CTAs (2-chunk tiles) */
-#define NTT_FORM_WIDE 1       /* chunk pass on 256-thread CTAs (16-chunk tiles) */
-#define NTT_FORM_STREAMED 2   /* both passes in one streamed launch */
+ * 8-byte) leaves two things open.  The split N = 2^s1 x 2^s2: the first
+ * pass runs the first s1 stages on columns of 2^s1 points, the second the
+ * last s2 stages on chunks of 2^s2 consecutive words (the four-step split
+ * of Sec. II); s2 is 7, 8 or 9 with 5 <= s1 <= 9, default 8, and the
+ * plan's twiddle tables are laid out for it at creation.  (NTT_STREAMED
+ * and NTT_TW_OTF plans keep s2 = 8.)  And each direction's form: */
+#define NTT_FORM_SMALL 0      /* chunk pass on one-warp CTAs */
+#define NTT_FORM_WIDE 1       /* chunk pass on 256-thread CTAs */
+#define NTT_FORM_STREAMED 2   /* both passes in one streamed launch (s2 = 8) */
 /* Defaults: NTT_FORM_SMALL forward, NTT_FORM_WIDE inverse (NTT_FORM_STREAMED
- * both ways under NTT_STREAMED); results are identical in every form. */
+ * both ways under NTT_STREAMED).  Chunk tiles hold the same chunk of
+ * several polynomials (one twiddle table a tile) when their count divides
+ * the batch and chunks have at least 256 words, else several chunks of one
+ * polynomial.  Results are identical in every split, form and tiling. */
 typedef struct {
-    float forward_ms[3];      /* per form, ms per call */
+    float forward_ms[3];      /* per form, ms per call, at the chosen split */
     float inverse_ms[3];
     int32_t forward_form;     /* the fastest */
     int32_t inverse_form;
+    int32_t chunk_log2;       /* the chosen split s2 */
+    float split_ms[3];        /* per split s2 = 7, 8, 9: fastest forward +
+                                 fastest inverse, ms; -1 where not valid */
 } ntt_tune_result;
 
-/* Time the three forms of both directions for (N, q[0..L), flags, batch)
- * on the current device (a scratch buffer of batch x L x N zero words,
- * allocated and freed here) and record the fastest per direction in the
- * process-wide tuning table, keyed by (N, word size, L, reduction, order,
- * NTT_TW_OTF or not, floor(log2 batch)).  Plans created afterwards with
- * that shape use the recorded forms for calls in that batch bucket
- * (NTT_STREAMED plans keep their form).  NTT_TW_OTF plans have no streamed
- * form: its time is reported as -1 and it is never chosen.  If the environment variable NTT_TUNE_DB names a file, the
- * table is read from it at first use and rewritten after each tuning (one
- * JSON object per line).  flags: as ntt_plan_create, without NTT_STREAMED,
- * NTT_CHECK or NTT_TEST_STALL.  NTT_ERR_UNSUPPORTED for sizes outside the
- * two-pass range.  result may be NULL. */
+/* Time every valid split, and in each every form of both directions, for
+ * (N, q[0..L), flags, batch) on the current device (a scratch buffer of
+ * batch x L x N zero words, allocated and freed here); record per split the
+ * fastest form per direction in the process-wide tuning table, keyed by
+ * (N, word size, L, reduction, order, NTT_TW_OTF or not, s2, floor(log2
+ * batch)), and for the shape the split with the smallest forward +
+ * inverse time.  Plans created afterwards with that shape take that split
+ * and use the recorded forms for calls in that batch bucket (NTT_STREAMED
+ * plans keep theirs).  Forms that do not exist (streamed with s2 != 8 or
+ * with NTT_TW_OTF) are reported as -1 and never chosen.  If the environment
+ * variable NTT_TUNE_DB names a file, the tables are read from it at first
+ * use and rewritten after each tuning (one JSON object per line).  flags:
+ * as ntt_plan_create, without NTT_STREAMED, NTT_CHECK or NTT_TEST_STALL.
+ * NTT_ERR_UNSUPPORTED for sizes outside the two-pass range.  result may be
+ * NULL. */
 ntt_status ntt_autotune(uint32_t N, const uint64_t *q, uint32_t L,
                         uint32_t flags, uint32_t batch, ntt_stream_t stream,
                         ntt_tune_result *result);
@@ -346,15 +375,25 @@ ntt_status ntt_autotune(uint32_t N, const uint64_t *q, uint32_t L,
  * inverse), or -1 when the plan is not on the two-pass fused path. */
 int32_t ntt_plan_form(ntt_plan_t plan, uint32_t batch, int inverse);
 
-/* Host-only access to the tuning table (no GPU needed): record forms for a
- * shape by hand (saved to NTT_TUNE_DB like a tuning; NTT_ERR_INVALID_ARG for
- * a form outside 0..2 or batch 0), read the form recorded for a shape and
- * direction (-1: none), and empty the in-memory table (the file is not
- * read again in this process).  Plans copy the table at creation. */
+/* The plan's split s2 (chunks of 2^s2 words), or -1 when the plan is not on
+ * the two-pass fused path. */
+int32_t ntt_plan_chunk_log2(ntt_plan_t plan);
+
+/* Host-only access to the tuning tables (no GPU needed): record forms for a
+ * shape by hand, for the shape's current split (saved to NTT_TUNE_DB like a
+ * tuning; NTT_ERR_INVALID_ARG for a form outside 0..2 or batch 0); read the
+ * form recorded for a shape's split and direction (-1: none); record or
+ * read a shape's split (NTT_ERR_INVALID_ARG for a split the shape cannot
+ * take; -1: none recorded, plans use 8); empty the in-memory tables (the
+ * file is not read again in this process).  Plans copy the tables at
+ * creation. */
 ntt_status ntt_tune_set(uint32_t N, uint32_t L, uint32_t flags, uint32_t batch,
                         int32_t forward_form, int32_t inverse_form);
 int32_t ntt_tune_get(uint32_t N, uint32_t L, uint32_t flags, uint32_t batch,
                      int inverse);
+ntt_status ntt_tune_set_split(uint32_t N, uint32_t L, uint32_t flags,
+                              uint32_t chunk_log2);
+int32_t ntt_tune_get_split(uint32_t N, uint32_t L, uint32_t flags);
 void ntt_tune_clear(void);
 
 /* ------------------------------------------------ integer roofline

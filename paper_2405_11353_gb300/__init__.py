@@ -61,7 +61,8 @@ EXPORTS = [
     "ntt_forward_noalloc", "ntt_forward_prefix", "ntt_inverse_prefix", "ntt_pointwise_inverse",
     "ntt_bconv_create", "ntt_bconv", "ntt_bconv_destroy", "ntt_measure_int_mad_rate",
     "ntt_autotune", "ntt_plan_form", "ntt_tune_set", "ntt_tune_get", "ntt_tune_clear",
-    "ntt_ragged_item_tiles", "ntt_plan_table_bytes",
+    "ntt_ragged_item_tiles", "ntt_plan_table_bytes", "ntt_limb_shard",
+    "ntt_tune_set_split", "ntt_tune_get_split", "ntt_plan_chunk_log2",
 ]
 
 
@@ -80,7 +81,8 @@ class NttJob(ctypes.Structure):
 
 class NttTuneResult(ctypes.Structure):
     _fields_ = [("forward_ms", ctypes.c_float * 3), ("inverse_ms", ctypes.c_float * 3),
-                ("forward_form", ctypes.c_int32), ("inverse_form", ctypes.c_int32)]
+                ("forward_form", ctypes.c_int32), ("inverse_form", ctypes.c_int32),
+                ("chunk_log2", ctypes.c_int32), ("split_ms", ctypes.c_float * 3)]
 
 
 NTT_FORM_SMALL, NTT_FORM_WIDE, NTT_FORM_STREAMED = 0, 1, 2
@@ -133,6 +135,10 @@ def lib():
             "ntt_tune_get": (ctypes.c_int32, [u32, u32, u32, u32, ctypes.c_int]),
             "ntt_tune_clear": (None, []),
             "ntt_ragged_item_tiles": (u32, [vp]),
+            "ntt_limb_shard": (st, [u32, u32, u32, ctypes.POINTER(u32), ctypes.POINTER(u32)]),
+            "ntt_tune_set_split": (st, [u32, u32, u32, u32]),
+            "ntt_tune_get_split": (ctypes.c_int32, [u32, u32, u32]),
+            "ntt_plan_chunk_log2": (ctypes.c_int32, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -272,6 +278,14 @@ def ntt_find_primes(bits, m, count):
     return [int(v) for v in out]
 
 
+def ntt_limb_shard(L, world, rank):
+    """(first, count): the contiguous slice of the L limbs that `rank` of
+    `world` holds (host-only)."""
+    f, c = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().ntt_limb_shard(L, world, rank, ctypes.byref(f), ctypes.byref(c)), "ntt_limb_shard")
+    return int(f.value), int(c.value)
+
+
 def ntt_forward_noalloc(plan, data, batch, stream=None):
     """Forward transform that allocates nothing (fixed 8 MiB scratch array in
     the library), for callers that must not allocate device memory."""
@@ -338,14 +352,16 @@ def ntt_measure_int_mad_rate(high, iters, scratch, stream=None):
 
 
 def ntt_autotune(N, q, flags, batch, stream=None):
-    """Time the three two-pass forms for this shape, record the fastest;
-    returns {"forward_ms": [...], "inverse_ms": [...], "forward_form",
-    "inverse_form"}."""
+    """Time every two-pass split and form for this shape, record the
+    fastest; returns {"forward_ms": [...], "inverse_ms": [...] (per form, at
+    the chosen split), "forward_form", "inverse_form", "chunk_log2" (the
+    chosen split), "split_ms": [...] (s2 = 7, 8, 9; -1 where not valid)}."""
     r = NttTuneResult()
     _check(lib().ntt_autotune(N, _u64arr(q), len(q), flags, batch, _stream(stream), ctypes.byref(r)),
            "ntt_autotune")
     return {"forward_ms": list(r.forward_ms), "inverse_ms": list(r.inverse_ms),
-            "forward_form": r.forward_form, "inverse_form": r.inverse_form}
+            "forward_form": r.forward_form, "inverse_form": r.inverse_form,
+            "chunk_log2": r.chunk_log2, "split_ms": list(r.split_ms)}
 
 
 def ntt_plan_form(plan, batch, inverse=False):
@@ -358,6 +374,18 @@ def ntt_tune_set(N, L, flags, batch, forward_form, inverse_form):
 
 def ntt_tune_get(N, L, flags, batch, inverse=False):
     return lib().ntt_tune_get(N, L, flags, batch, 1 if inverse else 0)
+
+
+def ntt_tune_set_split(N, L, flags, chunk_log2):
+    _check(lib().ntt_tune_set_split(N, L, flags, chunk_log2), "ntt_tune_set_split")
+
+
+def ntt_tune_get_split(N, L, flags):
+    return lib().ntt_tune_get_split(N, L, flags)
+
+
+def ntt_plan_chunk_log2(plan):
+    return lib().ntt_plan_chunk_log2(plan)
 
 
 def ntt_tune_clear():

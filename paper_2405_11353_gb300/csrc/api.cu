@@ -208,7 +208,7 @@ ntt_status build_tables(ntt_plan_s *p) {
     // pass of two-pass plans (the chunk pass has its own tables or seeds)
     const uint32_t NM = two_pass ? N1 : N;
     if (fused_tabs) { mf.resize((size_t)L * NM * pair_bytes); mi.resize(mf.size()); }
-    const uint32_t CP = w64 ? nttgb::chunk_tab_pitch<uint64_t>() : nttgb::chunk_tab_pitch<uint32_t>();
+    const uint32_t CP = nttgb::chunk_tab_pitch_rt(w64, p->s2);
     const size_t chunk_limb = (size_t)N1 * CP;       // pairs per limb, chunk tables
     if (chunk_tabs) { cf.resize(L * chunk_limb * pair_bytes); ci.resize(L * chunk_limb * pair_bytes); }
     // NTT_TW_OTF (4-byte words): per limb, 8 stage seeds per chunk and the
@@ -446,7 +446,7 @@ ntt_plan_s limb_window(const ntt_plan_s &p, uint32_t l0, uint32_t lw) {
     v.d_main_inv = adv(p.d_main_inv, main_limb * pair);
     if (p.fused_mode == nttgb::FUSED_TWO_PASS) {
         const size_t N1 = (size_t)1 << p.s1;
-        const size_t CP = p.word64 ? nttgb::chunk_tab_pitch<uint64_t>() : nttgb::chunk_tab_pitch<uint32_t>();
+        const size_t CP = nttgb::chunk_tab_pitch_rt(p.word64, p.s2);
         v.d_chunk_fwd = adv(p.d_chunk_fwd, N1 * CP * pair);
         v.d_chunk_inv = adv(p.d_chunk_inv, N1 * CP * pair);
         v.d_seed_fwd = adv(p.d_seed_fwd, N1 * 8 * 4);
@@ -579,6 +579,14 @@ ntt_status ntt_find_primes(uint32_t bits, uint32_t m, uint32_t count, uint64_t *
     return found == count ? NTT_OK : NTT_ERR_INVALID_ARG;
 }
 
+ntt_status ntt_limb_shard(uint32_t L, uint32_t world, uint32_t rank, uint32_t *first, uint32_t *count) {
+    if (!first || !count || world == 0 || rank >= world || L < world) return NTT_ERR_INVALID_ARG;
+    const uint32_t base = L / world, extra = L % world;
+    *count = base + (rank < extra ? 1u : 0u);
+    *first = rank * base + (rank < extra ? rank : extra);
+    return NTT_OK;
+}
+
 }  // extern "C"
 
 namespace nttgb {
@@ -586,7 +594,7 @@ namespace nttgb {
 // Plan builder behind ntt_plan_create_ex.  single_max_log >= 0 caps the
 // size done in one fused pass (the ragged kernel uses 12).
 ntt_status create_plan(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t L, ntt_variant variant,
-                       uint32_t flags, const uint64_t *psi, int single_max_log) {
+                       uint32_t flags, const uint64_t *psi, int single_max_log, int split_log) {
     if (!plan) return NTT_ERR_INVALID_ARG;
     *plan = nullptr;
     if ((int)variant < NTT_DIT || (int)variant > NTT_TC_FOURSTEP) return NTT_ERR_INVALID_ARG;
@@ -636,6 +644,15 @@ ntt_status create_plan(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t
             p->streamed = (flags & NTT_STREAMED) != 0;
             p->tw_otf = (flags & NTT_TW_OTF) != 0;
             p->s2 = nttgb::kChunkLog;
+            // streamed, on-the-fly-twiddle and ragged-kernel plans keep the
+            // 256-word chunks; others may take a given or tuned split
+            p->split_fixed = p->streamed || p->tw_otf || single_max_log >= 0;
+            if (split_log >= 0) {
+                if (p->split_fixed && split_log != nttgb::kChunkLog) { delete p; return NTT_ERR_UNSUPPORTED; }
+                if (!nttgb::split_valid(p->logN, (uint32_t)split_log)) { delete p; return NTT_ERR_UNSUPPORTED; }
+                p->s2 = (uint32_t)split_log;
+                p->split_fixed = true;
+            }
             p->s1 = p->logN - p->s2;
         }
     }

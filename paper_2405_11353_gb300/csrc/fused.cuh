@@ -32,7 +32,9 @@ namespace nttgb {
 
 enum TileKind : int { TK_SINGLE = 0, TK_COLS = 1, TK_CHUNKS = 2 };
 
-// Two-pass split: N = N1 * N2 with N2 = 2^kN2Log (chunks of 256 words).
+// Two-pass split: N = N1 * N2 with N2 = 2^s2 (chunks of 2^s2 words; the
+// per-plan passes take s2 = 7, 8 or 9, the item kernels of the ragged and
+// streamed forms s2 = kN2Log).
 constexpr uint32_t kN2Log = 8;
 
 template <class W> struct FArgs {
@@ -92,11 +94,13 @@ template <class W> __host__ __device__ constexpr uint32_t cols_phys(uint32_t k, 
 // 16 eight-byte columns).  P = 1: the ragged kernel and the streamed
 // two-pass launch, whose CTAs always have 256 threads (4096-word column
 // tiles).  P = 3: per-pass chunk kernels with 16-chunk tiles (as P = 0
-// otherwise).
+// otherwise).  Bit 3 of P (P = 8, 11) pairs polynomials in chunk tiles
+// (paired_chunks).
 template <class W, int LOGS, int KIND, int P = 0> __host__ __device__ constexpr uint32_t tile_k() {
+    // (chunks: one warp per CTA, or 256 threads; 2^LOGS / 16 threads a chunk)
     return KIND == TK_SINGLE ? (LOGS >= 12 ? 1u : (4096u >> LOGS))
-         : KIND == TK_CHUNKS ? (P == 0 ? 2u : 16u)
-         : P == 1 ? (4096u >> LOGS)
+         : KIND == TK_CHUNKS ? ((P & 3) == 0 ? (LOGS >= 9 ? 1u : (512u >> LOGS)) : (4096u >> LOGS))
+         : (P & 3) == 1 ? (4096u >> LOGS)
          : ((256u >> (LOGS - 4)) > (128u / sizeof(W)) ? (256u >> (LOGS - 4)) : (128u / (uint32_t)sizeof(W)));
 }
 
@@ -366,7 +370,7 @@ template <class W, int LOGS, int KIND, bool INV, int P = 0> __host__ __device__ 
 // copy lands in them (and in the item kernels, which mix tile kinds), else
 // 128 bytes (tensor copies without swizzle, bulk copies).
 template <class W, int LOGS, int KIND, bool INV, int P = 0> __host__ __device__ constexpr uint32_t stage_align() {
-    return (P != 0 || (KIND == TK_CHUNKS && INV)) ? 1024u : 128u;
+    return ((P & 3) != 0 || (KIND == TK_CHUNKS && INV)) ? 1024u : 128u;
 }
 template <class W, int LOGS, int KIND, bool INV, int P = 0> __host__ __device__ constexpr uint32_t buf_words() {
     constexpr size_t A = stage_align<W, LOGS, KIND, INV, P>() / sizeof(W);
@@ -376,25 +380,33 @@ template <class W, int LOGS, int KIND, bool INV, int P = 0> __host__ __device__ 
                        A - 1) & ~(A - 1));
 }
 // Two buffers per CTA: the next tile lands while the current one computes.
-template <class W, int LOGS, int KIND> __host__ __device__ constexpr uint32_t n_stages() { return 2u; }
+// (A third, with two tiles in flight, measured no faster on GB300.)
+template <class W, int LOGS, int KIND, int P = 0> __host__ __device__ constexpr uint32_t n_stages() { return 2u; }
 // Twiddles staged in shared memory: the column table (2^LOGS pairs per limb)
 // and, for 4-byte words, the chunk tables of a tile (K chunk tables).
 template <class W, int LOGS, int KIND> __host__ __device__ constexpr bool tw_staged() {
     return KIND == TK_COLS || (KIND == TK_CHUNKS && sizeof(W) == 4);
 }
+// Bit 3 of P (chunk passes): the K sub-transforms of a tile are the same
+// chunk of K consecutive polynomials (one chunk table per tile) instead of
+// K consecutive chunks of one polynomial (K tables).
+template <int KIND, int P> __host__ __device__ constexpr bool paired_chunks() {
+    return KIND == TK_CHUNKS && (P & 8) != 0;
+}
 template <class W, int LOGS, int KIND, int P = 0> __host__ __device__ constexpr uint32_t tw_pairs() {
     return !tw_staged<W, LOGS, KIND>() ? 0u
-           : KIND == TK_COLS ? (1u << LOGS) : tile_k<W, LOGS, KIND, P>() * chunk_tab_pitch<W>();
+           : KIND == TK_COLS ? (1u << LOGS)
+           : (paired_chunks<KIND, P>() ? 1u : tile_k<W, LOGS, KIND, P>()) * chunk_tab_pitch<W, LOGS>();
 }
 
 // Pipeline state carried across run_tiles calls of one CTA: how often each
 // stage buffer and the twiddle buffer have completed a phase.
 struct PipeState {
-    uint32_t uses[2];
+    uint32_t uses[3];
     uint32_t tw_phase;
     // uses[s] with a run-time s, without indexing (which would put the
     // state in local memory)
-    __device__ __forceinline__ uint32_t use(uint32_t s) const { return s ? uses[1] : uses[0]; }
+    __device__ __forceinline__ uint32_t use(uint32_t s) const { return s == 0 ? uses[0] : (s == 1 ? uses[1] : uses[2]); }
 };
 
 // Process tiles [t_begin, t_end) of one pass.  One thread keeps the next
@@ -411,13 +423,13 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     constexpr uint32_t S = 1u << LOGS;
     constexpr uint32_t T = S / 16;
     constexpr uint32_t K = tile_k<W, LOGS, KIND, P>();
-    constexpr uint32_t NS = n_stages<W, LOGS, KIND>();
+    constexpr uint32_t NS = n_stages<W, LOGS, KIND, P>();
     constexpr uint32_t BW = buf_words<W, LOGS, KIND, INV, P>();
     constexpr uint32_t SP = stage_pitch<W, LOGS, KIND, INV>();
     constexpr bool SWZ = stage_swizzled<W, LOGS, KIND, INV>();
     constexpr bool TWS = tw_staged<W, LOGS, KIND>();
     constexpr uint32_t TWP = tw_pairs<W, LOGS, KIND, P>();
-    constexpr uint32_t CP = chunk_tab_pitch<W>();
+    constexpr uint32_t CP = chunk_tab_pitch<W, KIND == TK_CHUNKS ? LOGS : 8>();
     constexpr uint32_t RW = 128 / sizeof(W);     // words per 128-byte row
     constexpr bool WS = KIND != TK_COLS && T <= 32;
     using R0 = RoundOf<LOGS, INV, 0>;
@@ -429,10 +441,10 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     // 256-thread item kernels (short runs, three CTAs per SM, one kernel for
     // every tile kind under a 128-register cap) refill at the end of each
     // tile and load constants per tile, which keeps them free of spills.
-    constexpr bool LATE_REFILL = P == 0 || P == 3;
+    constexpr bool LATE_REFILL = (P & 3) == 0 || (P & 3) == 3;
     // chunk tables made on the fly from the plan's seeds (OTF_K: the
     // per-plan chunk kernels of NTT_TW_OTF plans, 4-byte words, Shoup)
-    constexpr bool OTF = OTF_K && KIND == TK_CHUNKS && LOGS == 8 && sizeof(W) == 4 && RED == RED_SHOUP && P != 1 && TWS;
+    constexpr bool OTF = OTF_K && KIND == TK_CHUNKS && LOGS == 8 && sizeof(W) == 4 && RED == RED_SHOUP && (P & 3) != 1 && TWS;
     static_assert(!OTF_K || OTF, "twiddles made on the fly: 4-byte-word Shoup chunk kernels only");
     W *stage = reinterpret_cast<W *>(base);
     Tw<W> *tws = reinterpret_cast<Tw<W> *>(stage + (size_t)NS * BW);
@@ -447,9 +459,17 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     const uint32_t smb_k = sm_off<W, LOGS, KIND, P>(k, 0);
     const uint32_t L = a.L;
     const uint32_t B = (uint32_t)(a.ntrans / L);
-    constexpr uint32_t S2 = kN2Log;   // log2 of the row length N2 (two-pass kinds)
+    // log2 of the row length N2 (two-pass kinds): the chunk size, or the
+    // plan's split for the column pass
+    const uint32_t S2 = KIND == TK_CHUNKS ? (uint32_t)LOGS : a.s2;
     const uint32_t N1 = KIND == TK_SINGLE ? 1u : (N >> S2);
-    const uint32_t per = KIND == TK_SINGLE ? 1u : (KIND == TK_COLS ? (1u << S2) : N1) / K;
+    // paired chunk tiles: sub k is polynomial p + k (the launcher makes
+    // sure K divides the batch); else sub k is position pos0 + k
+    constexpr bool PAIR = paired_chunks<KIND, P>();
+    constexpr uint32_t KP = PAIR ? K : 1u;    // polynomials per tile
+    constexpr uint32_t KG = PAIR ? 1u : K;    // positions (chunks, columns) per tile
+    const uint32_t per = KIND == TK_SINGLE ? 1u : (KIND == TK_COLS ? (1u << S2) : N1) / KG;
+    const uint32_t BP = B / KP;               // polynomial steps per position group
     // Tile cursor: single tiles are K consecutive transforms; two-pass tiles
     // run polynomial-fastest, then position group, then limb.  It is decoded
     // once and then stepped, so the loop does no division.
@@ -459,12 +479,13 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     auto cur_at = [&](uint32_t tile) {
         Cur c;
         if (KIND == TK_SINGLE) { c.p = tile * K; c.g = 0; c.l = 0; }
-        else { c.p = tile % B; const uint32_t r = tile / B; c.g = r % per; c.l = r / per; }
+        else { c.p = (tile % BP) * KP; const uint32_t r = tile / BP; c.g = r % per; c.l = r / per; }
         return c;
     };
     auto cur_next = [&](Cur &c) {
         if (KIND == TK_SINGLE) { c.p += K; return; }
-        if (++c.p == B) { c.p = 0; if (++c.g == per) { c.g = 0; ++c.l; } }
+        c.p += KP;
+        if (c.p == B) { c.p = 0; if (++c.g == per) { c.g = 0; ++c.l; } }
     };
     auto cur_t = [&](const Cur &c) -> uint64_t {
         return KIND == TK_SINGLE ? (uint64_t)c.p : (uint64_t)c.p * L + c.l;
@@ -472,12 +493,12 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     // twiddle table of limb l (column pass: [L][N1] tables) or of the
     // chunks of group g
     auto tw_src = [&](uint32_t l, uint32_t g) -> const Tw<W> * {
-        if (KIND == TK_CHUNKS) return a.tw + (size_t)l * N1 * CP + (size_t)g * K * CP;
+        if (KIND == TK_CHUNKS) return a.tw + (size_t)l * N1 * CP + (size_t)g * KG * CP;
         return a.tw + (size_t)l * S;
     };
     auto issue = [&](const Cur &c, uint32_t s) {
         const uint64_t t = cur_t(c);
-        const uint32_t pos0 = c.g * K;
+        const uint32_t pos0 = c.g * KG;
         W *dst = stage + (size_t)s * BW;
         if (KIND == TK_COLS) {
             const uint32_t rows = S < 256 ? S : 256u;
@@ -486,15 +507,29 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
                 tma_2d_g2s(dst + r0 * K, tmap, (int)pos0, (int)(t * N1 + r0), &bar[s]);
         } else if (SWZ) {
             mbar_expect_tx(&bar[s], K * S * (uint32_t)sizeof(W));
-            const uint64_t row0 = (t * N + ((size_t)pos0 << S2)) / RW;
-            tma_2d_g2s(dst, tmap, 0, (int)row0, &bar[s]);
-            // the fused product's second operand (read by plain loads) into
-            // L2 while this tile's copy is in flight
-            if (a.pw_b) prefetch_l2(a.pw_b + t * N + ((size_t)pos0 << S2), K * S * (uint32_t)sizeof(W));
+            if constexpr (PAIR) {
+                // one box of S / RW rows per polynomial (1 KiB-aligned
+                // blocks, so the swizzle phase is the smem row's)
+                for (uint32_t c2 = 0; c2 < K; ++c2) {
+                    const uint64_t row0 = ((t + (uint64_t)c2 * L) * N + ((size_t)pos0 << S2)) / RW;
+                    tma_2d_g2s(dst + c2 * S, tmap, 0, (int)row0, &bar[s]);
+                    if (a.pw_b) prefetch_l2(a.pw_b + (t + (uint64_t)c2 * L) * N + ((size_t)pos0 << S2),
+                                            S * (uint32_t)sizeof(W));
+                }
+            } else {
+                const uint64_t row0 = (t * N + ((size_t)pos0 << S2)) / RW;
+                tma_2d_g2s(dst, tmap, 0, (int)row0, &bar[s]);
+                // the fused product's second operand (read by plain loads)
+                // into L2 while this tile's copy is in flight
+                if (a.pw_b) prefetch_l2(a.pw_b + t * N + ((size_t)pos0 << S2), K * S * (uint32_t)sizeof(W));
+            }
         } else if (KIND == TK_CHUNKS) {
             mbar_expect_tx(&bar[s], K * S * (uint32_t)sizeof(W));
             const W *src = a.data + t * N + ((size_t)pos0 << S2);
-            for (uint32_t c2 = 0; c2 < K; ++c2) bulk_g2s(dst + c2 * SP, src + (size_t)c2 * S, S * sizeof(W), &bar[s]);
+            // sub c2: the next chunk of the polynomial, or (paired) the same
+            // chunk of the next polynomial
+            const size_t sub = PAIR ? (size_t)L * N : (size_t)S;
+            for (uint32_t c2 = 0; c2 < K; ++c2) bulk_g2s(dst + c2 * SP, src + c2 * sub, S * sizeof(W), &bar[s]);
         } else {
             const uint64_t nval = a.ntrans - t < K ? a.ntrans - t : K;
             const uint32_t bytes = (uint32_t)(nval * S * sizeof(W));
@@ -506,12 +541,17 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     // L2 prefetch of a tile (one beyond the ones staged in shared memory)
     auto prefetch = [&](const Cur &c) {
         const uint64_t t = cur_t(c);
-        const uint32_t pos0 = c.g * K;
+        const uint32_t pos0 = c.g * KG;
         if (KIND == TK_COLS) {
             const uint32_t rows = S < 256 ? S : 256u;
             for (uint32_t r0 = 0; r0 < S; r0 += rows) prefetch_tensor_2d(tmap, (int)pos0, (int)(t * N1 + r0));
         } else if (KIND == TK_CHUNKS) {
-            prefetch_l2(a.data + t * N + ((size_t)pos0 << S2), K * S * (uint32_t)sizeof(W));
+            if constexpr (PAIR) {
+                for (uint32_t c2 = 0; c2 < K; ++c2)
+                    prefetch_l2(a.data + (t + (uint64_t)c2 * L) * N + ((size_t)pos0 << S2), S * (uint32_t)sizeof(W));
+            } else {
+                prefetch_l2(a.data + t * N + ((size_t)pos0 << S2), K * S * (uint32_t)sizeof(W));
+            }
         } else {
             const uint64_t nval = a.ntrans - t < K ? a.ntrans - t : K;
             prefetch_l2(a.data + t * N, (uint32_t)(nval * S * sizeof(W)));
@@ -560,7 +600,7 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
         // (test hook: the first barrier waits for bytes no copy delivers)
         // (per-plan launches: CTA 0; one-launch two-pass form: the item
         // holding the first tile)
-        if (a.stall_tx && (P == 0 ? blockIdx.x == 0 : t_begin == 0)) mbar_add_tx(&bar[0], a.stall_tx);
+        if (a.stall_tx && ((P & 3) == 0 ? blockIdx.x == 0 : t_begin == 0)) mbar_add_tx(&bar[0], a.stall_tx);
         for (uint32_t s = 0; s < NS && t_begin + s < t_end; ++s) { issue(ahead, s); cur_next(ahead); }
         if (t_begin + NS < t_end) prefetch(ahead);
     }
@@ -572,8 +612,10 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     for (uint32_t tile = t_begin; tile < t_end; ++tile, ++i, cur_next(cur)) {
         const uint32_t s = i % NS;
         const uint32_t parity = (ps.use(s) + i / NS) & 1u;
-        const uint32_t pos0 = cur.g * K;
-        const uint64_t t = KIND == TK_SINGLE ? cur_t(cur) + k : cur_t(cur);
+        const uint32_t pos0 = cur.g * KG;
+        // this thread's sub-transform: transform t, chunk / column position pk
+        const uint64_t t = KIND == TK_SINGLE ? cur_t(cur) + k : (PAIR ? cur_t(cur) + (uint64_t)k * L : cur_t(cur));
+        const uint32_t pk = PAIR ? pos0 : pos0 + k;
         const bool valid = t < a.ntrans;
         const uint32_t l = KIND == TK_SINGLE ? (uint32_t)((valid ? t : 0) % L) : cur.l;
         if (!LATE_REFILL || l != kk_l) load_limb(l);
@@ -603,26 +645,27 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
                     // are all issued before their products, so their
                     // latencies overlap)
                     constexpr uint32_t NT = K * T, JPT = S / NT, MB = JPT < 4 ? JPT : 4;
+                    constexpr uint32_t KT = KG;     // tables in the tile
                     static_assert(NT <= S && S % NT == 0 && JPT % MB == 0, "threads per chunk table");
                     const W *sd = a.tw_seed + ((size_t)cur.l * N1 + pos0) * 8;
                     const Tw<W> *rt = a.tw_root + (size_t)cur.l * S;
 #pragma unroll 1
                     for (uint32_t m0 = 0; m0 < JPT; m0 += MB) {
                         Tw<W> rb[MB];
-                        W sa[MB][K];
+                        W sa[MB][KT];
 #pragma unroll
                         for (uint32_t m = 0; m < MB; ++m) {
                             const uint32_t j = tid + (m0 + m) * NT;
                             const uint32_t lv = j ? 31 - __clz(j) : 0;
                             rb[m] = ldtw(rt + j);
 #pragma unroll
-                            for (uint32_t c2 = 0; c2 < K; ++c2) sa[m][c2] = __ldg(sd + c2 * 8 + lv);
+                            for (uint32_t c2 = 0; c2 < KT; ++c2) sa[m][c2] = __ldg(sd + c2 * 8 + lv);
                         }
 #pragma unroll
                         for (uint32_t m = 0; m < MB; ++m) {
                             const uint32_t j = tid + (m0 + m) * NT;
 #pragma unroll
-                            for (uint32_t c2 = 0; c2 < K; ++c2) {
+                            for (uint32_t c2 = 0; c2 < KT; ++c2) {
                                 Tw<W> tv{0, 0};
                                 if (j != 0) {
                                     tv.w = mul_full<RED_SHOUP, W>(sa[m][c2], rb[m], kk);
@@ -644,9 +687,9 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
                 }
                 tw_key = key;
             }
-            twb = tws + (KIND == TK_CHUNKS ? k * CP : 0);
+            twb = tws + (KIND == TK_CHUNKS && !PAIR ? k * CP : 0);
         } else {
-            twb = KIND == TK_CHUNKS ? tw_src(l, 0) + (size_t)(pos0 + k) * CP : a.tw + (size_t)l * N;
+            twb = KIND == TK_CHUNKS ? tw_src(l, 0) + (size_t)pk * CP : a.tw + (size_t)l * N;
         }
         // fused pointwise product (inverse chunk pass): b's 16 words at this
         // thread's positions, loaded before the tile wait so they overlap it
@@ -655,7 +698,7 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
         using V16 = typename std::conditional<sizeof(W) == 4, uint4, ulonglong2>::type;
         V16 bv[PW ? NV : 1];
         const bool use_pw = PW && a.pw_b && valid;
-        const V16 *bq = use_pw ? reinterpret_cast<const V16 *>(a.pw_b + t * N + ((size_t)(pos0 + k) << S2) +
+        const V16 *bq = use_pw ? reinterpret_cast<const V16 *>(a.pw_b + t * N + ((size_t)pk << S2) +
                                                               R0::A(tau))
                                : nullptr;
         if constexpr (PW && LATE_REFILL) {
@@ -773,7 +816,7 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
 #pragma unroll
                 for (int e = 0; e < 16; ++e) g[(size_t)(AL | RL::E(e)) << S2] = x[e];
             } else {
-                W *g = KIND == TK_SINGLE ? a.out + t * N : a.out + t * N + ((size_t)(pos0 + k) << S2);
+                W *g = KIND == TK_SINGLE ? a.out + t * N : a.out + t * N + ((size_t)pk << S2);
                 if (RL::RR == 4 && RL::LO == 0) {
                     W *q = g + AL;
 #pragma unroll
@@ -835,7 +878,7 @@ __global__ void __launch_bounds__(fused_max_threads<W, RED, LOGS, KIND, INV>(),
                                   fused_min_blocks<W, RED, LOGS, KIND, INV>())
 k_fused(const __grid_constant__ FArgs<W> a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    constexpr uint32_t NS = n_stages<W, LOGS, KIND>();
+    constexpr uint32_t NS = n_stages<W, LOGS, KIND, PP>();
     constexpr uint32_t BW = buf_words<W, LOGS, KIND, INV, PP>();
     constexpr uint32_t TWP = tw_pairs<W, LOGS, KIND, PP>();
     constexpr uint32_t AL = stage_align<W, LOGS, KIND, INV, PP>();
@@ -849,14 +892,14 @@ k_fused(const __grid_constant__ FArgs<W> a) {
     // previous one before its first data access
     griddep_launch_dependents();
     __syncthreads();
-    PipeState ps{{0, 0}, 0};
+    PipeState ps{{0, 0, 0}, 0};
     const uint32_t t_begin = (uint32_t)((uint64_t)blockIdx.x * a.ntiles / gridDim.x);
     const uint32_t t_end = (uint32_t)((uint64_t)(blockIdx.x + 1) * a.ntiles / gridDim.x);
     run_tiles<W, RED, INV, LOGS, KIND, PP, OTF_K, true>(a, &a.tmap, t_begin, t_end, base, bar, ps);
 }
 
 template <class W, int LOGS, int KIND, bool INV, int P = 0> __host__ __device__ constexpr size_t fused_smem_bytes() {
-    return (size_t)n_stages<W, LOGS, KIND>() * buf_words<W, LOGS, KIND, INV, P>() * sizeof(W) +
+    return (size_t)n_stages<W, LOGS, KIND, P>() * buf_words<W, LOGS, KIND, INV, P>() * sizeof(W) +
            (size_t)tw_pairs<W, LOGS, KIND, P>() * 2 * sizeof(W) + 8 * 4 + 16 + stage_align<W, LOGS, KIND, INV, P>();
 }
 

@@ -108,12 +108,13 @@ inline cudaError_t make_rows_tmap(CUtensorMap *m, void *data, bool w64, uint64_t
 template <class W, int RED, bool INV, int KIND, int PP, bool OTF_K = false, int LOGS = 4>
 cudaError_t pass_dispatch(int logS, const FArgs<W> &a, uint32_t threads, size_t smem, cudaStream_t st) {
     constexpr int MAXS = KIND == TK_SINGLE ? (sizeof(W) == 4 ? kSingleMaxLog32 : kSingleMaxLog64)
-                                           : (KIND == TK_COLS ? 9 : kChunkLog);
-    constexpr int MINS = KIND == TK_SINGLE ? 4 : (KIND == TK_COLS ? 5 : kChunkLog);
+                                           : (KIND == TK_COLS ? 9 : kChunkLogMax);
+    constexpr int MINS = KIND == TK_SINGLE ? 4 : (KIND == TK_COLS ? 5 : kChunkLogMin);
     if constexpr (LOGS > MAXS) {
         return cudaErrorInvalidValue;
     } else {
-        if constexpr (LOGS >= MINS) {
+        // (chunk twiddles made on the fly: 256-word chunks only)
+        if constexpr (LOGS >= MINS && !(OTF_K && LOGS != (int)kN2Log)) {
             if (logS == LOGS) return launch_pass<W, RED, INV, LOGS, KIND, PP, OTF_K>(a, threads, smem, st);
         }
         return pass_dispatch<W, RED, INV, KIND, PP, OTF_K, LOGS + 1>(logS, a, threads, smem, st);
@@ -159,7 +160,7 @@ template <class W, int KIND, int P> uint32_t tile_k_p(int logS) {
 // pointwise + inverse) from `data` times pw_b into `out`.
 template <class W, bool INV, int KIND>
 cudaError_t fill_pass(FArgs<W> &a, ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, int logS,
-                      bool final_pass, uint32_t K, W *out, const W *pw_b) {
+                      bool final_pass, uint32_t K, W *out, const W *pw_b, bool paired = false) {
     std::memset(&a, 0, sizeof(a));
     a.data = data;
     a.out = out ? out : data;
@@ -192,10 +193,12 @@ cudaError_t fill_pass(FArgs<W> &a, ntt_plan_s &p, W *data, const void *tw, uint6
         if (e != cudaSuccess) return e;
     }
     if (KIND == TK_CHUNKS && INV) {
-        // inverse chunk tiles: 128-byte rows, swizzled (see fused.cuh)
+        // inverse chunk tiles: 128-byte rows, swizzled (see fused.cuh); a
+        // box holds the tile's K chunks, or one chunk when the tile pairs
+        // polynomials (one copy per polynomial)
         const uint32_t RW = 128 / sizeof(W);
         cudaError_t e = make_rows_tmap(&a.tmap, data, sizeof(W) == 8, ntrans * p.N / RW, RW,
-                                       K * (1u << logS) / RW);
+                                       (paired ? 1u : K) * (1u << logS) / RW);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -209,7 +212,9 @@ cudaError_t run_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, in
     FArgs<W> a;
     const uint32_t T = (1u << logS) / 16;
     const uint32_t K = tile_k_for<W, KIND, PP>(logS);
-    cudaError_t e = fill_pass<W, INV, KIND>(a, p, data, tw, ntrans, logS, final_pass, K, out, pw_b);
+    constexpr bool paired = paired_chunks<KIND, PP>();
+    if (paired && (ntrans / p.L) % K != 0) return cudaErrorInvalidValue;   // whole polynomial groups
+    cudaError_t e = fill_pass<W, INV, KIND>(a, p, data, tw, ntrans, logS, final_pass, K, out, pw_b, paired);
     if (e != cudaSuccess) return e;
     size_t smem = smem_for<W, KIND, INV, PP>(logS);
     ++p.last_launches;
@@ -217,23 +222,37 @@ cudaError_t run_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, in
     return pass_dispatch<W, RED, INV, KIND, PP, OTF_K>(logS, a, K * T, smem, st);
 }
 
-// The chunk pass in the plan's form for this direction.
+// The chunk pass in the plan's form for this direction.  Tiles pair
+// polynomials (the same chunk of K polynomials: one twiddle table per tile,
+// so a CTA needs less shared memory and more of them fit on an SM) when K
+// divides the batch, else they hold K consecutive chunks of one polynomial.
 template <class W, int RED, bool INV>
 cudaError_t run_chunk_pass(ntt_plan_s &p, int form, W *data, const void *tw, uint64_t ntrans, bool final_pass,
                            cudaStream_t st, W *out = nullptr, const W *pw_b = nullptr) {
+    const int logS = (int)p.s2;
+    // pairing needs K | batch, and chunks of at least 256 words (each
+    // polynomial's box of swizzled rows then starts on a 1 KiB boundary)
+    const uint64_t B = logS >= 8 ? ntrans / p.L : 1;
     if constexpr (sizeof(W) == 4 && RED == RED_SHOUP) {
         // NTT_TW_OTF plans: kernels that make the chunk tables from seeds
         if (p.tw_otf) {
             if (form == FORM_SMALL)
-                return run_pass<W, RED, INV, TK_CHUNKS, 0, true>(p, data, tw, ntrans, (int)p.s2, final_pass, st, out,
-                                                                 pw_b);
-            return run_pass<W, RED, INV, TK_CHUNKS, 3, true>(p, data, tw, ntrans, (int)p.s2, final_pass, st, out,
-                                                             pw_b);
+                return B % 2 == 0
+                           ? run_pass<W, RED, INV, TK_CHUNKS, 8, true>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b)
+                           : run_pass<W, RED, INV, TK_CHUNKS, 0, true>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b);
+            return B % 16 == 0
+                       ? run_pass<W, RED, INV, TK_CHUNKS, 11, true>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b)
+                       : run_pass<W, RED, INV, TK_CHUNKS, 3, true>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b);
         }
     }
+    const uint64_t ks = tile_k_for<W, TK_CHUNKS, 0>(logS), kw = tile_k_for<W, TK_CHUNKS, 3>(logS);
     if (form == FORM_SMALL)
-        return run_pass<W, RED, INV, TK_CHUNKS, 0>(p, data, tw, ntrans, (int)p.s2, final_pass, st, out, pw_b);
-    return run_pass<W, RED, INV, TK_CHUNKS, 3>(p, data, tw, ntrans, (int)p.s2, final_pass, st, out, pw_b);
+        return B % ks == 0 && B > 1
+                   ? run_pass<W, RED, INV, TK_CHUNKS, 8>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b)
+                   : run_pass<W, RED, INV, TK_CHUNKS, 0>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b);
+    return B % kw == 0 && B > 1
+               ? run_pass<W, RED, INV, TK_CHUNKS, 11>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b)
+               : run_pass<W, RED, INV, TK_CHUNKS, 3>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b);
 }
 
 // Tuning of the one-launch two-pass form: tiles per work item and the lag

@@ -232,10 +232,12 @@ inline uint32_t level_pos(uint32_t idx, uint32_t LOGS) {
     return (1u << l) + (off % cnt) * ntau + off / cnt;
 }
 
-// Pairs per chunk table (256 entries + 64 bytes, so the tables of the two
-// chunks a warp works on fall on different bank halves in shared memory).
-template <class W> __host__ __device__ constexpr uint32_t chunk_tab_pitch() {
-    return 256u + 64u / (2u * (uint32_t)sizeof(W));
+// Pairs per chunk table of a 2^LOGS-word chunk (2^LOGS entries + 64
+// bytes, so the tables of neighbouring chunks of a tile fall on different
+// bank halves in shared memory).
+template <class W, int LOGS = 8> __host__ __device__ constexpr uint32_t chunk_tab_pitch() {
+    return (1u << LOGS) + 64u / (2u * (uint32_t)sizeof(W));
 }
+inline uint32_t chunk_tab_pitch_rt(bool w64, uint32_t logs) { return (1u << logs) + (w64 ? 4u : 8u); }
 
 }  // namespace nttgb

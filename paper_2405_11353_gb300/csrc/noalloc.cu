@@ -208,8 +208,8 @@ extern "C" ntt_status ntt_forward_noalloc(ntt_plan_t plan, void *d_data, uint32_
     if ((reinterpret_cast<uintptr_t>(d_data) & 15u) != 0) return NTT_ERR_ALIGNMENT;
     ntt_plan_s &p = *plan;
     // the Stockham dataflow needs the per-stage tables, which every plan
-    // builds except the fused ones with N >= 16 and the tensor-core
-    // four-step ones
+    // builds except the fused ones with N >= 16 (tensor-core four-step
+    // plans build them too)
     if (!p.d_w_fwd || !p.d_twist) return NTT_ERR_UNSUPPORTED;
     const size_t bytes = (size_t)batch * p.L * p.N * p.word_bytes();
     if (bytes > kNoAllocScratchBytes) return NTT_ERR_SCRATCH_LIMIT;

@@ -21,7 +21,13 @@ enum TwoPassForm : int { FORM_SMALL = 0, FORM_WIDE = 1, FORM_STREAMED = 2 };
 constexpr int kSingleMaxLog32 = 14;
 constexpr int kSingleMaxLog64 = 13;
 constexpr int kLogR = 4;          // 16 words per thread in the fused kernel
-constexpr int kChunkLog = 8;      // pass-B sub-transform size 256
+constexpr int kChunkLog = 8;      // default pass-B sub-transform size 256
+// Two-pass splits N = 2^s1 x 2^s2 the per-plan kernels take (the autotuner
+// picks one per shape): chunks of 2^7 .. 2^9 words, column passes of
+// 2^5 .. 2^9 points.  NTT_STREAMED and NTT_TW_OTF plans and the ragged
+// kernel's plans keep s2 = kChunkLog.
+constexpr int kChunkLogMin = 7, kChunkLogMax = 9;
+constexpr int kColsLogMin = 5, kColsLogMax = 9;
 // One pass on a cluster of eight CTAs (cluster.cuh, flag NTT_CLUSTER):
 // N = 2^16, 4-byte words.
 constexpr int kClusterLogN = 16;
@@ -88,8 +94,10 @@ struct ntt_plan_s {
         uint32_t b = 0;
         while (b < 31 && (2u << b) <= batch) ++b;
         const int t = tuned_form[inverse ? 1 : 0][b];
-        if (t >= 0 && !(tw_otf && t == nttgb::FORM_STREAMED)) return t;
-        if (streamed) return nttgb::FORM_STREAMED;
+        // (the streamed form exists for 256-word chunks, not with NTT_TW_OTF)
+        const bool stream_ok = !tw_otf && s2 == (uint32_t)nttgb::kChunkLog;
+        if (t >= 0 && (t != nttgb::FORM_STREAMED || stream_ok)) return t;
+        if (streamed && stream_ok) return nttgb::FORM_STREAMED;
         return inverse ? nttgb::FORM_WIDE : nttgb::FORM_SMALL;
     }
     uint32_t *d_status = nullptr;
@@ -103,6 +111,8 @@ struct ntt_plan_s {
 
     int fused_mode = nttgb::FUSED_STAGES;
     uint32_t s1 = 0, s2 = 0;     // two-pass split: N = 2^s1 * 2^s2
+    bool split_fixed = false;    // the split was given (autotuner candidates,
+                                 // the ragged kernel's plans): not from tuning
 
     size_t word_bytes() const { return word64 ? 8 : 4; }
     size_t limb_words() const { return (size_t)N; }
@@ -120,12 +130,20 @@ cudaError_t launch_tc(ntt_plan_s &p, void *data, uint32_t batch, bool inverse, c
 cudaError_t launch_tc5(ntt_plan_s &p, void *data, uint32_t batch, bool inverse, cudaStream_t st);
 
 ntt_status ensure_scratch(ntt_plan_s &p, uint32_t batch, cudaStream_t st);
-// Copy the autotuner's table entries for the plan's shape into the plan (tune.cu).
+// The autotuner's choices for the plan's shape (tune.cu): its two-pass
+// split (unless fixed), then the forms per direction and batch bucket.
 void apply_tuning(ntt_plan_s &p);
+// Whether a two-pass split s2 (chunks of 2^s2 words) serves a plan of
+// 2^logN words: column passes of 2^5 .. 2^9 points, chunks of 2^7 .. 2^9.
+inline bool split_valid(uint32_t logN, uint32_t s2) {
+    return s2 >= (uint32_t)kChunkLogMin && s2 <= (uint32_t)kChunkLogMax && logN > s2 &&
+           logN - s2 >= (uint32_t)kColsLogMin && logN - s2 <= (uint32_t)kColsLogMax;
+}
 
-// Plan builder (ntt_plan_create_ex with a cap on the single-pass size).
+// Plan builder (ntt_plan_create_ex with a cap on the single-pass size, and
+// a given two-pass split: split_log < 0 takes the tuned or default one).
 ntt_status create_plan(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t L, ntt_variant variant,
-                       uint32_t flags, const uint64_t *psi, int single_max_log);
+                       uint32_t flags, const uint64_t *psi, int single_max_log, int split_log = -1);
 ntt_status validate_plan_args(uint32_t N, const uint64_t *q, uint32_t L, uint32_t flags);
 
 // fused path, instantiated in fused_<word>_<reduction>.cu

@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256, 2) k_ragged(const __grid_constant__ Ragge
         fence_mbar_init();
     }
     __syncthreads();
-    PipeState ps{{0, 0}, 0};
+    PipeState ps{{0, 0, 0}, 0};
     for (int phase = 0; phase < 4; ++phase) {
         for (;;) {
             if (threadIdx.x == 0) s_item = ra.phase_begin[phase] + atomicAdd(&ra.counters[phase], 1u);

@@ -101,7 +101,7 @@ k_stream(const __grid_constant__ StreamArgs<W> sa) {
     const uint32_t n0 = sa.items_per_limb[0], n1 = sa.items_per_limb[1];
     const uint32_t slots = n0 + n1;                       // items per round
     const uint64_t total = (uint64_t)(L + sa.lag) * slots;
-    PipeState ps{{0, 0}, 0};
+    PipeState ps{{0, 0, 0}, 0};
     bool ok = true;
     // thread 0 takes the next item while this one runs (its atomic's
     // latency hides behind the work); holding one item ahead cannot

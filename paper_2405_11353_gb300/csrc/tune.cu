@@ -1,19 +1,23 @@
-// tune.cu -- autotuner of the two-pass fused path and its table.
+// tune.cu -- autotuner of the two-pass fused path and its tables.
 //
-// A two-pass direction (forward, or inverse with or without the fused
-// product) runs in one of three forms: the chunk pass on one-warp CTAs
-// (2-chunk tiles), on 256-thread CTAs (16-chunk tiles), or both passes in
-// one streamed launch (stream.cuh).  Which is fastest depends on N, the word
-// size, the limb count and the batch, so ntt_autotune times all three on
-// the current device for one shape and records the fastest per direction
-// in a process-wide table keyed by (N, word size, L, reduction, order,
-// twiddles made on the fly or read, floor(log2 batch)).  Plans whose chunk
-// twiddles are made on the fly (NTT_TW_OTF) have no streamed form: its time
-// is reported as -1 and it is never chosen.  ntt_plan_create copies the table's entries for its
-// shape into the plan; each call then looks up its batch bucket.  The
-// table is also kept in the JSON-lines file named by NTT_TUNE_DB, read at
-// first use and rewritten after every tuning, so tuning survives the
-// process.
+// What the two-pass fused path leaves open at run time, per shape (N, word
+// size, L, reduction, order, twiddles made on the fly or read):
+//   * the split N = 2^s1 x 2^s2: how many stages each pass does (column
+//     passes of 2^s1 points, chunks of 2^s2 = 128, 256 or 512 words); the
+//     plan's twiddle tables are laid out for it, so it is fixed when a plan
+//     is made;
+//   * per direction (forward, or inverse with or without the fused
+//     product) and batch bucket floor(log2 batch), the form: the chunk pass
+//     on one-warp CTAs, on 256-thread CTAs, or both passes in one streamed
+//     launch (stream.cuh; 256-word chunks only, not with NTT_TW_OTF).
+// ntt_autotune times every valid split with every form of both directions
+// on the current device and records, per split, the fastest form of each
+// direction for the batch's bucket, and for the shape the split whose two
+// directions together are fastest.  ntt_plan_create takes the shape's split
+// (before it builds its tables) and copies the form entries of that split;
+// each call then looks up its batch bucket.  Both tables are kept in the
+// JSON-lines file named by NTT_TUNE_DB, read at first use and rewritten
+// after every tuning, so tuning survives the process.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -30,19 +34,27 @@ namespace nttgb {
 namespace {
 
 struct TuneKey {
-    uint32_t N, word, L, red, bitrev, bucket, otf;
+    uint32_t N, word, L, red, bitrev, bucket, otf, split;
     bool operator<(const TuneKey &o) const {
-        return std::tie(N, word, L, red, bitrev, bucket, otf) <
-               std::tie(o.N, o.word, o.L, o.red, o.bitrev, o.bucket, o.otf);
+        return std::tie(N, word, L, red, bitrev, bucket, otf, split) <
+               std::tie(o.N, o.word, o.L, o.red, o.bitrev, o.bucket, o.otf, o.split);
     }
 };
 struct TuneVal {
     int form[2];
     float ms[2][3];
 };
+// shape (a TuneKey without bucket and split) -> chosen split
+struct ShapeKey {
+    uint32_t N, word, L, red, bitrev, otf;
+    bool operator<(const ShapeKey &o) const {
+        return std::tie(N, word, L, red, bitrev, otf) < std::tie(o.N, o.word, o.L, o.red, o.bitrev, o.otf);
+    }
+};
 
 std::mutex g_mu;
 std::map<TuneKey, TuneVal> g_table;
+std::map<ShapeKey, uint32_t> g_split;
 bool g_loaded = false;
 
 uint32_t bucket_of(uint32_t batch) {
@@ -62,24 +74,44 @@ void load_locked() {
     while (std::fgets(line, sizeof(line), f)) {
         TuneKey k;
         TuneVal v;
+        ShapeKey sk;
+        uint32_t split = 0;
+        if (std::sscanf(line,
+                        "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
+                        "\"tw_otf\": %u, \"split_log2\": %u}",
+                        &sk.N, &sk.word, &sk.L, &sk.red, &sk.bitrev, &sk.otf, &split) == 7) {
+            if (sk.otf <= 1 && split >= (uint32_t)kChunkLogMin && split <= (uint32_t)kChunkLogMax)
+                g_split[sk] = split;
+            continue;
+        }
         int n = std::sscanf(line,
                             "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
-                            "\"tw_otf\": %u, \"batch_log2\": %u, \"forward_form\": %d, \"inverse_form\": %d, "
-                            "\"forward_ms\": [%f, %f, %f], \"inverse_ms\": [%f, %f, %f]}",
-                            &k.N, &k.word, &k.L, &k.red, &k.bitrev, &k.otf, &k.bucket, &v.form[0], &v.form[1],
-                            &v.ms[0][0], &v.ms[0][1], &v.ms[0][2], &v.ms[1][0], &v.ms[1][1], &v.ms[1][2]);
-        if (n != 15) {
-            // lines written before the twiddle-mode field existed
-            k.otf = 0;
+                            "\"tw_otf\": %u, \"chunk_log2\": %u, \"batch_log2\": %u, \"forward_form\": %d, "
+                            "\"inverse_form\": %d, \"forward_ms\": [%f, %f, %f], \"inverse_ms\": [%f, %f, %f]}",
+                            &k.N, &k.word, &k.L, &k.red, &k.bitrev, &k.otf, &k.split, &k.bucket, &v.form[0],
+                            &v.form[1], &v.ms[0][0], &v.ms[0][1], &v.ms[0][2], &v.ms[1][0], &v.ms[1][1], &v.ms[1][2]);
+        if (n != 16) {
+            // lines written before the split field existed: 256-word chunks
+            k.split = (uint32_t)kChunkLog;
             n = 1 + std::sscanf(line,
+                                "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
+                                "\"tw_otf\": %u, \"batch_log2\": %u, \"forward_form\": %d, \"inverse_form\": %d, "
+                                "\"forward_ms\": [%f, %f, %f], \"inverse_ms\": [%f, %f, %f]}",
+                                &k.N, &k.word, &k.L, &k.red, &k.bitrev, &k.otf, &k.bucket, &v.form[0], &v.form[1],
+                                &v.ms[0][0], &v.ms[0][1], &v.ms[0][2], &v.ms[1][0], &v.ms[1][1], &v.ms[1][2]);
+        }
+        if (n != 16) {
+            // and before the twiddle-mode field: table twiddles
+            k.otf = 0;
+            n = 2 + std::sscanf(line,
                                 "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
                                 "\"batch_log2\": %u, \"forward_form\": %d, \"inverse_form\": %d, "
                                 "\"forward_ms\": [%f, %f, %f], \"inverse_ms\": [%f, %f, %f]}",
                                 &k.N, &k.word, &k.L, &k.red, &k.bitrev, &k.bucket, &v.form[0], &v.form[1],
                                 &v.ms[0][0], &v.ms[0][1], &v.ms[0][2], &v.ms[1][0], &v.ms[1][1], &v.ms[1][2]);
         }
-        if (n != 15 || k.bucket > 31 || k.otf > 1 || v.form[0] < 0 || v.form[0] > 2 || v.form[1] < 0 ||
-            v.form[1] > 2)
+        if (n != 16 || k.bucket > 31 || k.otf > 1 || v.form[0] < 0 || v.form[0] > 2 || v.form[1] < 0 ||
+            v.form[1] > 2 || k.split < (uint32_t)kChunkLogMin || k.split > (uint32_t)kChunkLogMax)
             continue;
         g_table[k] = v;
     }
@@ -91,32 +123,52 @@ void save_locked() {
     if (!path || !*path) return;
     FILE *f = std::fopen(path, "w");
     if (!f) return;
+    for (const auto &e : g_split) {
+        const ShapeKey &k = e.first;
+        std::fprintf(f,
+                     "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
+                     "\"tw_otf\": %u, \"split_log2\": %u}\n",
+                     k.N, k.word, k.L, k.red, k.bitrev, k.otf, e.second);
+    }
     for (const auto &e : g_table) {
         const TuneKey &k = e.first;
         const TuneVal &v = e.second;
         std::fprintf(f,
                      "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
-                     "\"tw_otf\": %u, \"batch_log2\": %u, \"forward_form\": %d, \"inverse_form\": %d, "
-                     "\"forward_ms\": [%.6f, %.6f, %.6f], \"inverse_ms\": [%.6f, %.6f, %.6f]}\n",
-                     k.N, k.word, k.L, k.red, k.bitrev, k.otf, k.bucket, v.form[0], v.form[1], v.ms[0][0], v.ms[0][1],
-                     v.ms[0][2], v.ms[1][0], v.ms[1][1], v.ms[1][2]);
+                     "\"tw_otf\": %u, \"chunk_log2\": %u, \"batch_log2\": %u, \"forward_form\": %d, "
+                     "\"inverse_form\": %d, \"forward_ms\": [%.6f, %.6f, %.6f], \"inverse_ms\": [%.6f, %.6f, %.6f]}\n",
+                     k.N, k.word, k.L, k.red, k.bitrev, k.otf, k.split, k.bucket, v.form[0], v.form[1], v.ms[0][0],
+                     v.ms[0][1], v.ms[0][2], v.ms[1][0], v.ms[1][1], v.ms[1][2]);
     }
     std::fclose(f);
 }
 
+ShapeKey shape_of(const ntt_plan_s &p) {
+    return ShapeKey{p.N, (uint32_t)p.word_bytes(), p.L, (uint32_t)p.red, p.bitrev_order ? 1u : 0u,
+                    p.tw_otf ? 1u : 0u};
+}
 TuneKey key_of(const ntt_plan_s &p, uint32_t bucket) {
     return TuneKey{p.N, (uint32_t)p.word_bytes(), p.L, (uint32_t)p.red, p.bitrev_order ? 1u : 0u, bucket,
-                   p.tw_otf ? 1u : 0u};
+                   p.tw_otf ? 1u : 0u, p.s2};
 }
 
 }  // namespace
 
-// Copy the table's entries for the plan's shape into the plan.
+// The shape's tuned split (plans whose split is not fixed), then the form
+// entries of the plan's split.
 void apply_tuning(ntt_plan_s &p) {
     std::memset(p.tuned_form, -1, sizeof(p.tuned_form));
-    if (p.variant != NTT_FUSED || p.fused_mode != FUSED_TWO_PASS || p.streamed) return;
+    if (p.variant != NTT_FUSED || p.fused_mode != FUSED_TWO_PASS) return;
     std::lock_guard<std::mutex> g(g_mu);
     load_locked();
+    if (!p.split_fixed) {
+        auto it = g_split.find(shape_of(p));
+        if (it != g_split.end() && split_valid(p.logN, it->second)) {
+            p.s2 = it->second;
+            p.s1 = p.logN - p.s2;
+        }
+    }
+    if (p.streamed) return;
     for (uint32_t b = 0; b < 32; ++b) {
         auto it = g_table.find(key_of(p, b));
         if (it == g_table.end()) continue;
@@ -132,90 +184,131 @@ extern "C" {
 ntt_status ntt_autotune(uint32_t N, const uint64_t *q, uint32_t L, uint32_t flags, uint32_t batch,
                         ntt_stream_t stream, ntt_tune_result *result) {
     if (!q || batch == 0 || (flags & (NTT_STREAMED | NTT_CHECK | NTT_TEST_STALL))) return NTT_ERR_INVALID_ARG;
-    ntt_plan_t p = nullptr;
-    ntt_status s = ntt_plan_create(&p, N, q, L, NTT_FUSED, flags);
+    // the shape's plan with its default split, to validate and size
+    ntt_plan_t p0 = nullptr;
+    ntt_status s = nttgb::create_plan(&p0, N, q, L, NTT_FUSED, flags, nullptr, -1, nttgb::kChunkLog);
     if (s != NTT_OK) return s;
-    if (p->fused_mode != nttgb::FUSED_TWO_PASS) {
-        ntt_plan_destroy(p);
+    if (p0->fused_mode != nttgb::FUSED_TWO_PASS) {
+        ntt_plan_destroy(p0);
         return NTT_ERR_UNSUPPORTED;
     }
+    const bool otf = p0->tw_otf;
+    const uint32_t logN = p0->logN;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const size_t bytes = (size_t)batch * L * N * p->word_bytes();
+    const size_t bytes = (size_t)batch * L * N * p0->word_bytes();
+    ntt_plan_destroy(p0);
     void *d = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaMalloc(&d, bytes) != cudaSuccess) {
         cudaGetLastError();
-        ntt_plan_destroy(p);
         return NTT_ERR_OOM;
     }
-    nttgb::TuneVal v;
     bool ok = cudaMemsetAsync(d, 0, bytes, st) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
               cudaEventCreate(&e1) == cudaSuccess;
     const uint32_t bucket = nttgb::bucket_of(batch);
-    // time every form of each direction on zero words (valid residues)
-    for (int dir = 0; dir < 2 && ok; ++dir) {
-        for (int form = 0; form < 3 && ok; ++form) {
-            if (form == nttgb::FORM_STREAMED && p->tw_otf) {
-                v.ms[dir][form] = -1.f;
-                continue;
+    // per candidate split (chunks of 2^7, 2^8, 2^9 words): every form of
+    // each direction, timed on zero words (valid residues)
+    constexpr int NSPLIT = nttgb::kChunkLogMax - nttgb::kChunkLogMin + 1;
+    nttgb::TuneVal vals[NSPLIT];
+    float total[NSPLIT];
+    nttgb::TuneKey keys[NSPLIT];
+    nttgb::ShapeKey shape{};
+    int best_split = -1;
+    ntt_status dev = NTT_OK;
+    for (int si = 0; si < NSPLIT && ok; ++si) {
+        const uint32_t s2 = (uint32_t)(nttgb::kChunkLogMin + si);
+        total[si] = -1.f;
+        if (!nttgb::split_valid(logN, s2) || (otf && s2 != (uint32_t)nttgb::kChunkLog)) continue;
+        ntt_plan_t p = nullptr;
+        if (nttgb::create_plan(&p, N, q, L, NTT_FUSED, flags, nullptr, -1, (int)s2) != NTT_OK) continue;
+        nttgb::TuneVal &v = vals[si];
+        for (int dir = 0; dir < 2 && ok; ++dir) {
+            for (int form = 0; form < 3 && ok; ++form) {
+                if (form == nttgb::FORM_STREAMED && (p->tw_otf || s2 != (uint32_t)nttgb::kChunkLog)) {
+                    v.ms[dir][form] = -1.f;
+                    continue;
+                }
+                p->tuned_form[dir][bucket] = (int8_t)form;
+                auto call = [&]() {
+                    return dir == 0 ? ntt_forward(p, d, batch, stream) : ntt_inverse(p, d, batch, stream);
+                };
+                for (int w = 0; w < 2 && ok; ++w) ok = call() == NTT_OK;
+                // about 20 ms of calls, at least 3
+                float ms = 0.f;
+                ok = ok && cudaEventRecord(e0, st) == cudaSuccess && call() == NTT_OK &&
+                     cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                     cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+                int reps = ms > 0.f ? (int)(20.f / ms) : 3;
+                reps = reps < 3 ? 3 : (reps > 200 ? 200 : reps);
+                ok = ok && cudaEventRecord(e0, st) == cudaSuccess;
+                for (int r = 0; r < reps && ok; ++r) ok = call() == NTT_OK;
+                ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                     cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+                v.ms[dir][form] = ms / (float)reps;
             }
-            p->tuned_form[dir][bucket] = (int8_t)form;
-            auto call = [&]() {
-                return dir == 0 ? ntt_forward(p, d, batch, stream) : ntt_inverse(p, d, batch, stream);
-            };
-            for (int w = 0; w < 2 && ok; ++w) ok = call() == NTT_OK;
-            // about 20 ms of calls, at least 3
-            float ms = 0.f;
-            ok = ok && cudaEventRecord(e0, st) == cudaSuccess && call() == NTT_OK &&
-                 cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
-                 cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
-            int reps = ms > 0.f ? (int)(20.f / ms) : 3;
-            reps = reps < 3 ? 3 : (reps > 200 ? 200 : reps);
-            ok = ok && cudaEventRecord(e0, st) == cudaSuccess;
-            for (int r = 0; r < reps && ok; ++r) ok = call() == NTT_OK;
-            ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
-                 cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
-            v.ms[dir][form] = ms / (float)reps;
+            int best = 0;
+            for (int form = 1; form < 3; ++form)
+                if (v.ms[dir][form] >= 0.f && v.ms[dir][form] < v.ms[dir][best]) best = form;
+            v.form[dir] = best;
         }
-        int best = 0;
-        for (int form = 1; form < 3; ++form)
-            if (v.ms[dir][form] >= 0.f && v.ms[dir][form] < v.ms[dir][best]) best = form;
-        v.form[dir] = best;
+        if (ok) {
+            const ntt_status ds = ntt_get_device_status(p, stream);
+            if (ds != NTT_OK) { dev = ds; ok = false; }
+        }
+        if (ok) {
+            total[si] = v.ms[0][v.form[0]] + v.ms[1][v.form[1]];
+            keys[si] = nttgb::key_of(*p, bucket);
+            shape = nttgb::shape_of(*p);
+            if (best_split < 0 || total[si] < total[best_split]) best_split = si;
+        }
+        ntt_plan_destroy(p);
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    const ntt_status dev = ntt_get_device_status(p, stream);
     cudaFree(d);
-    if (ok && dev == NTT_OK) {
-        std::lock_guard<std::mutex> g(nttgb::g_mu);
-        nttgb::load_locked();
-        nttgb::g_table[nttgb::key_of(*p, bucket)] = v;
-        nttgb::save_locked();
-    }
-    ntt_plan_destroy(p);
     if (!ok) {
         cudaGetLastError();
-        return NTT_ERR_CUDA;
+        return dev != NTT_OK ? dev : NTT_ERR_CUDA;
     }
-    if (dev != NTT_OK) return dev;
+    if (best_split < 0) return NTT_ERR_UNSUPPORTED;
+    {
+        std::lock_guard<std::mutex> g(nttgb::g_mu);
+        nttgb::load_locked();
+        for (int si = 0; si < NSPLIT; ++si)
+            if (total[si] >= 0.f) nttgb::g_table[keys[si]] = vals[si];
+        nttgb::g_split[shape] = (uint32_t)(nttgb::kChunkLogMin + best_split);
+        nttgb::save_locked();
+    }
     if (result) {
+        const nttgb::TuneVal &v = vals[best_split];
         for (int f = 0; f < 3; ++f) {
             result->forward_ms[f] = v.ms[0][f];
             result->inverse_ms[f] = v.ms[1][f];
         }
         result->forward_form = v.form[0];
         result->inverse_form = v.form[1];
+        result->chunk_log2 = nttgb::kChunkLogMin + best_split;
+        for (int si = 0; si < NSPLIT; ++si) result->split_ms[si] = total[si];
     }
     return NTT_OK;
 }
 
 namespace {
-nttgb::TuneKey key_from_flags(uint32_t N, uint32_t L, uint32_t flags, uint32_t batch) {
+nttgb::ShapeKey shape_from_flags(uint32_t N, uint32_t L, uint32_t flags) {
     const uint32_t red = (flags & NTT_RED_MASK) == NTT_RED_MONTGOMERY ? nttgb::RED_MONTGOMERY
                          : (flags & NTT_RED_MASK) == NTT_RED_BARRETT   ? nttgb::RED_BARRETT
                                                                        : nttgb::RED_SHOUP;
-    return nttgb::TuneKey{N, (flags & NTT_WORD64) ? 8u : 4u, L, red, (flags & NTT_ORDER_BITREV) ? 1u : 0u,
-                          nttgb::bucket_of(batch), (flags & NTT_TW_OTF) ? 1u : 0u};
+    return nttgb::ShapeKey{N, (flags & NTT_WORD64) ? 8u : 4u, L, red, (flags & NTT_ORDER_BITREV) ? 1u : 0u,
+                           (flags & NTT_TW_OTF) ? 1u : 0u};
+}
+// (the caller holds g_mu) the split plans of this shape take
+uint32_t split_of_locked(const nttgb::ShapeKey &sk) {
+    if (sk.otf) return (uint32_t)nttgb::kChunkLog;
+    auto it = nttgb::g_split.find(sk);
+    return it == nttgb::g_split.end() ? (uint32_t)nttgb::kChunkLog : it->second;
+}
+nttgb::TuneKey key_from_shape(const nttgb::ShapeKey &sk, uint32_t batch, uint32_t split) {
+    return nttgb::TuneKey{sk.N, sk.word, sk.L, sk.red, sk.bitrev, nttgb::bucket_of(batch), sk.otf, split};
 }
 }  // namespace
 
@@ -230,7 +323,8 @@ ntt_status ntt_tune_set(uint32_t N, uint32_t L, uint32_t flags, uint32_t batch, 
         for (int f = 0; f < 3; ++f) v.ms[d][f] = -1.f;      // set by hand, not timed
     std::lock_guard<std::mutex> g(nttgb::g_mu);
     nttgb::load_locked();
-    nttgb::g_table[key_from_flags(N, L, flags, batch)] = v;
+    const nttgb::ShapeKey sk = shape_from_flags(N, L, flags);
+    nttgb::g_table[key_from_shape(sk, batch, split_of_locked(sk))] = v;
     nttgb::save_locked();
     return NTT_OK;
 }
@@ -239,14 +333,41 @@ int32_t ntt_tune_get(uint32_t N, uint32_t L, uint32_t flags, uint32_t batch, int
     if (batch == 0) return -1;
     std::lock_guard<std::mutex> g(nttgb::g_mu);
     nttgb::load_locked();
-    auto it = nttgb::g_table.find(key_from_flags(N, L, flags, batch));
+    const nttgb::ShapeKey sk = shape_from_flags(N, L, flags);
+    auto it = nttgb::g_table.find(key_from_shape(sk, batch, split_of_locked(sk)));
     return it == nttgb::g_table.end() ? -1 : it->second.form[inverse ? 1 : 0];
+}
+
+ntt_status ntt_tune_set_split(uint32_t N, uint32_t L, uint32_t flags, uint32_t chunk_log2) {
+    uint32_t n = 0;
+    while (n < 31 && (1u << n) < N) ++n;
+    if (L == 0 || (1u << n) != N || !nttgb::split_valid(n, chunk_log2) ||
+        ((flags & NTT_TW_OTF) && chunk_log2 != (uint32_t)nttgb::kChunkLog))
+        return NTT_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(nttgb::g_mu);
+    nttgb::load_locked();
+    nttgb::g_split[shape_from_flags(N, L, flags)] = chunk_log2;
+    nttgb::save_locked();
+    return NTT_OK;
+}
+
+int32_t ntt_tune_get_split(uint32_t N, uint32_t L, uint32_t flags) {
+    std::lock_guard<std::mutex> g(nttgb::g_mu);
+    nttgb::load_locked();
+    auto it = nttgb::g_split.find(shape_from_flags(N, L, flags));
+    return it == nttgb::g_split.end() ? -1 : (int32_t)it->second;
 }
 
 void ntt_tune_clear(void) {
     std::lock_guard<std::mutex> g(nttgb::g_mu);
     nttgb::g_table.clear();
+    nttgb::g_split.clear();
     nttgb::g_loaded = true;      // do not read the file again
+}
+
+int32_t ntt_plan_chunk_log2(ntt_plan_t plan) {
+    if (!plan || plan->variant != NTT_FUSED || plan->fused_mode != nttgb::FUSED_TWO_PASS) return -1;
+    return (int32_t)plan->s2;
 }
 
 int32_t ntt_plan_form(ntt_plan_t plan, uint32_t batch, int inverse) {

@@ -494,6 +494,60 @@ def test_pointwise_inverse_fused_and_fallback(nt, orc, red):
             p.close()
 
 
+@pytest.mark.parametrize("red", ["shoup", "barrett", "montgomery"])
+@pytest.mark.parametrize("w64", [False, True])
+def test_paired_chunk_tiles(nt, orc, red, w64):
+    """Chunk-pass tiles that pair polynomials (the same chunk of K
+    polynomials, one twiddle table per tile) run when K divides the batch:
+    K = 2 in the one-warp form, K = 16 in the 16-chunk form.  Batches 2, 16
+    and 32 take them, 17 and 1 the unpaired tiles; every form of both
+    directions, and the pointwise product fused into the paired inverse."""
+    N = 1 << (15 if w64 else 16)
+    qs = primes_for(orc, N, w64, 3)
+    psis = [orc.psi(q, N) for q in qs]
+    flags = nt.REDUCTIONS[red] | nt.NTT_ORDER_BITREV | (nt.NTT_WORD64 if w64 else 0)
+    for i, batch in enumerate((2, 16, 17, 1, 32)):
+        for form in ("small", "wide"):
+            nt.ntt_tune_clear()
+            nt.ntt_tune_set(N, len(qs), flags, batch, nt.FORMS[form], nt.FORMS[form])
+            try:
+                roundtrip_check(nt, orc, N, qs, batch, "fused", red=red, w64=w64, bitrev=True, seed=1900 + i)
+            finally:
+                nt.ntt_tune_clear()
+    batch = 16
+    A = ntt_synth.rns_batch(1950, qs, N, batch)
+    Bm = ntt_synth.rns_batch(1951, qs, N, batch)
+    fa, fb = orc.ntt_batch(A, qs, psis), orc.ntt_batch(Bm, qs, psis)
+    want = orc.ntt_batch(orc.pointwise_batch(fa, fb, qs), qs, psis, inverse=True)
+    p = Plan(nt, N, qs, "fused", red=red, w64=w64, bitrev=True)
+    try:
+        assert nt.ntt_plan_form(p.h, batch, True) == nt.NTT_FORM_WIDE
+        da, db = to_dev(reorder(fa, True, orc), w64), to_dev(reorder(fb, True, orc), w64)
+        dc = torch.zeros_like(da)
+        nt.ntt_pointwise_inverse(p.h, dc, da, db, batch)
+        assert np.array_equal(to_host(dc, w64, A.shape), want)
+        assert nt.ntt_get_device_status(p.h) == nt.NTT_OK
+    finally:
+        p.close()
+
+
+def test_paired_chunk_tiles_twiddles_on_the_fly(nt, orc):
+    """The same pairing in the kernels that make the chunk twiddles from
+    seeds (NTT_TW_OTF), both forms, batches that pair and that do not."""
+    N = 1 << 16
+    qs = primes_for(orc, N, False, 3)
+    flags = nt.NTT_ORDER_BITREV | nt.NTT_TW_OTF
+    for i, batch in enumerate((2, 16, 3)):
+        for form in ("small", "wide"):
+            nt.ntt_tune_clear()
+            nt.ntt_tune_set(N, len(qs), flags, batch, nt.FORMS[form], nt.FORMS[form])
+            try:
+                roundtrip_check(nt, orc, N, qs, batch, "fused", bitrev=True, seed=1960 + i,
+                                extra_flags=nt.NTT_TW_OTF)
+            finally:
+                nt.ntt_tune_clear()
+
+
 def test_polymul_host_entry(nt, orc):
     """The host-buffer entry point: copies, transforms and products in one
     call, pipelined in chunks of pairs (1, 3 and 13 pairs: one chunk, chunks

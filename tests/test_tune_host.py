@@ -73,3 +73,41 @@ def test_tune_table_keys_twiddle_mode_and_reads_older_lines(nt, tmp_path):
     assert out.split() == ["1", "2", "-1", "1", "1"]
     rows = [json.loads(x) for x in open(db)]
     assert sorted(r["tw_otf"] for r in rows) == [0, 1]
+
+
+def test_split_table_set_get_persist(nt, tmp_path):
+    """A shape's split (chunks of 2^s2 words) is recorded by hand, refused
+    where the size cannot take it, written as its own line, keys the form
+    entries, and is read by a fresh process; older lines without a split
+    field are forms of the default 256-word split."""
+    db = str(tmp_path / "tune.jsonl")
+    with open(db, "w") as f:
+        f.write('{"N": 65536, "word_bytes": 4, "L": 3, "reduction": 0, "bitrev": 1, "tw_otf": 0, '
+                '"batch_log2": 2, "forward_form": 1, "inverse_form": 0, "forward_ms": [-1.0, -1.0, -1.0], '
+                '"inverse_ms": [-1.0, -1.0, -1.0]}\n')
+    out = _run("import paper_2405_11353_gb300 as nt\n"
+               "f = nt.NTT_ORDER_BITREV\n"
+               "print(nt.ntt_tune_get_split(1 << 16, 3, f), nt.ntt_tune_get(1 << 16, 3, f, 4))\n"
+               "nt.ntt_tune_set_split(1 << 16, 3, f, 9)\n"
+               "print(nt.ntt_tune_get_split(1 << 16, 3, f), nt.ntt_tune_get(1 << 16, 3, f, 4))\n"
+               "nt.ntt_tune_set(1 << 16, 3, f, 4, nt.NTT_FORM_SMALL, nt.NTT_FORM_SMALL)\n"
+               "print(nt.ntt_tune_get(1 << 16, 3, f, 4, True))\n"
+               "bad = 0\n"
+               "for args in ((1 << 17, 3, f, 7), (1 << 15, 3, f, 10), (1 << 16, 3, f | nt.NTT_TW_OTF, 7),\n"
+               "             (1000, 3, f, 8), (1 << 16, 0, f, 8)):\n"
+               "    try:\n"
+               "        nt.ntt_tune_set_split(*args)\n"
+               "    except nt.NttError:\n"
+               "        bad += 1\n"
+               "print(bad)\n", db)
+    assert out.split() == ["-1", "1", "9", "-1", "0", "5"]
+    rows = [json.loads(x) for x in open(db)]
+    assert [r["split_log2"] for r in rows if "split_log2" in r] == [9]
+    forms = sorted((r["chunk_log2"], r["forward_form"]) for r in rows if "chunk_log2" in r)
+    assert forms == [(8, 1), (9, 0)]
+    out = _run("import paper_2405_11353_gb300 as nt\n"
+               "f = nt.NTT_ORDER_BITREV\n"
+               "print(nt.ntt_tune_get_split(1 << 16, 3, f), nt.ntt_tune_get(1 << 16, 3, f, 4))\n"
+               "nt.ntt_tune_clear()\n"
+               "print(nt.ntt_tune_get_split(1 << 16, 3, f))\n", db)
+    assert out.split() == ["9", "0", "-1"]

@@ -100,15 +100,30 @@ def test_noalloc_full_array_and_limits(nt, orc):
         nt.ntt_plan_destroy(plan)
 
 
-def test_noalloc_rejects_plans_without_stage_tables(nt):
+def test_noalloc_rejects_fused_plans_and_serves_tensor_core_plans(nt):
+    """Fused plans with N >= 16 have no per-stage tables and are rejected;
+    tensor-core four-step plans carry them and give ntt_forward's result,
+    in both output orders."""
     d = torch.zeros(1 << 16, dtype=torch.int32, device="cuda")
-    for N, variant, qs in ((1024, nt.NTT_FUSED, [12289]),
-                           (1 << 16, nt.NTT_TC_FOURSTEP, nt.ntt_find_primes(30, 17, 1))):
-        plan = nt.ntt_plan_create(N, qs, variant, 0)
+    fused = nt.ntt_plan_create(1024, [12289], nt.NTT_FUSED, 0)
+    try:
+        with pytest.raises(nt.NttError) as e:
+            nt.ntt_forward_noalloc(fused, d, 1)
+        assert e.value.status == nt.NTT_ERR_UNSUPPORTED
+    finally:
+        nt.ntt_plan_destroy(fused)
+    N = 1 << 16
+    qs = nt.ntt_find_primes(30, 17, 2)
+    host = ntt_synth.rns_batch(41, qs, N, 1)
+    for flags in (0, nt.NTT_ORDER_BITREV):
+        plan = nt.ntt_plan_create(N, qs, nt.NTT_TC_FOURSTEP, flags)
         try:
-            with pytest.raises(nt.NttError) as e:
-                nt.ntt_forward_noalloc(plan, d, 1)
-            assert e.value.status == nt.NTT_ERR_UNSUPPORTED
+            ref = _dev(host, False)
+            got = _dev(host, False)
+            nt.ntt_forward(plan, ref, 1)
+            nt.ntt_forward_noalloc(plan, got, 1)
+            torch.cuda.synchronize()
+            assert torch.equal(ref, got), "flags %#x" % flags
         finally:
             nt.ntt_plan_destroy(plan)
 
