@@ -9,10 +9,17 @@ reduction, bit-reversed evaluation order.  Inputs are seeded synthetic residues 
 for this method); four copies of the batch rotate so every step reads a
 working set (4 x 128 MiB) larger than L2.
 
-Output: one JSON line (rank 0).  `value` is NTTs per second for the whole
-job; `roofline` describes the forward transform (the dominant call);
-`cpu_baseline` times the CPU oracle on a bounded sample; `e2e` is the same
-metric through ntt_polymul_host with pinned host buffers.
+Several GPUs (torchrun, one process each): the limbs are sharded -- the job
+is 16 polynomials of 32 x world limbs and each rank transforms its own 32
+(ntt_limb_shard); no data moves between ranks in the step.
+
+Output: detail lines for the side measurements, then one JSON line (rank
+0, printed last).  `value` is NTTs per second for the whole job, from K
+steps run back to back; `roofline` describes the forward transform (the
+dominant call), timed by events around each call in a second run of the
+same K steps; `cpu_baseline` times the CPU oracle on a bounded sample;
+`e2e` is the same metric through ntt_polymul_host with pinned host buffers;
+`side` closes the line with the side measurements' headline figures.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -683,7 +690,12 @@ def main():
     from paper_2405_11353_gb300 import build as nb
     digest = nb.kernel_digest(nb.FORWARD_U32_SOURCES)
 
-    qs = nt.ntt_find_primes(BITS, M, L)
+    # limb sharding across ranks: the job is 16 polynomials of L x world
+    # limbs and each rank transforms its slice of L limbs (its own primes),
+    # so the work per GPU is fixed as ranks are added; one rank: all L limbs
+    qs_all = nt.ntt_find_primes(BITS, M, L * world)
+    first, count = nt.ntt_limb_shard(L * world, world, rank)
+    qs = qs_all[first:first + count]
     flags = nt.NTT_ORDER_BITREV | nt.NTT_RED_SHOUP
     # the autotuner picks the two-pass form of each direction for the two
     # batch sizes of the step (forward of 16 polynomials, product + inverse
@@ -696,6 +708,7 @@ def main():
     form_names = {v: k for k, v in nt.FORMS.items()}
     forms = {"forward": form_names.get(nt.ntt_plan_form(plan, POLYS)),
              "product_inverse": form_names.get(nt.ntt_plan_form(plan, PAIRS, True))}
+    split = nt.ntt_plan_chunk_log2(plan)
     host = ntt_synth.rns_batch(1005 + 7919 * rank, qs, N, POLYS, dtype=np.uint32)
     words = POLYS * L * N
     half = PAIRS * L * N
@@ -724,7 +737,10 @@ def main():
         step(bufs[i % ROTATE])
     torch.cuda.synchronize()
 
-    # ---------------- timed region: K steps, events per call for the roofline
+    # ---------------- timed region: K steps back to back (the metric), then
+    # the same K steps with an event around each call (per-call times for
+    # the roofline; an event between two launches ends their programmatic
+    # overlap, so these steps run a little slower than the first K)
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     sampler = ClockSampler(dev.index) if rank == 0 else None
@@ -738,6 +754,12 @@ def main():
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
     for i in range(K):
+        step(bufs[i % ROTATE])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    for i in range(K):
         b = bufs[i % ROTATE]
         e = ev[i]
         e[0].record(stream)
@@ -745,7 +767,6 @@ def main():
         e[1].record(stream)
         nt.ntt_pointwise_inverse(plan, b, b, b[half:], PAIRS, sh)
         e[2].record(stream)
-    t_end.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -753,6 +774,7 @@ def main():
     elapsed_ms = t_start.elapsed_time(t_end)
     fwd_ms = statistics.mean(ev[i][0].elapsed_time(ev[i][1]) for i in range(K))
     pwinv_ms = statistics.mean(ev[i][1].elapsed_time(ev[i][2]) for i in range(K))
+    evented_step_ms = statistics.mean(ev[i][0].elapsed_time(ev[i][2]) for i in range(K))
     elapsed_ms = max_over_ranks(elapsed_ms, dist if world > 1 else None, dev)
     ms_per_step = elapsed_ms / K
     value = job_rate(NTT_PER_STEP, world, K, elapsed_ms)
@@ -785,7 +807,8 @@ def main():
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": achieved / peak, "traffic": traffic_from_profiles(digest),
-        "kernel": "ntt_forward: column pass + 256-point chunk pass (%s form), %d transforms" % (forms["forward"], n_fwd),
+        "kernel": "ntt_forward: %d-point column pass + %d-word chunk pass (%s form), %d transforms" % (
+            N >> split, 1 << split, forms["forward"], n_fwd),
         "algorithmic_bytes_per_call": fwd_bytes, "avg_ms": fwd_ms,
         "peak_source": "measured hbm_gbs" if peak_kind == "measured" else "fallback 6.8 TB/s",
     }
@@ -828,10 +851,12 @@ def main():
             "dtype": "u32", "data": "synthetic (seeded SplitMix64 residues, uniform in [0,q))",
             "config": {"workload": WORKLOAD, "N": N, "L": L, "polys": POLYS, "word": "u32",
                        "variant": "fused", "reduction": "shoup", "order": "bitrev",
-                       "two_pass_forms": forms,
+                       "two_pass_forms": forms, "chunk_log2": split,
                        "l2": "4 rotating input copies (512 MiB) > 129 MB L2",
-                       "parallelism": "replicas x%d" % world},
-            "per_call_ms": {"forward_16polys": fwd_ms, "pointwise_inverse_8pairs": pwinv_ms},
+                       "parallelism": ("limb-sharded x%d: %d limbs per rank of %d" % (world, count, L * world))
+                       if world > 1 else "1 GPU"},
+            "per_call_ms": {"forward_16polys": fwd_ms, "pointwise_inverse_8pairs": pwinv_ms,
+                            "step_with_events": evented_step_ms},
             "roofline": roofline,
             "int_roofline": int_roofline,
             "cpu_baseline": cpu,
