@@ -709,6 +709,7 @@ def main():
     forms = {"forward": form_names.get(nt.ntt_plan_form(plan, POLYS)),
              "product_inverse": form_names.get(nt.ntt_plan_form(plan, PAIRS, True))}
     split = nt.ntt_plan_chunk_log2(plan)
+    radix = nt.ntt_plan_radix_log2(plan)
     host = ntt_synth.rns_batch(1005 + 7919 * rank, qs, N, POLYS, dtype=np.uint32)
     words = POLYS * L * N
     half = PAIRS * L * N
@@ -807,8 +808,8 @@ def main():
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": achieved / peak, "traffic": traffic_from_profiles(digest),
-        "kernel": "ntt_forward: %d-point column pass + %d-word chunk pass (%s form), %d transforms" % (
-            N >> split, 1 << split, forms["forward"], n_fwd),
+        "kernel": "ntt_forward: %d-point column pass + %d-word chunk pass (%s form, radix %d), %d transforms" % (
+            N >> split, 1 << split, forms["forward"], 1 << radix, n_fwd),
         "algorithmic_bytes_per_call": fwd_bytes, "avg_ms": fwd_ms,
         "peak_source": "measured hbm_gbs" if peak_kind == "measured" else "fallback 6.8 TB/s",
     }
@@ -851,7 +852,7 @@ def main():
             "dtype": "u32", "data": "synthetic (seeded SplitMix64 residues, uniform in [0,q))",
             "config": {"workload": WORKLOAD, "N": N, "L": L, "polys": POLYS, "word": "u32",
                        "variant": "fused", "reduction": "shoup", "order": "bitrev",
-                       "two_pass_forms": forms, "chunk_log2": split,
+                       "two_pass_forms": forms, "chunk_log2": split, "radix_log2": radix,
                        "l2": "4 rotating input copies (512 MiB) > 129 MB L2",
                        "parallelism": ("limb-sharded x%d: %d limbs per rank of %d" % (world, count, L * world))
                        if world > 1 else "1 GPU"},

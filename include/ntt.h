@@ -328,12 +328,15 @@ ntt_status ntt_limb_shard(uint32_t L, uint32_t world, uint32_t rank,
 
 /* ------------------------------------------------------------ autotuner
  * The two-pass fused path (N > 2^14 with 4-byte words, N > 2^13 with
- * 8-byte) leaves two things open.  The split N = 2^s1 x 2^s2: the first
+ * 8-byte) leaves three things open.  The split N = 2^s1 x 2^s2: the first
  * pass runs the first s1 stages on columns of 2^s1 points, the second the
  * last s2 stages on chunks of 2^s2 consecutive words (the four-step split
- * of Sec. II); s2 is 7, 8 or 9 with 5 <= s1 <= 9, default 8, and the
- * plan's twiddle tables are laid out for it at creation.  (NTT_STREAMED
- * and NTT_TW_OTF plans keep s2 = 8.)  And each direction's form: */
+ * of Sec. II); s2 is 7, 8 or 9 with 5 <= s1 <= 9, default 8.  The radix of
+ * the register rounds inside each pass: radix_log2 = 4 (rounds of four
+ * radix-2 stages on 16 words a thread, the default) or 3 (three stages on
+ * 8 words).  The plan's twiddle tables are laid out for both at creation.
+ * (NTT_STREAMED and NTT_TW_OTF plans keep s2 = 8, radix_log2 = 4.)  And
+ * each direction's form: */
 #define NTT_FORM_SMALL 0      /* chunk pass on one-warp CTAs */
 #define NTT_FORM_WIDE 1       /* chunk pass on 256-thread CTAs */
 #define NTT_FORM_STREAMED 2   /* both passes in one streamed launch (s2 = 8) */
@@ -343,25 +346,28 @@ ntt_status ntt_limb_shard(uint32_t L, uint32_t world, uint32_t rank,
  * the batch and chunks have at least 256 words, else several chunks of one
  * polynomial.  Results are identical in every split, form and tiling. */
 typedef struct {
-    float forward_ms[3];      /* per form, ms per call, at the chosen split */
+    float forward_ms[3];      /* per form, ms per call, at the chosen
+                                 radix and split */
     float inverse_ms[3];
     int32_t forward_form;     /* the fastest */
     int32_t inverse_form;
     int32_t chunk_log2;       /* the chosen split s2 */
-    float split_ms[3];        /* per split s2 = 7, 8, 9: fastest forward +
+    int32_t radix_log2;       /* the chosen radix (3 or 4) */
+    float config_ms[2][3];    /* [radix_log2 - 3][s2 - 7]: fastest forward +
                                  fastest inverse, ms; -1 where not valid */
 } ntt_tune_result;
 
-/* Time every valid split, and in each every form of both directions, for
- * (N, q[0..L), flags, batch) on the current device (a scratch buffer of
- * batch x L x N zero words, allocated and freed here); record per split the
- * fastest form per direction in the process-wide tuning table, keyed by
- * (N, word size, L, reduction, order, NTT_TW_OTF or not, s2, floor(log2
- * batch)), and for the shape the split with the smallest forward +
- * inverse time.  Plans created afterwards with that shape take that split
- * and use the recorded forms for calls in that batch bucket (NTT_STREAMED
- * plans keep theirs).  Forms that do not exist (streamed with s2 != 8 or
- * with NTT_TW_OTF) are reported as -1 and never chosen.  If the environment
+/* Time every valid (radix, split), and in each every form of both
+ * directions, for (N, q[0..L), flags, batch) on the current device (a
+ * scratch buffer of batch x L x N zero words, allocated and freed here);
+ * record per (radix, split) the fastest form per direction in the
+ * process-wide tuning table, keyed by (N, word size, L, reduction, order,
+ * NTT_TW_OTF or not, s2, radix, floor(log2 batch)), and for the shape the
+ * (radix, split) with the smallest forward + inverse time.  Plans created
+ * afterwards with that shape take that radix and split and use the
+ * recorded forms for calls in that batch bucket (NTT_STREAMED plans keep
+ * theirs).  Forms that do not exist (streamed with s2 != 8, radix 3 or
+ * NTT_TW_OTF) are reported as -1 and never chosen.  If the environment
  * variable NTT_TUNE_DB names a file, the tables are read from it at first
  * use and rewritten after each tuning (one JSON object per line).  flags:
  * as ntt_plan_create, without NTT_STREAMED, NTT_CHECK or NTT_TEST_STALL.
@@ -375,25 +381,29 @@ ntt_status ntt_autotune(uint32_t N, const uint64_t *q, uint32_t L,
  * inverse), or -1 when the plan is not on the two-pass fused path. */
 int32_t ntt_plan_form(ntt_plan_t plan, uint32_t batch, int inverse);
 
-/* The plan's split s2 (chunks of 2^s2 words), or -1 when the plan is not on
- * the two-pass fused path. */
+/* The plan's split s2 (chunks of 2^s2 words) and radix (3 or 4), or -1
+ * when the plan is not on the two-pass fused path. */
 int32_t ntt_plan_chunk_log2(ntt_plan_t plan);
+int32_t ntt_plan_radix_log2(ntt_plan_t plan);
 
 /* Host-only access to the tuning tables (no GPU needed): record forms for a
- * shape by hand, for the shape's current split (saved to NTT_TUNE_DB like a
- * tuning; NTT_ERR_INVALID_ARG for a form outside 0..2 or batch 0); read the
- * form recorded for a shape's split and direction (-1: none); record or
- * read a shape's split (NTT_ERR_INVALID_ARG for a split the shape cannot
- * take; -1: none recorded, plans use 8); empty the in-memory tables (the
- * file is not read again in this process).  Plans copy the tables at
- * creation. */
+ * shape by hand, for the shape's current radix and split (saved to
+ * NTT_TUNE_DB like a tuning; NTT_ERR_INVALID_ARG for a form outside 0..2 or
+ * batch 0); read the form recorded for a shape's radix, split and
+ * direction (-1: none); record a shape's split and radix
+ * (NTT_ERR_INVALID_ARG for a pair the shape cannot take); read them (the
+ * split is returned, the radix stored in *radix_log2 if not NULL; -1 for
+ * both: none recorded, plans use s2 = 8, radix 4); empty the in-memory
+ * tables (the file is not read again in this process).  Plans copy the
+ * tables at creation. */
 ntt_status ntt_tune_set(uint32_t N, uint32_t L, uint32_t flags, uint32_t batch,
                         int32_t forward_form, int32_t inverse_form);
 int32_t ntt_tune_get(uint32_t N, uint32_t L, uint32_t flags, uint32_t batch,
                      int inverse);
 ntt_status ntt_tune_set_split(uint32_t N, uint32_t L, uint32_t flags,
-                              uint32_t chunk_log2);
-int32_t ntt_tune_get_split(uint32_t N, uint32_t L, uint32_t flags);
+                              uint32_t chunk_log2, uint32_t radix_log2);
+int32_t ntt_tune_get_split(uint32_t N, uint32_t L, uint32_t flags,
+                           int32_t *radix_log2);
 void ntt_tune_clear(void);
 
 /* ------------------------------------------------ integer roofline

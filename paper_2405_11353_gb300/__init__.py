@@ -62,7 +62,7 @@ EXPORTS = [
     "ntt_bconv_create", "ntt_bconv", "ntt_bconv_destroy", "ntt_measure_int_mad_rate",
     "ntt_autotune", "ntt_plan_form", "ntt_tune_set", "ntt_tune_get", "ntt_tune_clear",
     "ntt_ragged_item_tiles", "ntt_plan_table_bytes", "ntt_limb_shard",
-    "ntt_tune_set_split", "ntt_tune_get_split", "ntt_plan_chunk_log2",
+    "ntt_tune_set_split", "ntt_tune_get_split", "ntt_plan_chunk_log2", "ntt_plan_radix_log2",
 ]
 
 
@@ -82,7 +82,8 @@ class NttJob(ctypes.Structure):
 class NttTuneResult(ctypes.Structure):
     _fields_ = [("forward_ms", ctypes.c_float * 3), ("inverse_ms", ctypes.c_float * 3),
                 ("forward_form", ctypes.c_int32), ("inverse_form", ctypes.c_int32),
-                ("chunk_log2", ctypes.c_int32), ("split_ms", ctypes.c_float * 3)]
+                ("chunk_log2", ctypes.c_int32), ("radix_log2", ctypes.c_int32),
+                ("config_ms", (ctypes.c_float * 3) * 2)]
 
 
 NTT_FORM_SMALL, NTT_FORM_WIDE, NTT_FORM_STREAMED = 0, 1, 2
@@ -136,9 +137,10 @@ def lib():
             "ntt_tune_clear": (None, []),
             "ntt_ragged_item_tiles": (u32, [vp]),
             "ntt_limb_shard": (st, [u32, u32, u32, ctypes.POINTER(u32), ctypes.POINTER(u32)]),
-            "ntt_tune_set_split": (st, [u32, u32, u32, u32]),
-            "ntt_tune_get_split": (ctypes.c_int32, [u32, u32, u32]),
+            "ntt_tune_set_split": (st, [u32, u32, u32, u32, u32]),
+            "ntt_tune_get_split": (ctypes.c_int32, [u32, u32, u32, ctypes.POINTER(ctypes.c_int32)]),
             "ntt_plan_chunk_log2": (ctypes.c_int32, [vp]),
+            "ntt_plan_radix_log2": (ctypes.c_int32, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -352,16 +354,20 @@ def ntt_measure_int_mad_rate(high, iters, scratch, stream=None):
 
 
 def ntt_autotune(N, q, flags, batch, stream=None):
-    """Time every two-pass split and form for this shape, record the
-    fastest; returns {"forward_ms": [...], "inverse_ms": [...] (per form, at
-    the chosen split), "forward_form", "inverse_form", "chunk_log2" (the
-    chosen split), "split_ms": [...] (s2 = 7, 8, 9; -1 where not valid)}."""
+    """Time every two-pass radix, split and form for this shape, record
+    the fastest; returns {"forward_ms": [...], "inverse_ms": [...] (per form,
+    at the chosen radix and split), "forward_form", "inverse_form",
+    "chunk_log2", "radix_log2" (the chosen split and radix), "config_ms":
+    {"radix_log2,chunk_log2": fastest forward + inverse ms, for the valid
+    pairs}}."""
     r = NttTuneResult()
     _check(lib().ntt_autotune(N, _u64arr(q), len(q), flags, batch, _stream(stream), ctypes.byref(r)),
            "ntt_autotune")
     return {"forward_ms": list(r.forward_ms), "inverse_ms": list(r.inverse_ms),
             "forward_form": r.forward_form, "inverse_form": r.inverse_form,
-            "chunk_log2": r.chunk_log2, "split_ms": list(r.split_ms)}
+            "chunk_log2": r.chunk_log2, "radix_log2": r.radix_log2,
+            "config_ms": {"%d,%d" % (3 + i, 7 + j): r.config_ms[i][j] for i in range(2) for j in range(3)
+                          if r.config_ms[i][j] >= 0}}
 
 
 def ntt_plan_form(plan, batch, inverse=False):
@@ -376,16 +382,23 @@ def ntt_tune_get(N, L, flags, batch, inverse=False):
     return lib().ntt_tune_get(N, L, flags, batch, 1 if inverse else 0)
 
 
-def ntt_tune_set_split(N, L, flags, chunk_log2):
-    _check(lib().ntt_tune_set_split(N, L, flags, chunk_log2), "ntt_tune_set_split")
+def ntt_tune_set_split(N, L, flags, chunk_log2, radix_log2=4):
+    _check(lib().ntt_tune_set_split(N, L, flags, chunk_log2, radix_log2), "ntt_tune_set_split")
 
 
 def ntt_tune_get_split(N, L, flags):
-    return lib().ntt_tune_get_split(N, L, flags)
+    """(chunk_log2, radix_log2) recorded for the shape, or (-1, -1)."""
+    r = ctypes.c_int32()
+    s = lib().ntt_tune_get_split(N, L, flags, ctypes.byref(r))
+    return int(s), int(r.value)
 
 
 def ntt_plan_chunk_log2(plan):
     return lib().ntt_plan_chunk_log2(plan)
+
+
+def ntt_plan_radix_log2(plan):
+    return lib().ntt_plan_radix_log2(plan)
 
 
 def ntt_tune_clear():

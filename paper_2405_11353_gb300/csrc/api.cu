@@ -222,7 +222,7 @@ ntt_status build_tables(ntt_plan_s *p) {
     if (clu_tabs) { kf.resize((size_t)L * 8 * (8192 + 16) * pair_bytes); ki.resize(kf.size()); }
     // main-table position of entry i (see level_pos in modarith.cuh)
     auto main_pos = [&](uint32_t i) -> uint32_t {
-        return nttgb::level_pos(i, p->fused_mode == nttgb::FUSED_SINGLE ? n : p->s1);
+        return p->fused_mode == nttgb::FUSED_SINGLE ? nttgb::level_pos(i, n) : nttgb::level_pos(i, p->s1, p->lr);
     };
 
     std::vector<uint64_t> pw(N), pwi(N);
@@ -289,7 +289,7 @@ ntt_status build_tables(ntt_plan_s *p) {
                     for (uint32_t ip = 0; ip < (1u << s); ++ip) {
                         uint32_t gi = (1u << s) * (N1 + r) + ip;
                         uint32_t e = H::bitrev(gi, (int)n);
-                        size_t at = cbase + (size_t)r * CP + nttgb::level_pos((1u << s) + ip, p->s2);
+                        size_t at = cbase + (size_t)r * CP + nttgb::level_pos((1u << s) + ip, p->s2, p->lr);
                         enc(pw[e], v, cc); put_pair(cf, at, v, cc, w64);
                         enc(pwi[e], v, cc); put_pair(ci, at, v, cc, w64);
                     }
@@ -325,7 +325,7 @@ ntt_status build_tables(ntt_plan_s *p) {
             for (uint32_t s = 0; s < p->s2; ++s)
                 for (uint32_t ip = 0; ip < (1u << s); ++ip) {
                     const uint64_t e = (1ull << (n - s)) * (uint64_t)H::bitrev(ip, (int)s);
-                    const size_t at = rb + nttgb::level_pos((1u << s) + ip, p->s2);
+                    const size_t at = rb + nttgb::level_pos((1u << s) + ip, p->s2, p->lr);
                     enc(pw2[e], v, cc); put_pair(rf, at, v, cc, w64);
                     enc(pwi2[e], v, cc); put_pair(ri, at, v, cc, w64);
                 }
@@ -594,7 +594,7 @@ namespace nttgb {
 // Plan builder behind ntt_plan_create_ex.  single_max_log >= 0 caps the
 // size done in one fused pass (the ragged kernel uses 12).
 ntt_status create_plan(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t L, ntt_variant variant,
-                       uint32_t flags, const uint64_t *psi, int single_max_log, int split_log) {
+                       uint32_t flags, const uint64_t *psi, int single_max_log, int split_log, int radix_log) {
     if (!plan) return NTT_ERR_INVALID_ARG;
     *plan = nullptr;
     if ((int)variant < NTT_DIT || (int)variant > NTT_TC_FOURSTEP) return NTT_ERR_INVALID_ARG;
@@ -648,9 +648,16 @@ ntt_status create_plan(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t
             // 256-word chunks; others may take a given or tuned split
             p->split_fixed = p->streamed || p->tw_otf || single_max_log >= 0;
             if (split_log >= 0) {
-                if (p->split_fixed && split_log != nttgb::kChunkLog) { delete p; return NTT_ERR_UNSUPPORTED; }
-                if (!nttgb::split_valid(p->logN, (uint32_t)split_log)) { delete p; return NTT_ERR_UNSUPPORTED; }
+                if (p->split_fixed && (split_log != nttgb::kChunkLog || radix_log != 4)) {
+                    delete p;
+                    return NTT_ERR_UNSUPPORTED;
+                }
+                if (!nttgb::split_valid(p->logN, (uint32_t)split_log) || (radix_log != 3 && radix_log != 4)) {
+                    delete p;
+                    return NTT_ERR_UNSUPPORTED;
+                }
                 p->s2 = (uint32_t)split_log;
+                p->lr = (uint32_t)radix_log;
                 p->split_fixed = true;
             }
             p->s1 = p->logN - p->s2;

@@ -95,33 +95,47 @@ template <class W> __host__ __device__ constexpr uint32_t cols_phys(uint32_t k, 
 // two-pass launch, whose CTAs always have 256 threads (4096-word column
 // tiles).  P = 3: per-pass chunk kernels with 16-chunk tiles (as P = 0
 // otherwise).  Bit 3 of P (P = 8, 11) pairs polynomials in chunk tiles
-// (paired_chunks).
+// (paired_chunks).  Bit 4 of P (per-plan column and chunk passes): rounds
+// of three stages on 8 words a thread instead of four stages on 16
+// (radix_log).
+template <int P> __host__ __device__ constexpr int radix_log() { return (P & 16) ? 3 : 4; }
 template <class W, int LOGS, int KIND, int P = 0> __host__ __device__ constexpr uint32_t tile_k() {
-    // (chunks: one warp per CTA, or 256 threads; 2^LOGS / 16 threads a chunk)
+    // threads per sub-transform: 2^(LOGS - LR).  Chunks: one warp per CTA
+    // (at least one chunk), or 256 threads.  Columns: 128-byte rows (or
+    // more columns for short columns), at most 1024 threads (512 with
+    // 8-byte words, the kernels' launch bound).
+    constexpr int LR = radix_log<P>();
+    constexpr uint32_t T = 1u << (LOGS > LR ? LOGS - LR : 0);
+    constexpr uint32_t KC = (256u >> (LOGS - LR)) > (128u / sizeof(W)) ? (256u >> (LOGS - LR))
+                                                                        : (128u / (uint32_t)sizeof(W));
+    constexpr uint32_t TMAX = sizeof(W) == 4 ? 1024u : 512u;
     return KIND == TK_SINGLE ? (LOGS >= 12 ? 1u : (4096u >> LOGS))
-         : KIND == TK_CHUNKS ? ((P & 3) == 0 ? (LOGS >= 9 ? 1u : (512u >> LOGS)) : (4096u >> LOGS))
+         : KIND == TK_CHUNKS ? ((P & 3) == 0 ? (T >= 32 ? 1u : 32u / T) : (T >= 256 ? 1u : 256u / T))
          : (P & 3) == 1 ? (4096u >> LOGS)
-         : ((256u >> (LOGS - 4)) > (128u / sizeof(W)) ? (256u >> (LOGS - 4)) : (128u / (uint32_t)sizeof(W)));
+         : (KC * T > TMAX ? TMAX / T : KC);
 }
 
-// Round J of a sub-transform covers bits [LO, LO+RR) of the index u.
-// Forward: from the top down with the short round (LOGS mod 4 bits) first;
-// inverse: from the bottom up with the short round last.  Thread tau holds
-// the 16 words u = A(tau) | E(e), e = 0..15, where E places e's bits on the
-// round's bits (and, in a short round, the spare bits of e just above tau's
-// share) and A places tau's bits elsewhere; A and E are disjoint bit fields,
-// so every layout below maps u to A's address plus a constant for E.
-template <int LOGS, bool INV, int J> struct RoundOf {
-    static constexpr int SHORT = LOGS % 4;
-    static constexpr int NR = (LOGS + 3) / 4;
-    static constexpr int RR = INV ? ((LOGS - 4 * J) < 4 ? (LOGS - 4 * J) : 4) : ((SHORT && J == 0) ? SHORT : 4);
-    static constexpr int LO = INV ? 4 * J : ((SHORT && J == 0) ? LOGS - SHORT : LOGS - SHORT - 4 * J - (SHORT ? 0 : 4));
+// Round J of a sub-transform covers bits [LO, LO+RR) of the index u, in
+// rounds of LR = 4 (or 3) stages on 2^LR words a thread.  Forward: from the
+// top down with the short round (LOGS mod LR bits) first; inverse: from
+// the bottom up with the short round last.  Thread tau holds the 2^LR
+// words u = A(tau) | E(e), e < 2^LR, where E places e's bits on the
+// round's bits (and, in a short round, the spare bits of e just above
+// tau's share) and A places tau's bits elsewhere; A and E are disjoint bit
+// fields, so every layout below maps u to A's address plus a constant for
+// E.
+template <int LOGS, bool INV, int J, int LR = 4> struct RoundOf {
+    static constexpr int SHORT = LOGS % LR;
+    static constexpr int NR = (LOGS + LR - 1) / LR;
+    static constexpr int RR = INV ? ((LOGS - LR * J) < LR ? (LOGS - LR * J) : LR) : ((SHORT && J == 0) ? SHORT : LR);
+    static constexpr int LO = INV ? LR * J
+                                  : ((SHORT && J == 0) ? LOGS - SHORT : LOGS - SHORT - LR * J - (SHORT ? 0 : LR));
     __host__ __device__ static constexpr uint32_t E(int e) {
-        return RR == 4 ? ((uint32_t)e << LO)
-                       : (((uint32_t)e >> RR) | (((uint32_t)e & ((1u << RR) - 1)) << LO));
+        return RR == LR ? ((uint32_t)e << LO)
+                        : (((uint32_t)e >> RR) | (((uint32_t)e & ((1u << RR) - 1)) << LO));
     }
     __device__ static __forceinline__ uint32_t A(uint32_t tau) {
-        return RR == 4 ? ((tau & ((1u << LO) - 1)) | ((tau >> LO) << (LO + 4))) : (tau << (4 - RR));
+        return RR == LR ? ((tau & ((1u << LO) - 1)) | ((tau >> LO) << (LO + LR))) : (tau << (LR - RR));
     }
 };
 
@@ -159,10 +173,10 @@ __device__ __forceinline__ void load_tw(Tw<W> (&t)[8], const Tw<W> *__restrict__
     }
 }
 
-template <class W, int RED, bool INV, int LOGS, int J, bool SMEM>
-__device__ __forceinline__ void round_bfly(W (&x)[16], uint32_t tau, const Tw<W> *__restrict__ tw, const Lc<W> &k,
-                                           bool last_pass, Tw<W> tn, Tw<W> twn) {
-    using R = RoundOf<LOGS, INV, J>;
+template <class W, int RED, bool INV, int LOGS, int J, bool SMEM, int LR = 4>
+__device__ __forceinline__ void round_bfly(W (&x)[1 << LR], uint32_t tau, const Tw<W> *__restrict__ tw,
+                                           const Lc<W> &k, bool last_pass, Tw<W> tn, Tw<W> twn) {
+    using R = RoundOf<LOGS, INV, J, LR>;
     constexpr int RR = R::RR, LO = R::LO;
 #pragma unroll
     for (int dd = 0; dd < RR; ++dd) {
@@ -172,11 +186,11 @@ __device__ __forceinline__ void round_bfly(W (&x)[16], uint32_t tau, const Tw<W>
         Tw<W> t[8];
         const bool fold = INV && b == LOGS - 1 && last_pass;
         if (!fold) {
-            if constexpr (RR == 4) {
+            if constexpr (RR == LR) {
                 // full round: pair j of thread tau at 2^lvl + j * ntau + (tau >> LO)
-                constexpr int NTAU_LOG = LOGS - 4 - LO >= 0 ? LOGS - 4 - LO : 0;
+                constexpr int NTAU_LOG = LOGS - LR - LO >= 0 ? LOGS - LR - LO : 0;
                 const Tw<W> *p = tw + (1u << lvl) + (tau >> LO);
-                switch (3 - d) {
+                switch (LR - 1 - d) {
                 case 0: load_tw<W, 1, (1 << NTAU_LOG), SMEM>(t, p); break;
                 case 1: load_tw<W, 2, (1 << NTAU_LOG), SMEM>(t, p); break;
                 case 2: load_tw<W, 4, (1 << NTAU_LOG), SMEM>(t, p); break;
@@ -193,7 +207,7 @@ __device__ __forceinline__ void round_bfly(W (&x)[16], uint32_t tau, const Tw<W>
             }
         }
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
+        for (int e = 0; e < (1 << LR); ++e) {
             if (e & (1 << d)) continue;
             const int j = (e & ((1 << RR) - 1)) >> (d + 1);
             if (!INV) {
@@ -284,23 +298,25 @@ __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wa
 // padded layout sm_off in `xs` (the tile's own stage buffer, whose staged
 // words have all been read by then).
 template <class W, int RED, bool INV, int LOGS, int KIND, bool WS, bool SMEM, int J, int P>
-__device__ __forceinline__ void later_rounds(W (&x)[16], W *xs, uint32_t smb_k, uint32_t tau,
+__device__ __forceinline__ void later_rounds(W (&x)[1 << radix_log<P>()], W *xs, uint32_t smb_k, uint32_t tau,
                                              const Tw<W> *__restrict__ tw, const Lc<W> &kk, bool last_pass,
                                              Tw<W> tn, Tw<W> twn) {
-    using R = RoundOf<LOGS, INV, J>;
+    constexpr int LR = radix_log<P>();
+    constexpr int NW = 1 << LR;
+    using R = RoundOf<LOGS, INV, J, LR>;
     if constexpr (J < R::NR) {
-        using RP = RoundOf<LOGS, INV, J - 1>;
-        // a thread's 16 words are consecutive (round at bit 0) in the rows
+        using RP = RoundOf<LOGS, INV, J - 1, LR>;
+        // a thread's words are consecutive (round at bit 0) in the rows
         // layout: move them as 16-byte vectors
-        constexpr bool VST = KIND != TK_COLS && RP::LO == 0 && RP::RR == 4;
-        constexpr bool VLD = KIND != TK_COLS && R::LO == 0 && R::RR == 4;
+        constexpr bool VST = KIND != TK_COLS && RP::LO == 0 && RP::RR == LR;
+        constexpr bool VLD = KIND != TK_COLS && R::LO == 0 && R::RR == LR;
         constexpr int V = 16 / sizeof(W);
         {
             const uint32_t base = smb_k + sm_off<W, LOGS, KIND, P>(0, RP::A(tau));
             if (J > 1) tile_sync<W, WS>();   // readers of the previous exchange are done
             if constexpr (VST) {
 #pragma unroll
-                for (int v = 0; v < 16 / V; ++v) {
+                for (int v = 0; v < NW / V; ++v) {
                     W *q = xs + base + sm_off<W, LOGS, KIND, P>(0, (uint32_t)(v * V));
                     if (sizeof(W) == 4)
                         *reinterpret_cast<uint4 *>(q) = make_uint4((uint32_t)x[4 * v], (uint32_t)x[4 * v + 1],
@@ -311,7 +327,7 @@ __device__ __forceinline__ void later_rounds(W (&x)[16], W *xs, uint32_t smb_k, 
                 }
             } else {
 #pragma unroll
-                for (int e = 0; e < 16; ++e) xs[base + sm_off<W, LOGS, KIND, P>(0, RP::E(e))] = x[e];
+                for (int e = 0; e < NW; ++e) xs[base + sm_off<W, LOGS, KIND, P>(0, RP::E(e))] = x[e];
             }
         }
         tile_sync<W, WS>();
@@ -319,7 +335,7 @@ __device__ __forceinline__ void later_rounds(W (&x)[16], W *xs, uint32_t smb_k, 
             const uint32_t base = smb_k + sm_off<W, LOGS, KIND, P>(0, R::A(tau));
             if constexpr (VLD) {
 #pragma unroll
-                for (int v = 0; v < 16 / V; ++v) {
+                for (int v = 0; v < NW / V; ++v) {
                     const W *q = xs + base + sm_off<W, LOGS, KIND, P>(0, (uint32_t)(v * V));
                     if (sizeof(W) == 4) {
                         uint4 w4 = *reinterpret_cast<const uint4 *>(q);
@@ -331,10 +347,10 @@ __device__ __forceinline__ void later_rounds(W (&x)[16], W *xs, uint32_t smb_k, 
                 }
             } else {
 #pragma unroll
-                for (int e = 0; e < 16; ++e) x[e] = xs[base + sm_off<W, LOGS, KIND, P>(0, R::E(e))];
+                for (int e = 0; e < NW; ++e) x[e] = xs[base + sm_off<W, LOGS, KIND, P>(0, R::E(e))];
             }
         }
-        round_bfly<W, RED, INV, LOGS, J, SMEM>(x, tau, tw, kk, last_pass, tn, twn);
+        round_bfly<W, RED, INV, LOGS, J, SMEM, LR>(x, tau, tw, kk, last_pass, tn, twn);
         later_rounds<W, RED, INV, LOGS, KIND, WS, SMEM, J + 1, P>(x, xs, smb_k, tau, tw, kk, last_pass, tn, twn);
     }
 }
@@ -420,8 +436,10 @@ struct PipeState {
 template <class W, int RED, bool INV, int LOGS, int KIND, int P, bool OTF_K = false, bool DEP = false>
 __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *tmap, uint32_t t_begin,
                                           uint32_t t_end, unsigned char *base, uint64_t *bar, PipeState &ps) {
+    constexpr int LR = radix_log<P>();          // 2^LR words a thread
+    constexpr int NW = 1 << LR;
     constexpr uint32_t S = 1u << LOGS;
-    constexpr uint32_t T = S / 16;
+    constexpr uint32_t T = S >> LR;
     constexpr uint32_t K = tile_k<W, LOGS, KIND, P>();
     constexpr uint32_t NS = n_stages<W, LOGS, KIND, P>();
     constexpr uint32_t BW = buf_words<W, LOGS, KIND, INV, P>();
@@ -432,8 +450,8 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     constexpr uint32_t CP = chunk_tab_pitch<W, KIND == TK_CHUNKS ? LOGS : 8>();
     constexpr uint32_t RW = 128 / sizeof(W);     // words per 128-byte row
     constexpr bool WS = KIND != TK_COLS && T <= 32;
-    using R0 = RoundOf<LOGS, INV, 0>;
-    using RL = RoundOf<LOGS, INV, R0::NR - 1>;
+    using R0 = RoundOf<LOGS, INV, 0, LR>;
+    using RL = RoundOf<LOGS, INV, R0::NR - 1, LR>;
     // Per-plan passes (long runs of tiles per CTA, registers to spare):
     // refill a buffer right after the next tile's first barrier, which saves
     // a barrier per tile; keep the limb constants in registers across tiles;
@@ -693,8 +711,8 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
         }
         // fused pointwise product (inverse chunk pass): b's 16 words at this
         // thread's positions, loaded before the tile wait so they overlap it
-        constexpr bool PW = KIND == TK_CHUNKS && INV && R0::RR == 4 && R0::LO == 0;
-        constexpr int NV = 16 / (16 / (int)sizeof(W));
+        constexpr bool PW = KIND == TK_CHUNKS && INV && R0::RR == LR && R0::LO == 0;
+        constexpr int NV = NW / (16 / (int)sizeof(W));
         using V16 = typename std::conditional<sizeof(W) == 4, uint4, ulonglong2>::type;
         V16 bv[PW ? NV : 1];
         const bool use_pw = PW && a.pw_b && valid;
@@ -710,17 +728,17 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
         // ---- round 0 from the staged tile
         ok = ok && mbar_wait_bounded(&bar[s], parity);
         W *sb = stage + (size_t)s * BW;
-        W x[16];
+        W x[NW];
         {
             const uint32_t A0 = R0::A(tau);
             if (KIND == TK_COLS) {
 #pragma unroll
-                for (int e = 0; e < 16; ++e) x[e] = sb[(A0 | R0::E(e)) * K + k];
-            } else if (SWZ && R0::RR == 4 && R0::LO == 0) {
-                // 16 consecutive words of chunk k from swizzled 128-byte rows
+                for (int e = 0; e < NW; ++e) x[e] = sb[(A0 | R0::E(e)) * K + k];
+            } else if (SWZ && R0::RR == LR && R0::LO == 0) {
+                // 2^LR consecutive words of chunk k from swizzled 128-byte rows
                 constexpr int V = 16 / sizeof(W);            // words per 16-byte unit
 #pragma unroll
-                for (int v = 0; v < 16 / V; ++v) {
+                for (int v = 0; v < NW / V; ++v) {
                     const uint32_t u = A0 + v * V;            // first word of the unit
                     const uint32_t row = k * (S / RW) + u / RW;
                     const uint32_t unit = ((u % RW) / V) ^ (row & 7u);
@@ -733,11 +751,11 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
                         x[2 * v] = (W)w2.x; x[2 * v + 1] = (W)w2.y;
                     }
                 }
-            } else if (R0::RR == 4 && R0::LO == 0) {
-                // sixteen consecutive words: four 16-byte loads
+            } else if (R0::RR == LR && R0::LO == 0) {
+                // 2^LR consecutive words: 16-byte loads
                 const W *q = sb + k * SP + A0;
 #pragma unroll
-                for (int v = 0; v < 16 / (16 / (int)sizeof(W)); ++v) {
+                for (int v = 0; v < NW / (16 / (int)sizeof(W)); ++v) {
                     if (sizeof(W) == 4) {
                         uint4 w4 = reinterpret_cast<const uint4 *>(q)[v];
                         x[4 * v] = (W)w4.x; x[4 * v + 1] = (W)w4.y; x[4 * v + 2] = (W)w4.z; x[4 * v + 3] = (W)w4.w;
@@ -748,7 +766,7 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
                 }
             } else {
 #pragma unroll
-                for (int e = 0; e < 16; ++e) x[e] = sb[k * SP + (A0 | R0::E(e))];
+                for (int e = 0; e < NW; ++e) x[e] = sb[k * SP + (A0 | R0::E(e))];
             }
         }
         if constexpr (PW) {
@@ -787,7 +805,7 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
             ++n_issued;
             if (tile + NS < t_end) prefetch(ahead);
         }
-        round_bfly<W, RED, INV, LOGS, 0, TWS>(x, tau, twb, kk, INV && a.final_pass, tn, twn);
+        round_bfly<W, RED, INV, LOGS, 0, TWS, LR>(x, tau, twb, kk, INV && a.final_pass, tn, twn);
         later_rounds<W, RED, INV, LOGS, KIND, WS, TWS, 1, P>(x, sb, smb_k, tau, twb, kk, INV && a.final_pass, tn, twn);
         if (!LATE_REFILL) {
             // the buffer and the twiddles are free: refill with the tile NS ahead
@@ -802,7 +820,7 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
         }
         if (a.final_pass) {
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
+            for (int e = 0; e < NW; ++e) {
                 W y = x[e];
                 if (!INV) y = csub<W>(y, kk.two_q);
                 x[e] = csub<W>(y, kk.q);
@@ -814,13 +832,13 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
             if (KIND == TK_COLS) {
                 W *g = a.out + t * N + pos0 + k;
 #pragma unroll
-                for (int e = 0; e < 16; ++e) g[(size_t)(AL | RL::E(e)) << S2] = x[e];
+                for (int e = 0; e < NW; ++e) g[(size_t)(AL | RL::E(e)) << S2] = x[e];
             } else {
                 W *g = KIND == TK_SINGLE ? a.out + t * N : a.out + t * N + ((size_t)pk << S2);
-                if (RL::RR == 4 && RL::LO == 0) {
+                if (RL::RR == LR && RL::LO == 0) {
                     W *q = g + AL;
 #pragma unroll
-                    for (int v = 0; v < 16 / (16 / (int)sizeof(W)); ++v) {
+                    for (int v = 0; v < NW / (16 / (int)sizeof(W)); ++v) {
                         if (sizeof(W) == 4)
                             reinterpret_cast<uint4 *>(q)[v] = make_uint4((uint32_t)x[4 * v], (uint32_t)x[4 * v + 1],
                                                                          (uint32_t)x[4 * v + 2], (uint32_t)x[4 * v + 3]);
@@ -830,7 +848,7 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
                     }
                 } else {
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) g[AL | RL::E(e)] = x[e];
+                    for (int e = 0; e < NW; ++e) g[AL | RL::E(e)] = x[e];
                 }
             }
         }
@@ -864,19 +882,22 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
 // words (512 threads) and Shoup or Montgomery twiddles are held to the
 // registers that let three CTAs share an SM, as their shared memory allows
 // (40 a thread, no spills); 512-point column passes take 1024 threads.
-template <class W, int RED, int LOGS, int KIND, bool INV> __host__ __device__ constexpr bool fused_cols3() {
-    return KIND == TK_COLS && INV && sizeof(W) == 4 && RED != RED_BARRETT && LOGS <= 8;
+template <class W, int RED, int LOGS, int KIND, bool INV, int P> __host__ __device__ constexpr bool fused_cols3() {
+    return KIND == TK_COLS && INV && sizeof(W) == 4 && RED != RED_BARRETT && LOGS <= 8 && radix_log<P>() == 4;
 }
-template <class W, int RED, int LOGS, int KIND, bool INV> __host__ __device__ constexpr int fused_max_threads() {
-    return fused_cols3<W, RED, LOGS, KIND, INV>() ? 512 : (sizeof(W) == 4 ? 1024 : 512);
+template <class W, int RED, int LOGS, int KIND, bool INV, int P> __host__ __device__ constexpr int fused_max_threads() {
+    return fused_cols3<W, RED, LOGS, KIND, INV, P>() ? 512 : (sizeof(W) == 4 ? 1024 : 512);
 }
-template <class W, int RED, int LOGS, int KIND, bool INV> __host__ __device__ constexpr int fused_min_blocks() {
-    return fused_cols3<W, RED, LOGS, KIND, INV>() ? 3 : 1;
+template <class W, int RED, int LOGS, int KIND, bool INV, int P> __host__ __device__ constexpr int fused_min_blocks() {
+    return fused_cols3<W, RED, LOGS, KIND, INV, P>() ? 3 : 1;
 }
 template <class W, int RED, bool INV, int LOGS, int KIND, int PP, bool OTF_K = false>
-__global__ void __launch_bounds__(fused_max_threads<W, RED, LOGS, KIND, INV>(),
-                                  fused_min_blocks<W, RED, LOGS, KIND, INV>())
+__global__ void __launch_bounds__(fused_max_threads<W, RED, LOGS, KIND, INV, PP>(),
+                                  fused_min_blocks<W, RED, LOGS, KIND, INV, PP>())
 k_fused(const __grid_constant__ FArgs<W> a) {
+    static_assert(tile_k<W, LOGS, KIND, PP>() * ((1u << LOGS) >> radix_log<PP>()) <=
+                      (uint32_t)fused_max_threads<W, RED, LOGS, KIND, INV, PP>(),
+                  "a tile's threads must fit the launch bound");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     constexpr uint32_t NS = n_stages<W, LOGS, KIND, PP>();
     constexpr uint32_t BW = buf_words<W, LOGS, KIND, INV, PP>();

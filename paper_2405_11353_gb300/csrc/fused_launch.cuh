@@ -210,7 +210,7 @@ template <class W, int RED, bool INV, int KIND, int PP = 0, bool OTF_K = false>
 cudaError_t run_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, int logS, bool final_pass,
                      cudaStream_t st, W *out = nullptr, const W *pw_b = nullptr) {
     FArgs<W> a;
-    const uint32_t T = (1u << logS) / 16;
+    const uint32_t T = (1u << logS) >> radix_log<PP>();
     const uint32_t K = tile_k_for<W, KIND, PP>(logS);
     constexpr bool paired = paired_chunks<KIND, PP>();
     if (paired && (ntrans / p.L) % K != 0) return cudaErrorInvalidValue;   // whole polynomial groups
@@ -226,14 +226,18 @@ cudaError_t run_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, in
 // polynomials (the same chunk of K polynomials: one twiddle table per tile,
 // so a CTA needs less shared memory and more of them fit on an SM) when K
 // divides the batch, else they hold K consecutive chunks of one polynomial.
-template <class W, int RED, bool INV>
+template <class W, int RED, bool INV, int LRB = 0>
 cudaError_t run_chunk_pass(ntt_plan_s &p, int form, W *data, const void *tw, uint64_t ntrans, bool final_pass,
                            cudaStream_t st, W *out = nullptr, const W *pw_b = nullptr) {
+    // (LRB = 16: the plan's rounds are of three stages on 8 words a thread)
+    if constexpr (LRB == 0) {
+        if (p.lr == 3) return run_chunk_pass<W, RED, INV, 16>(p, form, data, tw, ntrans, final_pass, st, out, pw_b);
+    }
     const int logS = (int)p.s2;
     // pairing needs K | batch, and chunks of at least 256 words (each
     // polynomial's box of swizzled rows then starts on a 1 KiB boundary)
     const uint64_t B = logS >= 8 ? ntrans / p.L : 1;
-    if constexpr (sizeof(W) == 4 && RED == RED_SHOUP) {
+    if constexpr (sizeof(W) == 4 && RED == RED_SHOUP && LRB == 0) {
         // NTT_TW_OTF plans: kernels that make the chunk tables from seeds
         if (p.tw_otf) {
             if (form == FORM_SMALL)
@@ -245,14 +249,14 @@ cudaError_t run_chunk_pass(ntt_plan_s &p, int form, W *data, const void *tw, uin
                        : run_pass<W, RED, INV, TK_CHUNKS, 3, true>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b);
         }
     }
-    const uint64_t ks = tile_k_for<W, TK_CHUNKS, 0>(logS), kw = tile_k_for<W, TK_CHUNKS, 3>(logS);
+    const uint64_t ks = tile_k_for<W, TK_CHUNKS, LRB>(logS), kw = tile_k_for<W, TK_CHUNKS, LRB | 3>(logS);
     if (form == FORM_SMALL)
         return B % ks == 0 && B > 1
-                   ? run_pass<W, RED, INV, TK_CHUNKS, 8>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b)
-                   : run_pass<W, RED, INV, TK_CHUNKS, 0>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b);
+                   ? run_pass<W, RED, INV, TK_CHUNKS, LRB | 8>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b)
+                   : run_pass<W, RED, INV, TK_CHUNKS, LRB>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b);
     return B % kw == 0 && B > 1
-               ? run_pass<W, RED, INV, TK_CHUNKS, 11>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b)
-               : run_pass<W, RED, INV, TK_CHUNKS, 3>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b);
+               ? run_pass<W, RED, INV, TK_CHUNKS, LRB | 11>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b)
+               : run_pass<W, RED, INV, TK_CHUNKS, LRB | 3>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b);
 }
 
 // Tuning of the one-launch two-pass form: tiles per work item and the lag
@@ -328,6 +332,14 @@ cudaError_t run_stream(ntt_plan_s &p, W *data, uint64_t ntrans, cudaStream_t st,
     return cudaErrorInvalidValue;
 }
 
+// The column pass of a two-pass plan, in the plan's radix.
+template <class W, int RED, bool INV>
+cudaError_t run_cols_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, bool final_pass,
+                          cudaStream_t st) {
+    if (p.lr == 3) return run_pass<W, RED, INV, TK_COLS, 16>(p, data, tw, ntrans, (int)p.s1, final_pass, st);
+    return run_pass<W, RED, INV, TK_COLS>(p, data, tw, ntrans, (int)p.s1, final_pass, st);
+}
+
 template <class W, int RED>
 cudaError_t run_fused_t(ntt_plan_s &p, void *data_v, uint32_t batch, bool inverse, cudaStream_t st) {
     W *data = reinterpret_cast<W *>(data_v);
@@ -343,13 +355,13 @@ cudaError_t run_fused_t(ntt_plan_s &p, void *data_v, uint32_t batch, bool invers
         return run_stream<W, RED, true>(p, data, ntrans, st, nullptr, nullptr);
     }
     if (!inverse) {
-        e = run_pass<W, RED, false, TK_COLS>(p, data, p.d_main_fwd, ntrans, p.s1, false, st);
+        e = run_cols_pass<W, RED, false>(p, data, p.d_main_fwd, ntrans, false, st);
         if (e != cudaSuccess) return e;
         return run_chunk_pass<W, RED, false>(p, form, data, p.d_chunk_fwd, ntrans, true, st);
     }
     e = run_chunk_pass<W, RED, true>(p, form, data, p.d_chunk_inv, ntrans, false, st);
     if (e != cudaSuccess) return e;
-    return run_pass<W, RED, true, TK_COLS>(p, data, p.d_main_inv, ntrans, p.s1, true, st);
+    return run_cols_pass<W, RED, true>(p, data, p.d_main_inv, ntrans, true, st);
 }
 
 // c = inverse(a (.) b) for two-pass plans: the product is taken in the
@@ -368,7 +380,7 @@ cudaError_t run_fused_pwinv_t(ntt_plan_s &p, void *c, const void *a, const void 
                                                  p.d_chunk_inv, ntrans, false, st, cw,
                                                  reinterpret_cast<const W *>(b));
     if (e != cudaSuccess) return e;
-    return run_pass<W, RED, true, TK_COLS>(p, cw, p.d_main_inv, ntrans, p.s1, true, st);
+    return run_cols_pass<W, RED, true>(p, cw, p.d_main_inv, ntrans, true, st);
 }
 
 }  // namespace nttgb

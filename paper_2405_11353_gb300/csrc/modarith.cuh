@@ -211,22 +211,22 @@ template <class W> __device__ __forceinline__ Tw<W> ldtw(const Tw<W> *p) {
 // ------------------------------------------------ fused-path table layout
 // A sub-transform of 2^LOGS points uses the table entries 1 .. 2^LOGS - 1,
 // entry 2^l + i for its stage l (l = 0 first in the forward order).  The
-// fused kernels process the stages in rounds of four with a thread holding
-// 16 words; in a full round starting at bit LO the thread tau needs, for
-// stage l, 2^(l+LO+4-LOGS) consecutive entries starting at
-// 2^l + (tau >> LO) * count.  The table is stored "level-transposed" so that
-// entry j of every thread of one stage are adjacent:
+// fused kernels process the stages in rounds of LR (4, or 3) with a thread
+// holding 2^LR words; in a full round starting at bit LO the thread tau
+// needs, for stage l, 2^(l+LO+LR-LOGS) consecutive entries starting at
+// 2^l + (tau >> LO) * count.  The table is stored "level-transposed" so
+// that entry j of every thread of one stage are adjacent:
 //   position(2^l + hi * count + j) = 2^l + j * (2^l / count) + hi.
-// Stages of the short round (the top LOGS mod 4 bits) keep their order.
-inline uint32_t level_pos(uint32_t idx, uint32_t LOGS) {
+// Stages of the short round (the top LOGS mod LR bits) keep their order.
+inline uint32_t level_pos(uint32_t idx, uint32_t LOGS, uint32_t LR = 4) {
     if (idx == 0) return 0;
     uint32_t l = 0;
     while ((idx >> (l + 1)) != 0) ++l;
     const uint32_t b = LOGS - 1 - l;                 // the index bit this stage pairs
-    const uint32_t full_top = (LOGS / 4) * 4;        // bits >= full_top: short round
+    const uint32_t full_top = (LOGS / LR) * LR;      // bits >= full_top: short round
     if (b >= full_top) return idx;
-    const uint32_t LO = (b / 4) * 4, d = b - LO;
-    const uint32_t cnt = 1u << (3 - d);
+    const uint32_t LO = (b / LR) * LR, d = b - LO;
+    const uint32_t cnt = 1u << (LR - 1 - d);
     const uint32_t ntau = (1u << l) / cnt;
     const uint32_t off = idx - (1u << l);
     return (1u << l) + (off % cnt) * ntau + off / cnt;

@@ -94,8 +94,9 @@ struct ntt_plan_s {
         uint32_t b = 0;
         while (b < 31 && (2u << b) <= batch) ++b;
         const int t = tuned_form[inverse ? 1 : 0][b];
-        // (the streamed form exists for 256-word chunks, not with NTT_TW_OTF)
-        const bool stream_ok = !tw_otf && s2 == (uint32_t)nttgb::kChunkLog;
+        // (the streamed form exists for 256-word chunks in rounds of four
+        // stages, not with NTT_TW_OTF)
+        const bool stream_ok = !tw_otf && s2 == (uint32_t)nttgb::kChunkLog && lr == 4;
         if (t >= 0 && (t != nttgb::FORM_STREAMED || stream_ok)) return t;
         if (streamed && stream_ok) return nttgb::FORM_STREAMED;
         return inverse ? nttgb::FORM_WIDE : nttgb::FORM_SMALL;
@@ -111,8 +112,12 @@ struct ntt_plan_s {
 
     int fused_mode = nttgb::FUSED_STAGES;
     uint32_t s1 = 0, s2 = 0;     // two-pass split: N = 2^s1 * 2^s2
-    bool split_fixed = false;    // the split was given (autotuner candidates,
-                                 // the ragged kernel's plans): not from tuning
+    bool split_fixed = false;    // the split and radix were given (autotuner
+                                 // candidates, the ragged kernel's plans,
+                                 // streamed and on-the-fly-twiddle plans)
+    uint32_t lr = 4;             // two-pass passes: rounds of lr stages on
+                                 // 2^lr words a thread (4 or 3; tables laid
+                                 // out for it)
 
     size_t word_bytes() const { return word64 ? 8 : 4; }
     size_t limb_words() const { return (size_t)N; }
@@ -141,9 +146,11 @@ inline bool split_valid(uint32_t logN, uint32_t s2) {
 }
 
 // Plan builder (ntt_plan_create_ex with a cap on the single-pass size, and
-// a given two-pass split: split_log < 0 takes the tuned or default one).
+// a given two-pass split and radix: split_log < 0 takes the tuned or
+// default ones, radix_log is then ignored).
 ntt_status create_plan(ntt_plan_t *plan, uint32_t N, const uint64_t *q, uint32_t L, ntt_variant variant,
-                       uint32_t flags, const uint64_t *psi, int single_max_log, int split_log = -1);
+                       uint32_t flags, const uint64_t *psi, int single_max_log, int split_log = -1,
+                       int radix_log = 4);
 ntt_status validate_plan_args(uint32_t N, const uint64_t *q, uint32_t L, uint32_t flags);
 
 // fused path, instantiated in fused_<word>_<reduction>.cu

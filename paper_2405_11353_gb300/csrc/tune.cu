@@ -3,18 +3,20 @@
 // What the two-pass fused path leaves open at run time, per shape (N, word
 // size, L, reduction, order, twiddles made on the fly or read):
 //   * the split N = 2^s1 x 2^s2: how many stages each pass does (column
-//     passes of 2^s1 points, chunks of 2^s2 = 128, 256 or 512 words); the
-//     plan's twiddle tables are laid out for it, so it is fixed when a plan
-//     is made;
+//     passes of 2^s1 points, chunks of 2^s2 = 128, 256 or 512 words), and
+//     the radix of the register rounds (four stages on 16 words a thread,
+//     or three on 8); the plan's twiddle tables are laid out for both, so
+//     they are fixed when a plan is made;
 //   * per direction (forward, or inverse with or without the fused
 //     product) and batch bucket floor(log2 batch), the form: the chunk pass
 //     on one-warp CTAs, on 256-thread CTAs, or both passes in one streamed
 //     launch (stream.cuh; 256-word chunks only, not with NTT_TW_OTF).
-// ntt_autotune times every valid split with every form of both directions
-// on the current device and records, per split, the fastest form of each
-// direction for the batch's bucket, and for the shape the split whose two
-// directions together are fastest.  ntt_plan_create takes the shape's split
-// (before it builds its tables) and copies the form entries of that split;
+// ntt_autotune times every valid (radix, split) with every form of both
+// directions on the current device and records, per (radix, split), the
+// fastest form of each direction for the batch's bucket, and for the shape
+// the (radix, split) whose two directions together are fastest.
+// ntt_plan_create takes the shape's radix and split (before it builds its
+// tables) and copies the form entries of that pair;
 // each call then looks up its batch bucket.  Both tables are kept in the
 // JSON-lines file named by NTT_TUNE_DB, read at first use and rewritten
 // after every tuning, so tuning survives the process.
@@ -34,17 +36,20 @@ namespace nttgb {
 namespace {
 
 struct TuneKey {
-    uint32_t N, word, L, red, bitrev, bucket, otf, split;
+    uint32_t N, word, L, red, bitrev, bucket, otf, split, lr;
     bool operator<(const TuneKey &o) const {
-        return std::tie(N, word, L, red, bitrev, bucket, otf, split) <
-               std::tie(o.N, o.word, o.L, o.red, o.bitrev, o.bucket, o.otf, o.split);
+        return std::tie(N, word, L, red, bitrev, bucket, otf, split, lr) <
+               std::tie(o.N, o.word, o.L, o.red, o.bitrev, o.bucket, o.otf, o.split, o.lr);
     }
 };
 struct TuneVal {
     int form[2];
     float ms[2][3];
 };
-// shape (a TuneKey without bucket and split) -> chosen split
+// shape (a TuneKey without bucket, split and radix) -> chosen split, radix
+struct ShapeVal {
+    uint32_t split, lr;
+};
 struct ShapeKey {
     uint32_t N, word, L, red, bitrev, otf;
     bool operator<(const ShapeKey &o) const {
@@ -54,7 +59,7 @@ struct ShapeKey {
 
 std::mutex g_mu;
 std::map<TuneKey, TuneVal> g_table;
-std::map<ShapeKey, uint32_t> g_split;
+std::map<ShapeKey, ShapeVal> g_split;
 bool g_loaded = false;
 
 uint32_t bucket_of(uint32_t batch) {
@@ -75,21 +80,35 @@ void load_locked() {
         TuneKey k;
         TuneVal v;
         ShapeKey sk;
-        uint32_t split = 0;
+        uint32_t split = 0, lr = 0;
         if (std::sscanf(line,
                         "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
-                        "\"tw_otf\": %u, \"split_log2\": %u}",
-                        &sk.N, &sk.word, &sk.L, &sk.red, &sk.bitrev, &sk.otf, &split) == 7) {
-            if (sk.otf <= 1 && split >= (uint32_t)kChunkLogMin && split <= (uint32_t)kChunkLogMax)
-                g_split[sk] = split;
+                        "\"tw_otf\": %u, \"split_log2\": %u, \"radix_log2\": %u}",
+                        &sk.N, &sk.word, &sk.L, &sk.red, &sk.bitrev, &sk.otf, &split, &lr) == 8) {
+            if (sk.otf <= 1 && split >= (uint32_t)kChunkLogMin && split <= (uint32_t)kChunkLogMax &&
+                (lr == 3 || lr == 4))
+                g_split[sk] = ShapeVal{split, lr};
             continue;
         }
+        k.lr = 4;
         int n = std::sscanf(line,
+                            "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
+                            "\"tw_otf\": %u, \"chunk_log2\": %u, \"radix_log2\": %u, \"batch_log2\": %u, "
+                            "\"forward_form\": %d, \"inverse_form\": %d, \"forward_ms\": [%f, %f, %f], "
+                            "\"inverse_ms\": [%f, %f, %f]}",
+                            &k.N, &k.word, &k.L, &k.red, &k.bitrev, &k.otf, &k.split, &k.lr, &k.bucket, &v.form[0],
+                            &v.form[1], &v.ms[0][0], &v.ms[0][1], &v.ms[0][2], &v.ms[1][0], &v.ms[1][1], &v.ms[1][2]);
+        n -= 1;                 // the radix field: 16 values in all when it was read
+        if (n != 16) {
+            // lines written before the radix field existed: rounds of four
+            k.lr = 4;
+            n = std::sscanf(line,
                             "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
                             "\"tw_otf\": %u, \"chunk_log2\": %u, \"batch_log2\": %u, \"forward_form\": %d, "
                             "\"inverse_form\": %d, \"forward_ms\": [%f, %f, %f], \"inverse_ms\": [%f, %f, %f]}",
                             &k.N, &k.word, &k.L, &k.red, &k.bitrev, &k.otf, &k.split, &k.bucket, &v.form[0],
                             &v.form[1], &v.ms[0][0], &v.ms[0][1], &v.ms[0][2], &v.ms[1][0], &v.ms[1][1], &v.ms[1][2]);
+        }
         if (n != 16) {
             // lines written before the split field existed: 256-word chunks
             k.split = (uint32_t)kChunkLog;
@@ -111,7 +130,8 @@ void load_locked() {
                                 &v.ms[0][0], &v.ms[0][1], &v.ms[0][2], &v.ms[1][0], &v.ms[1][1], &v.ms[1][2]);
         }
         if (n != 16 || k.bucket > 31 || k.otf > 1 || v.form[0] < 0 || v.form[0] > 2 || v.form[1] < 0 ||
-            v.form[1] > 2 || k.split < (uint32_t)kChunkLogMin || k.split > (uint32_t)kChunkLogMax)
+            v.form[1] > 2 || k.split < (uint32_t)kChunkLogMin || k.split > (uint32_t)kChunkLogMax ||
+            (k.lr != 3 && k.lr != 4))
             continue;
         g_table[k] = v;
     }
@@ -127,18 +147,19 @@ void save_locked() {
         const ShapeKey &k = e.first;
         std::fprintf(f,
                      "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
-                     "\"tw_otf\": %u, \"split_log2\": %u}\n",
-                     k.N, k.word, k.L, k.red, k.bitrev, k.otf, e.second);
+                     "\"tw_otf\": %u, \"split_log2\": %u, \"radix_log2\": %u}\n",
+                     k.N, k.word, k.L, k.red, k.bitrev, k.otf, e.second.split, e.second.lr);
     }
     for (const auto &e : g_table) {
         const TuneKey &k = e.first;
         const TuneVal &v = e.second;
         std::fprintf(f,
                      "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
-                     "\"tw_otf\": %u, \"chunk_log2\": %u, \"batch_log2\": %u, \"forward_form\": %d, "
-                     "\"inverse_form\": %d, \"forward_ms\": [%.6f, %.6f, %.6f], \"inverse_ms\": [%.6f, %.6f, %.6f]}\n",
-                     k.N, k.word, k.L, k.red, k.bitrev, k.otf, k.split, k.bucket, v.form[0], v.form[1], v.ms[0][0],
-                     v.ms[0][1], v.ms[0][2], v.ms[1][0], v.ms[1][1], v.ms[1][2]);
+                     "\"tw_otf\": %u, \"chunk_log2\": %u, \"radix_log2\": %u, \"batch_log2\": %u, "
+                     "\"forward_form\": %d, \"inverse_form\": %d, \"forward_ms\": [%.6f, %.6f, %.6f], "
+                     "\"inverse_ms\": [%.6f, %.6f, %.6f]}\n",
+                     k.N, k.word, k.L, k.red, k.bitrev, k.otf, k.split, k.lr, k.bucket, v.form[0], v.form[1],
+                     v.ms[0][0], v.ms[0][1], v.ms[0][2], v.ms[1][0], v.ms[1][1], v.ms[1][2]);
     }
     std::fclose(f);
 }
@@ -149,7 +170,7 @@ ShapeKey shape_of(const ntt_plan_s &p) {
 }
 TuneKey key_of(const ntt_plan_s &p, uint32_t bucket) {
     return TuneKey{p.N, (uint32_t)p.word_bytes(), p.L, (uint32_t)p.red, p.bitrev_order ? 1u : 0u, bucket,
-                   p.tw_otf ? 1u : 0u, p.s2};
+                   p.tw_otf ? 1u : 0u, p.s2, p.lr};
 }
 
 }  // namespace
@@ -163,9 +184,10 @@ void apply_tuning(ntt_plan_s &p) {
     load_locked();
     if (!p.split_fixed) {
         auto it = g_split.find(shape_of(p));
-        if (it != g_split.end() && split_valid(p.logN, it->second)) {
-            p.s2 = it->second;
+        if (it != g_split.end() && split_valid(p.logN, it->second.split)) {
+            p.s2 = it->second.split;
             p.s1 = p.logN - p.s2;
+            p.lr = it->second.lr;
         }
     }
     if (p.streamed) return;
@@ -206,25 +228,28 @@ ntt_status ntt_autotune(uint32_t N, const uint64_t *q, uint32_t L, uint32_t flag
     bool ok = cudaMemsetAsync(d, 0, bytes, st) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
               cudaEventCreate(&e1) == cudaSuccess;
     const uint32_t bucket = nttgb::bucket_of(batch);
-    // per candidate split (chunks of 2^7, 2^8, 2^9 words): every form of
-    // each direction, timed on zero words (valid residues)
+    // per candidate (radix, split): rounds of 3 or 4 stages, chunks of 2^7,
+    // 2^8, 2^9 words; every form of each direction, timed on zero words
+    // (valid residues)
     constexpr int NSPLIT = nttgb::kChunkLogMax - nttgb::kChunkLogMin + 1;
-    nttgb::TuneVal vals[NSPLIT];
-    float total[NSPLIT];
-    nttgb::TuneKey keys[NSPLIT];
+    constexpr int NCFG = 2 * NSPLIT;             // index (lr - 3) * NSPLIT + (s2 - 7)
+    nttgb::TuneVal vals[NCFG];
+    float total[NCFG];
+    nttgb::TuneKey keys[NCFG];
     nttgb::ShapeKey shape{};
-    int best_split = -1;
+    int best = -1;
     ntt_status dev = NTT_OK;
-    for (int si = 0; si < NSPLIT && ok; ++si) {
-        const uint32_t s2 = (uint32_t)(nttgb::kChunkLogMin + si);
-        total[si] = -1.f;
-        if (!nttgb::split_valid(logN, s2) || (otf && s2 != (uint32_t)nttgb::kChunkLog)) continue;
+    for (int ci = 0; ci < NCFG && ok; ++ci) {
+        const uint32_t lr = 3 + (uint32_t)(ci / NSPLIT);
+        const uint32_t s2 = (uint32_t)(nttgb::kChunkLogMin + ci % NSPLIT);
+        total[ci] = -1.f;
+        if (!nttgb::split_valid(logN, s2) || (otf && (s2 != (uint32_t)nttgb::kChunkLog || lr != 4))) continue;
         ntt_plan_t p = nullptr;
-        if (nttgb::create_plan(&p, N, q, L, NTT_FUSED, flags, nullptr, -1, (int)s2) != NTT_OK) continue;
-        nttgb::TuneVal &v = vals[si];
+        if (nttgb::create_plan(&p, N, q, L, NTT_FUSED, flags, nullptr, -1, (int)s2, (int)lr) != NTT_OK) continue;
+        nttgb::TuneVal &v = vals[ci];
         for (int dir = 0; dir < 2 && ok; ++dir) {
             for (int form = 0; form < 3 && ok; ++form) {
-                if (form == nttgb::FORM_STREAMED && (p->tw_otf || s2 != (uint32_t)nttgb::kChunkLog)) {
+                if (form == nttgb::FORM_STREAMED && (p->tw_otf || s2 != (uint32_t)nttgb::kChunkLog || lr != 4)) {
                     v.ms[dir][form] = -1.f;
                     continue;
                 }
@@ -246,20 +271,20 @@ ntt_status ntt_autotune(uint32_t N, const uint64_t *q, uint32_t L, uint32_t flag
                      cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
                 v.ms[dir][form] = ms / (float)reps;
             }
-            int best = 0;
+            int bf = 0;
             for (int form = 1; form < 3; ++form)
-                if (v.ms[dir][form] >= 0.f && v.ms[dir][form] < v.ms[dir][best]) best = form;
-            v.form[dir] = best;
+                if (v.ms[dir][form] >= 0.f && v.ms[dir][form] < v.ms[dir][bf]) bf = form;
+            v.form[dir] = bf;
         }
         if (ok) {
             const ntt_status ds = ntt_get_device_status(p, stream);
             if (ds != NTT_OK) { dev = ds; ok = false; }
         }
         if (ok) {
-            total[si] = v.ms[0][v.form[0]] + v.ms[1][v.form[1]];
-            keys[si] = nttgb::key_of(*p, bucket);
+            total[ci] = v.ms[0][v.form[0]] + v.ms[1][v.form[1]];
+            keys[ci] = nttgb::key_of(*p, bucket);
             shape = nttgb::shape_of(*p);
-            if (best_split < 0 || total[si] < total[best_split]) best_split = si;
+            if (best < 0 || total[ci] < total[best]) best = ci;
         }
         ntt_plan_destroy(p);
     }
@@ -270,25 +295,27 @@ ntt_status ntt_autotune(uint32_t N, const uint64_t *q, uint32_t L, uint32_t flag
         cudaGetLastError();
         return dev != NTT_OK ? dev : NTT_ERR_CUDA;
     }
-    if (best_split < 0) return NTT_ERR_UNSUPPORTED;
+    if (best < 0) return NTT_ERR_UNSUPPORTED;
     {
         std::lock_guard<std::mutex> g(nttgb::g_mu);
         nttgb::load_locked();
-        for (int si = 0; si < NSPLIT; ++si)
-            if (total[si] >= 0.f) nttgb::g_table[keys[si]] = vals[si];
-        nttgb::g_split[shape] = (uint32_t)(nttgb::kChunkLogMin + best_split);
+        for (int ci = 0; ci < NCFG; ++ci)
+            if (total[ci] >= 0.f) nttgb::g_table[keys[ci]] = vals[ci];
+        nttgb::g_split[shape] = nttgb::ShapeVal{(uint32_t)(nttgb::kChunkLogMin + best % NSPLIT),
+                                                3u + (uint32_t)(best / NSPLIT)};
         nttgb::save_locked();
     }
     if (result) {
-        const nttgb::TuneVal &v = vals[best_split];
+        const nttgb::TuneVal &v = vals[best];
         for (int f = 0; f < 3; ++f) {
             result->forward_ms[f] = v.ms[0][f];
             result->inverse_ms[f] = v.ms[1][f];
         }
         result->forward_form = v.form[0];
         result->inverse_form = v.form[1];
-        result->chunk_log2 = nttgb::kChunkLogMin + best_split;
-        for (int si = 0; si < NSPLIT; ++si) result->split_ms[si] = total[si];
+        result->chunk_log2 = nttgb::kChunkLogMin + best % NSPLIT;
+        result->radix_log2 = 3 + best / NSPLIT;
+        for (int ci = 0; ci < NCFG; ++ci) result->config_ms[ci / NSPLIT][ci % NSPLIT] = total[ci];
     }
     return NTT_OK;
 }
@@ -301,14 +328,15 @@ nttgb::ShapeKey shape_from_flags(uint32_t N, uint32_t L, uint32_t flags) {
     return nttgb::ShapeKey{N, (flags & NTT_WORD64) ? 8u : 4u, L, red, (flags & NTT_ORDER_BITREV) ? 1u : 0u,
                            (flags & NTT_TW_OTF) ? 1u : 0u};
 }
-// (the caller holds g_mu) the split plans of this shape take
-uint32_t split_of_locked(const nttgb::ShapeKey &sk) {
-    if (sk.otf) return (uint32_t)nttgb::kChunkLog;
+// (the caller holds g_mu) the split and radix plans of this shape take
+nttgb::ShapeVal config_of_locked(const nttgb::ShapeKey &sk) {
+    const nttgb::ShapeVal def{(uint32_t)nttgb::kChunkLog, 4u};
+    if (sk.otf) return def;
     auto it = nttgb::g_split.find(sk);
-    return it == nttgb::g_split.end() ? (uint32_t)nttgb::kChunkLog : it->second;
+    return it == nttgb::g_split.end() ? def : it->second;
 }
-nttgb::TuneKey key_from_shape(const nttgb::ShapeKey &sk, uint32_t batch, uint32_t split) {
-    return nttgb::TuneKey{sk.N, sk.word, sk.L, sk.red, sk.bitrev, nttgb::bucket_of(batch), sk.otf, split};
+nttgb::TuneKey key_from_shape(const nttgb::ShapeKey &sk, uint32_t batch, nttgb::ShapeVal c) {
+    return nttgb::TuneKey{sk.N, sk.word, sk.L, sk.red, sk.bitrev, nttgb::bucket_of(batch), sk.otf, c.split, c.lr};
 }
 }  // namespace
 
@@ -324,7 +352,7 @@ ntt_status ntt_tune_set(uint32_t N, uint32_t L, uint32_t flags, uint32_t batch, 
     std::lock_guard<std::mutex> g(nttgb::g_mu);
     nttgb::load_locked();
     const nttgb::ShapeKey sk = shape_from_flags(N, L, flags);
-    nttgb::g_table[key_from_shape(sk, batch, split_of_locked(sk))] = v;
+    nttgb::g_table[key_from_shape(sk, batch, config_of_locked(sk))] = v;
     nttgb::save_locked();
     return NTT_OK;
 }
@@ -334,28 +362,33 @@ int32_t ntt_tune_get(uint32_t N, uint32_t L, uint32_t flags, uint32_t batch, int
     std::lock_guard<std::mutex> g(nttgb::g_mu);
     nttgb::load_locked();
     const nttgb::ShapeKey sk = shape_from_flags(N, L, flags);
-    auto it = nttgb::g_table.find(key_from_shape(sk, batch, split_of_locked(sk)));
+    auto it = nttgb::g_table.find(key_from_shape(sk, batch, config_of_locked(sk)));
     return it == nttgb::g_table.end() ? -1 : it->second.form[inverse ? 1 : 0];
 }
 
-ntt_status ntt_tune_set_split(uint32_t N, uint32_t L, uint32_t flags, uint32_t chunk_log2) {
+ntt_status ntt_tune_set_split(uint32_t N, uint32_t L, uint32_t flags, uint32_t chunk_log2, uint32_t radix_log2) {
     uint32_t n = 0;
     while (n < 31 && (1u << n) < N) ++n;
-    if (L == 0 || (1u << n) != N || !nttgb::split_valid(n, chunk_log2) ||
-        ((flags & NTT_TW_OTF) && chunk_log2 != (uint32_t)nttgb::kChunkLog))
+    if (L == 0 || (1u << n) != N || !nttgb::split_valid(n, chunk_log2) || (radix_log2 != 3 && radix_log2 != 4) ||
+        ((flags & NTT_TW_OTF) && (chunk_log2 != (uint32_t)nttgb::kChunkLog || radix_log2 != 4)))
         return NTT_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> g(nttgb::g_mu);
     nttgb::load_locked();
-    nttgb::g_split[shape_from_flags(N, L, flags)] = chunk_log2;
+    nttgb::g_split[shape_from_flags(N, L, flags)] = nttgb::ShapeVal{chunk_log2, radix_log2};
     nttgb::save_locked();
     return NTT_OK;
 }
 
-int32_t ntt_tune_get_split(uint32_t N, uint32_t L, uint32_t flags) {
+int32_t ntt_tune_get_split(uint32_t N, uint32_t L, uint32_t flags, int32_t *radix_log2) {
     std::lock_guard<std::mutex> g(nttgb::g_mu);
     nttgb::load_locked();
     auto it = nttgb::g_split.find(shape_from_flags(N, L, flags));
-    return it == nttgb::g_split.end() ? -1 : (int32_t)it->second;
+    if (it == nttgb::g_split.end()) {
+        if (radix_log2) *radix_log2 = -1;
+        return -1;
+    }
+    if (radix_log2) *radix_log2 = (int32_t)it->second.lr;
+    return (int32_t)it->second.split;
 }
 
 void ntt_tune_clear(void) {
@@ -368,6 +401,11 @@ void ntt_tune_clear(void) {
 int32_t ntt_plan_chunk_log2(ntt_plan_t plan) {
     if (!plan || plan->variant != NTT_FUSED || plan->fused_mode != nttgb::FUSED_TWO_PASS) return -1;
     return (int32_t)plan->s2;
+}
+
+int32_t ntt_plan_radix_log2(ntt_plan_t plan) {
+    if (!plan || plan->variant != NTT_FUSED || plan->fused_mode != nttgb::FUSED_TWO_PASS) return -1;
+    return (int32_t)plan->lr;
 }
 
 int32_t ntt_plan_form(ntt_plan_t plan, uint32_t batch, int inverse) {

@@ -78,20 +78,24 @@ def test_autotune_records_forms_the_next_plan_uses(nt, orc):
     try:
         r = nt.ntt_autotune(N, qs, flags, batch)
         assert r["forward_form"] in (0, 1, 2) and r["inverse_form"] in (0, 1, 2)
-        # splits 2^7 x 2^9, 2^8 x 2^8, 2^9 x 2^7 are all valid at N = 2^16;
-        # the chosen one has the smallest forward + inverse time
-        assert r["chunk_log2"] in (7, 8, 9) and all(ms > 0 for ms in r["split_ms"])
-        assert r["split_ms"][r["chunk_log2"] - 7] == min(r["split_ms"])
-        # (the streamed form exists only with 256-word chunks)
-        streamed_ok = r["chunk_log2"] == 8
+        # splits 2^7 x 2^9, 2^8 x 2^8, 2^9 x 2^7 and both radices are all
+        # valid at N = 2^16; the chosen pair has the smallest forward +
+        # inverse time
+        assert r["chunk_log2"] in (7, 8, 9) and r["radix_log2"] in (3, 4)
+        assert sorted(r["config_ms"]) == ["%d,%d" % (lr, s2) for lr in (3, 4) for s2 in (7, 8, 9)]
+        assert all(ms > 0 for ms in r["config_ms"].values())
+        assert r["config_ms"]["%d,%d" % (r["radix_log2"], r["chunk_log2"])] == min(r["config_ms"].values())
+        # (the streamed form exists only with 256-word chunks and radix 16)
+        streamed_ok = r["chunk_log2"] == 8 and r["radix_log2"] == 4
         for ms in (r["forward_ms"], r["inverse_ms"]):
             assert all(v > 0 for v in ms[:2]) and (ms[2] > 0) == streamed_ok
         assert r["forward_ms"][r["forward_form"]] == min(v for v in r["forward_ms"] if v > 0)
-        assert nt.ntt_tune_get_split(N, L, flags) == r["chunk_log2"]
+        assert nt.ntt_tune_get_split(N, L, flags) == (r["chunk_log2"], r["radix_log2"])
         assert nt.ntt_tune_get(N, L, flags, batch) == r["forward_form"]
         p = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, flags)
         try:
             assert nt.ntt_plan_chunk_log2(p) == r["chunk_log2"]
+            assert nt.ntt_plan_radix_log2(p) == r["radix_log2"]
             assert nt.ntt_plan_form(p, batch) == r["forward_form"]
             assert nt.ntt_plan_form(p, batch, True) == r["inverse_form"]
             assert nt.ntt_plan_form(p, 4 * batch) == nt.NTT_FORM_SMALL        # untuned bucket: default
@@ -116,11 +120,14 @@ SPLITS = [(15, False, (7, 8, 9)), (16, False, (7, 8, 9)), (17, False, (8, 9)), (
           (16, True, (7, 8, 9))]
 
 
+@pytest.mark.parametrize("radix", [4, 3])
 @pytest.mark.parametrize("n,w64,splits", SPLITS)
-def test_every_split_bit_exact(nt, orc, n, w64, splits):
-    """Every split N = 2^s1 x 2^s2 a size takes, with both chunk-pass forms,
-    batches whose tiles pair polynomials and batches that do not: forward,
-    the product fused into the inverse, and the inverse, bit-exact."""
+def test_every_split_bit_exact(nt, orc, n, w64, splits, radix):
+    """Every split N = 2^s1 x 2^s2 a size takes, in both radices (rounds of
+    four stages on 16 words a thread, or three on 8), with both chunk-pass
+    forms, batches whose tiles pair polynomials and batches that do not:
+    forward, the product fused into the inverse, and the inverse,
+    bit-exact."""
     N, L = 1 << n, 3
     qs = orc.find_primes(60 if w64 else 30, 18, L)
     psis = [orc.psi(q, N) for q in qs]
@@ -130,16 +137,16 @@ def test_every_split_bit_exact(nt, orc, n, w64, splits):
             for batch, form in ((4, nt.NTT_FORM_SMALL), (3, nt.NTT_FORM_WIDE), (16, nt.NTT_FORM_WIDE),
                                 (2, nt.NTT_FORM_SMALL)):
                 nt.ntt_tune_clear()
-                nt.ntt_tune_set_split(N, L, flags, s2)
+                nt.ntt_tune_set_split(N, L, flags, s2, radix)
                 nt.ntt_tune_set(N, L, flags, batch, form, form)
                 pairs = batch // 2
                 if pairs:
                     nt.ntt_tune_set(N, L, flags, pairs, form, form)
-                host = ntt_synth.rns_batch(2400 + 10 * s2 + batch, qs, N, batch)
+                host = ntt_synth.rns_batch(2400 + 10 * s2 + batch + 100 * radix, qs, N, batch)
                 A = orc.ntt_batch(host, qs, psis)
                 p = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, flags)
                 try:
-                    assert nt.ntt_plan_chunk_log2(p) == s2
+                    assert (nt.ntt_plan_chunk_log2(p), nt.ntt_plan_radix_log2(p)) == (s2, radix)
                     assert nt.ntt_plan_form(p, batch) == form
                     d = to_dev(host, w64)
                     nt.ntt_forward(p, d, batch)
@@ -161,30 +168,36 @@ def test_every_split_bit_exact(nt, orc, n, w64, splits):
 
 
 def test_split_limits(nt, orc):
-    """Splits a size cannot take are refused; streamed and on-the-fly
-    twiddle plans keep 256-word chunks whatever the table says."""
+    """Splits and radices a size cannot take are refused; streamed and
+    on-the-fly twiddle plans keep 256-word chunks and radix 16 whatever the
+    table says, and a radix-8 or non-256 split plan has no streamed form."""
     qs = orc.find_primes(30, 18, 2)
+    f = nt.NTT_ORDER_BITREV
     with pytest.raises(nt.NttError):
-        nt.ntt_tune_set_split(1 << 17, 2, nt.NTT_ORDER_BITREV, 7)        # 2^10-point columns
+        nt.ntt_tune_set_split(1 << 17, 2, f, 7)                      # 2^10-point columns
     with pytest.raises(nt.NttError):
-        nt.ntt_tune_set_split(1 << 15, 2, nt.NTT_ORDER_BITREV | nt.NTT_TW_OTF, 9)
+        nt.ntt_tune_set_split(1 << 15, 2, f | nt.NTT_TW_OTF, 9)
+    with pytest.raises(nt.NttError):
+        nt.ntt_tune_set_split(1 << 16, 2, f, 8, 5)
     try:
-        nt.ntt_tune_set_split(1 << 16, 2, nt.NTT_ORDER_BITREV | nt.NTT_STREAMED, 9)
-        p = nt.ntt_plan_create(1 << 16, qs, nt.NTT_FUSED, nt.NTT_ORDER_BITREV | nt.NTT_STREAMED)
+        nt.ntt_tune_set_split(1 << 16, 2, f | nt.NTT_STREAMED, 9, 3)
+        p = nt.ntt_plan_create(1 << 16, qs, nt.NTT_FUSED, f | nt.NTT_STREAMED)
         try:
-            assert nt.ntt_plan_chunk_log2(p) == 8
+            assert (nt.ntt_plan_chunk_log2(p), nt.ntt_plan_radix_log2(p)) == (8, 4)
             assert nt.ntt_plan_form(p, 4) == nt.NTT_FORM_STREAMED
         finally:
             nt.ntt_plan_destroy(p)
-        nt.ntt_tune_set_split(1 << 16, 2, nt.NTT_ORDER_BITREV, 9)
-        nt.ntt_tune_set(1 << 16, 2, nt.NTT_ORDER_BITREV, 4, nt.NTT_FORM_STREAMED, nt.NTT_FORM_STREAMED)
-        p = nt.ntt_plan_create(1 << 16, qs, nt.NTT_FUSED, nt.NTT_ORDER_BITREV)
-        try:
-            assert nt.ntt_plan_chunk_log2(p) == 9
-            # no streamed form with 512-word chunks: the defaults serve
-            assert nt.ntt_plan_form(p, 4) == nt.NTT_FORM_SMALL
-            assert nt.ntt_plan_form(p, 4, True) == nt.NTT_FORM_WIDE
-        finally:
-            nt.ntt_plan_destroy(p)
+        for s2, radix in ((9, 4), (8, 3)):
+            nt.ntt_tune_clear()
+            nt.ntt_tune_set_split(1 << 16, 2, f, s2, radix)
+            nt.ntt_tune_set(1 << 16, 2, f, 4, nt.NTT_FORM_STREAMED, nt.NTT_FORM_STREAMED)
+            p = nt.ntt_plan_create(1 << 16, qs, nt.NTT_FUSED, f)
+            try:
+                assert (nt.ntt_plan_chunk_log2(p), nt.ntt_plan_radix_log2(p)) == (s2, radix)
+                # no streamed form there: the defaults serve
+                assert nt.ntt_plan_form(p, 4) == nt.NTT_FORM_SMALL
+                assert nt.ntt_plan_form(p, 4, True) == nt.NTT_FORM_WIDE
+            finally:
+                nt.ntt_plan_destroy(p)
     finally:
         nt.ntt_tune_clear()

@@ -76,38 +76,46 @@ def test_tune_table_keys_twiddle_mode_and_reads_older_lines(nt, tmp_path):
 
 
 def test_split_table_set_get_persist(nt, tmp_path):
-    """A shape's split (chunks of 2^s2 words) is recorded by hand, refused
-    where the size cannot take it, written as its own line, keys the form
-    entries, and is read by a fresh process; older lines without a split
-    field are forms of the default 256-word split."""
+    """A shape's split (chunks of 2^s2 words) and radix are recorded by hand,
+    refused where the size cannot take them, written as their own line, key
+    the form entries, and are read by a fresh process; older lines without a
+    split or radix field are forms of the default 256-word split, radix 16."""
     db = str(tmp_path / "tune.jsonl")
     with open(db, "w") as f:
         f.write('{"N": 65536, "word_bytes": 4, "L": 3, "reduction": 0, "bitrev": 1, "tw_otf": 0, '
                 '"batch_log2": 2, "forward_form": 1, "inverse_form": 0, "forward_ms": [-1.0, -1.0, -1.0], '
                 '"inverse_ms": [-1.0, -1.0, -1.0]}\n')
+        f.write('{"N": 65536, "word_bytes": 4, "L": 5, "reduction": 0, "bitrev": 1, "tw_otf": 0, '
+                '"chunk_log2": 7, "batch_log2": 2, "forward_form": 2, "inverse_form": 2, '
+                '"forward_ms": [-1.0, -1.0, -1.0], "inverse_ms": [-1.0, -1.0, -1.0]}\n')
     out = _run("import paper_2405_11353_gb300 as nt\n"
                "f = nt.NTT_ORDER_BITREV\n"
-               "print(nt.ntt_tune_get_split(1 << 16, 3, f), nt.ntt_tune_get(1 << 16, 3, f, 4))\n"
-               "nt.ntt_tune_set_split(1 << 16, 3, f, 9)\n"
-               "print(nt.ntt_tune_get_split(1 << 16, 3, f), nt.ntt_tune_get(1 << 16, 3, f, 4))\n"
+               "print(*nt.ntt_tune_get_split(1 << 16, 3, f), nt.ntt_tune_get(1 << 16, 3, f, 4))\n"
+               "nt.ntt_tune_set_split(1 << 16, 3, f, 9, 3)\n"
+               "print(*nt.ntt_tune_get_split(1 << 16, 3, f), nt.ntt_tune_get(1 << 16, 3, f, 4))\n"
                "nt.ntt_tune_set(1 << 16, 3, f, 4, nt.NTT_FORM_SMALL, nt.NTT_FORM_SMALL)\n"
                "print(nt.ntt_tune_get(1 << 16, 3, f, 4, True))\n"
+               "nt.ntt_tune_set_split(1 << 16, 5, f, 7, 4)\n"
+               "print(nt.ntt_tune_get(1 << 16, 5, f, 4))\n"
                "bad = 0\n"
-               "for args in ((1 << 17, 3, f, 7), (1 << 15, 3, f, 10), (1 << 16, 3, f | nt.NTT_TW_OTF, 7),\n"
-               "             (1000, 3, f, 8), (1 << 16, 0, f, 8)):\n"
+               "for args in ((1 << 17, 3, f, 7, 4), (1 << 15, 3, f, 10, 4), (1 << 16, 3, f | nt.NTT_TW_OTF, 7, 4),\n"
+               "             (1 << 16, 3, f | nt.NTT_TW_OTF, 8, 3), (1 << 16, 3, f, 8, 5), (1000, 3, f, 8, 4),\n"
+               "             (1 << 16, 0, f, 8, 4)):\n"
                "    try:\n"
                "        nt.ntt_tune_set_split(*args)\n"
                "    except nt.NttError:\n"
                "        bad += 1\n"
                "print(bad)\n", db)
-    assert out.split() == ["-1", "1", "9", "-1", "0", "5"]
+    assert out.split() == ["-1", "-1", "1", "9", "3", "-1", "0", "2", "7"]
     rows = [json.loads(x) for x in open(db)]
-    assert [r["split_log2"] for r in rows if "split_log2" in r] == [9]
-    forms = sorted((r["chunk_log2"], r["forward_form"]) for r in rows if "chunk_log2" in r)
-    assert forms == [(8, 1), (9, 0)]
+    assert sorted((r["L"], r["split_log2"], r["radix_log2"]) for r in rows if "split_log2" in r) == [
+        (3, 9, 3), (5, 7, 4)]
+    forms = sorted((r["L"], r["chunk_log2"], r["radix_log2"], r["forward_form"]) for r in rows
+                   if "chunk_log2" in r)
+    assert forms == [(3, 8, 4, 1), (3, 9, 3, 0), (5, 7, 4, 2)]
     out = _run("import paper_2405_11353_gb300 as nt\n"
                "f = nt.NTT_ORDER_BITREV\n"
-               "print(nt.ntt_tune_get_split(1 << 16, 3, f), nt.ntt_tune_get(1 << 16, 3, f, 4))\n"
+               "print(*nt.ntt_tune_get_split(1 << 16, 3, f), nt.ntt_tune_get(1 << 16, 3, f, 4))\n"
                "nt.ntt_tune_clear()\n"
-               "print(nt.ntt_tune_get_split(1 << 16, 3, f))\n", db)
-    assert out.split() == ["9", "0", "-1"]
+               "print(*nt.ntt_tune_get_split(1 << 16, 3, f))\n", db)
+    assert out.split() == ["9", "3", "0", "-1", "-1"]
