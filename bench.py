@@ -74,17 +74,24 @@ _MAD_RATES = {}
 
 def traffic_from_profiles(digest):
     """Per-launch DRAM bytes of the forward transform from the committed ncu
-    summary, if it was taken on the current kernel sources."""
-    p = os.path.join(ROOT, "profiles", "fused_forward_n65536_L32_u32.md")
+    figures (profiles/fused_forward_n65536_L32_u32.traffic.txt: `key: value`
+    lines), if they were taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "fused_forward_n65536_L32_u32.traffic.txt")
+    vals = {}
     try:
-        txt = open(p).read()
+        for line in open(p):
+            line = line.split("#", 1)[0].strip()
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
     except OSError:
         return None
-    m1 = re.search(r"forward_dram_bytes_per_call:\s*([0-9]+)", txt)
-    m2 = re.search(r"source_digest:\s*([0-9a-f]+)", txt)
-    if not m1 or not m2 or m2.group(1) != digest:
+    if vals.get("source_digest") != digest:
         return None
-    return int(m1.group(1))
+    try:
+        return int(vals["forward_dram_bytes_per_call"])
+    except (KeyError, ValueError):
+        return None
 
 
 class ClockSampler:
@@ -256,14 +263,13 @@ def side_summary(extras):
     if "rns_n2p14" in extras:
         out["rns_n2p14"] = {"ms": g("rns_n2p14", "ms_per_step"), "ntt_s": g("rns_n2p14", "value")}
     if "variants_n1024" in extras:
-        out["variants_n1024_ms"] = {k: _sig(v.get("ms_per_step")) for k, v in extras["variants_n1024"].items()
-                                    if isinstance(v, dict)}
+        ms = [(k, v.get("ms_per_step")) for k, v in extras["variants_n1024"].items() if isinstance(v, dict)]
+        ms = [(k, m) for k, m in ms if m]
+        if ms:
+            out["variants_n1024_ms_min_max"] = [_sig(min(m for _, m in ms)), _sig(max(m for _, m in ms))]
     if "cluster_form" in extras:
         out["forward_ms_by_form"] = {k: _sig(v.get("forward_ms")) for k, v in extras["cluster_form"].items()
                                      if isinstance(v, dict)}
-    if "tw_otf" in extras:
-        out["tw_otf_fwd_ms"] = {k: _sig(v.get("forward_ms")) for k, v in extras["tw_otf"].items()
-                                if isinstance(v, dict)}
     errors = [k for k, v in extras.items() if isinstance(v, dict) and "error" in v]
     if errors:
         out["errors"] = errors
@@ -739,11 +745,10 @@ def main():
     torch.cuda.synchronize()
 
     # ---------------- timed region: K steps back to back (the metric), then
-    # the same K steps with an event around each call (per-call times for
-    # the roofline; an event between two launches ends their programmatic
-    # overlap, so these steps run a little slower than the first K)
+    # K calls of each of the step's two calls back to back (their per-call
+    # times, for the roofline).  Events sit only at the ends of each run:
+    # an event between two launches would end their programmatic overlap.
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     sampler = ClockSampler(dev.index) if rank == 0 else None
     if sampler:
         sampler.start()
@@ -751,31 +756,25 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
     for i in range(K):
         step(bufs[i % ROTATE])
-    t_end.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    ev[1].record(stream)
+    for i in range(K):
+        nt.ntt_forward(plan, bufs[i % ROTATE], POLYS, sh)
+    ev[2].record(stream)
     for i in range(K):
         b = bufs[i % ROTATE]
-        e = ev[i]
-        e[0].record(stream)
-        nt.ntt_forward(plan, b, POLYS, sh)
-        e[1].record(stream)
         nt.ntt_pointwise_inverse(plan, b, b, b[half:], PAIRS, sh)
-        e[2].record(stream)
+    ev[3].record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
-    elapsed_ms = t_start.elapsed_time(t_end)
-    fwd_ms = statistics.mean(ev[i][0].elapsed_time(ev[i][1]) for i in range(K))
-    pwinv_ms = statistics.mean(ev[i][1].elapsed_time(ev[i][2]) for i in range(K))
-    evented_step_ms = statistics.mean(ev[i][0].elapsed_time(ev[i][2]) for i in range(K))
+    elapsed_ms = ev[0].elapsed_time(ev[1])
+    fwd_ms = ev[1].elapsed_time(ev[2]) / K
+    pwinv_ms = ev[2].elapsed_time(ev[3]) / K
     elapsed_ms = max_over_ranks(elapsed_ms, dist if world > 1 else None, dev)
     ms_per_step = elapsed_ms / K
     value = job_rate(NTT_PER_STEP, world, K, elapsed_ms)
@@ -808,7 +807,7 @@ def main():
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": achieved / peak, "traffic": traffic_from_profiles(digest),
-        "kernel": "ntt_forward: %d-point column pass + %d-word chunk pass (%s form, radix %d), %d transforms" % (
+        "kernel": "ntt_forward: %d-pt cols + %d-word chunks, %s, radix %d, %d NTTs" % (
             N >> split, 1 << split, forms["forward"], 1 << radix, n_fwd),
         "algorithmic_bytes_per_call": fwd_bytes, "avg_ms": fwd_ms,
         "peak_source": "measured hbm_gbs" if peak_kind == "measured" else "fallback 6.8 TB/s",
@@ -856,8 +855,7 @@ def main():
                        "l2": "4 rotating input copies (512 MiB) > 129 MB L2",
                        "parallelism": ("limb-sharded x%d: %d limbs per rank of %d" % (world, count, L * world))
                        if world > 1 else "1 GPU"},
-            "per_call_ms": {"forward_16polys": fwd_ms, "pointwise_inverse_8pairs": pwinv_ms,
-                            "step_with_events": evented_step_ms},
+            "per_call_ms": {"forward_16polys": fwd_ms, "pointwise_inverse_8pairs": pwinv_ms},
             "roofline": roofline,
             "int_roofline": int_roofline,
             "cpu_baseline": cpu,

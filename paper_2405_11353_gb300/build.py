@@ -41,7 +41,7 @@ def _digest(extra=""):
 
 
 # Sources of the fused forward transform with 4-byte words and Shoup
-# twiddles (the streamed two-pass launch the benchmark times).
+# twiddles (the two launches of the two-pass split the benchmark times).
 FORWARD_U32_SOURCES = ("fused.cuh", "stream.cuh", "fused_launch.cuh", "modarith.cuh", "fused_u32_shoup.cu")
 
 

@@ -97,7 +97,8 @@ template <class W> __host__ __device__ constexpr uint32_t cols_phys(uint32_t k, 
 // otherwise).  Bit 3 of P (P = 8, 11) pairs polynomials in chunk tiles
 // (paired_chunks).  Bit 4 of P (per-plan column and chunk passes): rounds
 // of three stages on 8 words a thread instead of four stages on 16
-// (radix_log).
+// (radix_log).  Bit 5 (column passes): rows of the plan's 2^s2 words
+// instead of 256.
 template <int P> __host__ __device__ constexpr int radix_log() { return (P & 16) ? 3 : 4; }
 template <class W, int LOGS, int KIND, int P = 0> __host__ __device__ constexpr uint32_t tile_k() {
     // threads per sub-transform: 2^(LOGS - LR).  Chunks: one warp per CTA
@@ -477,9 +478,10 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     const uint32_t smb_k = sm_off<W, LOGS, KIND, P>(k, 0);
     const uint32_t L = a.L;
     const uint32_t B = (uint32_t)(a.ntrans / L);
-    // log2 of the row length N2 (two-pass kinds): the chunk size, or the
-    // plan's split for the column pass
-    const uint32_t S2 = KIND == TK_CHUNKS ? (uint32_t)LOGS : a.s2;
+    // log2 of the row length N2 (two-pass kinds): the chunk size, or, for
+    // the column pass, 256 (a compile-time constant, so the strided stores
+    // take immediate offsets) unless bit 5 of P asks for the plan's split
+    const uint32_t S2 = KIND == TK_CHUNKS ? (uint32_t)LOGS : ((P & 32) ? a.s2 : kN2Log);
     const uint32_t N1 = KIND == TK_SINGLE ? 1u : (N >> S2);
     // paired chunk tiles: sub k is polynomial p + k (the launcher makes
     // sure K divides the batch); else sub k is position pos0 + k

@@ -336,6 +336,11 @@ cudaError_t run_stream(ntt_plan_s &p, W *data, uint64_t ntrans, cudaStream_t st,
 template <class W, int RED, bool INV>
 cudaError_t run_cols_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, bool final_pass,
                           cudaStream_t st) {
+    // (bit 5: rows of 2^s2 words other than 256, read from the arguments)
+    if (p.s2 != kN2Log) {
+        if (p.lr == 3) return run_pass<W, RED, INV, TK_COLS, 48>(p, data, tw, ntrans, (int)p.s1, final_pass, st);
+        return run_pass<W, RED, INV, TK_COLS, 32>(p, data, tw, ntrans, (int)p.s1, final_pass, st);
+    }
     if (p.lr == 3) return run_pass<W, RED, INV, TK_COLS, 16>(p, data, tw, ntrans, (int)p.s1, final_pass, st);
     return run_pass<W, RED, INV, TK_COLS>(p, data, tw, ntrans, (int)p.s1, final_pass, st);
 }
