@@ -18,7 +18,11 @@
 //     accumulators are zeroed once and again by each epilogue after reading.  A diagonal sums at most 4 x 256
 //     products of magnitude <= 128 * 128 = 2^14, so every partial sum is an
 //     integer of magnitude <= 2^24: exactly representable, so fp32
-//     accumulation loses nothing, in any order.
+//     accumulation loses nothing, in any order -- ASSUMING the tensor core
+//     adds with a full 24-bit fp32 significand.  The instruction set does not
+//     state the internal precision of the accumulation; the tests that drive
+//     every diagonal to its extreme (all digits -128, or +127) are what
+//     guard this.
 //   * The epilogue reads the diagonals back (tcgen05.ld), recombines
 //     sum_s D_s (2^(8 s) mod q) in 64-bit integers (|.| < 7 2^24 q < 2^57),
 //     adds a multiple of q above 2^57 to make it positive and reduces mod q
@@ -26,7 +30,7 @@
 //     the inter-step twiddle (Shoup) where the pass has one.
 //
 // GEMM view, D[m][n] = sum_k A[m][k] B[n][k], both operands K-major in shared
-// memory (128-byte swizzle, tile M = 128, N = 64, K chunks of 64); A is 128
+// memory (64-byte swizzle, tile M = 128, N = 64, K chunks of 32); A is 128
 // data rows (converted to digits by the CTA), B 64 matrix rows (TMA):
 //   column pass  A[n2][n1] = src[n1][n2], B = matrix [u][n1],
 //                D[n2][u] -> out[u][n2];
@@ -35,16 +39,20 @@
 // Each pass reads src and writes dst (out of place: a tile's output rows are
 // other tiles' input rows).
 //
-// Roles in a CTA (one per SM: 224 KiB of shared memory, 448 of the 512
-// tensor-memory columns): warps 0-7 convert data digits into the stage
-// buffers and run the epilogue (warp w reads tensor-memory lanes
-// 32 (w % 4) ..); warp 8 lane 0 issues the TMA copies of the matrix digits;
-// warp 9 lane 0 issues the MMAs.  Two data stage buffers (64 KiB) and three
-// matrix stage buffers (32 KiB; the copies run further ahead), mbarriers
-// between the roles, every wait bounded (about a second of SM clock) -- on expiry the
-// call records NTT_ERR_TIMEOUT, all roles leave their loops, and the CTA
-// waits (bounded) for its copies and products in flight before it frees its
-// tensor memory.
+// Roles in a CTA (one per SM: 208 KiB of stage buffers, 448 of the 512
+// tensor-memory columns): warp 16 lane 0 issues the TMA copies of both
+// operands' sources, a chunk ahead -- the data words (four 16 KiB stages)
+// and the matrix digit planes (three 16 KiB stages); warps 0-7 turn the
+// staged data words into digit planes (three 32 KiB stages); warp 17 lane 0
+// issues the MMAs; warps 8-15 run the epilogue (warp w reads tensor-memory
+// lanes 32 (w % 4) ..).  The accumulators are one set: the next tile's MMAs
+// start when the epilogue has read and zeroed them (two sets of half-width
+// tiles were measured slower: each 32-column tile converts the whole data
+// block again, and the extra digit traffic through shared memory costs more
+// than the overlap gains).  mbarriers between the roles, every wait bounded
+// (about a second of SM clock) -- on expiry the call records
+// NTT_ERR_TIMEOUT, all roles leave their loops, and the CTA waits (bounded)
+// for its copies and products in flight before it frees its tensor memory.
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -56,28 +64,35 @@
 
 namespace nttgb {
 
-constexpr uint32_t kT5M = 128, kT5N = 64, kT5KC = 64;
+constexpr uint32_t kT5M = 128, kT5N = 64, kT5KC = 32;   // K chunks of 32: 64-byte operand rows
 constexpr uint32_t kT5Dig = 4, kT5Diag = 7;
-constexpr uint32_t kT5StageA = kT5Dig * kT5M * 128;   // 64 KiB
-constexpr uint32_t kT5StageB = kT5Dig * kT5N * 128;   // 32 KiB
-constexpr uint32_t kT5NA = 2, kT5NB = 3;              // data / matrix stage buffers
-constexpr uint32_t kT5ConvWarps = 8;
-constexpr uint32_t kT5Threads = (kT5ConvWarps + 2) * 32;
+constexpr uint32_t kT5Row = kT5KC * 2;                 // bytes of one operand row (fp16)
+constexpr uint32_t kT5StageA = kT5Dig * kT5M * kT5Row;   // 32 KiB
+constexpr uint32_t kT5StageB = kT5Dig * kT5N * kT5Row;   // 16 KiB
+constexpr uint32_t kT5StageR = kT5M * kT5KC * 4;          // 16 KiB of data words
+constexpr uint32_t kT5NA = 3, kT5NB = 3, kT5NR = 4;       // digit / matrix / data-word stage buffers
+constexpr uint32_t kT5Chunks = 256 / kT5KC;               // K chunks per tile
+constexpr uint32_t kT5ConvWarps = 8;                 // warps 0-7: data digits
+constexpr uint32_t kT5EpiWarps = 8;                  // warps 8-15: epilogue
+constexpr uint32_t kT5TmaWarp = kT5ConvWarps + kT5EpiWarps, kT5MmaWarp = kT5TmaWarp + 1;
+constexpr uint32_t kT5Threads = (kT5MmaWarp + 1) * 32;
 constexpr uint32_t kT5TmemCols = 512;
-constexpr size_t kT5SmemData = (size_t)kT5NA * kT5StageA + (size_t)kT5NB * kT5StageB;   // 224 KiB
+constexpr size_t kT5SmemData =
+    (size_t)kT5NA * kT5StageA + (size_t)kT5NB * kT5StageB + (size_t)kT5NR * kT5StageR;   // 208 KiB
 constexpr size_t kT5Smem = kT5SmemData + 1024 + 256;
 
 struct Tc5Args {
     const uint32_t *src;
     uint32_t *dst;
-    CUtensorMap cmap;               // matrix digit planes, fp16 (k: 256, rows), box 64 x 64, 128-byte swizzle
+    CUtensorMap cmap;               // matrix digit planes, fp16 (k: 256, rows), box 32 x 64, 64-byte swizzle
+    CUtensorMap dmap;               // src words (256 a row), box 128 x 32 (column pass) or 32 x 128 (row pass)
     uint32_t mat_row0;              // cmap row of (this pass's matrix, limb 0, digit 0, row 0)
     const Tw<uint32_t> *tw;         // [L][256][256] epilogue twiddles, or null
     const LimbConst *lc;
     const uint32_t *wdiag;          // [L][8]: 2^(8 s) mod q for s < 7
     uint32_t *status;
     uint32_t L;
-    uint32_t ntiles;                // 8 per transform
+    uint32_t ntiles;                // 8 per transform (2 row blocks x 4 column tiles)
     uint32_t stall_tx;              // test hook: extra bytes CTA 0's first matrix copy waits for
 };
 
@@ -102,30 +117,22 @@ __device__ __forceinline__ void t5_commit(uint64_t *bar) {
                      smem_addr(bar))
                  : "memory");
 }
-__device__ __forceinline__ void t5_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
 __device__ __forceinline__ void t5_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
-// 1 KiB one after another (stride 1024 bytes), start at `saddr`.
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle (rows of 32
+// fp16), 8-row atoms of 512 bytes one after another (stride 512 bytes),
+// start at `saddr`.
 __device__ __forceinline__ uint64_t t5_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);          // start address
     d |= (uint64_t)1u << 16;                          // leading byte offset (unused when swizzled)
-    d |= (uint64_t)(1024u >> 4) << 32;                // stride byte offset
+    d |= (uint64_t)(512u >> 4) << 32;                 // stride byte offset
     d |= (uint64_t)1u << 46;                          // descriptor version
-    d |= (uint64_t)2u << 61;                          // 128-byte swizzle
+    d |= (uint64_t)4u << 61;                          // 64-byte swizzle
     return d;
 }
 // Instruction descriptor, kind::f16: fp16 A and B, fp32 D, both K-major,
-// M = 128, N = 64.
-constexpr uint32_t kT5Idesc = (1u << 4) | (0u << 7) | (0u << 10) | ((kT5N >> 3) << 17) | ((kT5M >> 4) << 24);
+// M = 128.
 // The four matrix digit planes of a stage lie one after another, so they
 // form one 256-row B operand: a single M = 128, N = 256 product of data
 // digit plane i with all of them adds A_i B_j to the accumulator of
@@ -140,10 +147,10 @@ __device__ __forceinline__ void t5_st_zero8(uint32_t taddr) {
 }
 __device__ __forceinline__ void t5_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// byte offset of 16-byte unit `unit` (0..7) of row `row` in a K-major
-// 128-byte-swizzled operand
+// byte offset of 16-byte unit `unit` (0..3) of row `row` in a K-major
+// 64-byte-swizzled operand (unit index XOR bits 1-2 of the row)
 __device__ __forceinline__ uint32_t t5_swz(uint32_t row, uint32_t unit) {
-    return (row >> 3) * 1024u + (row & 7u) * 128u + ((unit ^ (row & 7u)) << 4);
+    return (row >> 3) * 512u + (row & 7u) * 64u + ((unit ^ ((row >> 1) & 3u)) << 4);
 }
 
 // Balanced digits of eight words as fp16, packed for one 16-byte unit per
@@ -203,26 +210,33 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
     extern __shared__ __align__(1024) unsigned char t5_smem_raw[];
     unsigned char *base = t5_smem_raw + ((1024u - (smem_addr(t5_smem_raw) & 1023u)) & 1023u);
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + kT5SmemData);
-    // full_c / empty_b: matrix stages (TMA in, products done), full_d /
-    // empty: data stages (digits written, products done)
-    uint64_t *full_c = bars, *empty_b = bars + 3, *full_d = bars + 6, *empty = bars + 8, *acc_full = bars + 10,
-             *acc_empty = bars + 11, *drain = bars + 12;
+    // b_full / b_empty: matrix stages (TMA in, products done); r_full /
+    // r_empty: data-word stages (TMA in, converted); a_full / a_empty:
+    // digit stages (digits written, products done)
+    uint64_t *b_full = bars, *b_empty = bars + kT5NB, *r_full = bars + 2 * kT5NB,
+             *r_empty = bars + 2 * kT5NB + kT5NR, *a_full = bars + 2 * kT5NB + 2 * kT5NR,
+             *a_empty = bars + 2 * kT5NB + 2 * kT5NR + kT5NA, *acc_full = bars + 2 * kT5NB + 2 * kT5NR + 2 * kT5NA,
+             *acc_empty = acc_full + 1, *drain = acc_full + 2;
     __shared__ uint32_t s_tmem;
     __shared__ uint32_t s_abort;
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr uint32_t NCONV = kT5ConvWarps * 32;
+    constexpr uint32_t NCONV = kT5ConvWarps * 32, NEPI = kT5EpiWarps * 32;
 
     if (tid == 0) {
         for (int s = 0; s < (int)kT5NB; ++s) {
-            mbar_init(&full_c[s], 1);
-            mbar_init(&empty_b[s], 1);
+            mbar_init(&b_full[s], 1);
+            mbar_init(&b_empty[s], 1);
+        }
+        for (int s = 0; s < (int)kT5NR; ++s) {
+            mbar_init(&r_full[s], 1);
+            mbar_init(&r_empty[s], NCONV);
         }
         for (int s = 0; s < (int)kT5NA; ++s) {
-            mbar_init(&full_d[s], NCONV);
-            mbar_init(&empty[s], 1);
+            mbar_init(&a_full[s], NCONV);
+            mbar_init(&a_empty[s], 1);
         }
         mbar_init(acc_full, 1);
-        mbar_init(acc_empty, NCONV);
+        mbar_init(acc_empty, NEPI);
         mbar_init(drain, 1);
         fence_mbar_init();
         s_abort = 0;
@@ -239,56 +253,76 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
     const uint32_t tmem = s_tmem;
     volatile uint32_t *abort_flag = &s_abort;
     const uint32_t ntiles = a.ntiles;
-    // stage s: A = data digit planes (converted here), B = matrix digit planes (TMA)
+    // stages: A = data digit planes (converted here), B = matrix digit
+    // planes (TMA), R = data words of a chunk (TMA, read by the converters)
     auto stage_a = [&](uint32_t s) { return base + (size_t)s * kT5StageA; };
     auto stage_b = [&](uint32_t s) { return base + (size_t)kT5NA * kT5StageA + (size_t)s * kT5StageB; };
+    auto stage_r = [&](uint32_t s) {
+        return base + (size_t)kT5NA * kT5StageA + (size_t)kT5NB * kT5StageB + (size_t)s * kT5StageR;
+    };
+    const uint32_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const uint32_t nchunks = kT5Chunks * my_tiles;
+    auto tile_of = [&](uint32_t g) { return blockIdx.x + (g / kT5Chunks) * gridDim.x; };
     bool ok = true;
 
-    if (warp == kT5ConvWarps) {
+    if (warp == kT5TmaWarp) {
         // ------------------------------------------------ TMA producer
+        // chunk g: its data words into R stage g % NR and its matrix digit
+        // planes into B stage g % NB, each as soon as that stage is free
         if (lane == 0) {
-            uint32_t g = 0;
-            for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-                const T5Tile T = t5_tile(tile, a.L);
+            uint32_t nr = 0, nb = 0;      // copies issued: data-word chunks, matrix chunks
+            for (uint32_t g = 0; g < nchunks && ok; ++g) {
+                const T5Tile T = t5_tile(tile_of(g), a.L);
+                const uint32_t c = g % kT5Chunks;
+                const uint32_t sr = g % kT5NR, sb = g % kT5NB;
+                if (g >= kT5NR && !t5_wait(&r_empty[sr], ((g - kT5NR) / kT5NR) & 1u, abort_flag)) { ok = false; break; }
+                mbar_expect_tx(&r_full[sr], kT5StageR);
+                // column pass: words src[32 c + k][128 mb + m]; row pass:
+                // src[128 mb + m][32 c + k]
+                if (ROWP)
+                    tma_2d_g2s(stage_r(sr), &a.dmap, (int)(c * kT5KC), (int)(T.t * 256 + T.mb * kT5M), &r_full[sr]);
+                else
+                    tma_2d_g2s(stage_r(sr), &a.dmap, (int)(T.mb * kT5M), (int)(T.t * 256 + c * kT5KC), &r_full[sr]);
+                ++nr;
+                if (g >= kT5NB && !t5_wait(&b_empty[sb], ((g - kT5NB) / kT5NB) & 1u, abort_flag)) { ok = false; break; }
                 const uint32_t mrow0 = a.mat_row0 + T.l * kT5Dig * 256 + T.nb * kT5N;
-                for (uint32_t c = 0; c < 4 && ok; ++c, ++g) {
-                    const uint32_t s = g % kT5NB;
-                    if (g >= kT5NB && !t5_wait(&empty_b[s], ((g - kT5NB) / kT5NB) & 1u, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    unsigned char *dst = stage_b(s);
-                    mbar_expect_tx(&full_c[s], kT5Dig * kT5N * 128);
-                    // (test hook: this copy's barrier waits for bytes that never come)
-                    if (a.stall_tx && g == 0 && blockIdx.x == 0) mbar_add_tx(&full_c[s], a.stall_tx);
-                    for (uint32_t d = 0; d < kT5Dig; ++d)
-                        tma_2d_g2s(dst + d * kT5N * 128, &a.cmap, (int)(c * kT5KC), (int)(mrow0 + d * 256),
-                                   &full_c[s]);
-                }
+                mbar_expect_tx(&b_full[sb], kT5StageB);
+                // (test hook: this copy's barrier waits for bytes that never come)
+                if (a.stall_tx && g == 0 && blockIdx.x == 0) mbar_add_tx(&b_full[sb], a.stall_tx);
+                for (uint32_t d = 0; d < kT5Dig; ++d)
+                    tma_2d_g2s(stage_b(sb) + d * kT5N * kT5Row, &a.cmap, (int)(c * kT5KC), (int)(mrow0 + d * 256),
+                               &b_full[sb]);
+                ++nb;
             }
             if (!ok) {
                 atomicExch(const_cast<uint32_t *>(abort_flag), 1u);
-                // copies still in flight land before the CTA leaves: chunk
-                // h used stage h % 3 for its ((h / 3) + 1)-th phase
-                for (uint32_t h = g >= kT5NB ? g - kT5NB : 0; h < g; ++h) {
+                // copies still in flight land before the CTA leaves (bounded):
+                // chunk h used R stage h % NR and B stage h % NB for their
+                // (h / NR + 1)-th and (h / NB + 1)-th phases
+                for (uint32_t h = nr >= kT5NR ? nr - kT5NR : 0; h < nr; ++h) {
                     const long long t0 = clock64();
-                    while (!mbar_try_wait(&full_c[h % kT5NB], (h / kT5NB) & 1u) && clock64() - t0 < (1ll << 30)) {
+                    while (!mbar_try_wait(&r_full[h % kT5NR], (h / kT5NR) & 1u) && clock64() - t0 < (1ll << 30)) {
+                    }
+                }
+                for (uint32_t h = nb >= kT5NB ? nb - kT5NB : 0; h < nb; ++h) {
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(&b_full[h % kT5NB], (h / kT5NB) & 1u) && clock64() - t0 < (1ll << 30)) {
                     }
                 }
             }
         }
-    } else if (warp == kT5ConvWarps + 1) {
+    } else if (warp == kT5MmaWarp) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            uint32_t g = 0, ti = 0;
-            for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++ti) {
+            uint32_t g = 0;
+            for (uint32_t ti = 0; ti < my_tiles && ok; ++ti) {
                 // accumulators zeroed (at the start, then by each epilogue)
                 if (!t5_wait(acc_empty, ti & 1u, abort_flag)) { ok = false; break; }
                 t5_fence_after();
-                for (uint32_t c = 0; c < 4 && ok; ++c, ++g) {
-                    const uint32_t s = g & 1u, sb = g % kT5NB;
-                    if (!t5_wait(&full_c[sb], (g / kT5NB) & 1u, abort_flag) ||
-                        !t5_wait(&full_d[s], (g >> 1) & 1u, abort_flag)) {
+                for (uint32_t c = 0; c < kT5Chunks && ok; ++c, ++g) {
+                    const uint32_t s = g % kT5NA, sb = g % kT5NB;
+                    if (!t5_wait(&b_full[sb], (g / kT5NB) & 1u, abort_flag) ||
+                        !t5_wait(&a_full[s], (g / kT5NA) & 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
@@ -300,11 +334,11 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
                     for (uint32_t ks = 0; ks < kT5KC / 16; ++ks) {
 #pragma unroll
                         for (uint32_t i = 0; i < kT5Dig; ++i)
-                            t5_mma(tmem + i * kT5N, da + ((i * (kT5M * 128) + ks * 32) >> 4), db + ((ks * 32) >> 4),
-                                   kT5IdescAll, 1u);
+                            t5_mma(tmem + i * kT5N, da + ((i * (kT5M * kT5Row) + ks * 32) >> 4),
+                                   db + ((ks * 32) >> 4), kT5IdescAll, 1u);
                     }
-                    t5_commit(&empty[s]);
-                    t5_commit(&empty_b[sb]);
+                    t5_commit(&a_empty[s]);
+                    t5_commit(&b_empty[sb]);
                 }
                 if (ok) t5_commit(acc_full);
             }
@@ -317,40 +351,46 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
             }
         }
     } else {
-        // ------------------------------------- converters and epilogue
-        // Data operand A[m][k] of a tile, m < 128, for chunk c (k in 64 c ..):
-        //   column pass  m = n2 - 128 mb, k = n1: word src[k][128 mb + m]
-        //   row pass     m = r - 128 mb,  k = n2: word src[128 mb + m][k]
+        // ------------------------------------- converters (warps 0-7) and
+        // epilogue (warps 8-15): the next tile's digits are made while the
+        // epilogue drains the accumulators of the last one
+        const bool conv = warp < kT5ConvWarps;
+        const uint32_t ew = warp - kT5ConvWarps;        // epilogue warp 0..7
+        // Data operand A[m][k] of a tile, m < 128, for chunk c (k in 32 c ..):
+        //   column pass  m = n2 - 128 mb, k = n1: word src[k][128 mb + m],
+        //                staged as R[k][m];
+        //   row pass     m = r - 128 mb,  k = n2: word src[128 mb + m][k],
+        //                staged as R[m][k].
         // 16-byte unit u (k = 8u .. 8u + 7) of row m is task (m, u); each
         // thread takes TASKS of them (lanes along m for the column pass,
-        // along u for the row pass, so the loads coalesce).
-        constexpr uint32_t TASKS = kT5M * 8 / NCONV;
+        // along u for the row pass: conflict-free shared-memory reads).
+        constexpr uint32_t UNITS = kT5KC / 8;
+        constexpr uint32_t TASKS = kT5M * UNITS / NCONV;
         auto task_mu = [&](uint32_t q, uint32_t &m, uint32_t &u) {
             const uint32_t task = tid + q * NCONV;
-            if (ROWP) { m = task >> 3; u = task & 7u; }
-            else { m = task & 127u; u = task >> 7; }
+            if (ROWP) { m = task / UNITS; u = task % UNITS; }
+            else { m = task % kT5M; u = task / kT5M; }
         };
-        auto load_chunk = [&](uint32_t tile, uint32_t c, uint32_t (&xw)[TASKS][8]) {
-            const T5Tile T = t5_tile(tile, a.L);
-            const uint32_t *src = a.src + (size_t)T.t * 65536;
+        // one chunk: words from R stage sr to digit planes in A stage s
+        auto convert_chunk = [&](uint32_t sr, uint32_t s) {
+            const uint32_t *R = reinterpret_cast<const uint32_t *>(stage_r(sr));
+            uint32_t xw[TASKS][8];
 #pragma unroll
             for (uint32_t q = 0; q < TASKS; ++q) {
                 uint32_t m, u;
                 task_mu(q, m, u);
                 if (ROWP) {
-                    const uint4 *p = reinterpret_cast<const uint4 *>(src + (size_t)(T.mb * kT5M + m) * 256 +
-                                                                     c * kT5KC + 8 * u);
-                    const uint4 v0 = __ldg(p), v1 = __ldg(p + 1);
+                    const uint4 *p = reinterpret_cast<const uint4 *>(R + m * kT5KC + 8 * u);
+                    const uint4 v0 = p[0], v1 = p[1];
                     xw[q][0] = v0.x; xw[q][1] = v0.y; xw[q][2] = v0.z; xw[q][3] = v0.w;
                     xw[q][4] = v1.x; xw[q][5] = v1.y; xw[q][6] = v1.z; xw[q][7] = v1.w;
                 } else {
-                    const uint32_t *p = src + (size_t)(c * kT5KC + 8 * u) * 256 + T.mb * kT5M + m;
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) xw[q][e] = __ldg(p + (size_t)e * 256);
+                    for (int e = 0; e < 8; ++e) xw[q][e] = R[(8 * u + e) * kT5M + m];
                 }
             }
-        };
-        auto store_chunk = [&](uint32_t s, const uint32_t (&xw)[TASKS][8]) {
+            // the words are read: the stage takes the chunk NR ahead
+            t5_arrive(&r_empty[sr]);
             unsigned char *dst = stage_a(s);
 #pragma unroll
             for (uint32_t q = 0; q < TASKS; ++q) {
@@ -360,20 +400,16 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
                 t5_digits(xw[q], dg);
                 const uint32_t off = t5_swz(m, u);
 #pragma unroll
-                for (uint32_t d = 0; d < kT5Dig; ++d) *reinterpret_cast<uint4 *>(dst + d * (kT5M * 128) + off) = dg[d];
+                for (uint32_t d = 0; d < kT5Dig; ++d) *reinterpret_cast<uint4 *>(dst + d * (kT5M * kT5Row) + off) = dg[d];
             }
             // generic-proxy stores, read next by the tensor cores
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            t5_arrive(&full_d[s]);
+            t5_arrive(&a_full[s]);
         };
-        // epilogue of tile `tile` (its ti-th): the seven diagonals of this
-        // thread's row m (tensor-memory lane) over 32 of the 64 columns n
         auto epilogue = [&](uint32_t tile, uint32_t ti) -> bool {
-            if (!t5_wait(acc_full, ti & 1u, abort_flag)) return false;
-            t5_fence_after();
             const T5Tile T = t5_tile(tile, a.L);
-            const uint32_t m = 32 * (warp & 3u) + lane;
-            const uint32_t n0 = (warp >> 2) * 32;
+            const uint32_t m = 32 * (ew & 3u) + lane;
+            const uint32_t n0 = (ew >> 2) * 32;
             Lc<uint32_t> kk;
             kk.load(a.lc + T.l);
             uint32_t w7[kT5Diag];
@@ -386,32 +422,40 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
             // out[r][v] = out[128 mb + m][64 nb + n]
             uint32_t *outt = a.dst + (size_t)T.t * 65536;
             const Tw<uint32_t> *twt = a.tw ? a.tw + (size_t)T.l * 65536 : nullptr;
+            auto tw_at = [&](uint32_t n) -> const Tw<uint32_t> * {
+                return twt + (ROWP ? (size_t)(T.mb * kT5M + m) * 256 + T.nb * kT5N + n
+                                   : (size_t)(T.nb * kT5N + n) * 256 + T.mb * kT5M + m);
+            };
+            // the inter-step twiddles of the first column group, loaded
+            // before the wait for the products (their latency overlaps it);
+            // each group's loads are issued one group ahead
+            Tw<uint32_t> tw8[8], twn[8];
+            if (twt) {
+#pragma unroll
+                for (int cc = 0; cc < 8; ++cc) tw8[cc] = ldtw(tw_at(n0 + cc));
+            }
+            if (!t5_wait(acc_full, ti & 1u, abort_flag)) return false;
+            t5_fence_after();
 #pragma unroll 1
             for (uint32_t grp = 0; grp < 4; ++grp) {
                 uint32_t f[kT5Diag][8];
 #pragma unroll
                 for (uint32_t d = 0; d < kT5Diag; ++d) {
-                    const uint32_t taddr = tmem + ((32u * (warp & 3u)) << 16) + d * kT5N + n0 + 8 * grp;
+                    const uint32_t taddr = tmem + ((32u * (ew & 3u)) << 16) + d * kT5N + n0 + 8 * grp;
                     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                                  : "=r"(f[d][0]), "=r"(f[d][1]), "=r"(f[d][2]), "=r"(f[d][3]), "=r"(f[d][4]),
                                    "=r"(f[d][5]), "=r"(f[d][6]), "=r"(f[d][7])
                                  : "r"(taddr));
                 }
-                Tw<uint32_t> tw8[8];
-                if (twt) {
+                if (twt && grp < 3) {
 #pragma unroll
-                    for (int cc = 0; cc < 8; ++cc) {
-                        const uint32_t n = n0 + 8 * grp + cc;
-                        const size_t at = ROWP ? (size_t)(T.mb * kT5M + m) * 256 + T.nb * kT5N + n
-                                               : (size_t)(T.nb * kT5N + n) * 256 + T.mb * kT5M + m;
-                        tw8[cc] = ldtw(twt + at);
-                    }
+                    for (int cc = 0; cc < 8; ++cc) twn[cc] = ldtw(tw_at(n0 + 8 * (grp + 1) + cc));
                 }
                 t5_wait_ld();
                 // the next tile accumulates onto zeros
 #pragma unroll
                 for (uint32_t d = 0; d < kT5Diag; ++d)
-                    t5_st_zero8(tmem + ((32u * (warp & 3u)) << 16) + d * kT5N + n0 + 8 * grp);
+                    t5_st_zero8(tmem + ((32u * (ew & 3u)) << 16) + d * kT5N + n0 + 8 * grp);
                 uint32_t v[8];
 #pragma unroll
                 for (int cc = 0; cc < 8; ++cc) {
@@ -422,6 +466,10 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
                     uint32_t r = csub<uint32_t>(barrett_lazy((uint64_t)comb + off, kk), kk.q);
                     if (twt) r = mul_full<RED_SHOUP>(r, tw8[cc], kk);
                     v[cc] = r;
+                }
+                if (twt) {
+#pragma unroll
+                    for (int cc = 0; cc < 8; ++cc) tw8[cc] = twn[cc];
                 }
                 if (ROWP) {
                     uint4 *o = reinterpret_cast<uint4 *>(outt + (size_t)(T.mb * kT5M + m) * 256 + T.nb * kT5N + n0 +
@@ -440,35 +488,29 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
             return true;
         };
 
-        // chunks in order g = 4 (tile index) + c; the words of chunk g + 1
-        // are loaded while chunk g is converted; the epilogue of a tile runs
-        // after the next tile's first chunk is in its stage buffer
-        uint32_t xa[TASKS][8], xb[TASKS][8];
-        const uint32_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-        const uint32_t nchunks = 4 * my_tiles;
-        auto tile_of = [&](uint32_t g) { return blockIdx.x + (g >> 2) * gridDim.x; };
-        if (nchunks) load_chunk(tile_of(0), 0, xa);
-        // the accumulators start at zero (every product accumulates):
-        // this thread's row, its 32 of the 64 columns of each diagonal
-        for (uint32_t d = 0; d < kT5Diag; ++d)
-            for (uint32_t c8 = 0; c8 < 4; ++c8)
-                t5_st_zero8(tmem + ((32u * (warp & 3u)) << 16) + d * kT5N + (warp >> 2) * 32 + 8 * c8);
-        t5_wait_st();
-        t5_fence_before();
-        t5_arrive(acc_empty);
-        auto step = [&](uint32_t g, uint32_t (&cur)[TASKS][8], uint32_t (&nxt)[TASKS][8]) -> bool {
-            if (g + 1 < nchunks) load_chunk(tile_of(g + 1), (g + 1) & 3u, nxt);
-            const uint32_t s = g & 1u;
-            if (g >= 2 && !t5_wait(&empty[s], ((g - 2) >> 1) & 1u, abort_flag)) return false;
-            store_chunk(s, cur);
-            if ((g & 3u) == 0 && g > 0 && !epilogue(tile_of(g - 1), (g >> 2) - 1)) return false;
-            return true;
-        };
-        for (uint32_t g = 0; g < nchunks && ok; g += 2) {
-            ok = step(g, xa, xb);
-            if (ok && g + 1 < nchunks) ok = step(g + 1, xb, xa);
+        if (conv) {
+            // chunk g: wait for its data words (TMA) and for its digit stage
+            // (the products of chunk g - NA done), then convert
+            for (uint32_t g = 0; g < nchunks && ok; ++g) {
+                const uint32_t sr = g % kT5NR, s = g % kT5NA;
+                if (!t5_wait(&r_full[sr], (g / kT5NR) & 1u, abort_flag)) { ok = false; break; }
+                if (g >= kT5NA && !t5_wait(&a_empty[s], ((g - kT5NA) / kT5NA) & 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                convert_chunk(sr, s);
+            }
+        } else {
+            // the accumulators start at zero (every product accumulates):
+            // this thread's row, its 32 of the 64 columns of each diagonal
+            for (uint32_t d = 0; d < kT5Diag; ++d)
+                for (uint32_t c8 = 0; c8 < 4; ++c8)
+                    t5_st_zero8(tmem + ((32u * (ew & 3u)) << 16) + d * kT5N + (ew >> 2) * 32 + 8 * c8);
+            t5_wait_st();
+            t5_fence_before();
+            t5_arrive(acc_empty);
+            for (uint32_t ti = 0; ti < my_tiles && ok; ++ti) ok = epilogue(tile_of(kT5Chunks * ti), ti);
         }
-        if (ok && nchunks) ok = epilogue(tile_of(nchunks - 1), my_tiles - 1);
         if (!ok) atomicExch(const_cast<uint32_t *>(abort_flag), 1u);
     }
     // ---------------------------------------------------------- teardown
@@ -487,25 +529,44 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
 namespace nttgb {
 
 namespace {
-cudaError_t make_t5_cmap(CUtensorMap *m, const void *tab, uint64_t rows) {
-    using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeFn t5_encoder() {
     static EncodeFn encode = nullptr;
     if (!encode) {
         void *fn = nullptr;
         cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !fn)
-            return cudaErrorNotSupported;
-        encode = reinterpret_cast<EncodeFn>(fn);
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess && fn)
+            encode = reinterpret_cast<EncodeFn>(fn);
     }
+    return encode;
+}
+// matrix digit planes: fp16 rows of 256, box of 32 (K) x 64 rows, 64-byte swizzle
+cudaError_t make_t5_cmap(CUtensorMap *m, const void *tab, uint64_t rows) {
+    EncodeFn encode = t5_encoder();
+    if (!encode) return cudaErrorNotSupported;
     cuuint64_t dims[2] = {256, rows};
     cuuint64_t strides[1] = {256 * 2};
-    cuuint32_t box[2] = {64, 64};
+    cuuint32_t box[2] = {kT5KC, kT5N};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(tab), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+// data words of a pass: rows of 256 words; box 128 x 32 (column pass:
+// 32 rows k of 128 columns m) or 32 x 128 (row pass: 128 rows m of 32 k)
+cudaError_t make_t5_dmap(CUtensorMap *m, const void *src, uint64_t ntrans, bool rowp) {
+    EncodeFn encode = t5_encoder();
+    if (!encode) return cudaErrorNotSupported;
+    cuuint64_t dims[2] = {256, ntrans * 256};
+    cuuint64_t strides[1] = {256 * 4};
+    cuuint32_t box[2] = {rowp ? kT5KC : kT5M, rowp ? kT5M : kT5KC};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void *>(src), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -547,16 +608,23 @@ cudaError_t launch_tc5(ntt_plan_s &p, void *data, uint32_t batch, bool inverse, 
     a.stall_tx = (p.flags & NTT_TEST_STALL) && !inverse ? 16u : 0u;
     uint32_t *d = reinterpret_cast<uint32_t *>(data), *s = reinterpret_cast<uint32_t *>(p.d_scratch);
     auto row0 = [&](int m) { return (uint32_t)m * p.L * 1024; };
+    auto pass = [&](bool rowp, const uint32_t *src, uint32_t *dst) -> cudaError_t {
+        a.src = src;
+        a.dst = dst;
+        cudaError_t pe = make_t5_dmap(&a.dmap, src, ntrans, rowp);
+        if (pe != cudaSuccess) return pe;
+        return rowp ? t5_launch<true>(a, st) : t5_launch<false>(a, st);
+    };
     if (!inverse) {
-        a.src = d; a.dst = s; a.mat_row0 = row0(0); a.tw = tws;
-        if ((e = t5_launch<false>(a, st)) != cudaSuccess) return e;
-        a.src = s; a.dst = d; a.mat_row0 = row0(1); a.tw = nullptr; a.stall_tx = 0;
-        e = t5_launch<true>(a, st);
+        a.mat_row0 = row0(0); a.tw = tws;
+        if ((e = pass(false, d, s)) != cudaSuccess) return e;
+        a.mat_row0 = row0(1); a.tw = nullptr; a.stall_tx = 0;
+        e = pass(true, s, d);
     } else {
-        a.src = d; a.dst = s; a.mat_row0 = row0(2); a.tw = tws + (size_t)p.L * 65536;
-        if ((e = t5_launch<true>(a, st)) != cudaSuccess) return e;
-        a.src = s; a.dst = d; a.mat_row0 = row0(3); a.tw = nullptr;
-        e = t5_launch<false>(a, st);
+        a.mat_row0 = row0(2); a.tw = tws + (size_t)p.L * 65536;
+        if ((e = pass(true, d, s)) != cudaSuccess) return e;
+        a.mat_row0 = row0(3); a.tw = nullptr;
+        e = pass(false, s, d);
     }
     p.last_launches += 2;
     return e;
