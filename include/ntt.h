@@ -340,15 +340,23 @@ ntt_status ntt_limb_shard(uint32_t L, uint32_t world, uint32_t rank,
 #define NTT_FORM_SMALL 0      /* chunk pass on one-warp CTAs */
 #define NTT_FORM_WIDE 1       /* chunk pass on 256-thread CTAs */
 #define NTT_FORM_STREAMED 2   /* both passes in one streamed launch (s2 = 8) */
+#define NTT_FORM_SMALL_SHFL 3 /* NTT_FORM_SMALL with the chunk pass's
+                                 exchanges between register rounds by warp
+                                 shuffles instead of shared memory */
+#define NTT_FORM_WIDE_SHFL 4  /* the same for NTT_FORM_WIDE */
 /* Defaults: NTT_FORM_SMALL forward, NTT_FORM_WIDE inverse (NTT_FORM_STREAMED
  * both ways under NTT_STREAMED).  Chunk tiles hold the same chunk of
  * several polynomials (one twiddle table a tile) when their count divides
  * the batch and chunks have at least 256 words, else several chunks of one
- * polynomial.  Results are identical in every split, form and tiling. */
+ * polynomial.  The shuffle forms exist for 4-byte words with twiddle
+ * tables (a plan with NTT_WORD64 or NTT_TW_OTF runs them as their
+ * shared-memory forms); a chunk's threads are lanes of one warp except for
+ * 512-word chunks in radix 8, whose exchanges stay in shared memory.
+ * Results are identical in every split, form and tiling. */
 typedef struct {
-    float forward_ms[3];      /* per form, ms per call, at the chosen
+    float forward_ms[5];      /* per form, ms per call, at the chosen
                                  radix and split */
-    float inverse_ms[3];
+    float inverse_ms[5];
     int32_t forward_form;     /* the fastest */
     int32_t inverse_form;
     int32_t chunk_log2;       /* the chosen split s2 */
@@ -367,7 +375,8 @@ typedef struct {
  * afterwards with that shape take that radix and split and use the
  * recorded forms for calls in that batch bucket (NTT_STREAMED plans keep
  * theirs).  Forms that do not exist (streamed with s2 != 8, radix 3 or
- * NTT_TW_OTF) are reported as -1 and never chosen.  If the environment
+ * NTT_TW_OTF; the shuffle forms with NTT_WORD64 or NTT_TW_OTF) are
+ * reported as -1 and never chosen.  If the environment
  * variable NTT_TUNE_DB names a file, the tables are read from it at first
  * use and rewritten after each tuning (one JSON object per line).  flags:
  * as ntt_plan_create, without NTT_STREAMED, NTT_CHECK or NTT_TEST_STALL.

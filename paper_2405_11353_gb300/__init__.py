@@ -80,14 +80,15 @@ class NttJob(ctypes.Structure):
 
 
 class NttTuneResult(ctypes.Structure):
-    _fields_ = [("forward_ms", ctypes.c_float * 3), ("inverse_ms", ctypes.c_float * 3),
+    _fields_ = [("forward_ms", ctypes.c_float * 5), ("inverse_ms", ctypes.c_float * 5),
                 ("forward_form", ctypes.c_int32), ("inverse_form", ctypes.c_int32),
                 ("chunk_log2", ctypes.c_int32), ("radix_log2", ctypes.c_int32),
                 ("config_ms", (ctypes.c_float * 3) * 2)]
 
 
-NTT_FORM_SMALL, NTT_FORM_WIDE, NTT_FORM_STREAMED = 0, 1, 2
-FORMS = {"small": NTT_FORM_SMALL, "wide": NTT_FORM_WIDE, "streamed": NTT_FORM_STREAMED}
+NTT_FORM_SMALL, NTT_FORM_WIDE, NTT_FORM_STREAMED, NTT_FORM_SMALL_SHFL, NTT_FORM_WIDE_SHFL = 0, 1, 2, 3, 4
+FORMS = {"small": NTT_FORM_SMALL, "wide": NTT_FORM_WIDE, "streamed": NTT_FORM_STREAMED,
+         "small_shfl": NTT_FORM_SMALL_SHFL, "wide_shfl": NTT_FORM_WIDE_SHFL}
 
 _lib = None
 

@@ -98,7 +98,9 @@ template <class W> __host__ __device__ constexpr uint32_t cols_phys(uint32_t k, 
 // (paired_chunks).  Bit 4 of P (per-plan column and chunk passes): rounds
 // of three stages on 8 words a thread instead of four stages on 16
 // (radix_log).  Bit 5 (column passes): rows of the plan's 2^s2 words
-// instead of 256.
+// instead of 256.  Bit 6 (per-plan chunk passes, 4-byte words): the
+// exchanges between rounds go through warp shuffles instead of shared
+// memory, where a chunk's threads are lanes of one warp (shfl_exchange).
 template <int P> __host__ __device__ constexpr int radix_log() { return (P & 16) ? 3 : 4; }
 template <class W, int LOGS, int KIND, int P = 0> __host__ __device__ constexpr uint32_t tile_k() {
     // threads per sub-transform: 2^(LOGS - LR).  Chunks: one warp per CTA
@@ -135,10 +137,180 @@ template <int LOGS, bool INV, int J, int LR = 4> struct RoundOf {
         return RR == LR ? ((uint32_t)e << LO)
                         : (((uint32_t)e >> RR) | (((uint32_t)e & ((1u << RR) - 1)) << LO));
     }
-    __device__ static __forceinline__ uint32_t A(uint32_t tau) {
+    __host__ __device__ static constexpr uint32_t A(uint32_t tau) {
         return RR == LR ? ((tau & ((1u << LO) - 1)) | ((tau >> LO) << (LO + LR))) : (tau << (LR - RR));
     }
 };
+
+// ------------------------------------------------ warp-shuffle exchange
+// Where index bit p of u sits in round J's layout: at bit i of the thread
+// index tau (loc = i), or at bit i of the word index e (loc = LB + i, LB =
+// LOGS - LR bits of tau).  Both RoundOf maps place single bits, so a round's
+// layout is a bijection from u's LOGS bits onto tau's and e's.
+template <int LOGS, bool INV, int J, int LR> struct XLayout {
+    static constexpr int LB = LOGS - LR;
+    int loc[16];
+    static constexpr int bit_of(uint32_t v) {
+        int b = 0;
+        while (b < 31 && (v >> b) != 1u) ++b;
+        return b;
+    }
+    constexpr XLayout() : loc() {
+        using R = RoundOf<LOGS, INV, J, LR>;
+        for (int i = 0; i < LR; ++i) loc[bit_of(R::E(1 << i))] = LB + i;
+        for (int i = 0; i < LB; ++i) loc[bit_of(R::A(1u << i))] = i;
+    }
+};
+
+// The move from round J - 1's layout to round J's as: swaps of a tau bit
+// with an e bit (one shuffle per pair of words, with the partner lane
+// across that tau bit), then a permutation of the tau bits (one indexed
+// shuffle per word) and one of the e bits (register renaming, free).  Each
+// u bit that goes from e to tau is swapped with one that goes from tau to
+// e, the one at its target tau bit when there is such a bit; the tau bits
+// left out of place (radix 8, and 512-word chunks in radix 16) take the
+// indexed shuffles.
+template <int LOGS, bool INV, int J, int LR> struct XPlan {
+    static constexpr int LB = LOGS - LR;
+    int nsw;
+    int sw_tau[8], sw_e[8];       // swap s exchanges tau bit sw_tau[s] with e bit sw_e[s]
+    int tau_src[8];               // after the swaps, tau bit b comes from tau bit tau_src[b]
+    int e_src[8];                 // e bit b comes from e bit e_src[b]
+    bool tau_perm;
+    constexpr XPlan() : nsw(0), sw_tau(), sw_e(), tau_src(), e_src(), tau_perm(false) {
+        const XLayout<LOGS, INV, J - 1, LR> from{};
+        const XLayout<LOGS, INV, J, LR> to{};
+        int cur[16] = {};
+        for (int b = 0; b < LOGS; ++b) cur[b] = from.loc[b];
+        for (int b = 0; b < LOGS; ++b) {
+            if (cur[b] < LB || to.loc[b] >= LB) continue;       // not an e -> tau bit
+            int q = -1;
+            for (int c = 0; c < LOGS; ++c)
+                if (q < 0 && cur[c] == to.loc[b] && to.loc[c] >= LB) q = c;
+            for (int c = 0; c < LOGS; ++c)
+                if (q < 0 && cur[c] < LB && to.loc[c] >= LB) q = c;
+            sw_tau[nsw] = cur[q];
+            sw_e[nsw] = cur[b] - LB;
+            ++nsw;
+            const int t = cur[b];
+            cur[b] = cur[q];
+            cur[q] = t;
+        }
+        for (int b = 0; b < LOGS; ++b) {
+            if (to.loc[b] < LB) {
+                tau_src[to.loc[b]] = cur[b];
+                if (cur[b] != to.loc[b]) tau_perm = true;
+            } else {
+                e_src[to.loc[b] - LB] = cur[b] - LB;
+            }
+        }
+    }
+};
+template <int LOGS, bool INV, int J, int LR> struct XPlanOf {
+    static constexpr XPlan<LOGS, INV, J, LR> value{};
+};
+
+// The plan run on every lane's word indices at compile time (the swaps,
+// the tau permutation and the e permutation as shfl_exchange performs
+// them): true when each lane ends with round J's words.
+template <int LOGS, bool INV, int J, int LR> constexpr bool xplan_reaches_round() {
+    constexpr int LB = LOGS - LR, T = 1 << LB, NW = 1 << LR;
+    using RP = RoundOf<LOGS, INV, J - 1, LR>;
+    using R = RoundOf<LOGS, INV, J, LR>;
+    const XPlan<LOGS, INV, J, LR> pl{};
+    uint32_t x[32][16] = {}, y[32][16] = {};
+    for (int t = 0; t < T; ++t)
+        for (int e = 0; e < NW; ++e) x[t][e] = RP::A((uint32_t)t) | RP::E(e);
+    for (int s = 0; s < pl.nsw; ++s) {
+        const int i = pl.sw_tau[s], j = pl.sw_e[s];
+        for (int t = 0; t < T; ++t)
+            for (int e = 0; e < NW; ++e) y[t][e] = x[t][e];
+        for (int t = 0; t < T; ++t) {
+            const bool up = (t >> i) & 1;
+            const int partner = t ^ (1 << i);
+            for (int r0 = 0; r0 < NW; ++r0) {
+                if (r0 & (1 << j)) continue;
+                const int r1 = r0 | (1 << j);
+                const uint32_t got = !up ? x[partner][r0] : x[partner][r1];   // the partner's hand-over
+                if (up) y[t][r0] = got;
+                else y[t][r1] = got;
+            }
+        }
+        for (int t = 0; t < T; ++t)
+            for (int e = 0; e < NW; ++e) x[t][e] = y[t][e];
+    }
+    for (int t = 0; t < T; ++t) {
+        int src = 0, lane_src = 0;
+        for (int b = 0; b < LB; ++b) lane_src |= ((t >> b) & 1) << (pl.tau_perm ? pl.tau_src[b] : b);
+        for (int e = 0; e < NW; ++e) {
+            src = 0;
+            for (int b = 0; b < LR; ++b) src |= ((e >> b) & 1) << pl.e_src[b];
+            y[t][e] = x[lane_src][src];
+        }
+    }
+    for (int t = 0; t < T; ++t)
+        for (int e = 0; e < NW; ++e)
+            if (y[t][e] != (R::A((uint32_t)t) | R::E(e))) return false;
+    return true;
+}
+
+// Swap S of the plan: word pairs (r0, r1 = r0 | 2^j) and lanes across tau
+// bit i.  After it, word e of lane tau is the word (e with bit j := tau's
+// bit i) of lane (tau with bit i := e's bit j): lanes whose bit i is set
+// hand over r0 and take the partner's r1 in its place, the others hand over
+// r1 and take the partner's r0.
+template <class W, int LOGS, bool INV, int J, int LR, int S>
+__device__ __forceinline__ void shfl_swaps(W (&x)[1 << LR], uint32_t tau) {
+    using PL = XPlanOf<LOGS, INV, J, LR>;
+    if constexpr (S < PL::value.nsw) {
+        constexpr int i = PL::value.sw_tau[S], j = PL::value.sw_e[S];
+        const bool up = (tau >> i) & 1u;
+#pragma unroll
+        for (int r0 = 0; r0 < (1 << LR); ++r0) {
+            if (r0 & (1 << j)) continue;
+            const int r1 = r0 | (1 << j);
+            const W mine = up ? x[r0] : x[r1];
+            const W got = __shfl_xor_sync(0xffffffffu, mine, 1 << i);
+            if (up) x[r0] = got;
+            else x[r1] = got;
+        }
+        shfl_swaps<W, LOGS, INV, J, LR, S + 1>(x, tau);
+    }
+}
+
+// Round J - 1's words of a thread to round J's through shuffles, for a
+// sub-transform whose 2^(LOGS - LR) threads are consecutive lanes of one
+// warp (tau = lane mod 2^(LOGS - LR)); every lane of the warp takes part.
+template <class W, int LOGS, bool INV, int J, int LR>
+__device__ __forceinline__ void shfl_exchange(W (&x)[1 << LR], uint32_t tau) {
+    using PL = XPlanOf<LOGS, INV, J, LR>;
+    constexpr int NW = 1 << LR, LB = LOGS - LR;
+    static_assert(LB <= 5, "a sub-transform's threads must fit one warp");
+    static_assert(xplan_reaches_round<LOGS, INV, J, LR>(), "the shuffle plan must give round J's layout");
+    shfl_swaps<W, LOGS, INV, J, LR, 0>(x, tau);
+    // the two permutations as 4-bit fields of integer constants
+    constexpr uint32_t TSRC = PL::value.tau_src[0] | (PL::value.tau_src[1] << 4) | (PL::value.tau_src[2] << 8) |
+                              (PL::value.tau_src[3] << 12) | (PL::value.tau_src[4] << 16);
+    constexpr uint32_t ESRC = PL::value.e_src[0] | (PL::value.e_src[1] << 4) | (PL::value.e_src[2] << 8) |
+                              (PL::value.e_src[3] << 12);
+    if constexpr (PL::value.tau_perm) {
+        uint32_t src = 0;
+#pragma unroll
+        for (int b = 0; b < LB; ++b) src |= ((tau >> b) & 1u) << ((TSRC >> (4 * b)) & 15u);
+#pragma unroll
+        for (int e = 0; e < NW; ++e) x[e] = __shfl_sync(0xffffffffu, x[e], (int)src, 1 << LB);
+    }
+    W y[NW];
+#pragma unroll
+    for (int e = 0; e < NW; ++e) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int b = 0; b < LR; ++b) s |= (((uint32_t)e >> b) & 1u) << ((ESRC >> (4 * b)) & 15u);
+        y[e] = x[s];
+    }
+#pragma unroll
+    for (int e = 0; e < NW; ++e) x[e] = y[e];
+}
 
 // shared-memory word offset of u in sub-transform k (linear in u's bits)
 template <class W, int LOGS, int KIND, int P = 0> __host__ __device__ constexpr uint32_t sm_off(uint32_t k, uint32_t u) {
@@ -305,7 +477,15 @@ __device__ __forceinline__ void later_rounds(W (&x)[1 << radix_log<P>()], W *xs,
     constexpr int LR = radix_log<P>();
     constexpr int NW = 1 << LR;
     using R = RoundOf<LOGS, INV, J, LR>;
-    if constexpr (J < R::NR) {
+    // bit 6 of P: exchanges by warp shuffles where a chunk's threads are
+    // lanes of one warp (not for 512-word chunks in rounds of three stages,
+    // whose 64 threads span two warps)
+    constexpr bool SHFL = (P & 64) != 0 && KIND == TK_CHUNKS && LOGS - LR <= 5;
+    if constexpr (J < R::NR && SHFL) {
+        shfl_exchange<W, LOGS, INV, J, LR>(x, tau);
+        round_bfly<W, RED, INV, LOGS, J, SMEM, LR>(x, tau, tw, kk, last_pass, tn, twn);
+        later_rounds<W, RED, INV, LOGS, KIND, WS, SMEM, J + 1, P>(x, xs, smb_k, tau, tw, kk, last_pass, tn, twn);
+    } else if constexpr (J < R::NR) {
         using RP = RoundOf<LOGS, INV, J - 1, LR>;
         // a thread's words are consecutive (round at bit 0) in the rows
         // layout: move them as 16-byte vectors

@@ -226,13 +226,28 @@ cudaError_t run_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, in
 // polynomials (the same chunk of K polynomials: one twiddle table per tile,
 // so a CTA needs less shared memory and more of them fit on an SM) when K
 // divides the batch, else they hold K consecutive chunks of one polynomial.
+//
+// The shuffle forms' chunk passes (bit 6 of P) for 4-byte words: compiled
+// in units of their own (fused_u32_<reduction>_shfl.cu), declared here.
+template <class W, int RED, bool INV, int LRB>
+cudaError_t run_chunk_pass_shfl(ntt_plan_s &p, int form, W *data, const void *tw, uint64_t ntrans, bool final_pass,
+                                cudaStream_t st, W *out, const W *pw_b);
+
 template <class W, int RED, bool INV, int LRB = 0>
 cudaError_t run_chunk_pass(ntt_plan_s &p, int form, W *data, const void *tw, uint64_t ntrans, bool final_pass,
                            cudaStream_t st, W *out = nullptr, const W *pw_b = nullptr) {
-    // (LRB = 16: the plan's rounds are of three stages on 8 words a thread)
-    if constexpr (LRB == 0) {
-        if (p.lr == 3) return run_chunk_pass<W, RED, INV, 16>(p, form, data, tw, ntrans, final_pass, st, out, pw_b);
+    // (LRB = 16: the plan's rounds are of three stages on 8 words a thread;
+    // + 64: exchanges by warp shuffles)
+    if constexpr ((LRB & 16) == 0) {
+        if (p.lr == 3)
+            return run_chunk_pass<W, RED, INV, LRB | 16>(p, form, data, tw, ntrans, final_pass, st, out, pw_b);
     }
+    if constexpr ((LRB & 64) == 0 && sizeof(W) == 4) {
+        if (form_is_shfl(form) && !p.tw_otf)
+            return run_chunk_pass_shfl<W, RED, INV, LRB | 64>(p, form == FORM_SMALL_SHFL ? FORM_SMALL : FORM_WIDE,
+                                                              data, tw, ntrans, final_pass, st, out, pw_b);
+    }
+    if (form_is_shfl(form)) form = form == FORM_SMALL_SHFL ? FORM_SMALL : FORM_WIDE;
     const int logS = (int)p.s2;
     // pairing needs K | batch, and chunks of at least 256 words (each
     // polynomial's box of swizzled rows then starts on a 1 KiB boundary)
@@ -258,6 +273,14 @@ cudaError_t run_chunk_pass(ntt_plan_s &p, int form, W *data, const void *tw, uin
                ? run_pass<W, RED, INV, TK_CHUNKS, LRB | 11>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b)
                : run_pass<W, RED, INV, TK_CHUNKS, LRB | 3>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b);
 }
+
+#ifdef NTTGB_SHFL_UNIT
+template <class W, int RED, bool INV, int LRB>
+cudaError_t run_chunk_pass_shfl(ntt_plan_s &p, int form, W *data, const void *tw, uint64_t ntrans, bool final_pass,
+                                cudaStream_t st, W *out, const W *pw_b) {
+    return run_chunk_pass<W, RED, INV, LRB>(p, form, data, tw, ntrans, final_pass, st, out, pw_b);
+}
+#endif
 
 // Tuning of the one-launch two-pass form: tiles per work item and the lag
 // (in rounds of one limb) between a limb's first and second pass; unset or

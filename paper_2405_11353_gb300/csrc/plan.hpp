@@ -13,8 +13,11 @@ namespace nttgb {
 enum FusedMode : int { FUSED_STAGES = 0, FUSED_SINGLE = 1, FUSED_TWO_PASS = 2, FUSED_CLUSTER = 3 };
 // Forms of a two-pass direction: chunk pass on one-warp CTAs (2-chunk
 // tiles), on 256-thread CTAs (16-chunk tiles), or both passes in one
-// streamed launch.
-enum TwoPassForm : int { FORM_SMALL = 0, FORM_WIDE = 1, FORM_STREAMED = 2 };
+// streamed launch; the first two again with the chunk pass's exchanges
+// between rounds by warp shuffles (4-byte words, table twiddles).
+enum TwoPassForm : int { FORM_SMALL = 0, FORM_WIDE = 1, FORM_STREAMED = 2, FORM_SMALL_SHFL = 3, FORM_WIDE_SHFL = 4 };
+constexpr int kForms = 5;
+inline bool form_is_shfl(int f) { return f == FORM_SMALL_SHFL || f == FORM_WIDE_SHFL; }
 
 // Largest transform done in one pass of the fused kernel (one CTA holds the
 // whole transform in shared memory): 2^14 words of 4 bytes, 2^13 of 8.
@@ -97,7 +100,9 @@ struct ntt_plan_s {
         // (the streamed form exists for 256-word chunks in rounds of four
         // stages, not with NTT_TW_OTF)
         const bool stream_ok = !tw_otf && s2 == (uint32_t)nttgb::kChunkLog && lr == 4;
-        if (t >= 0 && (t != nttgb::FORM_STREAMED || stream_ok)) return t;
+        // (the shuffle forms: 4-byte words and twiddle tables)
+        const bool shfl_ok = !tw_otf && !word64;
+        if (t >= 0 && (t != nttgb::FORM_STREAMED || stream_ok) && (!nttgb::form_is_shfl(t) || shfl_ok)) return t;
         if (streamed && stream_ok) return nttgb::FORM_STREAMED;
         return inverse ? nttgb::FORM_WIDE : nttgb::FORM_SMALL;
     }

@@ -20,9 +20,9 @@
 //     integer of magnitude <= 2^24: exactly representable, so fp32
 //     accumulation loses nothing, in any order -- ASSUMING the tensor core
 //     adds with a full 24-bit fp32 significand.  The instruction set does not
-//     state the internal precision of the accumulation; the tests that drive
-//     every diagonal to its extreme (all digits -128, or +127) are what
-//     guard this.
+//     state the internal precision of the accumulation; bit-exact results on
+//     data words whose digits sit at the ends of their range (-128 and +127),
+//     against the matrices of many primes, are the evidence for it.
 //   * The epilogue reads the diagonals back (tcgen05.ld), recombines
 //     sum_s D_s (2^(8 s) mod q) in 64-bit integers (|.| < 7 2^24 q < 2^57),
 //     adds a multiple of q above 2^57 to make it positive and reduces mod q

@@ -10,7 +10,9 @@
 //   * per direction (forward, or inverse with or without the fused
 //     product) and batch bucket floor(log2 batch), the form: the chunk pass
 //     on one-warp CTAs, on 256-thread CTAs, or both passes in one streamed
-//     launch (stream.cuh; 256-word chunks only, not with NTT_TW_OTF).
+//     launch (stream.cuh; 256-word chunks only, not with NTT_TW_OTF), and
+//     the first two again with the chunk pass's exchanges between rounds by
+//     warp shuffles (4-byte words, twiddle tables).
 // ntt_autotune times every valid (radix, split) with every form of both
 // directions on the current device and records, per (radix, split), the
 // fastest form of each direction for the batch's bucket, and for the shape
@@ -44,7 +46,7 @@ struct TuneKey {
 };
 struct TuneVal {
     int form[2];
-    float ms[2][3];
+    float ms[2][kForms];
 };
 // shape (a TuneKey without bucket, split and radix) -> chosen split, radix
 struct ShapeVal {
@@ -66,6 +68,25 @@ uint32_t bucket_of(uint32_t batch) {
     uint32_t b = 0;
     while (b < 31 && (2u << b) <= batch) ++b;
     return b;
+}
+
+// The numbers of the JSON array after `key` (at most kForms; the rest -1).
+int read_ms(const char *line, const char *key, float *ms) {
+    for (int f = 0; f < kForms; ++f) ms[f] = -1.f;
+    const char *s = std::strstr(line, key);
+    if (!s || !(s = std::strchr(s, '['))) return 0;
+    ++s;
+    int n = 0;
+    while (n < kForms) {
+        char *end = nullptr;
+        const float v = std::strtof(s, &end);
+        if (end == s) break;
+        ms[n++] = v;
+        s = end;
+        while (*s == ' ' || *s == ',') ++s;
+        if (*s == ']') break;
+    }
+    return n;
 }
 
 void load_locked() {
@@ -90,47 +111,44 @@ void load_locked() {
                 g_split[sk] = ShapeVal{split, lr};
             continue;
         }
+        // the fixed fields, in the newest layout first, then in those of
+        // older tables: before the radix field (rounds of four), before the
+        // split field (256-word chunks), before the twiddle-mode field
+        // (table twiddles)
         k.lr = 4;
         int n = std::sscanf(line,
                             "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
                             "\"tw_otf\": %u, \"chunk_log2\": %u, \"radix_log2\": %u, \"batch_log2\": %u, "
-                            "\"forward_form\": %d, \"inverse_form\": %d, \"forward_ms\": [%f, %f, %f], "
-                            "\"inverse_ms\": [%f, %f, %f]}",
+                            "\"forward_form\": %d, \"inverse_form\": %d,",
                             &k.N, &k.word, &k.L, &k.red, &k.bitrev, &k.otf, &k.split, &k.lr, &k.bucket, &v.form[0],
-                            &v.form[1], &v.ms[0][0], &v.ms[0][1], &v.ms[0][2], &v.ms[1][0], &v.ms[1][1], &v.ms[1][2]);
-        n -= 1;                 // the radix field: 16 values in all when it was read
-        if (n != 16) {
-            // lines written before the radix field existed: rounds of four
+                            &v.form[1]);
+        if (n != 11) {
             k.lr = 4;
-            n = std::sscanf(line,
-                            "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
-                            "\"tw_otf\": %u, \"chunk_log2\": %u, \"batch_log2\": %u, \"forward_form\": %d, "
-                            "\"inverse_form\": %d, \"forward_ms\": [%f, %f, %f], \"inverse_ms\": [%f, %f, %f]}",
-                            &k.N, &k.word, &k.L, &k.red, &k.bitrev, &k.otf, &k.split, &k.bucket, &v.form[0],
-                            &v.form[1], &v.ms[0][0], &v.ms[0][1], &v.ms[0][2], &v.ms[1][0], &v.ms[1][1], &v.ms[1][2]);
-        }
-        if (n != 16) {
-            // lines written before the split field existed: 256-word chunks
-            k.split = (uint32_t)kChunkLog;
             n = 1 + std::sscanf(line,
                                 "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
-                                "\"tw_otf\": %u, \"batch_log2\": %u, \"forward_form\": %d, \"inverse_form\": %d, "
-                                "\"forward_ms\": [%f, %f, %f], \"inverse_ms\": [%f, %f, %f]}",
-                                &k.N, &k.word, &k.L, &k.red, &k.bitrev, &k.otf, &k.bucket, &v.form[0], &v.form[1],
-                                &v.ms[0][0], &v.ms[0][1], &v.ms[0][2], &v.ms[1][0], &v.ms[1][1], &v.ms[1][2]);
+                                "\"tw_otf\": %u, \"chunk_log2\": %u, \"batch_log2\": %u, \"forward_form\": %d, "
+                                "\"inverse_form\": %d,",
+                                &k.N, &k.word, &k.L, &k.red, &k.bitrev, &k.otf, &k.split, &k.bucket, &v.form[0],
+                                &v.form[1]);
         }
-        if (n != 16) {
-            // and before the twiddle-mode field: table twiddles
-            k.otf = 0;
+        if (n != 11) {
+            k.split = (uint32_t)kChunkLog;
             n = 2 + std::sscanf(line,
                                 "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
-                                "\"batch_log2\": %u, \"forward_form\": %d, \"inverse_form\": %d, "
-                                "\"forward_ms\": [%f, %f, %f], \"inverse_ms\": [%f, %f, %f]}",
-                                &k.N, &k.word, &k.L, &k.red, &k.bitrev, &k.bucket, &v.form[0], &v.form[1],
-                                &v.ms[0][0], &v.ms[0][1], &v.ms[0][2], &v.ms[1][0], &v.ms[1][1], &v.ms[1][2]);
+                                "\"tw_otf\": %u, \"batch_log2\": %u, \"forward_form\": %d, \"inverse_form\": %d,",
+                                &k.N, &k.word, &k.L, &k.red, &k.bitrev, &k.otf, &k.bucket, &v.form[0], &v.form[1]);
         }
-        if (n != 16 || k.bucket > 31 || k.otf > 1 || v.form[0] < 0 || v.form[0] > 2 || v.form[1] < 0 ||
-            v.form[1] > 2 || k.split < (uint32_t)kChunkLogMin || k.split > (uint32_t)kChunkLogMax ||
+        if (n != 11) {
+            k.otf = 0;
+            n = 3 + std::sscanf(line,
+                                "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
+                                "\"batch_log2\": %u, \"forward_form\": %d, \"inverse_form\": %d,",
+                                &k.N, &k.word, &k.L, &k.red, &k.bitrev, &k.bucket, &v.form[0], &v.form[1]);
+        }
+        // the per-form times: five forms, or the first three in older tables
+        if (n != 11 || read_ms(line, "\"forward_ms\"", v.ms[0]) < 3 || read_ms(line, "\"inverse_ms\"", v.ms[1]) < 3 ||
+            k.bucket > 31 || k.otf > 1 || v.form[0] < 0 || v.form[0] >= kForms || v.form[1] < 0 ||
+            v.form[1] >= kForms || k.split < (uint32_t)kChunkLogMin || k.split > (uint32_t)kChunkLogMax ||
             (k.lr != 3 && k.lr != 4))
             continue;
         g_table[k] = v;
@@ -156,10 +174,11 @@ void save_locked() {
         std::fprintf(f,
                      "{\"N\": %u, \"word_bytes\": %u, \"L\": %u, \"reduction\": %u, \"bitrev\": %u, "
                      "\"tw_otf\": %u, \"chunk_log2\": %u, \"radix_log2\": %u, \"batch_log2\": %u, "
-                     "\"forward_form\": %d, \"inverse_form\": %d, \"forward_ms\": [%.6f, %.6f, %.6f], "
-                     "\"inverse_ms\": [%.6f, %.6f, %.6f]}\n",
+                     "\"forward_form\": %d, \"inverse_form\": %d, \"forward_ms\": [%.6f, %.6f, %.6f, %.6f, %.6f], "
+                     "\"inverse_ms\": [%.6f, %.6f, %.6f, %.6f, %.6f]}\n",
                      k.N, k.word, k.L, k.red, k.bitrev, k.otf, k.split, k.lr, k.bucket, v.form[0], v.form[1],
-                     v.ms[0][0], v.ms[0][1], v.ms[0][2], v.ms[1][0], v.ms[1][1], v.ms[1][2]);
+                     v.ms[0][0], v.ms[0][1], v.ms[0][2], v.ms[0][3], v.ms[0][4], v.ms[1][0], v.ms[1][1], v.ms[1][2],
+                     v.ms[1][3], v.ms[1][4]);
     }
     std::fclose(f);
 }
@@ -248,8 +267,9 @@ ntt_status ntt_autotune(uint32_t N, const uint64_t *q, uint32_t L, uint32_t flag
         if (nttgb::create_plan(&p, N, q, L, NTT_FUSED, flags, nullptr, -1, (int)s2, (int)lr) != NTT_OK) continue;
         nttgb::TuneVal &v = vals[ci];
         for (int dir = 0; dir < 2 && ok; ++dir) {
-            for (int form = 0; form < 3 && ok; ++form) {
-                if (form == nttgb::FORM_STREAMED && (p->tw_otf || s2 != (uint32_t)nttgb::kChunkLog || lr != 4)) {
+            for (int form = 0; form < nttgb::kForms && ok; ++form) {
+                if ((form == nttgb::FORM_STREAMED && (p->tw_otf || s2 != (uint32_t)nttgb::kChunkLog || lr != 4)) ||
+                    (nttgb::form_is_shfl(form) && (p->tw_otf || p->word64))) {
                     v.ms[dir][form] = -1.f;
                     continue;
                 }
@@ -272,7 +292,7 @@ ntt_status ntt_autotune(uint32_t N, const uint64_t *q, uint32_t L, uint32_t flag
                 v.ms[dir][form] = ms / (float)reps;
             }
             int bf = 0;
-            for (int form = 1; form < 3; ++form)
+            for (int form = 1; form < nttgb::kForms; ++form)
                 if (v.ms[dir][form] >= 0.f && v.ms[dir][form] < v.ms[dir][bf]) bf = form;
             v.form[dir] = bf;
         }
@@ -307,7 +327,7 @@ ntt_status ntt_autotune(uint32_t N, const uint64_t *q, uint32_t L, uint32_t flag
     }
     if (result) {
         const nttgb::TuneVal &v = vals[best];
-        for (int f = 0; f < 3; ++f) {
+        for (int f = 0; f < nttgb::kForms; ++f) {
             result->forward_ms[f] = v.ms[0][f];
             result->inverse_ms[f] = v.ms[1][f];
         }
@@ -342,13 +362,14 @@ nttgb::TuneKey key_from_shape(const nttgb::ShapeKey &sk, uint32_t batch, nttgb::
 
 ntt_status ntt_tune_set(uint32_t N, uint32_t L, uint32_t flags, uint32_t batch, int32_t forward_form,
                         int32_t inverse_form) {
-    if (batch == 0 || L == 0 || forward_form < 0 || forward_form > 2 || inverse_form < 0 || inverse_form > 2)
+    if (batch == 0 || L == 0 || forward_form < 0 || forward_form >= nttgb::kForms || inverse_form < 0 ||
+        inverse_form >= nttgb::kForms)
         return NTT_ERR_INVALID_ARG;
     nttgb::TuneVal v;
     v.form[0] = forward_form;
     v.form[1] = inverse_form;
     for (int d = 0; d < 2; ++d)
-        for (int f = 0; f < 3; ++f) v.ms[d][f] = -1.f;      // set by hand, not timed
+        for (int f = 0; f < nttgb::kForms; ++f) v.ms[d][f] = -1.f;      // set by hand, not timed
     std::lock_guard<std::mutex> g(nttgb::g_mu);
     nttgb::load_locked();
     const nttgb::ShapeKey sk = shape_from_flags(N, L, flags);

@@ -91,24 +91,29 @@ def test_tc_matches_butterfly_form_and_natural_order(nt, orc):
 
 @pytest.mark.parametrize("form", FORMS)
 def test_tc_extreme_inputs(nt, orc, form):
-    """Words that put the digits at their extremes: q - 1 (unsigned digits
-    all large), 0x3F7F7F80 (balanced digits -128, -128, -128, 64), 0 and
-    alternating patterns, forward and back."""
+    """Words that put the digits at their extremes, against the matrices of
+    12 primes: q - 1 (unsigned digits all large), 0x3F7F7F80 (balanced
+    digits -128, -128, -128, 64), 0x3F7F7F7F (127, 127, 127, 63: the
+    largest positive digits a word below 2^30 has), 0 and alternating
+    patterns, forward and back.  The fp32 accumulation in the tensor core is
+    exact only if it keeps 24 significand bits; this is the check."""
     N = 1 << 16
-    qs = orc.find_primes(30, 17, 4)
-    h = np.zeros((2, 4, N), np.uint64)
+    qs = orc.find_primes(30, 17, 12)
+    h = np.zeros((3, 12, N), np.uint64)
     for l, q in enumerate(qs):
         h[0, l] = q - 1
         h[1, l, 0::2] = 0x3F7F7F80 % q
         h[1, l, 1::4] = 0
         h[1, l, 3::4] = 0x00808080
+        h[2, l] = 0x3F7F7F7F % q
+        h[2, l, 1::3] = 0x3F7F7F80 % q
     p = nt.ntt_plan_create(N, qs, nt.NTT_TC_FOURSTEP, nt.NTT_ORDER_BITREV | form_flags(nt, form))
     try:
         d = dev(h)
-        nt.ntt_forward(p, d, 2)
+        nt.ntt_forward(p, d, 3)
         psis = [orc.psi(q, N) for q in qs]
         assert np.array_equal(host(d, h.shape), bitrev_rows(orc.ntt_batch(h, qs, psis), orc))
-        nt.ntt_inverse(p, d, 2)
+        nt.ntt_inverse(p, d, 3)
         assert np.array_equal(host(d, h.shape), h)
     finally:
         nt.ntt_plan_destroy(p)

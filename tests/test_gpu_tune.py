@@ -38,6 +38,8 @@ def bitrev_rows(X, orc):
 
 @pytest.mark.parametrize("n,w64", [(16, False), (15, True)])
 def test_every_form_pair_bit_exact(nt, orc, n, w64):
+    """Every (forward, inverse) pair of the five forms; 8-byte plans take
+    the shuffle forms as their shared-memory defaults."""
     N, L, pairs = 1 << n, 3, 2
     qs = orc.find_primes(60 if w64 else 30, 18, L)
     psis = [orc.psi(q, N) for q in qs]
@@ -46,14 +48,15 @@ def test_every_form_pair_bit_exact(nt, orc, n, w64):
     want_prod = orc.ntt_batch(orc.pointwise_batch(A[:pairs], A[pairs:], qs), qs, psis, inverse=True)
     flags = nt.NTT_ORDER_BITREV | (nt.NTT_WORD64 if w64 else 0)
     try:
-        for fwd in range(3):
-            for inv in range(3):
+        shfl = (nt.NTT_FORM_SMALL_SHFL, nt.NTT_FORM_WIDE_SHFL)
+        for fwd in range(5):
+            for inv in range(5):
                 nt.ntt_tune_set(N, L, flags, 2 * pairs, fwd, inv)     # forward batch
                 nt.ntt_tune_set(N, L, flags, pairs, fwd, inv)         # product batch
                 p = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, flags)
                 try:
-                    assert nt.ntt_plan_form(p, 2 * pairs) == fwd
-                    assert nt.ntt_plan_form(p, pairs, True) == inv
+                    assert nt.ntt_plan_form(p, 2 * pairs) == (nt.NTT_FORM_SMALL if w64 and fwd in shfl else fwd)
+                    assert nt.ntt_plan_form(p, pairs, True) == (nt.NTT_FORM_WIDE if w64 and inv in shfl else inv)
                     d = to_dev(host, w64)
                     nt.ntt_forward(p, d, 2 * pairs)
                     assert nt.ntt_plan_last_launches(p) == (1 if fwd == 2 else 2)
@@ -77,7 +80,7 @@ def test_autotune_records_forms_the_next_plan_uses(nt, orc):
     flags = nt.NTT_ORDER_BITREV
     try:
         r = nt.ntt_autotune(N, qs, flags, batch)
-        assert r["forward_form"] in (0, 1, 2) and r["inverse_form"] in (0, 1, 2)
+        assert r["forward_form"] in range(5) and r["inverse_form"] in range(5)
         # splits 2^7 x 2^9, 2^8 x 2^8, 2^9 x 2^7 and both radices are all
         # valid at N = 2^16; the chosen pair has the smallest forward +
         # inverse time
@@ -88,7 +91,7 @@ def test_autotune_records_forms_the_next_plan_uses(nt, orc):
         # (the streamed form exists only with 256-word chunks and radix 16)
         streamed_ok = r["chunk_log2"] == 8 and r["radix_log2"] == 4
         for ms in (r["forward_ms"], r["inverse_ms"]):
-            assert all(v > 0 for v in ms[:2]) and (ms[2] > 0) == streamed_ok
+            assert len(ms) == 5 and all(v > 0 for v in ms[:2] + ms[3:]) and (ms[2] > 0) == streamed_ok
         assert r["forward_ms"][r["forward_form"]] == min(v for v in r["forward_ms"] if v > 0)
         assert nt.ntt_tune_get_split(N, L, flags) == (r["chunk_log2"], r["radix_log2"])
         assert nt.ntt_tune_get(N, L, flags, batch) == r["forward_form"]
@@ -120,22 +123,27 @@ SPLITS = [(15, False, (7, 8, 9)), (16, False, (7, 8, 9)), (17, False, (8, 9)), (
           (16, True, (7, 8, 9))]
 
 
+@pytest.mark.parametrize("shfl", [False, True])
 @pytest.mark.parametrize("radix", [4, 3])
 @pytest.mark.parametrize("n,w64,splits", SPLITS)
-def test_every_split_bit_exact(nt, orc, n, w64, splits, radix):
+def test_every_split_bit_exact(nt, orc, n, w64, splits, radix, shfl):
     """Every split N = 2^s1 x 2^s2 a size takes, in both radices (rounds of
     four stages on 16 words a thread, or three on 8), with both chunk-pass
-    forms, batches whose tiles pair polynomials and batches that do not:
-    forward, the product fused into the inverse, and the inverse,
+    forms -- with shared-memory exchanges, and (4-byte words) with warp
+    shuffles --, batches whose tiles pair polynomials and batches that do
+    not: forward, the product fused into the inverse, and the inverse,
     bit-exact."""
+    if shfl and w64:
+        pytest.skip("the shuffle forms are for 4-byte words")
     N, L = 1 << n, 3
     qs = orc.find_primes(60 if w64 else 30, 18, L)
     psis = [orc.psi(q, N) for q in qs]
     flags = nt.NTT_ORDER_BITREV | (nt.NTT_WORD64 if w64 else 0)
     try:
         for s2 in splits:
-            for batch, form in ((4, nt.NTT_FORM_SMALL), (3, nt.NTT_FORM_WIDE), (16, nt.NTT_FORM_WIDE),
-                                (2, nt.NTT_FORM_SMALL)):
+            small, wide = ((nt.NTT_FORM_SMALL_SHFL, nt.NTT_FORM_WIDE_SHFL) if shfl
+                           else (nt.NTT_FORM_SMALL, nt.NTT_FORM_WIDE))
+            for batch, form in ((4, small), (3, wide), (16, wide), (2, small)):
                 nt.ntt_tune_clear()
                 nt.ntt_tune_set_split(N, L, flags, s2, radix)
                 nt.ntt_tune_set(N, L, flags, batch, form, form)
@@ -163,6 +171,47 @@ def test_every_split_bit_exact(nt, orc, n, w64, splits, radix):
                     assert nt.ntt_get_device_status(p) == nt.NTT_OK
                 finally:
                     nt.ntt_plan_destroy(p)
+    finally:
+        nt.ntt_tune_clear()
+
+
+@pytest.mark.parametrize("red", ["barrett", "montgomery"])
+@pytest.mark.parametrize("radix", [4, 3])
+def test_shuffle_forms_other_reductions(nt, orc, red, radix):
+    """The shuffle forms with Barrett and Montgomery twiddles (each has its
+    own kernels): forward, product + inverse and inverse against the
+    oracle, paired and unpaired tiles."""
+    N, L = 1 << 16, 3
+    qs = orc.find_primes(30, 17, L)
+    psis = [orc.psi(q, N) for q in qs]
+    flags = nt.NTT_ORDER_BITREV | (nt.NTT_RED_BARRETT if red == "barrett" else nt.NTT_RED_MONTGOMERY)
+    try:
+        for batch, fwd, inv in ((4, nt.NTT_FORM_SMALL_SHFL, nt.NTT_FORM_WIDE_SHFL),
+                                (3, nt.NTT_FORM_WIDE_SHFL, nt.NTT_FORM_SMALL_SHFL)):
+            nt.ntt_tune_clear()
+            nt.ntt_tune_set_split(N, L, flags, 8, radix)
+            nt.ntt_tune_set(N, L, flags, batch, fwd, inv)
+            pairs = batch // 2
+            nt.ntt_tune_set(N, L, flags, pairs, fwd, inv)
+            host = ntt_synth.rns_batch(2500 + batch + 10 * radix, qs, N, batch)
+            A = orc.ntt_batch(host, qs, psis)
+            p = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, flags)
+            try:
+                assert (nt.ntt_plan_form(p, batch), nt.ntt_plan_form(p, pairs, True)) == (fwd, inv)
+                d = to_dev(host, False)
+                nt.ntt_forward(p, d, batch)
+                assert np.array_equal(to_host(d, False, host.shape), bitrev_rows(A, orc)), batch
+                want = orc.ntt_batch(orc.pointwise_batch(A[:pairs], A[pairs:2 * pairs], qs), qs, psis,
+                                     inverse=True)
+                half = pairs * L * N
+                c = torch.empty_like(d[:half])
+                nt.ntt_pointwise_inverse(p, c, d[:half], d[half:2 * half], pairs)
+                assert np.array_equal(to_host(c, False, (pairs, L, N)), want), batch
+                nt.ntt_inverse(p, d, batch)
+                assert np.array_equal(to_host(d, False, host.shape), host), batch
+                assert nt.ntt_get_device_status(p) == nt.NTT_OK
+            finally:
+                nt.ntt_plan_destroy(p)
     finally:
         nt.ntt_tune_clear()
 

@@ -50,7 +50,7 @@ def test_tune_table_set_get_persist(nt, tmp_path):
 
 
 def test_tune_set_rejects_bad_forms(nt):
-    for fwd, inv, batch in [(3, 0, 4), (0, -1, 4), (0, 0, 0)]:
+    for fwd, inv, batch in [(5, 0, 4), (0, -1, 4), (0, 0, 0), (1, 5, 4)]:
         with pytest.raises(nt.NttError):
             nt.ntt_tune_set(1 << 16, 2, 0, batch, fwd, inv)
 
@@ -119,3 +119,28 @@ def test_split_table_set_get_persist(nt, tmp_path):
                "nt.ntt_tune_clear()\n"
                "print(*nt.ntt_tune_get_split(1 << 16, 3, f))\n", db)
     assert out.split() == ["9", "3", "0", "-1", "-1"]
+
+
+def test_shuffle_forms_set_get_persist(nt, tmp_path):
+    """The shuffle forms (3, 4) are recorded, written with five per-form
+    times, and read back by a fresh process beside a three-time line."""
+    db = str(tmp_path / "tune.jsonl")
+    with open(db, "w") as f:
+        f.write('{"N": 65536, "word_bytes": 4, "L": 7, "reduction": 0, "bitrev": 1, "tw_otf": 0, '
+                '"chunk_log2": 8, "radix_log2": 4, "batch_log2": 3, "forward_form": 2, "inverse_form": 1, '
+                '"forward_ms": [-1.0, -1.0, -1.0], "inverse_ms": [-1.0, -1.0, -1.0]}\n')
+    out = _run("import paper_2405_11353_gb300 as nt\n"
+               "f = nt.NTT_ORDER_BITREV\n"
+               "nt.ntt_tune_set(1 << 16, 6, f, 4, nt.NTT_FORM_SMALL_SHFL, nt.NTT_FORM_WIDE_SHFL)\n"
+               "print(nt.ntt_tune_get(1 << 16, 6, f, 4), nt.ntt_tune_get(1 << 16, 6, f, 4, True),\n"
+               "      nt.ntt_tune_get(1 << 16, 7, f, 8))\n", db)
+    assert out.split() == ["3", "4", "2"]
+    rows = [json.loads(x) for x in open(db)]
+    row = [r for r in rows if r["L"] == 6][0]
+    assert (row["forward_form"], row["inverse_form"]) == (3, 4)
+    assert len(row["forward_ms"]) == 5 and len(row["inverse_ms"]) == 5
+    out = _run("import paper_2405_11353_gb300 as nt\n"
+               "f = nt.NTT_ORDER_BITREV\n"
+               "print(nt.ntt_tune_get(1 << 16, 6, f, 4), nt.ntt_tune_get(1 << 16, 6, f, 4, True),\n"
+               "      nt.ntt_tune_get(1 << 16, 7, f, 8, True))\n", db)
+    assert out.split() == ["3", "4", "1"]
