@@ -6,9 +6,9 @@
 // all jobs of a group share twiddle tables.  Transforms of 2^12 words run in
 // one pass, larger ones in two (column strips of N/256 rows, then 256-word
 // chunks).  The work is cut into items of a few tiles each, ordered by phase
-// (see ragged.hpp), and one cooperative launch of the persistent kernel --
-// preceded by zeroing the item counters -- is captured into a CUDA graph
-// that ntt_ragged_launch replays.  Like the fused plans it works in the
+// (see ragged.hpp), and the cooperative launches of the persistent kernels
+// -- one per word size present, preceded by zeroing the item counters --
+// are captured into a CUDA graph that ntt_ragged_launch replays.  Like the fused plans it works in the
 // bit-reversed evaluation order (NTT_ORDER_BITREV is required).
 #include <cuda_runtime.h>
 
@@ -26,14 +26,15 @@ using namespace nttgb;
 
 struct ntt_ragged_s {
     std::vector<ntt_plan_t> plans;
-    RaggedArgs args{};
+    RaggedArgs args[2]{};        // per word size (4-byte, 8-byte items)
+    uint32_t n_word_items[2] = {0, 0};
     void *d_jobs = nullptr, *d_tmaps = nullptr, *d_items = nullptr, *d_words = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint32_t n_items = 0, n_jobs = 0;
     uint32_t item_tiles = 0;     // tiles per work item (tuned with NTT_RAGGED_TUNE)
     int red = 0;
-    unsigned grid = 0;
+    unsigned grid[2] = {0, 0};
 };
 
 namespace {
@@ -52,20 +53,42 @@ void ragged_free(ntt_ragged_s *r) {
     delete r;
 }
 
-cudaError_t kernel_config(int red, size_t *smem, int *bps) {
+template <class W> cudaError_t kernel_config_w(int red, size_t *smem, int *bps) {
     switch (red) {
-    case RED_SHOUP: return ragged_kernel_config<RED_SHOUP>(smem, bps);
-    case RED_BARRETT: return ragged_kernel_config<RED_BARRETT>(smem, bps);
-    default: return ragged_kernel_config<RED_MONTGOMERY>(smem, bps);
+    case RED_SHOUP: return ragged_kernel_config<RED_SHOUP, W>(smem, bps);
+    case RED_BARRETT: return ragged_kernel_config<RED_BARRETT, W>(smem, bps);
+    default: return ragged_kernel_config<RED_MONTGOMERY, W>(smem, bps);
+    }
+}
+cudaError_t kernel_config(int red, bool w64, size_t *smem, int *bps) {
+    return w64 ? kernel_config_w<uint64_t>(red, smem, bps) : kernel_config_w<uint32_t>(red, smem, bps);
+}
+
+template <class W> cudaError_t kernel_launch_w(int red, const RaggedArgs &a, unsigned grid, cudaStream_t st) {
+    switch (red) {
+    case RED_SHOUP: return ragged_kernel_launch<RED_SHOUP, W>(a, grid, st);
+    case RED_BARRETT: return ragged_kernel_launch<RED_BARRETT, W>(a, grid, st);
+    default: return ragged_kernel_launch<RED_MONTGOMERY, W>(a, grid, st);
     }
 }
 
-cudaError_t kernel_launch(int red, const RaggedArgs &a, unsigned grid, cudaStream_t st) {
-    switch (red) {
-    case RED_SHOUP: return ragged_kernel_launch<RED_SHOUP>(a, grid, st);
-    case RED_BARRETT: return ragged_kernel_launch<RED_BARRETT>(a, grid, st);
-    default: return ragged_kernel_launch<RED_MONTGOMERY>(a, grid, st);
+// Device words of a ragged batch: per word-size kernel w its 4 item counters
+// (words 5 w .. 5 w + 3) and grid-barrier arrival count (5 w + 4), then the
+// shared abort flag -- the 11 words zeroed before every launch -- then the
+// barrier generations (11, 12) and the status word (13).
+constexpr uint32_t kRwZeroed = 11, kRwAbort = 10, kRwGen = 11, kRwStatus = 13, kRwWords = 16;
+
+// One replay's work on stream st: zero the counters, then the kernel of
+// each word size that has items.
+cudaError_t launch_all(const ntt_ragged_s *r, cudaStream_t st) {
+    uint32_t *w = reinterpret_cast<uint32_t *>(r->d_words);
+    cudaError_t e = cudaMemsetAsync(w, 0, kRwZeroed * sizeof(uint32_t), st);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        if (r->n_word_items[k] == 0) continue;
+        e = k == 0 ? kernel_launch_w<uint32_t>(r->red, r->args[0], r->grid[0], st)
+                   : kernel_launch_w<uint64_t>(r->red, r->args[1], r->grid[1], st);
     }
+    return e;
 }
 
 }  // namespace
@@ -79,7 +102,7 @@ ntt_status build_items(ntt_ragged_s *r, const ntt_job *jobs, uint32_t n_jobs, Da
     std::vector<RJob> rj(n_jobs);
     std::vector<CUtensorMap> maps(2 * (size_t)n_jobs);
     std::memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
-    std::vector<RItem> items[4];
+    std::vector<RItem> items[2][4];   // [word size][phase]
     for (uint32_t j = 0; j < n_jobs; ++j) {
         const ntt_job &J = jobs[j];
         ntt_plan_s &p = *plan_of(j);
@@ -94,7 +117,7 @@ ntt_status build_items(ntt_ragged_s *r, const ntt_job *jobs, uint32_t n_jobs, Da
         auto add = [&](int phase, uint32_t kind, uint64_t ntiles) {
             for (uint64_t t0 = 0; t0 < ntiles; t0 += item_tiles) {
                 uint64_t t1 = std::min<uint64_t>(ntiles, t0 + item_tiles);
-                items[phase].push_back({j, ragged_code(w64, inv, kind), (uint32_t)t0, (uint32_t)t1});
+                items[w64 ? 1 : 0][phase].push_back({j, ragged_code(w64, inv, kind), (uint32_t)t0, (uint32_t)t1});
             }
         };
         if (p.fused_mode == FUSED_SINGLE) {
@@ -115,17 +138,21 @@ ntt_status build_items(ntt_ragged_s *r, const ntt_job *jobs, uint32_t n_jobs, Da
             else { add(2, RK_CHUNKS, chunk_tiles); add(3, cols_kind, cols_tiles); }
         }
     }
+    // both kernels' items in one device array: the 4-byte kernel's, then
+    // the 8-byte kernel's, each in phase order
     std::vector<RItem> all;
-    uint32_t begin[5];
-    for (int ph = 0; ph < 4; ++ph) {
-        begin[ph] = (uint32_t)all.size();
-        // larger transforms first: items of 8-byte words and more rows cost more
-        std::stable_sort(items[ph].begin(), items[ph].end(),
-                         [&](const RItem &a, const RItem &b) { return rj[a.job].logN > rj[b.job].logN; });
-        all.insert(all.end(), items[ph].begin(), items[ph].end());
+    uint32_t begin[2][5];
+    for (int k = 0; k < 2; ++k) {
+        for (int ph = 0; ph < 4; ++ph) {
+            begin[k][ph] = (uint32_t)all.size();
+            // larger transforms first: items of more rows cost more
+            std::stable_sort(items[k][ph].begin(), items[k][ph].end(),
+                             [&](const RItem &a, const RItem &b) { return rj[a.job].logN > rj[b.job].logN; });
+            all.insert(all.end(), items[k][ph].begin(), items[k][ph].end());
+        }
+        begin[k][4] = (uint32_t)all.size();
     }
-    begin[4] = (uint32_t)all.size();
-    r->n_items = begin[4];
+    r->n_items = (uint32_t)all.size();
 
     auto up = [&](void **d, const void *h, size_t bytes) -> bool {
         if (cudaMalloc(d, bytes ? bytes : 16) != cudaSuccess) { *d = nullptr; cudaGetLastError(); return false; }
@@ -138,16 +165,19 @@ ntt_status build_items(ntt_ragged_s *r, const ntt_job *jobs, uint32_t n_jobs, Da
         !up(&r->d_items, all.data(), all.size() * sizeof(RItem)))
         return NTT_ERR_OOM;
     uint32_t *w = reinterpret_cast<uint32_t *>(r->d_words);
-    RaggedArgs &a = r->args;
-    a.jobs = reinterpret_cast<const RJob *>(r->d_jobs);
-    a.tmaps = reinterpret_cast<const CUtensorMap *>(r->d_tmaps);
-    a.items = reinterpret_cast<const RItem *>(r->d_items);
-    for (int i = 0; i < 5; ++i) a.phase_begin[i] = begin[i];
-    a.counters = w;
-    a.bar_count = w + 4;
-    a.bar_gen = w + 5;
-    a.status = w + 6;
-    a.abort_flag = w + 7;
+    for (int k = 0; k < 2; ++k) {
+        RaggedArgs &a = r->args[k];
+        a.jobs = reinterpret_cast<const RJob *>(r->d_jobs);
+        a.tmaps = reinterpret_cast<const CUtensorMap *>(r->d_tmaps);
+        a.items = reinterpret_cast<const RItem *>(r->d_items);
+        for (int i = 0; i < 5; ++i) a.phase_begin[i] = begin[k][i];
+        a.counters = w + 5 * k;
+        a.bar_count = w + 5 * k + 4;
+        a.bar_gen = w + kRwGen + k;
+        a.status = w + kRwStatus;
+        a.abort_flag = w + kRwAbort;
+        r->n_word_items[k] = begin[k][4] - begin[k][0];
+    }
     r->item_tiles = item_tiles;
     return NTT_OK;
 
@@ -207,9 +237,9 @@ ntt_status ntt_ragged_create(ntt_ragged_t *out, const ntt_job *jobs, uint32_t n_
         r->plans.push_back(g.plan);
     }
 
-    // words: 4 item counters, barrier count, barrier generation, status, abort
-    if (cudaMalloc(&r->d_words, 16 * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMemset(r->d_words, 0, 16 * sizeof(uint32_t)) != cudaSuccess) {
+    // counters, barrier words, status, abort flag (kRw*)
+    if (cudaMalloc(&r->d_words, kRwWords * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemset(r->d_words, 0, kRwWords * sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
         ragged_free(r);
         return NTT_ERR_OOM;
@@ -217,14 +247,20 @@ ntt_status ntt_ragged_create(ntt_ragged_t *out, const ntt_job *jobs, uint32_t n_
     uint32_t *w = reinterpret_cast<uint32_t *>(r->d_words);
     auto plan_of = [&](uint32_t j) { return groups[group_of[j]].plan; };
 
-    // ---- persistent grid
-    size_t smem = 0;
-    int bps = 0, dev = 0, sms = 0;
-    if (kernel_config(r->red, &smem, &bps) != cudaSuccess || bps < 1) { cudaGetLastError(); ragged_free(r); return NTT_ERR_CUDA; }
+    // ---- persistent grids: every CTA of a cooperative launch resident
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const unsigned grid = (unsigned)(sms * bps);
-    r->grid = grid;
+    for (int k = 0; k < 2; ++k) {
+        size_t smem = 0;
+        int bps = 0;
+        if (kernel_config(r->red, k == 1, &smem, &bps) != cudaSuccess || bps < 1) {
+            cudaGetLastError();
+            ragged_free(r);
+            return NTT_ERR_CUDA;
+        }
+        r->grid[k] = (unsigned)(sms * bps);
+    }
 
     // ---- autotuning of the work-item size: each candidate runs on zeroed
     // scratch copies of the jobs' buffers (same sizes; jobs that share a
@@ -252,18 +288,14 @@ ntt_status ntt_ragged_create(ntt_ragged_t *out, const ntt_job *jobs, uint32_t n_
                 return (void *)((char *)scratch + off[jobs[j].d_data]);
             };
             if (build_items(r, jobs, n_jobs, scratch_of, plan_of, kTuneItemTiles[c]) != NTT_OK) { ok = false; break; }
-            auto launch = [&]() {
-                return cudaMemsetAsync(w, 0, 5 * sizeof(uint32_t), ts) == cudaSuccess &&
-                       cudaMemsetAsync(w + 7, 0, sizeof(uint32_t), ts) == cudaSuccess &&
-                       kernel_launch(r->red, r->args, grid, ts) == cudaSuccess;
-            };
+            auto launch = [&]() { return launch_all(r, ts) == cudaSuccess; };
             float ms = 0.f;
             ok = launch() && cudaEventRecord(e0, ts) == cudaSuccess;
             for (int k = 0; k < 3 && ok; ++k) ok = launch();
             ok = ok && cudaEventRecord(e1, ts) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
                  cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
             uint32_t status = 0;
-            ok = ok && cudaMemcpy(&status, w + 6, sizeof(status), cudaMemcpyDeviceToHost) == cudaSuccess &&
+            ok = ok && cudaMemcpy(&status, w + kRwStatus, sizeof(status), cudaMemcpyDeviceToHost) == cudaSuccess &&
                  status == 0;
             if (ok && (c == 0 || ms < best_ms)) { best_ms = ms; best_tiles = kTuneItemTiles[c]; }
         }
@@ -275,19 +307,17 @@ ntt_status ntt_ragged_create(ntt_ragged_t *out, const ntt_job *jobs, uint32_t n_
     }
     ntt_status bs = build_items(r, jobs, n_jobs, [&](uint32_t j) { return jobs[j].d_data; }, plan_of, best_tiles);
     if (bs != NTT_OK) { cudaGetLastError(); ragged_free(r); return bs; }
-    r->args.stall = (flags & NTT_TEST_STALL) ? 1u : 0u;
-    const RaggedArgs &a = r->args;
+    // test hook: CTA 0 of the first kernel leaves before its first barrier
+    if (flags & NTT_TEST_STALL) r->args[r->n_word_items[0] ? 0 : 1].stall = 1u;
 
     // ---- graph capture
     cudaStream_t st;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); ragged_free(r); return NTT_ERR_CUDA; }
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        // item counters and the barrier count (a launch whose barrier wait
-        // ran out leaves arrivals behind), and the abort flag
-        cudaMemsetAsync(w, 0, 5 * sizeof(uint32_t), st);
-        cudaMemsetAsync(w + 7, 0, sizeof(uint32_t), st);
-        cudaError_t le = kernel_launch(r->red, a, grid, st);
+        // item counters and barrier counts (a launch whose barrier wait ran
+        // out leaves arrivals behind), the abort flag, then the kernels
+        cudaError_t le = launch_all(r, st);
         e = cudaStreamEndCapture(st, &r->graph);
         if (le != cudaSuccess) e = le;
     }
@@ -311,8 +341,8 @@ ntt_status ntt_ragged_status(ntt_ragged_t r, ntt_stream_t stream) {
     if (!r) return NTT_ERR_INVALID_ARG;
     if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) { cudaGetLastError(); return NTT_ERR_CUDA; }
     uint32_t v = 0;
-    if (cudaMemcpy(&v, r->args.status, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return NTT_ERR_CUDA;
-    if (v) cudaMemset(r->args.status, 0, sizeof(uint32_t));
+    if (cudaMemcpy(&v, r->args[0].status, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return NTT_ERR_CUDA;
+    if (v) cudaMemset(r->args[0].status, 0, sizeof(uint32_t));
     return (v & 2u) ? NTT_ERR_TIMEOUT : NTT_OK;
 }
 

@@ -8,8 +8,10 @@
 //   1: forward chunk passes
 //   2: inverse single-pass tiles and inverse chunk passes
 //   3: inverse column passes
-// One persistent cooperative kernel runs all phases; CTAs take items from an
-// atomic counter per phase and meet at a grid barrier between phases.
+// The items of each word size run in a persistent cooperative kernel of
+// their own (two launches in a row: the 4-byte kernel is not held to the
+// 8-byte one's registers); in each, CTAs take items from an atomic counter
+// per phase and meet at a grid barrier between phases.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -53,7 +55,8 @@ __host__ __device__ constexpr uint32_t ragged_code(bool w64, bool inv, uint32_t 
     return (w64 ? 2 * RK_KINDS : 0) + (inv ? RK_KINDS : 0) + kind;
 }
 
-template <int RED> cudaError_t ragged_kernel_launch(const RaggedArgs &a, unsigned grid, cudaStream_t st);
-template <int RED> cudaError_t ragged_kernel_config(size_t *smem, int *blocks_per_sm);
+// One persistent kernel per word size (W = uint32_t, uint64_t).
+template <int RED, class W> cudaError_t ragged_kernel_launch(const RaggedArgs &a, unsigned grid, cudaStream_t st);
+template <int RED, class W> cudaError_t ragged_kernel_config(size_t *smem, int *blocks_per_sm);
 
 }  // namespace nttgb

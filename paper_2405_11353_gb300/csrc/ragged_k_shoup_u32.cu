@@ -1,0 +1,7 @@
+// Instantiates the ragged persistent kernel for 4-byte words with RED_SHOUP.
+#include "ragged_kernel.cuh"
+
+namespace nttgb {
+template cudaError_t ragged_kernel_launch<RED_SHOUP, uint32_t>(const RaggedArgs &, unsigned, cudaStream_t);
+template cudaError_t ragged_kernel_config<RED_SHOUP, uint32_t>(size_t *, int *);
+}

@@ -20,16 +20,19 @@ template <class W, bool INV> __host__ __device__ constexpr size_t ragged_data_by
 #undef NTTGB_MAX
     return m;
 }
-__host__ __device__ constexpr size_t ragged_smem_bytes() {
-    size_t a = ragged_data_bytes_w<uint32_t, false>(), b = ragged_data_bytes_w<uint32_t, true>();
-    size_t c = ragged_data_bytes_w<uint64_t, false>(), d = ragged_data_bytes_w<uint64_t, true>();
-    size_t m = a > b ? a : b;
-    m = m > c ? m : c;
-    m = m > d ? m : d;
-    return m + 64;   // + barriers
+// Dynamic shared memory of the kernel for one word size (+ barriers).
+template <class W> __host__ __device__ constexpr size_t ragged_smem_bytes() {
+    size_t a = ragged_data_bytes_w<W, false>(), b = ragged_data_bytes_w<W, true>();
+    return (a > b ? a : b) + 64;
 }
 // barriers live at a fixed offset past the largest data footprint
-constexpr size_t kRaggedBarOffset = ((ragged_smem_bytes() - 64 - 1024) + 15) & ~size_t(15);
+template <class W> __host__ __device__ constexpr size_t ragged_bar_offset() {
+    return ((ragged_smem_bytes<W>() - 64 - 1024) + 15) & ~size_t(15);
+}
+// CTAs of 256 threads per SM the kernel is built for: three with 4-byte
+// words (73.8 KB of shared memory and at most 80 registers a thread), two
+// with 8-byte words (78.9 KB; the 64-bit butterflies take more registers).
+template <class W> __host__ __device__ constexpr int ragged_min_blocks() { return sizeof(W) == 4 ? 3 : 2; }
 
 // Grid-wide barrier of a cooperative launch: the last CTA to arrive resets
 // the count and bumps the generation; the others wait for the bump, giving
@@ -99,12 +102,13 @@ __device__ __forceinline__ bool ragged_dispatch_w(const RaggedArgs &ra, const RI
     }
 }
 
-template <int RED>
-__global__ void __launch_bounds__(256, 2) k_ragged(const __grid_constant__ RaggedArgs ra) {
+// The persistent kernel of the items of one word size W.
+template <int RED, class W>
+__global__ void __launch_bounds__(256, ragged_min_blocks<W>()) k_ragged(const __grid_constant__ RaggedArgs ra) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint32_t s_item;
     unsigned char *base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(base + kRaggedBarOffset);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + ragged_bar_offset<W>());
     if (threadIdx.x == 0) {
         for (uint32_t s = 0; s < 3; ++s) mbar_init(&bar[s], 1);
         fence_mbar_init();
@@ -121,12 +125,9 @@ __global__ void __launch_bounds__(256, 2) k_ragged(const __grid_constant__ Ragge
             const RItem it = ra.items[item];
             const uint32_t kind = it.code % RK_KINDS;
             const bool inv = (it.code / RK_KINDS) & 1u;
-            const bool w64 = it.code >= 2 * RK_KINDS;
-            bool ok;
-            if (!w64) ok = inv ? ragged_dispatch_w<uint32_t, RED, true>(ra, it, kind, base, bar, ps)
-                               : ragged_dispatch_w<uint32_t, RED, false>(ra, it, kind, base, bar, ps);
-            else ok = inv ? ragged_dispatch_w<uint64_t, RED, true>(ra, it, kind, base, bar, ps)
-                          : ragged_dispatch_w<uint64_t, RED, false>(ra, it, kind, base, bar, ps);
+            // (the host gives this kernel the items of its word size only)
+            const bool ok = inv ? ragged_dispatch_w<W, RED, true>(ra, it, kind, base, bar, ps)
+                                : ragged_dispatch_w<W, RED, false>(ra, it, kind, base, bar, ps);
             if (!ok) {
                 if (threadIdx.x == 0) atomicExch(ra.abort_flag, 1u);
                 break;
@@ -143,30 +144,30 @@ __global__ void __launch_bounds__(256, 2) k_ragged(const __grid_constant__ Ragge
     }
 }
 
-template <int RED> cudaError_t ragged_kernel_config(size_t *smem, int *blocks_per_sm) {
-    *smem = ragged_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(k_ragged<RED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+template <int RED, class W> cudaError_t ragged_kernel_config(size_t *smem, int *blocks_per_sm) {
+    *smem = ragged_smem_bytes<W>();
+    cudaError_t e = cudaFuncSetAttribute(k_ragged<RED, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_ragged<RED>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(k_ragged<RED, W>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_ragged<RED>, 256, *smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_ragged<RED, W>, 256, *smem);
 }
 
 // Cooperative launch: every CTA is resident, so the grid barrier cannot
 // wait on a CTA that has not started.
-template <int RED> cudaError_t ragged_kernel_launch(const RaggedArgs &a, unsigned grid, cudaStream_t st) {
+template <int RED, class W> cudaError_t ragged_kernel_launch(const RaggedArgs &a, unsigned grid, cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = ragged_smem_bytes();
+    cfg.dynamicSmemBytes = ragged_smem_bytes<W>();
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_ragged<RED>, a);
+    return cudaLaunchKernelEx(&cfg, k_ragged<RED, W>, a);
 }
 
 }  // namespace nttgb
