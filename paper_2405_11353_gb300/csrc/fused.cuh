@@ -1060,12 +1060,14 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
 
 // Per-plan fused pass: CTA c processes tiles [c T / G, (c+1) T / G).
 // PP: the tile configuration (see tile_k): 0, or 3 for 16-chunk tiles.
-// Launch bounds: inverse column passes of up to 256 points with 4-byte
-// words (512 threads) and Shoup or Montgomery twiddles are held to the
+// Launch bounds: column passes of up to 256 points with 4-byte words (512
+// threads), radix 16 and Shoup or Montgomery twiddles are held to the
 // registers that let three CTAs share an SM, as their shared memory allows
-// (40 a thread, no spills); 512-point column passes take 1024 threads.
+// (40 a thread, no spills; forward call at N = 2^16, 32 limbs, 16
+// polynomials 0.1214 -> 0.1195 ms with the forward pass held too);
+// 512-point column passes take 1024 threads.
 template <class W, int RED, int LOGS, int KIND, bool INV, int P> __host__ __device__ constexpr bool fused_cols3() {
-    return KIND == TK_COLS && INV && sizeof(W) == 4 && RED != RED_BARRETT && LOGS <= 8 && radix_log<P>() == 4;
+    return KIND == TK_COLS && sizeof(W) == 4 && RED != RED_BARRETT && LOGS <= 8 && radix_log<P>() == 4;
 }
 template <class W, int RED, int LOGS, int KIND, bool INV, int P> __host__ __device__ constexpr int fused_max_threads() {
     return fused_cols3<W, RED, LOGS, KIND, INV, P>() ? 512 : (sizeof(W) == 4 ? 1024 : 512);
