@@ -39,18 +39,19 @@
 // Each pass reads src and writes dst (out of place: a tile's output rows are
 // other tiles' input rows).
 //
-// Roles in a CTA (one per SM: 208 KiB of stage buffers, 448 of the 512
-// tensor-memory columns): warp 16 lane 0 issues the TMA copies of both
-// operands' sources, a chunk ahead -- the data words (four 16 KiB stages)
-// and the matrix digit planes (three 16 KiB stages); warps 0-7 turn the
-// staged data words into digit planes (three 32 KiB stages); warp 17 lane 0
-// issues the MMAs; warps 8-15 run the epilogue (warp w reads tensor-memory
-// lanes 32 (w % 4) ..).  The accumulators are one set: the next tile's MMAs
-// start when the epilogue has read and zeroed them (two sets of half-width
-// tiles were measured slower: each 32-column tile converts the whole data
-// block again, and the extra digit traffic through shared memory costs more
-// than the overlap gains).  mbarriers between the roles, every wait bounded
-// (about a second of SM clock) -- on expiry the call records
+// Roles in a CTA (one per SM: 224 KiB of stage buffers, 448 of the 512
+// tensor-memory columns): warp 16 lane 0 issues the TMA copies of the data
+// words (four 16 KiB stages), warp 18 lane 0 those of the matrix digit
+// planes (four 16 KiB stages), each as far ahead as its stages allow;
+// warps 0-7 turn the staged data words into digit planes (three 32 KiB
+// stages); warp 17 lane 0 issues the MMAs; warps 8-15 run the epilogue
+// (warp w reads tensor-memory lanes 32 (w % 4) ..).  The accumulators are
+// one set: the next tile's MMAs start when the epilogue has read and
+// zeroed them (two sets of half-width tiles were measured slower: each
+// 32-column tile converts the whole data block again, and the extra digit
+// traffic through shared memory costs more than the overlap gains).
+// mbarriers between the roles, every wait bounded (about a second of SM
+// clock) -- on expiry the call records
 // NTT_ERR_TIMEOUT, all roles leave their loops, and the CTA waits (bounded)
 // for its copies and products in flight before it frees its tensor memory.
 #include <cuda.h>
@@ -70,15 +71,18 @@ constexpr uint32_t kT5Row = kT5KC * 2;                 // bytes of one operand r
 constexpr uint32_t kT5StageA = kT5Dig * kT5M * kT5Row;   // 32 KiB
 constexpr uint32_t kT5StageB = kT5Dig * kT5N * kT5Row;   // 16 KiB
 constexpr uint32_t kT5StageR = kT5M * kT5KC * 4;          // 16 KiB of data words
-constexpr uint32_t kT5NA = 3, kT5NB = 3, kT5NR = 4;       // digit / matrix / data-word stage buffers
+constexpr uint32_t kT5NA = 3, kT5NB = 4, kT5NR = 4;       // digit / matrix / data-word stage buffers
 constexpr uint32_t kT5Chunks = 256 / kT5KC;               // K chunks per tile
 constexpr uint32_t kT5ConvWarps = 8;                 // warps 0-7: data digits
 constexpr uint32_t kT5EpiWarps = 8;                  // warps 8-15: epilogue
-constexpr uint32_t kT5TmaWarp = kT5ConvWarps + kT5EpiWarps, kT5MmaWarp = kT5TmaWarp + 1;
-constexpr uint32_t kT5Threads = (kT5MmaWarp + 1) * 32;
+// warp 16: TMA of the data words; warp 17: MMAs; warp 18: TMA of the
+// matrix digit planes
+constexpr uint32_t kT5TmaWarp = kT5ConvWarps + kT5EpiWarps, kT5MmaWarp = kT5TmaWarp + 1,
+                   kT5TmaBWarp = kT5MmaWarp + 1;
+constexpr uint32_t kT5Threads = (kT5TmaBWarp + 1) * 32;
 constexpr uint32_t kT5TmemCols = 512;
 constexpr size_t kT5SmemData =
-    (size_t)kT5NA * kT5StageA + (size_t)kT5NB * kT5StageB + (size_t)kT5NR * kT5StageR;   // 208 KiB
+    (size_t)kT5NA * kT5StageA + (size_t)kT5NB * kT5StageB + (size_t)kT5NR * kT5StageR;   // 224 KiB
 constexpr size_t kT5Smem = kT5SmemData + 1024 + 256;
 
 struct Tc5Args {
@@ -265,48 +269,48 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
     auto tile_of = [&](uint32_t g) { return blockIdx.x + (g / kT5Chunks) * gridDim.x; };
     bool ok = true;
 
-    if (warp == kT5TmaWarp) {
-        // ------------------------------------------------ TMA producer
-        // chunk g: its data words into R stage g % NR and its matrix digit
-        // planes into B stage g % NB, each as soon as that stage is free
+    if (warp == kT5TmaWarp || warp == kT5TmaBWarp) {
+        // ------------------------------------------------ TMA producers
+        // chunk g: its data words into R stage g % NR (warp 16) and its
+        // matrix digit planes into B stage g % NB (warp 18), each as soon
+        // as that stage is free; two threads, so that neither kind of copy
+        // waits behind the other's free stage
         if (lane == 0) {
-            uint32_t nr = 0, nb = 0;      // copies issued: data-word chunks, matrix chunks
+            const bool rw = warp == kT5TmaWarp;
+            const uint32_t NS = rw ? kT5NR : kT5NB;
+            uint64_t *full = rw ? r_full : b_full, *empty = rw ? r_empty : b_empty;
+            uint32_t n = 0;               // copies issued
             for (uint32_t g = 0; g < nchunks && ok; ++g) {
                 const T5Tile T = t5_tile(tile_of(g), a.L);
                 const uint32_t c = g % kT5Chunks;
-                const uint32_t sr = g % kT5NR, sb = g % kT5NB;
-                if (g >= kT5NR && !t5_wait(&r_empty[sr], ((g - kT5NR) / kT5NR) & 1u, abort_flag)) { ok = false; break; }
-                mbar_expect_tx(&r_full[sr], kT5StageR);
-                // column pass: words src[32 c + k][128 mb + m]; row pass:
-                // src[128 mb + m][32 c + k]
-                if (ROWP)
-                    tma_2d_g2s(stage_r(sr), &a.dmap, (int)(c * kT5KC), (int)(T.t * 256 + T.mb * kT5M), &r_full[sr]);
-                else
-                    tma_2d_g2s(stage_r(sr), &a.dmap, (int)(T.mb * kT5M), (int)(T.t * 256 + c * kT5KC), &r_full[sr]);
-                ++nr;
-                if (g >= kT5NB && !t5_wait(&b_empty[sb], ((g - kT5NB) / kT5NB) & 1u, abort_flag)) { ok = false; break; }
-                const uint32_t mrow0 = a.mat_row0 + T.l * kT5Dig * 256 + T.nb * kT5N;
-                mbar_expect_tx(&b_full[sb], kT5StageB);
-                // (test hook: this copy's barrier waits for bytes that never come)
-                if (a.stall_tx && g == 0 && blockIdx.x == 0) mbar_add_tx(&b_full[sb], a.stall_tx);
-                for (uint32_t d = 0; d < kT5Dig; ++d)
-                    tma_2d_g2s(stage_b(sb) + d * kT5N * kT5Row, &a.cmap, (int)(c * kT5KC), (int)(mrow0 + d * 256),
-                               &b_full[sb]);
-                ++nb;
+                const uint32_t st = g % NS;
+                if (g >= NS && !t5_wait(&empty[st], ((g - NS) / NS) & 1u, abort_flag)) { ok = false; break; }
+                if (rw) {
+                    mbar_expect_tx(&full[st], kT5StageR);
+                    // column pass: words src[32 c + k][128 mb + m]; row pass:
+                    // src[128 mb + m][32 c + k]
+                    if (ROWP)
+                        tma_2d_g2s(stage_r(st), &a.dmap, (int)(c * kT5KC), (int)(T.t * 256 + T.mb * kT5M), &full[st]);
+                    else
+                        tma_2d_g2s(stage_r(st), &a.dmap, (int)(T.mb * kT5M), (int)(T.t * 256 + c * kT5KC), &full[st]);
+                } else {
+                    const uint32_t mrow0 = a.mat_row0 + T.l * kT5Dig * 256 + T.nb * kT5N;
+                    mbar_expect_tx(&full[st], kT5StageB);
+                    // (test hook: this copy's barrier waits for bytes that never come)
+                    if (a.stall_tx && g == 0 && blockIdx.x == 0) mbar_add_tx(&full[st], a.stall_tx);
+                    for (uint32_t d = 0; d < kT5Dig; ++d)
+                        tma_2d_g2s(stage_b(st) + d * kT5N * kT5Row, &a.cmap, (int)(c * kT5KC), (int)(mrow0 + d * 256),
+                                   &full[st]);
+                }
+                ++n;
             }
             if (!ok) {
                 atomicExch(const_cast<uint32_t *>(abort_flag), 1u);
                 // copies still in flight land before the CTA leaves (bounded):
-                // chunk h used R stage h % NR and B stage h % NB for their
-                // (h / NR + 1)-th and (h / NB + 1)-th phases
-                for (uint32_t h = nr >= kT5NR ? nr - kT5NR : 0; h < nr; ++h) {
+                // chunk h used stage h % NS for its (h / NS + 1)-th phase
+                for (uint32_t h = n >= NS ? n - NS : 0; h < n; ++h) {
                     const long long t0 = clock64();
-                    while (!mbar_try_wait(&r_full[h % kT5NR], (h / kT5NR) & 1u) && clock64() - t0 < (1ll << 30)) {
-                    }
-                }
-                for (uint32_t h = nb >= kT5NB ? nb - kT5NB : 0; h < nb; ++h) {
-                    const long long t0 = clock64();
-                    while (!mbar_try_wait(&b_full[h % kT5NB], (h / kT5NB) & 1u) && clock64() - t0 < (1ll << 30)) {
+                    while (!mbar_try_wait(&full[h % NS], (h / NS) & 1u) && clock64() - t0 < (1ll << 30)) {
                     }
                 }
             }
@@ -389,8 +393,6 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
                     for (int e = 0; e < 8; ++e) xw[q][e] = R[(8 * u + e) * kT5M + m];
                 }
             }
-            // the words are read: the stage takes the chunk NR ahead
-            t5_arrive(&r_empty[sr]);
             unsigned char *dst = stage_a(s);
 #pragma unroll
             for (uint32_t q = 0; q < TASKS; ++q) {
@@ -402,6 +404,11 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
 #pragma unroll
                 for (uint32_t d = 0; d < kT5Dig; ++d) *reinterpret_cast<uint4 *>(dst + d * (kT5M * kT5Row) + off) = dg[d];
             }
+            // the words have been used (not only requested), so the stage
+            // may take the chunk NR ahead: the TMA copy into it is an
+            // async-proxy write, which the barrier does not order after
+            // loads still in flight
+            t5_arrive(&r_empty[sr]);
             // generic-proxy stores, read next by the tensor cores
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             t5_arrive(&a_full[s]);
