@@ -586,14 +586,21 @@ template <class W, int LOGS, int KIND> __host__ __device__ constexpr bool tw_sta
 }
 // Bit 3 of P (chunk passes): the K sub-transforms of a tile are the same
 // chunk of K consecutive polynomials (one chunk table per tile) instead of
-// K consecutive chunks of one polynomial (K tables).
+// K consecutive chunks of one polynomial (K tables); with bit 7 as well,
+// the same 2 consecutive chunks of K / 2 consecutive polynomials (two
+// tables), for batches that K / 2 divides but K does not.
 template <int KIND, int P> __host__ __device__ constexpr bool paired_chunks() {
     return KIND == TK_CHUNKS && (P & 8) != 0;
+}
+// chunk positions per paired tile (its twiddle tables)
+template <int KIND, int P> __host__ __device__ constexpr uint32_t pair_positions() {
+    return (P & 128) ? 2u : 1u;
 }
 template <class W, int LOGS, int KIND, int P = 0> __host__ __device__ constexpr uint32_t tw_pairs() {
     return !tw_staged<W, LOGS, KIND>() ? 0u
            : KIND == TK_COLS ? (1u << LOGS)
-           : (paired_chunks<KIND, P>() ? 1u : tile_k<W, LOGS, KIND, P>()) * chunk_tab_pitch<W, LOGS>();
+           : (paired_chunks<KIND, P>() ? pair_positions<KIND, P>() : tile_k<W, LOGS, KIND, P>()) *
+                 chunk_tab_pitch<W, LOGS>();
 }
 
 // Pipeline state carried across run_tiles calls of one CTA: how often each
@@ -663,11 +670,13 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
     // take immediate offsets) unless bit 5 of P asks for the plan's split
     const uint32_t S2 = KIND == TK_CHUNKS ? (uint32_t)LOGS : ((P & 32) ? a.s2 : kN2Log);
     const uint32_t N1 = KIND == TK_SINGLE ? 1u : (N >> S2);
-    // paired chunk tiles: sub k is polynomial p + k (the launcher makes
+    // paired chunk tiles: sub k is chunk position pos0 + k % KG of
+    // polynomial p + k / KG (the launcher makes
     // sure K divides the batch); else sub k is position pos0 + k
     constexpr bool PAIR = paired_chunks<KIND, P>();
-    constexpr uint32_t KP = PAIR ? K : 1u;    // polynomials per tile
-    constexpr uint32_t KG = PAIR ? 1u : K;    // positions (chunks, columns) per tile
+    constexpr uint32_t KG = PAIR ? pair_positions<KIND, P>() : K;   // positions (chunks, columns) per tile
+    constexpr uint32_t KP = K / KG;                                 // polynomials per tile
+    static_assert(!PAIR || (K % KG == 0 && KG * KP == K), "a paired tile is KP polynomials x KG chunks");
     const uint32_t per = KIND == TK_SINGLE ? 1u : (KIND == TK_COLS ? (1u << S2) : N1) / KG;
     const uint32_t BP = B / KP;               // polynomial steps per position group
     // Tile cursor: single tiles are K consecutive transforms; two-pass tiles
@@ -708,13 +717,13 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
         } else if (SWZ) {
             mbar_expect_tx(&bar[s], K * S * (uint32_t)sizeof(W));
             if constexpr (PAIR) {
-                // one box of S / RW rows per polynomial (1 KiB-aligned
+                // one box of KG S / RW rows per polynomial (1 KiB-aligned
                 // blocks, so the swizzle phase is the smem row's)
-                for (uint32_t c2 = 0; c2 < K; ++c2) {
+                for (uint32_t c2 = 0; c2 < KP; ++c2) {
                     const uint64_t row0 = ((t + (uint64_t)c2 * L) * N + ((size_t)pos0 << S2)) / RW;
-                    tma_2d_g2s(dst + c2 * S, tmap, 0, (int)row0, &bar[s]);
+                    tma_2d_g2s(dst + c2 * KG * S, tmap, 0, (int)row0, &bar[s]);
                     if (a.pw_b) prefetch_l2(a.pw_b + (t + (uint64_t)c2 * L) * N + ((size_t)pos0 << S2),
-                                            S * (uint32_t)sizeof(W));
+                                            KG * S * (uint32_t)sizeof(W));
                 }
             } else {
                 const uint64_t row0 = (t * N + ((size_t)pos0 << S2)) / RW;
@@ -726,10 +735,11 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
         } else if (KIND == TK_CHUNKS) {
             mbar_expect_tx(&bar[s], K * S * (uint32_t)sizeof(W));
             const W *src = a.data + t * N + ((size_t)pos0 << S2);
-            // sub c2: the next chunk of the polynomial, or (paired) the same
-            // chunk of the next polynomial
-            const size_t sub = PAIR ? (size_t)L * N : (size_t)S;
-            for (uint32_t c2 = 0; c2 < K; ++c2) bulk_g2s(dst + c2 * SP, src + c2 * sub, S * sizeof(W), &bar[s]);
+            // sub c2: chunk pos0 + c2 % KG of polynomial t + c2 / KG (the
+            // next chunk of the polynomial, or, paired, of the next one)
+            for (uint32_t c2 = 0; c2 < K; ++c2)
+                bulk_g2s(dst + c2 * SP, src + (size_t)(c2 / KG) * L * N + (size_t)(c2 % KG) * S, S * sizeof(W),
+                         &bar[s]);
         } else {
             const uint64_t nval = a.ntrans - t < K ? a.ntrans - t : K;
             const uint32_t bytes = (uint32_t)(nval * S * sizeof(W));
@@ -747,8 +757,9 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
             for (uint32_t r0 = 0; r0 < S; r0 += rows) prefetch_tensor_2d(tmap, (int)pos0, (int)(t * N1 + r0));
         } else if (KIND == TK_CHUNKS) {
             if constexpr (PAIR) {
-                for (uint32_t c2 = 0; c2 < K; ++c2)
-                    prefetch_l2(a.data + (t + (uint64_t)c2 * L) * N + ((size_t)pos0 << S2), S * (uint32_t)sizeof(W));
+                for (uint32_t c2 = 0; c2 < KP; ++c2)
+                    prefetch_l2(a.data + (t + (uint64_t)c2 * L) * N + ((size_t)pos0 << S2),
+                                KG * S * (uint32_t)sizeof(W));
             } else {
                 prefetch_l2(a.data + t * N + ((size_t)pos0 << S2), K * S * (uint32_t)sizeof(W));
             }
@@ -814,8 +825,8 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
         const uint32_t parity = (ps.use(s) + i / NS) & 1u;
         const uint32_t pos0 = cur.g * KG;
         // this thread's sub-transform: transform t, chunk / column position pk
-        const uint64_t t = KIND == TK_SINGLE ? cur_t(cur) + k : (PAIR ? cur_t(cur) + (uint64_t)k * L : cur_t(cur));
-        const uint32_t pk = PAIR ? pos0 : pos0 + k;
+        const uint64_t t = KIND == TK_SINGLE ? cur_t(cur) + k : (PAIR ? cur_t(cur) + (uint64_t)(k / KG) * L : cur_t(cur));
+        const uint32_t pk = PAIR ? pos0 + k % KG : pos0 + k;
         const bool valid = t < a.ntrans;
         const uint32_t l = KIND == TK_SINGLE ? (uint32_t)((valid ? t : 0) % L) : cur.l;
         if (!LATE_REFILL || l != kk_l) load_limb(l);
@@ -887,7 +898,7 @@ __device__ __forceinline__ bool run_tiles(const FArgs<W> &a, const CUtensorMap *
                 }
                 tw_key = key;
             }
-            twb = tws + (KIND == TK_CHUNKS && !PAIR ? k * CP : 0);
+            twb = tws + (KIND == TK_CHUNKS ? (k % KG) * CP : 0);
         } else {
             twb = KIND == TK_CHUNKS ? tw_src(l, 0) + (size_t)pk * CP : a.tw + (size_t)l * N;
         }

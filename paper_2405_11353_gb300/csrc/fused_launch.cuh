@@ -160,7 +160,7 @@ template <class W, int KIND, int P> uint32_t tile_k_p(int logS) {
 // pointwise + inverse) from `data` times pw_b into `out`.
 template <class W, bool INV, int KIND>
 cudaError_t fill_pass(FArgs<W> &a, ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, int logS,
-                      bool final_pass, uint32_t K, W *out, const W *pw_b, bool paired = false) {
+                      bool final_pass, uint32_t K, W *out, const W *pw_b, uint32_t pair_kg = 0) {
     std::memset(&a, 0, sizeof(a));
     a.data = data;
     a.out = out ? out : data;
@@ -198,7 +198,7 @@ cudaError_t fill_pass(FArgs<W> &a, ntt_plan_s &p, W *data, const void *tw, uint6
         // polynomials (one copy per polynomial)
         const uint32_t RW = 128 / sizeof(W);
         cudaError_t e = make_rows_tmap(&a.tmap, data, sizeof(W) == 8, ntrans * p.N / RW, RW,
-                                       (paired ? 1u : K) * (1u << logS) / RW);
+                                       (pair_kg ? pair_kg : K) * (1u << logS) / RW);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -213,8 +213,10 @@ cudaError_t run_pass(ntt_plan_s &p, W *data, const void *tw, uint64_t ntrans, in
     const uint32_t T = (1u << logS) >> radix_log<PP>();
     const uint32_t K = tile_k_for<W, KIND, PP>(logS);
     constexpr bool paired = paired_chunks<KIND, PP>();
-    if (paired && (ntrans / p.L) % K != 0) return cudaErrorInvalidValue;   // whole polynomial groups
-    cudaError_t e = fill_pass<W, INV, KIND>(a, p, data, tw, ntrans, logS, final_pass, K, out, pw_b, paired);
+    constexpr uint32_t KG = paired ? pair_positions<KIND, PP>() : 0u;
+    // whole polynomial groups of K / KG polynomials
+    if (paired && (K % KG != 0 || (ntrans / p.L) % (K / KG) != 0)) return cudaErrorInvalidValue;
+    cudaError_t e = fill_pass<W, INV, KIND>(a, p, data, tw, ntrans, logS, final_pass, K, out, pw_b, KG);
     if (e != cudaSuccess) return e;
     size_t smem = smem_for<W, KIND, INV, PP>(logS);
     ++p.last_launches;
@@ -269,9 +271,15 @@ cudaError_t run_chunk_pass(ntt_plan_s &p, int form, W *data, const void *tw, uin
         return B % ks == 0 && B > 1
                    ? run_pass<W, RED, INV, TK_CHUNKS, LRB | 8>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b)
                    : run_pass<W, RED, INV, TK_CHUNKS, LRB>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b);
-    return B % kw == 0 && B > 1
-               ? run_pass<W, RED, INV, TK_CHUNKS, LRB | 11>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b)
-               : run_pass<W, RED, INV, TK_CHUNKS, LRB | 3>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b);
+    if (B % kw == 0 && B > 1)
+        return run_pass<W, RED, INV, TK_CHUNKS, LRB | 11>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b);
+    if constexpr (sizeof(W) == 4) {
+        // K / 2 polynomials x 2 chunks a tile: two twiddle tables instead of
+        // K, so more CTAs fit an SM (a batch of 8 at K = 16: 4 instead of 3)
+        if (B % (kw / 2) == 0 && B > 1)
+            return run_pass<W, RED, INV, TK_CHUNKS, LRB | 139>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b);
+    }
+    return run_pass<W, RED, INV, TK_CHUNKS, LRB | 3>(p, data, tw, ntrans, logS, final_pass, st, out, pw_b);
 }
 
 #ifdef NTTGB_SHFL_UNIT

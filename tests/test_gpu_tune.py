@@ -130,9 +130,9 @@ def test_every_split_bit_exact(nt, orc, n, w64, splits, radix, shfl):
     """Every split N = 2^s1 x 2^s2 a size takes, in both radices (rounds of
     four stages on 16 words a thread, or three on 8), with both chunk-pass
     forms -- with shared-memory exchanges, and (4-byte words) with warp
-    shuffles --, batches whose tiles pair polynomials and batches that do
-    not: forward, the product fused into the inverse, and the inverse,
-    bit-exact."""
+    shuffles --, batches whose tiles pair polynomials (one chunk of K
+    polynomials, or two chunks of K / 2) and batches that do not: forward,
+    the product fused into the inverse, and the inverse, bit-exact."""
     if shfl and w64:
         pytest.skip("the shuffle forms are for 4-byte words")
     N, L = 1 << n, 3
@@ -143,7 +143,9 @@ def test_every_split_bit_exact(nt, orc, n, w64, splits, radix, shfl):
         for s2 in splits:
             small, wide = ((nt.NTT_FORM_SMALL_SHFL, nt.NTT_FORM_WIDE_SHFL) if shfl
                            else (nt.NTT_FORM_SMALL, nt.NTT_FORM_WIDE))
-            for batch, form in ((4, small), (3, wide), (16, wide), (2, small)):
+            # (8 and 12 on 256-thread tiles: K / 2 polynomials x 2 chunks a
+            # tile where K / 2 divides the batch and K does not)
+            for batch, form in ((4, small), (3, wide), (16, wide), (2, small), (8, wide), (12, wide)):
                 nt.ntt_tune_clear()
                 nt.ntt_tune_set_split(N, L, flags, s2, radix)
                 nt.ntt_tune_set(N, L, flags, batch, form, form)
