@@ -25,8 +25,8 @@
 //     against the matrices of many primes, are the evidence for it.
 //   * The epilogue reads the diagonals back (tcgen05.ld), recombines
 //     sum_s D_s (2^(8 s) mod q) in 64-bit integers (|.| < 7 2^24 q < 2^57),
-//     adds a multiple of q above 2^57 to make it positive and reduces mod q
-//     (Barrett), then applies
+//     adds 7 2^24 q to make it positive and reduces mod q (Barrett), then
+//     applies
 //     the inter-step twiddle (Shoup) where the pass has one.
 //
 // GEMM view, D[m][n] = sum_k A[m][k] B[n][k], both operands K-major in shared
@@ -44,12 +44,14 @@
 // words (four 16 KiB stages), warp 18 lane 0 those of the matrix digit
 // planes (four 16 KiB stages), each as far ahead as its stages allow;
 // warps 0-7 turn the staged data words into digit planes (three 32 KiB
-// stages); warp 17 lane 0 issues the MMAs; warps 8-15 run the epilogue
-// (warp w reads tensor-memory lanes 32 (w % 4) ..).  The accumulators are
-// one set: the next tile's MMAs start when the epilogue has read and
-// zeroed them (two sets of half-width tiles were measured slower: each
-// 32-column tile converts the whole data block again, and the extra digit
-// traffic through shared memory costs more than the overlap gains).
+// stages); warp 17 lane 0 issues the MMAs; warps 8-15, and warps 0-7 in
+// the gap between their conversions, run the epilogue (warp w reads
+// tensor-memory lanes 32 (w % 4) .. and 16 of the 64 columns of each
+// diagonal).  The accumulators are one set: the next tile's MMAs start
+// when the epilogue has read and zeroed them (two sets of half-width tiles
+// were measured slower: each 32-column tile converts the whole data block
+// again, and the extra digit traffic through shared memory costs more
+// than the overlap gains).
 // mbarriers between the roles, every wait bounded (about a second of SM
 // clock) -- on expiry the call records
 // NTT_ERR_TIMEOUT, all roles leave their loops, and the CTA waits (bounded)
@@ -144,6 +146,9 @@ __device__ __forceinline__ uint64_t t5_desc(uint32_t saddr) {
 constexpr uint32_t kT5IdescAll = (1u << 4) | (0u << 7) | (0u << 10) | (((kT5Dig * kT5N) >> 3) << 17) |
                                  ((kT5M >> 4) << 24);
 
+__device__ __forceinline__ void t5_st_zero4(uint32_t taddr) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %1, %1, %1};" ::"r"(taddr), "r"(0u) : "memory");
+}
 __device__ __forceinline__ void t5_st_zero8(uint32_t taddr) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
                  "r"(0u)
@@ -240,7 +245,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
             mbar_init(&a_empty[s], 1);
         }
         mbar_init(acc_full, 1);
-        mbar_init(acc_empty, NEPI);
+        mbar_init(acc_empty, NCONV + NEPI);
         mbar_init(drain, 1);
         fence_mbar_init();
         s_abort = 0;
@@ -356,8 +361,9 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
         }
     } else {
         // ------------------------------------- converters (warps 0-7) and
-        // epilogue (warps 8-15): the next tile's digits are made while the
-        // epilogue drains the accumulators of the last one
+        // epilogue (warps 8-15, and the converters between conversions): the
+        // next tile's first digit stages are made while the epilogue drains
+        // the accumulators of the last one
         const bool conv = warp < kT5ConvWarps;
         const uint32_t ew = warp - kT5ConvWarps;        // epilogue warp 0..7
         // Data operand A[m][k] of a tile, m < 128, for chunk c (k in 32 c ..):
@@ -413,17 +419,26 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             t5_arrive(&a_full[s]);
         };
+        // The epilogue is shared by all 16 warps: warp w reads tensor-memory
+        // lanes 32 (w % 4) .. (its rows m) and columns 16 slice .. of each
+        // diagonal, slice = w / 4 for the converter warps, 2 + (w - 8) / 4
+        // for the epilogue warps.
+        const uint32_t quad = warp & 3u;
+        const uint32_t slice = conv ? (warp >> 2) : 2 + (ew >> 2);
+        constexpr uint32_t kSliceCols = kT5N / 4;
         auto epilogue = [&](uint32_t tile, uint32_t ti) -> bool {
+            constexpr uint32_t GW = 4;      // columns a group (tcgen05.ld .x4)
             const T5Tile T = t5_tile(tile, a.L);
-            const uint32_t m = 32 * (ew & 3u) + lane;
-            const uint32_t n0 = (ew >> 2) * 32;
+            const uint32_t m = 32 * quad + lane;
+            const uint32_t n0 = slice * kSliceCols;
             Lc<uint32_t> kk;
             kk.load(a.lc + T.l);
             uint32_t w7[kT5Diag];
 #pragma unroll
             for (uint32_t d = 0; d < kT5Diag; ++d) w7[d] = __ldg(a.wdiag + 8 * T.l + d);
-            // a multiple of q above 7 * 2^24 * q > |sum|: makes the sum positive
-            const uint64_t off = (uint64_t)kk.q * ((1ull << 57) / kk.q + 1);
+            // a multiple of q above |sum| (seven diagonals of magnitude at
+            // most 2^24, each times a factor below q): makes the sum positive
+            const uint64_t off = (uint64_t)kk.q * (7ull << 24);
             // output word (row, column) of the transform: column pass
             // out[u][n2] = out[64 nb + n][128 mb + m]; row pass
             // out[r][v] = out[128 mb + m][64 nb + n]
@@ -436,57 +451,54 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
             // the inter-step twiddles of the first column group, loaded
             // before the wait for the products (their latency overlaps it);
             // each group's loads are issued one group ahead
-            Tw<uint32_t> tw8[8], twn[8];
+            Tw<uint32_t> twc[GW], twn[GW];
             if (twt) {
 #pragma unroll
-                for (int cc = 0; cc < 8; ++cc) tw8[cc] = ldtw(tw_at(n0 + cc));
+                for (uint32_t cc = 0; cc < GW; ++cc) twc[cc] = ldtw(tw_at(n0 + cc));
             }
             if (!t5_wait(acc_full, ti & 1u, abort_flag)) return false;
             t5_fence_after();
 #pragma unroll 1
-            for (uint32_t grp = 0; grp < 4; ++grp) {
-                uint32_t f[kT5Diag][8];
+            for (uint32_t grp = 0; grp < kSliceCols / GW; ++grp) {
+                uint32_t f[kT5Diag][GW];
 #pragma unroll
                 for (uint32_t d = 0; d < kT5Diag; ++d) {
-                    const uint32_t taddr = tmem + ((32u * (ew & 3u)) << 16) + d * kT5N + n0 + 8 * grp;
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                                 : "=r"(f[d][0]), "=r"(f[d][1]), "=r"(f[d][2]), "=r"(f[d][3]), "=r"(f[d][4]),
-                                   "=r"(f[d][5]), "=r"(f[d][6]), "=r"(f[d][7])
+                    const uint32_t taddr = tmem + ((32u * quad) << 16) + d * kT5N + n0 + GW * grp;
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                                 : "=r"(f[d][0]), "=r"(f[d][1]), "=r"(f[d][2]), "=r"(f[d][3])
                                  : "r"(taddr));
                 }
-                if (twt && grp < 3) {
+                if (twt && grp + 1 < kSliceCols / GW) {
 #pragma unroll
-                    for (int cc = 0; cc < 8; ++cc) twn[cc] = ldtw(tw_at(n0 + 8 * (grp + 1) + cc));
+                    for (uint32_t cc = 0; cc < GW; ++cc) twn[cc] = ldtw(tw_at(n0 + GW * (grp + 1) + cc));
                 }
                 t5_wait_ld();
                 // the next tile accumulates onto zeros
 #pragma unroll
                 for (uint32_t d = 0; d < kT5Diag; ++d)
-                    t5_st_zero8(tmem + ((32u * (ew & 3u)) << 16) + d * kT5N + n0 + 8 * grp);
-                uint32_t v[8];
+                    t5_st_zero4(tmem + ((32u * quad) << 16) + d * kT5N + n0 + GW * grp);
+                uint32_t v[GW];
 #pragma unroll
-                for (int cc = 0; cc < 8; ++cc) {
+                for (uint32_t cc = 0; cc < GW; ++cc) {
                     int64_t comb = 0;
 #pragma unroll
                     for (uint32_t d = 0; d < kT5Diag; ++d)
                         comb += (int64_t)__float2int_rn(__uint_as_float(f[d][cc])) * (int64_t)w7[d];
                     uint32_t r = csub<uint32_t>(barrett_lazy((uint64_t)comb + off, kk), kk.q);
-                    if (twt) r = mul_full<RED_SHOUP>(r, tw8[cc], kk);
+                    if (twt) r = mul_full<RED_SHOUP>(r, twc[cc], kk);
                     v[cc] = r;
                 }
                 if (twt) {
 #pragma unroll
-                    for (int cc = 0; cc < 8; ++cc) tw8[cc] = twn[cc];
+                    for (uint32_t cc = 0; cc < GW; ++cc) twc[cc] = twn[cc];
                 }
                 if (ROWP) {
-                    uint4 *o = reinterpret_cast<uint4 *>(outt + (size_t)(T.mb * kT5M + m) * 256 + T.nb * kT5N + n0 +
-                                                         8 * grp);
-                    o[0] = make_uint4(v[0], v[1], v[2], v[3]);
-                    o[1] = make_uint4(v[4], v[5], v[6], v[7]);
+                    *reinterpret_cast<uint4 *>(outt + (size_t)(T.mb * kT5M + m) * 256 + T.nb * kT5N + n0 + GW * grp) =
+                        make_uint4(v[0], v[1], v[2], v[3]);
                 } else {
 #pragma unroll
-                    for (int cc = 0; cc < 8; ++cc)
-                        outt[(size_t)(T.nb * kT5N + n0 + 8 * grp + cc) * 256 + T.mb * kT5M + m] = v[cc];
+                    for (uint32_t cc = 0; cc < GW; ++cc)
+                        outt[(size_t)(T.nb * kT5N + n0 + GW * grp + cc) * 256 + T.mb * kT5M + m] = v[cc];
                 }
             }
             t5_wait_st();
@@ -495,10 +507,28 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
             return true;
         };
 
+        // the accumulators start at zero (every product accumulates): this
+        // thread's row, its slice of each diagonal
+        for (uint32_t d = 0; d < kT5Diag; ++d)
+            for (uint32_t c8 = 0; c8 < kSliceCols / 8; ++c8)
+                t5_st_zero8(tmem + ((32u * quad) << 16) + d * kT5N + slice * kSliceCols + 8 * c8);
+        t5_wait_st();
+        t5_fence_before();
+        t5_arrive(acc_empty);
         if (conv) {
             // chunk g: wait for its data words (TMA) and for its digit stage
-            // (the products of chunk g - NA done), then convert
+            // (the products of chunk g - NA done), then convert.  The
+            // converters are idle while a tile's accumulators drain (the
+            // next tile's first NA digit stages are full, and its products
+            // wait for the drain), so they take half of each epilogue: that
+            // of tile i just before chunk NA of tile i + 1, the first chunk
+            // whose stage needs tile i + 1's products to have started
             for (uint32_t g = 0; g < nchunks && ok; ++g) {
+                if (g >= kT5Chunks && g % kT5Chunks == kT5NA) {
+                    const uint32_t ti = g / kT5Chunks - 1;
+                    ok = epilogue(tile_of(kT5Chunks * ti), ti);
+                    if (!ok) break;
+                }
                 const uint32_t sr = g % kT5NR, s = g % kT5NA;
                 if (!t5_wait(&r_full[sr], (g / kT5NR) & 1u, abort_flag)) { ok = false; break; }
                 if (g >= kT5NA && !t5_wait(&a_empty[s], ((g - kT5NA) / kT5NA) & 1u, abort_flag)) {
@@ -507,15 +537,9 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
                 }
                 convert_chunk(sr, s);
             }
+            // the last tile's accumulators
+            if (ok && my_tiles > 0) ok = epilogue(tile_of(kT5Chunks * (my_tiles - 1)), my_tiles - 1);
         } else {
-            // the accumulators start at zero (every product accumulates):
-            // this thread's row, its 32 of the 64 columns of each diagonal
-            for (uint32_t d = 0; d < kT5Diag; ++d)
-                for (uint32_t c8 = 0; c8 < 4; ++c8)
-                    t5_st_zero8(tmem + ((32u * (ew & 3u)) << 16) + d * kT5N + (ew >> 2) * 32 + 8 * c8);
-            t5_wait_st();
-            t5_fence_before();
-            t5_arrive(acc_empty);
             for (uint32_t ti = 0; ti < my_tiles && ok; ++ti) ok = epilogue(tile_of(kT5Chunks * ti), ti);
         }
         if (!ok) atomicExch(const_cast<uint32_t *>(abort_flag), 1u);
