@@ -24,9 +24,10 @@
 //     data words whose digits sit at the ends of their range (-128 and +127),
 //     against the matrices of many primes, are the evidence for it.
 //   * The epilogue reads the diagonals back (tcgen05.ld), recombines
-//     sum_s D_s (2^(8 s) mod q) in 64-bit integers (|.| < 7 2^24 q < 2^57),
-//     adds 7 2^24 q to make it positive and reduces mod q (Barrett), then
-//     applies
+//     sum_s (D_s + 2^24) (2^(8 s) mod q) in unsigned 64-bit integers
+//     (< 7 2^55: one 32 x 32 -> 64-bit multiply-add per diagonal), adds
+//     -2^24 sum_s 2^(8 s) mod q to remove the offsets and reduces mod q
+//     (Barrett), then applies
 //     the inter-step twiddle (Shoup) where the pass has one.
 //
 // GEMM view, D[m][n] = sum_k A[m][k] B[n][k], both operands K-major in shared
@@ -95,7 +96,7 @@ struct Tc5Args {
     uint32_t mat_row0;              // cmap row of (this pass's matrix, limb 0, digit 0, row 0)
     const Tw<uint32_t> *tw;         // [L][256][256] epilogue twiddles, or null
     const LimbConst *lc;
-    const uint32_t *wdiag;          // [L][8]: 2^(8 s) mod q for s < 7
+    const uint32_t *wdiag;          // [L][8]: 2^(8 s) mod q for s < 7; at 7, -2^24 sum_s 2^(8 s) mod q
     uint32_t *status;
     uint32_t L;
     uint32_t ntiles;                // 8 per transform (2 row blocks x 4 column tiles)
@@ -436,9 +437,11 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
             uint32_t w7[kT5Diag];
 #pragma unroll
             for (uint32_t d = 0; d < kT5Diag; ++d) w7[d] = __ldg(a.wdiag + 8 * T.l + d);
-            // a multiple of q above |sum| (seven diagonals of magnitude at
-            // most 2^24, each times a factor below q): makes the sum positive
-            const uint64_t off = (uint64_t)kk.q * (7ull << 24);
+            // each diagonal D is taken as D + 2^24 in [0, 2^25] (unsigned, so
+            // one 32 x 32 -> 64-bit multiply-add per diagonal, a sum below
+            // 7 2^55); this term, -2^24 sum_s 2^(8 s) mod q, removes the
+            // offsets mod q
+            const uint32_t corr = __ldg(a.wdiag + 8 * T.l + 7);
             // output word (row, column) of the transform: column pass
             // out[u][n2] = out[64 nb + n][128 mb + m]; row pass
             // out[r][v] = out[128 mb + m][64 nb + n]
@@ -448,17 +451,16 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
                 return twt + (ROWP ? (size_t)(T.mb * kT5M + m) * 256 + T.nb * kT5N + n
                                    : (size_t)(T.nb * kT5N + n) * 256 + T.mb * kT5M + m);
             };
-            // the inter-step twiddles of the first column group, loaded
-            // before the wait for the products (their latency overlaps it);
-            // each group's loads are issued one group ahead
-            Tw<uint32_t> twc[GW], twn[GW];
+            // the inter-step twiddles of the slice, loaded before the wait
+            // for the products (their latency overlaps it)
+            Tw<uint32_t> tws16[kSliceCols];
             if (twt) {
 #pragma unroll
-                for (uint32_t cc = 0; cc < GW; ++cc) twc[cc] = ldtw(tw_at(n0 + cc));
+                for (uint32_t cc = 0; cc < kSliceCols; ++cc) tws16[cc] = ldtw(tw_at(n0 + cc));
             }
             if (!t5_wait(acc_full, ti & 1u, abort_flag)) return false;
             t5_fence_after();
-#pragma unroll 1
+#pragma unroll
             for (uint32_t grp = 0; grp < kSliceCols / GW; ++grp) {
                 uint32_t f[kT5Diag][GW];
 #pragma unroll
@@ -468,10 +470,6 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
                                  : "=r"(f[d][0]), "=r"(f[d][1]), "=r"(f[d][2]), "=r"(f[d][3])
                                  : "r"(taddr));
                 }
-                if (twt && grp + 1 < kSliceCols / GW) {
-#pragma unroll
-                    for (uint32_t cc = 0; cc < GW; ++cc) twn[cc] = ldtw(tw_at(n0 + GW * (grp + 1) + cc));
-                }
                 t5_wait_ld();
                 // the next tile accumulates onto zeros
 #pragma unroll
@@ -480,17 +478,13 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
                 uint32_t v[GW];
 #pragma unroll
                 for (uint32_t cc = 0; cc < GW; ++cc) {
-                    int64_t comb = 0;
+                    uint64_t comb = corr;
 #pragma unroll
                     for (uint32_t d = 0; d < kT5Diag; ++d)
-                        comb += (int64_t)__float2int_rn(__uint_as_float(f[d][cc])) * (int64_t)w7[d];
-                    uint32_t r = csub<uint32_t>(barrett_lazy((uint64_t)comb + off, kk), kk.q);
-                    if (twt) r = mul_full<RED_SHOUP>(r, twc[cc], kk);
+                        comb += (uint64_t)(uint32_t)(__float2int_rn(__uint_as_float(f[d][cc])) + (1 << 24)) * w7[d];
+                    uint32_t r = csub<uint32_t>(barrett_lazy(comb, kk), kk.q);
+                    if (twt) r = mul_full<RED_SHOUP>(r, tws16[GW * grp + cc], kk);
                     v[cc] = r;
-                }
-                if (twt) {
-#pragma unroll
-                    for (uint32_t cc = 0; cc < GW; ++cc) twc[cc] = twn[cc];
                 }
                 if (ROWP) {
                     *reinterpret_cast<uint4 *>(outt + (size_t)(T.mb * kT5M + m) * 256 + T.nb * kT5N + n0 + GW * grp) =
