@@ -14,8 +14,10 @@
 //   * The 16 digit products are accumulated by diagonal s = i + j into seven
 //     fp32 accumulators in tensor memory: one M = 128, N = 256 product per
 //     data digit i against the four matrix digit planes at once (they are
-//     contiguous rows of one operand) lands A_i B_j in diagonal i + j; the
-//     accumulators are zeroed once and again by each epilogue after reading.  A diagonal sums at most 4 x 256
+//     contiguous rows of one operand) lands A_i B_j in diagonal i + j.  A
+//     tile's first product (digit 0, first K step) overwrites diagonals
+//     0-3; diagonals 4-6 are zeroed at the start and by each epilogue
+//     after reading.  A diagonal sums at most 4 x 256
 //     products of magnitude <= 128 * 128 = 2^14, so every partial sum is an
 //     integer of magnitude <= 2^24: exactly representable, so fp32
 //     accumulation loses nothing, in any order -- ASSUMING the tensor core
@@ -345,7 +347,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
 #pragma unroll
                         for (uint32_t i = 0; i < kT5Dig; ++i)
                             t5_mma(tmem + i * kT5N, da + ((i * (kT5M * kT5Row) + ks * 32) >> 4),
-                                   db + ((ks * 32) >> 4), kT5IdescAll, 1u);
+                                   db + ((ks * 32) >> 4), kT5IdescAll, (c | ks | i) != 0 ? 1u : 0u);
                     }
                     t5_commit(&a_empty[s]);
                     t5_commit(&b_empty[sb]);
@@ -471,9 +473,10 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
                                  : "r"(taddr));
                 }
                 t5_wait_ld();
-                // the next tile accumulates onto zeros
+                // the next tile's first product (digit 0, which does not
+                // accumulate) writes diagonals 0-3; 4-6 accumulate onto zeros
 #pragma unroll
-                for (uint32_t d = 0; d < kT5Diag; ++d)
+                for (uint32_t d = kT5Dig; d < kT5Diag; ++d)
                     t5_st_zero4(tmem + ((32u * quad) << 16) + d * kT5N + n0 + GW * grp);
                 uint32_t v[GW];
 #pragma unroll
@@ -501,9 +504,10 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
             return true;
         };
 
-        // the accumulators start at zero (every product accumulates): this
-        // thread's row, its slice of each diagonal
-        for (uint32_t d = 0; d < kT5Diag; ++d)
+        // diagonals 4-6 start at zero (the first product of a tile, data
+        // digit 0 against the four matrix digits, writes 0-3 without
+        // accumulating; the rest accumulate): this thread's row, its slice
+        for (uint32_t d = kT5Dig; d < kT5Diag; ++d)
             for (uint32_t c8 = 0; c8 < kSliceCols / 8; ++c8)
                 t5_st_zero8(tmem + ((32u * quad) << 16) + d * kT5N + slice * kSliceCols + 8 * c8);
         t5_wait_st();
