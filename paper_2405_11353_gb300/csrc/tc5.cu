@@ -517,12 +517,14 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
             // chunk g: wait for its data words (TMA) and for its digit stage
             // (the products of chunk g - NA done), then convert.  The
             // converters are idle while a tile's accumulators drain (the
-            // next tile's first NA digit stages are full, and its products
-            // wait for the drain), so they take half of each epilogue: that
-            // of tile i just before chunk NA of tile i + 1, the first chunk
-            // whose stage needs tile i + 1's products to have started
+            // next tile's products wait for the drain), so they take half of
+            // each epilogue: that of tile i just before chunk NA - 1 of tile
+            // i + 1.  Its chunks 0 .. NA - 2 are converted while tile i's
+            // last products run; chunk NA - 1's stage frees only when they
+            // end, and its digits are needed only NA - 1 chunks of products
+            // after the drain
             for (uint32_t g = 0; g < nchunks && ok; ++g) {
-                if (g >= kT5Chunks && g % kT5Chunks == kT5NA) {
+                if (g >= kT5Chunks && g % kT5Chunks == kT5NA - 1) {
                     const uint32_t ti = g / kT5Chunks - 1;
                     ok = epilogue(tile_of(kT5Chunks * ti), ti);
                     if (!ok) break;
