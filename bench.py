@@ -24,6 +24,7 @@ same K steps; `cpu_baseline` times the CPU oracle on a bounded sample;
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
 import argparse
+import itertools
 import json
 import os
 import re
@@ -542,6 +543,38 @@ def rns_n2p14(nt, torch, dev, reps=50):
             "ms_per_step": ms, "value": n / (ms / 1e3), "unit": "NTT/s"}
 
 
+def tune_step_inverse_form(nt, torch, dev, N, qs, flags, inv_tuning, reps=50):
+    """Time the step (forward of POLYS polynomials, then the product +
+    inverse of PAIRS pairs, back to back) with each inverse form the
+    autotuner found valid for the product batch; record the fastest in the
+    tuning table.  Returns {form name: ms per step}."""
+    names = {v: k for k, v in nt.FORMS.items()}
+    fwd_form = inv_tuning["forward_form"]
+    L = len(qs)
+    half = PAIRS * L * N
+    bufs = [torch.zeros(POLYS * L * N, dtype=torch.int32, device=dev) for _ in range(ROTATE)]
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    out = {}
+    for form, ms in enumerate(inv_tuning["inverse_ms"]):
+        if ms <= 0:
+            continue
+        nt.ntt_tune_set(N, L, flags, PAIRS, fwd_form, form)
+        p = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, flags)
+        try:
+            def step(b):
+                nt.ntt_forward(p, b, POLYS, sh)
+                nt.ntt_pointwise_inverse(p, b, b, b[half:], PAIRS, sh)
+            turn = itertools.count()
+            out[names[form]] = _time_loop(torch, stream, lambda: step(bufs[next(turn) % ROTATE]), reps)
+        finally:
+            nt.ntt_plan_destroy(p)
+    best = min(out, key=out.get)
+    nt.ntt_tune_set(N, L, flags, PAIRS, fwd_form, nt.FORMS[best])
+    del bufs
+    return out
+
+
 def autotune_shapes(nt, torch, dev):
     """The autotuner on other two-pass shapes: which form wins per
     direction (0: one-warp chunk CTAs, 1: 16-chunk CTAs, 2: streamed)."""
@@ -624,9 +657,11 @@ def tw_otf(nt, torch, dev, reps=50):
     sh = stream.cuda_stream
     out = {"workload": "N=2^16, L=32 primes q<2^30, u32, 16 polys: forward x16; pointwise x8 + inverse x8"}
     for name, extra in (("tables", 0), ("on_the_fly", nt.NTT_TW_OTF)):
-        # each plan in its fastest forms for these batches (autotuned)
-        for b in (B, B // 2):
-            nt.ntt_autotune(N, qs, nt.NTT_ORDER_BITREV | extra, b, sh)
+        # each plan in its fastest forms for these batches (autotuned, the
+        # product + inverse form on the step itself, as for the headline)
+        nt.ntt_autotune(N, qs, nt.NTT_ORDER_BITREV | extra, B, sh)
+        inv = nt.ntt_autotune(N, qs, nt.NTT_ORDER_BITREV | extra, B // 2, sh)
+        tune_step_inverse_form(nt, torch, dev, N, qs, nt.NTT_ORDER_BITREV | extra, inv)
         p = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, nt.NTT_ORDER_BITREV | extra)
         names = {v: k for k, v in nt.FORMS.items()}
         forms = {"forward": names[nt.ntt_plan_form(p, B)], "product_inverse": names[nt.ntt_plan_form(p, B // 2, True)]}
@@ -710,6 +745,13 @@ def main():
     if not args.no_tune:
         tuning = {"forward_batch%d" % POLYS: nt.ntt_autotune(N, qs, flags, POLYS),
                   "inverse_batch%d" % PAIRS: nt.ntt_autotune(N, qs, flags, PAIRS)}
+        # The autotuner times each call alone.  Back to back, the product +
+        # inverse follows the forward's chunk pass (a programmatic dependent
+        # launch), and inverse forms that time alike alone can differ in
+        # the step: time the step itself with each inverse form of the
+        # product batch and keep the fastest.
+        tuning["step_inverse_form_ms"] = tune_step_inverse_form(nt, torch, dev, N, qs, flags,
+                                                                tuning["inverse_batch%d" % PAIRS])
     plan = nt.ntt_plan_create(N, qs, nt.NTT_FUSED, flags)
     form_names = {v: k for k, v in nt.FORMS.items()}
     forms = {"forward": form_names.get(nt.ntt_plan_form(plan, POLYS)),
