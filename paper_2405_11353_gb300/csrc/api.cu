@@ -182,15 +182,7 @@ void build_tc_tables(ntt_plan_s *p, std::vector<uint8_t> &out) {
                 tws[2 * ai + 1] = (uint32_t)(((u128)wi << 32) / q);
             }
         }
-        // 2^(8 s) mod q for the seven diagonals s < 7; slot 7: the term
-        // that removes the tcgen05 epilogue's offset of 2^24 on each
-        // diagonal, q - (2^24 sum_s 2^(8 s)) mod q, reduced mod q
-        uint64_t wsum = 0;
-        for (int s = 0; s < 7; ++s) {
-            pow8[l * 8 + s] = (uint32_t)H::powm(2, 8ull * s, q);
-            wsum = (wsum + pow8[l * 8 + s]) % q;
-        }
-        pow8[l * 8 + 7] = (uint32_t)((q - (uint64_t)(((u128)wsum << 24) % q)) % q);
+        for (int s = 0; s < 8; ++s) pow8[l * 8 + s] = (uint32_t)H::powm(2, 8ull * s, q);
     }
 }
 

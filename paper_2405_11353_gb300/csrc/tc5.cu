@@ -26,10 +26,9 @@
 //     data words whose digits sit at the ends of their range (-128 and +127),
 //     against the matrices of many primes, are the evidence for it.
 //   * The epilogue reads the diagonals back (tcgen05.ld), recombines
-//     sum_s (D_s + 2^24) (2^(8 s) mod q) in unsigned 64-bit integers
-//     (< 7 2^55: one 32 x 32 -> 64-bit multiply-add per diagonal), adds
-//     -2^24 sum_s 2^(8 s) mod q to remove the offsets and reduces mod q
-//     (Barrett), then applies
+//     sum_s D_s (2^(8 s) mod q) plus 7 2^24 q (which makes it positive) in
+//     64-bit integers (< 2^58: one signed 32 x 32 -> 64-bit multiply-add
+//     per diagonal) and reduces mod q (Barrett), then applies
 //     the inter-step twiddle (Shoup) where the pass has one.
 //
 // GEMM view, D[m][n] = sum_k A[m][k] B[n][k], both operands K-major in shared
@@ -98,7 +97,7 @@ struct Tc5Args {
     uint32_t mat_row0;              // cmap row of (this pass's matrix, limb 0, digit 0, row 0)
     const Tw<uint32_t> *tw;         // [L][256][256] epilogue twiddles, or null
     const LimbConst *lc;
-    const uint32_t *wdiag;          // [L][8]: 2^(8 s) mod q for s < 7; at 7, -2^24 sum_s 2^(8 s) mod q
+    const uint32_t *wdiag;          // [L][8]: 2^(8 s) mod q for s < 7
     uint32_t *status;
     uint32_t L;
     uint32_t ntiles;                // 8 per transform (2 row blocks x 4 column tiles)
@@ -439,11 +438,10 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
             uint32_t w7[kT5Diag];
 #pragma unroll
             for (uint32_t d = 0; d < kT5Diag; ++d) w7[d] = __ldg(a.wdiag + 8 * T.l + d);
-            // each diagonal D is taken as D + 2^24 in [0, 2^25] (unsigned, so
-            // one 32 x 32 -> 64-bit multiply-add per diagonal, a sum below
-            // 7 2^55); this term, -2^24 sum_s 2^(8 s) mod q, removes the
-            // offsets mod q
-            const uint32_t corr = __ldg(a.wdiag + 8 * T.l + 7);
+            // each diagonal D (|D| <= 2^24) times its weight (< 2^30) is one
+            // signed 32 x 32 -> 64-bit multiply-add; |sum| < 7 2^24 q, so
+            // adding 7 2^24 q (a multiple of q) makes it positive
+            const int64_t off = (int64_t)kk.q * (7ll << 24);
             // output word (row, column) of the transform: column pass
             // out[u][n2] = out[64 nb + n][128 mb + m]; row pass
             // out[r][v] = out[128 mb + m][64 nb + n]
@@ -481,11 +479,11 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
                 uint32_t v[GW];
 #pragma unroll
                 for (uint32_t cc = 0; cc < GW; ++cc) {
-                    uint64_t comb = corr;
+                    int64_t comb = off;
 #pragma unroll
                     for (uint32_t d = 0; d < kT5Diag; ++d)
-                        comb += (uint64_t)(uint32_t)(__float2int_rn(__uint_as_float(f[d][cc])) + (1 << 24)) * w7[d];
-                    uint32_t r = csub<uint32_t>(barrett_lazy(comb, kk), kk.q);
+                        comb += (int64_t)__float2int_rn(__uint_as_float(f[d][cc])) * (int64_t)(int32_t)w7[d];
+                    uint32_t r = csub<uint32_t>(barrett_lazy((uint64_t)comb, kk), kk.q);
                     if (twt) r = mul_full<RED_SHOUP>(r, tws16[GW * grp + cc], kk);
                     v[cc] = r;
                 }
