@@ -580,16 +580,17 @@ def test_polymul_host_entry(nt, orc):
 
 def test_polymul_host_limb_windows(nt, orc):
     """One or two pairs are pipelined as windows of limbs (an uneven last
-    window with 5 limbs), on a two-pass size in both orders and on a
-    single-pass size; every product coefficient against the oracle's
-    transform pipeline, a sample against the schoolbook product."""
+    window with 5 limbs), 3 or 9 pairs as chunks of whole pairs.  On a
+    two-pass size in both orders and on a single-pass size; every product
+    coefficient against the oracle's transform pipeline, a sample against
+    the schoolbook product."""
     for n, L, bitrev in ((16, 5, True), (15, 5, False), (12, 3, True)):
         N = 1 << n
         qs = primes_for(orc, N, False, L)
         psis = [orc.psi(q, N) for q in qs]
         p = Plan(nt, N, qs, "fused", bitrev=bitrev)
         try:
-            for pairs in (1, 2):
+            for pairs in (1, 2, 3, 9):
                 host = ntt_synth.rns_batch(3000 + n + pairs, qs, N, 2 * pairs).astype(np.uint32)
                 h_in = torch.from_numpy(host.view(np.int32).copy()).pin_memory()
                 h_out = torch.zeros(pairs * L * N, dtype=torch.int32).pin_memory()
