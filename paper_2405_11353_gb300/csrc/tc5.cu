@@ -50,7 +50,7 @@
 // the gap between their conversions, run the epilogue (warp w reads
 // tensor-memory lanes 32 (w % 4) .. and 16 of the 64 columns of each
 // diagonal).  The accumulators are one set: the next tile's MMAs start
-// when the epilogue has read and zeroed them (two sets of half-width tiles
+// when the epilogue has read them (and zeroed 4-6) (two sets of half-width tiles
 // were measured slower: each 32-column tile converts the whole data block
 // again, and the extra digit traffic through shared memory costs more
 // than the overlap gains).
