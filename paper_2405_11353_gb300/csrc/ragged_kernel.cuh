@@ -116,12 +116,18 @@ __global__ void __launch_bounds__(256, ragged_min_blocks<W>()) k_ragged(const __
     __syncthreads();
     PipeState ps{{0, 0, 0}, 0};
     for (int phase = 0; phase < 4; ++phase) {
+        // thread 0 takes each item one ahead (the atomic's round trip runs
+        // under the current item); a CTA leaves a phase holding one index
+        // past its end, which the launch's counter reset makes harmless
+        uint32_t next = 0;
+        if (threadIdx.x == 0) next = ra.phase_begin[phase] + atomicAdd(&ra.counters[phase], 1u);
         for (;;) {
-            if (threadIdx.x == 0) s_item = ra.phase_begin[phase] + atomicAdd(&ra.counters[phase], 1u);
+            if (threadIdx.x == 0) s_item = next;
             __syncthreads();
             const uint32_t item = s_item;
             __syncthreads();
             if (item >= ra.phase_begin[phase + 1] || *(volatile uint32_t *)ra.abort_flag) break;
+            if (threadIdx.x == 0) next = ra.phase_begin[phase] + atomicAdd(&ra.counters[phase], 1u);
             const RItem it = ra.items[item];
             const uint32_t kind = it.code % RK_KINDS;
             const bool inv = (it.code / RK_KINDS) & 1u;
