@@ -483,9 +483,10 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_tc5(const __grid_constant__ T
 #pragma unroll
                     for (uint32_t d = 0; d < kT5Diag; ++d)
                         comb += (int64_t)__float2int_rn(__uint_as_float(f[d][cc])) * (int64_t)(int32_t)w7[d];
-                    uint32_t r = csub<uint32_t>(barrett_lazy((uint64_t)comb, kk), kk.q);
-                    if (twt) r = mul_full<RED_SHOUP>(r, tws16[GW * grp + cc], kk);
-                    v[cc] = r;
+                    // in [0, 2q); the Shoup twiddle product takes any word,
+                    // so only a pass without twiddles reduces it further
+                    const uint32_t r = barrett_lazy((uint64_t)comb, kk);
+                    v[cc] = twt ? mul_full<RED_SHOUP>(r, tws16[GW * grp + cc], kk) : csub<uint32_t>(r, kk.q);
                 }
                 if (ROWP) {
                     *reinterpret_cast<uint4 *>(outt + (size_t)(T.mb * kT5M + m) * 256 + T.nb * kT5N + n0 + GW * grp) =
