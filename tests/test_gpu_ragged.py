@@ -253,3 +253,37 @@ def test_ragged_barrier_timeout_reported_and_context_survives(nt, orc):
     for h, qs, t, n, w64 in hosts:
         psis = [orc.psi(q, 1 << n) for q in qs]
         assert np.array_equal(back(t, w64, h.shape), bitrev_rows(orc.ntt_batch(h, qs, psis), orc)), (n, w64)
+
+
+@pytest.mark.parametrize("w64", [False, True])
+def test_ragged_one_word_size(nt, orc, w64):
+    """A set whose jobs all have one word size runs one persistent kernel
+    (the other has no items and is not launched): every job's forward output
+    bit-exact, and the barrier test hook lands on the kernel that exists
+    (NTT_ERR_TIMEOUT, then a regular set is bit-exact again)."""
+    specs = [(12, 2), (15, 3), (16, 1)]
+    hosts, jobs = [], []
+    for i, (n, L) in enumerate(specs):
+        qs = primes(orc, w64)[:L]
+        h = ntt_synth.rns_batch(1300 + i + 10 * w64, qs, 1 << n, 2)
+        t = dev(h, w64)
+        hosts.append((h, qs, t, n))
+        jobs.append(dict(data=t, q=qs, N=1 << n, batch=2, word64=w64, inverse=False))
+
+    def check():
+        for h, qs, t, n in hosts:
+            psis = [orc.psi(q, 1 << n) for q in qs]
+            assert np.array_equal(back(t, w64, h.shape), bitrev_rows(orc.ntt_batch(h, qs, psis), orc)), (n, w64)
+
+    run(nt, jobs)
+    check()
+    r = nt.ntt_ragged_create(jobs, nt.NTT_ORDER_BITREV | nt.NTT_TEST_STALL)
+    try:
+        nt.ntt_ragged_launch(r)
+        assert nt.ntt_ragged_status(r) == nt.NTT_ERR_TIMEOUT
+    finally:
+        nt.ntt_ragged_destroy(r)
+    for h, qs, t, n in hosts:
+        t.copy_(dev(h, w64))
+    run(nt, jobs)
+    check()
